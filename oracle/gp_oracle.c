@@ -1,0 +1,333 @@
+/*
+ * gp_oracle.c -- CPU FP64 oracle for the Gaussian-process likelihood and
+ * kriging path of Franey, Ranjan & Chipman, "A Short Note on Gaussian Process
+ * Modeling for Large Datasets using Graphics Processing Units".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference that the GPU library is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA path, and the CUDA
+ * path never calls it.
+ *
+ * Everything is IEEE double, accumulated left to right in the order the
+ * definitions are written.  No blocking, no reordering, no BLAS/LAPACK.
+ *
+ * Matrices are dense row-major n x n: A[i*n + j].
+ *
+ * Readings of the paper where it is silent (each also listed in the design
+ * notes):
+ *   - nugget: R_delta = R + delta*I (the diagonal becomes 1 + delta); the
+ *     cross-correlation r(x*) used for prediction carries no delta.
+ *   - -2 log L is eq. (4) taken literally:  log|R| + n log Q  with
+ *     Q = (Y - 1 mu)' R^-1 (Y - 1 mu)  (not divided by n).  The full Gaussian
+ *     form log|R| + n log sigma2 + n (1 + log 2 pi) is returned beside it.
+ *   - Q == 0 (n = 1, or Y constant) gives -2logL = -inf and status DEGENERATE.
+ *   - a Cholesky pivot <= 0 (or not finite) gives status NOTPD and
+ *     -2logL = +inf; no pivoting, no jitter.
+ *   - the kriging variance is the ordinary-kriging mean squared error
+ *     sigma2 [ c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1) ] with
+ *     c0 = 1 + delta (nugget counted in the process variance) or c0 = 1.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GPO_OK 0
+#define GPO_NOTPD (-3)
+#define GPO_DEGENERATE (-6)
+#define GPO_ENOMEM (-2)
+
+/* Correlation between two points, eq. (2) of Section 2: the product over
+ * the d input dimensions of exp(-theta_k |x_ik - x_jk|^p). */
+static double gpo_corr_pair(int d, const double* xi, const double* xj,
+                            const double* theta, double p) {
+    double r = 1.0;
+    for (int k = 0; k < d; ++k) {
+        double diff = fabs(xi[k] - xj[k]);
+        r *= exp(-theta[k] * pow(diff, p));
+    }
+    return r;
+}
+
+/* R(theta) by eq. (2), full n x n, plus the nugget delta on the diagonal. */
+void gpo_corr_matrix(int n, int d, const double* x, const double* theta,
+                     double p, double delta, double* R) {
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double v = gpo_corr_pair(d, x + (size_t)i * d, x + (size_t)j * d, theta, p);
+            if (i == j) v += delta;
+            R[(size_t)i * n + j] = v;
+        }
+    }
+}
+
+/* Cross-correlations r_i(x*) = corr(z(x*), z(x_i)) by eq. (2); no nugget. */
+void gpo_cross_corr(int n, int d, const double* x, const double* xs,
+                    const double* theta, double p, double* r) {
+    for (int i = 0; i < n; ++i)
+        r[i] = gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p);
+}
+
+/* Unblocked Cholesky (Cholesky-Banachiewicz, row by row): R = L L'.
+ * L is written to the lower triangle of L (upper set to zero).  The paper's
+ * CPU path factors R by Cholesky (Section 3).  Returns 0, or (k+1) where k
+ * is the first column whose pivot is not positive and finite. */
+int gpo_cholesky(int n, const double* R, double* L) {
+    memset(L, 0, sizeof(double) * (size_t)n * n);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = R[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k)
+                s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            if (i == j) {
+                if (!(s > 0.0) || !isfinite(s)) return i + 1;
+                L[(size_t)i * n + i] = sqrt(s);
+            } else {
+                L[(size_t)i * n + j] = s / L[(size_t)j * n + j];
+            }
+        }
+    }
+    return 0;
+}
+
+/* Forward substitution L z = b. */
+void gpo_forward(int n, const double* L, const double* b, double* z) {
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * z[k];
+        z[i] = s / L[(size_t)i * n + i];
+    }
+}
+
+/* Back substitution L' w = e. */
+void gpo_backward(int n, const double* L, const double* e, double* w) {
+    for (int i = n - 1; i >= 0; --i) {
+        double s = e[i];
+        for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * w[k];
+        w[i] = s / L[(size_t)i * n + i];
+    }
+}
+
+/* 1-norm condition estimate kappa_1(A) = ||A||_1 * est(||A^-1||_1) for
+ * symmetric positive definite A = L L', with est(.) Hager's iteration
+ * (W. W. Hager, "Condition estimates", SIAM J. Sci. Stat. Comput. 5, 1984),
+ * at most 5 steps, using solves with L only.  The estimate is a lower bound
+ * of the true condition number. */
+double gpo_cond1_est(int n, const double* A, const double* L) {
+    double* work = (double*)malloc(sizeof(double) * 5 * (size_t)n);
+    if (!work) return NAN;
+    double* v = work;
+    double* yv = work + n;
+    double* z = work + 2 * n;
+    double* t = work + 3 * n;
+    double* sg = work + 4 * n;
+    double anorm = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += fabs(A[(size_t)i * n + j]);
+        if (c > anorm) anorm = c;
+    }
+    for (int i = 0; i < n; ++i) v[i] = 1.0 / n;
+    double est = 0.0;
+    int jprev = -1;
+    for (int iter = 0; iter < 5; ++iter) {
+        gpo_forward(n, L, v, t);
+        gpo_backward(n, L, t, yv);          /* yv = A^-1 v */
+        est = 0.0;
+        for (int i = 0; i < n; ++i) est += fabs(yv[i]);
+        for (int i = 0; i < n; ++i) sg[i] = (yv[i] >= 0.0) ? 1.0 : -1.0;
+        gpo_forward(n, L, sg, t);
+        gpo_backward(n, L, t, z);           /* z = A^-T sign(yv), A symmetric */
+        int jmax = 0;
+        double zmax = fabs(z[0]);
+        for (int i = 1; i < n; ++i)
+            if (fabs(z[i]) > zmax) { zmax = fabs(z[i]); jmax = i; }
+        double ztv = 0.0;
+        for (int i = 0; i < n; ++i) ztv += z[i] * v[i];
+        if (zmax <= ztv || jmax == jprev) break;
+        for (int i = 0; i < n; ++i) v[i] = 0.0;
+        v[jmax] = 1.0;
+        jprev = jmax;
+    }
+    free(work);
+    return anorm * est;
+}
+
+/* Q = e'e is zero in exact arithmetic when Y lies in the span of 1 (always
+ * so for n = 1).  In floating point e = b - mu a then holds only rounding
+ * noise of size ~u |b|, so Q is taken as zero when it is no larger than
+ * 16 n u^2 b'b (u = 2^-53), which includes Q == 0 exactly. */
+static int gpo_q_is_zero(int n, double Q, double bb) {
+    const double u = 1.1102230246251565e-16;
+    return Q <= 16.0 * n * u * u * bb;
+}
+
+/* Profile -2 log-likelihood at one theta, eqs. (3)-(4) of Section 2.
+ *
+ * out[0] = -2logL = log|R| + n log Q            (eq. 4, literal)
+ * out[1] = mu_hat = (1'R^-1 1)^-1 1'R^-1 Y       (eq. 3)
+ * out[2] = sigma2_hat = Q / n                     (eq. 3)
+ * out[3] = log|R| = 2 sum log L_ii
+ * out[4] = Q = (Y - 1 mu_hat)' R^-1 (Y - 1 mu_hat)
+ * out[5] = full Gaussian form log|R| + n log sigma2_hat + n (1 + log 2 pi)
+ * out[6] = 1-norm condition estimate of R (0 if not requested)
+ * Returns the status (0, NOTPD, DEGENERATE, ENOMEM).
+ *
+ * Route: R by eq. (2) -> Cholesky R = L L' -> a = L^-1 1, b = L^-1 Y, so that
+ * 1'R^-1 1 = a'a and 1'R^-1 Y = a'b; e = b - mu a = L^-1 (Y - 1 mu) and
+ * Q = e'e. */
+int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
+            double p, double delta, int want_cond, double* out) {
+    const double nan = NAN;
+    for (int i = 0; i < 7; ++i) out[i] = nan;
+    out[6] = 0.0;
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
+    double* a = (double*)malloc(sizeof(double) * (size_t)n);
+    double* b = (double*)malloc(sizeof(double) * (size_t)n);
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    int status = GPO_OK;
+    if (!R || !L || !ones || !a || !b || !e) { status = GPO_ENOMEM; goto done; }
+
+    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    if (gpo_cholesky(n, R, L) != 0) {
+        status = GPO_NOTPD;
+        out[0] = INFINITY;
+        out[5] = INFINITY;
+        goto done;
+    }
+    for (int i = 0; i < n; ++i) ones[i] = 1.0;
+    gpo_forward(n, L, ones, a);
+    gpo_forward(n, L, y, b);
+    double aa = 0.0, ab = 0.0;
+    for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
+    double mu = ab / aa;
+    double Q = 0.0, bb = 0.0;
+    for (int i = 0; i < n; ++i) { e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; bb += b[i] * b[i]; }
+    double logdet = 0.0;
+    for (int i = 0; i < n; ++i) logdet += log(L[(size_t)i * n + i]);
+    logdet *= 2.0;
+    double sigma2 = Q / n;
+    out[1] = mu;
+    out[2] = sigma2;
+    out[3] = logdet;
+    out[4] = Q;
+    if (gpo_q_is_zero(n, Q, bb)) {
+        status = GPO_DEGENERATE;
+        out[0] = -INFINITY;
+        out[5] = -INFINITY;
+    } else {
+        out[0] = logdet + n * log(Q);
+        out[5] = logdet + n * log(sigma2) + n * (1.0 + log(2.0 * M_PI));
+    }
+    if (want_cond) out[6] = gpo_cond1_est(n, R, L);
+done:
+    free(R); free(L); free(ones); free(a); free(b); free(e);
+    return status;
+}
+
+/* -2 log L at T candidate theta vectors (theta is T x d row-major); the
+ * candidates are independent, so they are spread over host threads.  Each
+ * evaluation is the single-threaded gpo_nll above.  out is T x 7. */
+void gpo_nll_batch(int n, int d, const double* x, const double* y, int T,
+                   const double* theta, double p, double delta, int want_cond,
+                   double* out, int* status) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < T; ++t)
+        status[t] = gpo_nll(n, d, x, y, theta + (size_t)t * d, p, delta,
+                            want_cond, out + (size_t)t * 7);
+}
+
+/* Kriging prediction at N points xs (N x d) with the fit at theta.
+ * yhat[m] = mu_hat + r' R^-1 (Y - 1 mu_hat)            (w = L^-T e)
+ * s2[m]   = sigma2_hat [ c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1) ]
+ * where v = L^-1 r gives r'R^-1 r = v'v and 1'R^-1 r = a'v, and
+ * c0 = 1 + delta if nugget_in_var else 1.  s2 may be NULL.
+ * Returns the status of the fit. */
+int gpo_predict(int n, int d, const double* x, const double* y, const double* theta,
+                double p, double delta, int N, const double* xs, int nugget_in_var,
+                double* yhat, double* s2) {
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
+    double* a = (double*)malloc(sizeof(double) * (size_t)n);
+    double* b = (double*)malloc(sizeof(double) * (size_t)n);
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    int status = GPO_OK;
+    if (!R || !L || !ones || !a || !b || !e || !w) { status = GPO_ENOMEM; goto done; }
+    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    if (gpo_cholesky(n, R, L) != 0) {
+        status = GPO_NOTPD;
+        for (int m = 0; m < N; ++m) { yhat[m] = NAN; if (s2) s2[m] = NAN; }
+        goto done;
+    }
+    for (int i = 0; i < n; ++i) ones[i] = 1.0;
+    gpo_forward(n, L, ones, a);
+    gpo_forward(n, L, y, b);
+    double aa = 0.0, ab = 0.0;
+    for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
+    double mu = ab / aa;
+    double Q = 0.0;
+    for (int i = 0; i < n; ++i) { e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; }
+    double sigma2 = Q / n;
+    gpo_backward(n, L, e, w);
+    double c0 = nugget_in_var ? 1.0 + delta : 1.0;
+#pragma omp parallel
+    {
+        double* r = (double*)malloc(sizeof(double) * (size_t)n);
+        double* v = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int m = 0; m < N; ++m) {
+            if (!r || !v) { yhat[m] = NAN; if (s2) s2[m] = NAN; continue; }
+            gpo_cross_corr(n, d, x, xs + (size_t)m * d, theta, p, r);
+            double yh = 0.0;
+            for (int i = 0; i < n; ++i) yh += r[i] * w[i];
+            yhat[m] = mu + yh;
+            if (s2) {
+                gpo_forward(n, L, r, v);
+                double vv = 0.0, av = 0.0;
+                for (int i = 0; i < n; ++i) { vv += v[i] * v[i]; av += a[i] * v[i]; }
+                double g = 1.0 - av;
+                s2[m] = sigma2 * (c0 - vv + g * g / aa);
+            }
+        }
+        free(r); free(v);
+    }
+done:
+    free(R); free(L); free(ones); free(a); free(b); free(e); free(w);
+    return status;
+}
+
+/* The factor and the solve vectors of one fit, for tests that check the
+ * intermediate quantities: L (n x n), a = L^-1 1, b = L^-1 Y, w = R^-1(Y-1mu).
+ * Returns the status. */
+int gpo_fit_parts(int n, int d, const double* x, const double* y, const double* theta,
+                  double p, double delta, double* R, double* L, double* a, double* b,
+                  double* w) {
+    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    if (gpo_cholesky(n, R, L) != 0) return GPO_NOTPD;
+    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!ones || !e) { free(ones); free(e); return GPO_ENOMEM; }
+    for (int i = 0; i < n; ++i) ones[i] = 1.0;
+    gpo_forward(n, L, ones, a);
+    gpo_forward(n, L, y, b);
+    double aa = 0.0, ab = 0.0;
+    for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
+    double mu = ab / aa;
+    for (int i = 0; i < n; ++i) e[i] = b[i] - mu * a[i];
+    gpo_backward(n, L, e, w);
+    free(ones); free(e);
+    return GPO_OK;
+}
+
+int gpo_num_threads(void) {
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,379 @@
+"""Checks that pin the CPU oracle to facts other than itself.
+
+Each check takes an ``oracle.Oracle`` and raises AssertionError when the
+oracle disagrees with the fact.  The facts come from the mathematics of
+Section 2 (eqs. 2-4) and from the paper's printed Table 2 row, never from the
+oracle's own code:
+
+  * Kac-Murdock-Szego closed form (d = 1, equispaced x, p = 1, delta = 0):
+    R_ij = rho^|i-j|, det R = (1 - rho^2)^(n-1), the Cholesky factor in closed
+    form and a tridiagonal inverse, so mu_hat, Q and -2logL follow in O(n).
+  * hand derivations for n = 1, 2 (with a nugget) and n = 3 (adjugate).
+  * log|R| against the eigenvalues from LAPACK's symmetric eigensolver.
+  * mu_hat, sigma2_hat, Q and kriging against LAPACK's general solver.
+  * invariants: row permutation, scaling and shifting of y, Hadamard's
+    inequality, symmetry and unit diagonal.
+  * the form of eq. (4) against the printed rows of Tables 1-2.
+
+The same checks run against planted-mistake copies of the oracle in
+``test_oracle_mutants.py`` to show that each plausible mistake is caught.
+"""
+import json
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+# ---------------------------------------------------------------- assembly --
+
+def check_corr_hand_values(orc):
+    """Eq. (2) at points where the value is known by hand."""
+    x = np.array([[0.0, 0.0], [0.5, 0.25], [1.0, 0.0]])
+    # p = 2: R_01 = exp(-2*0.25) * exp(-4*0.0625) = exp(-0.75)
+    R = orc.corr_matrix(x, [2.0, 4.0], 2.0, 0.0)
+    assert _rel(R[0, 1], math.exp(-0.75)) < 1e-15
+    # R_02: dims differ only in x1 by 1.0 -> exp(-2)
+    assert _rel(R[0, 2], math.exp(-2.0)) < 1e-15
+    # p = 1: R_01 = exp(-2*0.5 - 4*0.25) = exp(-2)
+    R1 = orc.corr_matrix(x, [2.0, 4.0], 1.0, 0.0)
+    assert _rel(R1[0, 1], math.exp(-2.0)) < 1e-15
+    # p = 1.5 at distance 0.25 in dim 2 only (points 0 and a shifted copy)
+    x2 = np.array([[0.0, 0.0], [0.0, 0.25]])
+    R2 = orc.corr_matrix(x2, [3.0, 5.0], 1.5, 0.0)
+    assert _rel(R2[0, 1], math.exp(-5.0 * 0.125)) < 1e-15   # 0.25^1.5 = 0.125
+    # nugget on the diagonal only
+    Rd = orc.corr_matrix(x, [2.0, 4.0], 2.0, 1e-3)
+    assert np.all(np.diag(Rd) == 1.0 + 1e-3)
+    assert Rd[0, 1] == R[0, 1]
+
+
+def check_corr_invariants(orc, seed=3):
+    g = np.random.default_rng(seed)
+    for (n, d, p) in [(17, 3, 1.95), (9, 5, 1.0), (12, 2, 2.0), (7, 4, 0.5)]:
+        x = g.random((n, d))
+        th = 10 ** g.uniform(-2, 1, d)
+        R = orc.corr_matrix(x, th, p, 0.0)
+        assert np.array_equal(R, R.T)
+        assert np.all(np.diag(R) == 1.0)
+        assert np.all(R > 0) and np.all(R <= 1.0)
+        # larger theta never raises a correlation
+        R2 = orc.corr_matrix(x, th * 2, p, 0.0)
+        assert np.all(R2 <= R)
+        # cross-correlation to a design point reproduces that row (no nugget)
+        r = orc.cross_corr(x, x[3], th, p)
+        assert np.array_equal(r, R[3])
+
+
+# ------------------------------------------------------------ KMS pins ------
+
+def kms_case(n, rho_target=0.8):
+    """d = 1, x_i = i h with h a power of two (exact), p = 1, delta = 0."""
+    h = 1.0 / 1024.0
+    x = (np.arange(n, dtype=np.float64) * h).reshape(n, 1)
+    theta = -math.log(rho_target) / h
+    rho = math.exp(-theta * h)
+    return x, theta, rho
+
+
+def kms_quadratic_forms(rho, u, v):
+    """u' R^-1 v for the KMS matrix R_ij = rho^|i-j| via its tridiagonal
+    inverse (1/(1-rho^2)) * [diag 1, 1+rho^2, ..., 1+rho^2, 1; off -rho]."""
+    n = len(u)
+    c = 1.0 / (1.0 - rho * rho)
+    diag = np.full(n, 1.0 + rho * rho)
+    diag[0] = diag[-1] = 1.0
+    s = np.dot(u * diag, v) - rho * (np.dot(u[1:], v[:-1]) + np.dot(u[:-1], v[1:]))
+    return c * s
+
+
+def check_kms(orc, n=60, rho_target=0.8, seed=5):
+    x, theta, rho = kms_case(n, rho_target)
+    R = orc.corr_matrix(x, [theta], 1.0, 0.0)
+    i = np.arange(n)
+    Rk = rho ** np.abs(i[:, None] - i[None, :])
+    assert np.max(np.abs(R - Rk)) < 1e-13
+    L, info = orc.cholesky(R)
+    assert info == 0
+    s = math.sqrt(1.0 - rho * rho)
+    Lk = np.zeros((n, n))
+    for a in range(n):
+        Lk[a, 0] = rho ** a
+        for b in range(1, a + 1):
+            Lk[a, b] = rho ** (a - b) * s
+    assert np.max(np.abs(L - Lk)) < 1e-12
+    g = np.random.default_rng(seed)
+    y = g.standard_normal(n)
+    one = np.ones(n)
+    A = kms_quadratic_forms(rho, one, one)
+    assert _rel(A, ((n - 2) * (1 - rho) + 2) / (1 + rho)) < 1e-13
+    B = kms_quadratic_forms(rho, one, y)
+    C = kms_quadratic_forms(rho, y, y)
+    mu = B / A
+    Q = C - B * B / A
+    logdet = (n - 1) * math.log(1.0 - rho * rho)
+    out, st = orc.nll(x, y, [theta], 1.0, 0.0)
+    assert st == 0
+    assert _rel(out["logdet"], logdet) < 1e-11
+    assert _rel(out["mu"], mu) < 1e-10
+    assert _rel(out["Q"], Q) < 1e-10
+    assert _rel(out["sigma2"], Q / n) < 1e-10
+    assert _rel(out["nll"], logdet + n * math.log(Q)) < 1e-11
+
+
+# ---------------------------------------------------- hand derivations ------
+
+def check_n1(orc):
+    """n = 1: R = [1 + delta], mu_hat = y_1, Q = 0 -> -2logL = -inf."""
+    out, st = orc.nll(np.array([[0.3, 0.7]]), np.array([2.5]), [1.0, 2.0], 1.9, 1e-3)
+    assert st == -6
+    assert out["nll"] == -math.inf
+    assert _rel(out["mu"], 2.5) < 1e-15
+    assert out["Q"] < 1e-28
+    # log near 1 turns the ulp of sqrt(1.001) into ~1e-13 relative
+    assert _rel(out["logdet"], math.log(1.001)) < 1e-12
+
+
+def check_n2(orc):
+    """n = 2 with correlation rho and nugget delta:
+    mu_hat = (y1+y2)/2, Q = (y1-y2)^2 / (2 (1 + delta - rho)),
+    log|R| = log((1+delta)^2 - rho^2), -2logL = log|R| + 2 log Q."""
+    for delta in (0.0, 1e-2):
+        x = np.array([[0.1, 0.2], [0.4, 0.6]])
+        th = np.array([1.5, 0.7])
+        p = 1.95
+        rho = math.exp(-1.5 * 0.3 ** p) * math.exp(-0.7 * 0.4 ** p)
+        y = np.array([1.25, -0.5])
+        out, st = orc.nll(x, y, th, p, delta)
+        assert st == 0
+        Q = (y[0] - y[1]) ** 2 / (2.0 * (1.0 + delta - rho))
+        logdet = math.log((1.0 + delta) ** 2 - rho * rho)
+        assert _rel(out["mu"], 0.375) < 1e-14
+        assert _rel(out["Q"], Q) < 1e-12
+        assert _rel(out["sigma2"], Q / 2) < 1e-12
+        assert _rel(out["logdet"], logdet) < 1e-12
+        assert _rel(out["nll"], logdet + 2 * math.log(Q)) < 1e-12
+
+
+def _inv3_adjugate(M):
+    (a, b, c), (d, e, f), (g, h, i) = M
+    det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g)
+    adj = [[e * i - f * h, c * h - b * i, b * f - c * e],
+           [f * g - d * i, a * i - c * g, c * d - a * f],
+           [d * h - e * g, b * g - a * h, a * e - b * d]]
+    return det, [[adj[r][s] / det for s in range(3)] for r in range(3)]
+
+
+def check_n3(orc):
+    """n = 3 through the 3 x 3 adjugate inverse and the determinant by cofactors."""
+    x = np.array([[0.0, 0.1], [0.3, 0.5], [0.9, 0.2]])
+    th = [2.0, 1.0]
+    p = 2.0
+    delta = 1e-4
+    M = [[0.0] * 3 for _ in range(3)]
+    for r in range(3):
+        for s in range(3):
+            q = sum(th[k] * (x[r, k] - x[s, k]) ** 2 for k in range(2))
+            M[r][s] = math.exp(-q) + (delta if r == s else 0.0)
+    det, Minv = _inv3_adjugate(M)
+    y = [0.3, -1.2, 2.0]
+    A = sum(Minv[r][s] for r in range(3) for s in range(3))
+    B = sum(Minv[r][s] * y[s] for r in range(3) for s in range(3))
+    mu = B / A
+    e = [y[r] - mu for r in range(3)]
+    Q = sum(e[r] * Minv[r][s] * e[s] for r in range(3) for s in range(3))
+    out, st = orc.nll(x, np.array(y), th, p, delta)
+    assert st == 0
+    assert _rel(out["mu"], mu) < 1e-11
+    assert _rel(out["Q"], Q) < 1e-11
+    assert _rel(out["logdet"], math.log(det)) < 1e-11
+    assert _rel(out["nll"], math.log(det) + 3 * math.log(Q)) < 1e-11
+
+
+# ------------------------------------------------ library cross-checks ------
+
+def check_eig_logdet(orc, seed=11):
+    g = np.random.default_rng(seed)
+    for (n, d, p, delta) in [(8, 2, 2.0, 1e-6), (33, 3, 1.95, 1e-8), (64, 4, 1.5, 0.0)]:
+        x = g.random((n, d))
+        th = 10 ** g.uniform(-0.5, 1, d)
+        y = g.standard_normal(n)
+        R = orc.corr_matrix(x, th, p, delta)
+        lam = np.linalg.eigvalsh(R)
+        out, st = orc.nll(x, y, th, p, delta)
+        assert st == 0
+        assert abs(out["logdet"] - np.sum(np.log(lam))) < 1e-9 * max(1.0, abs(out["logdet"]))
+
+
+def check_solve_estimates(orc, seed=13):
+    """mu_hat, Q, sigma2 and -2logL against LAPACK's general solver on R."""
+    g = np.random.default_rng(seed)
+    for (n, d, p, delta) in [(5, 2, 2.0, 1e-4), (16, 3, 1.95, 1e-6), (40, 6, 1.95, 1e-7)]:
+        x = g.random((n, d))
+        th = 10 ** g.uniform(0, 1, d)
+        y = np.sin(3 * x).sum(axis=1) + 0.1 * g.standard_normal(n)
+        R = orc.corr_matrix(x, th, p, delta)
+        one = np.ones(n)
+        Ri1 = np.linalg.solve(R, one)
+        Riy = np.linalg.solve(R, y)
+        mu = one @ Riy / (one @ Ri1)
+        res = y - mu
+        Q = res @ np.linalg.solve(R, res)
+        sign, ld = np.linalg.slogdet(R)
+        out, st = orc.nll(x, y, th, p, delta)
+        assert st == 0 and sign > 0
+        assert _rel(out["mu"], mu) < 1e-9
+        assert _rel(out["Q"], Q) < 1e-9
+        assert _rel(out["sigma2"], Q / n) < 1e-9
+        assert _rel(out["nll"], ld + n * math.log(Q)) < 1e-9
+        assert _rel(out["nll_full"], ld + n * math.log(Q / n) + n * (1 + math.log(2 * math.pi))) < 1e-9
+
+
+def check_cholesky_reconstructs(orc, seed=17):
+    g = np.random.default_rng(seed)
+    x = g.random((30, 3))
+    R = orc.corr_matrix(x, [3.0, 5.0, 7.0], 1.95, 1e-6)
+    L, info = orc.cholesky(R)
+    assert info == 0
+    assert np.all(np.triu(L, 1) == 0.0)
+    assert np.all(np.diag(L) > 0)
+    assert np.max(np.abs(L @ L.T - R)) < 1e-14
+    # forward and backward solves against LAPACK
+    b = g.standard_normal(30)
+    z = orc.forward(L, b)
+    assert np.max(np.abs(L @ z - b)) < 1e-10
+    w = orc.backward(L, b)
+    assert np.max(np.abs(L.T @ w - b)) < 1e-10
+
+
+def check_notpd(orc):
+    """Two equal design points with delta = 0: R is singular; the first pivot
+    after the duplicate is exactly zero -> NOTPD, -2logL = +inf."""
+    x = np.array([[0.2, 0.3], [0.2, 0.3], [0.7, 0.1], [0.5, 0.9]])
+    out, st = orc.nll(x, np.array([1.0, 2.0, 0.5, -1.0]), [1.0, 1.0], 2.0, 0.0)
+    assert st == -3
+    assert out["nll"] == math.inf
+    # the same design with a nugget is fine
+    out, st = orc.nll(x, np.array([1.0, 2.0, 0.5, -1.0]), [1.0, 1.0], 2.0, 1e-6)
+    assert st == 0 and math.isfinite(out["nll"])
+
+
+def check_cond_estimate(orc, seed=19):
+    g = np.random.default_rng(seed)
+    for (n, th) in [(20, 5.0), (50, 1.0), (40, 20.0)]:
+        x = g.random((n, 2))
+        R = orc.corr_matrix(x, [th, th], 1.95, 1e-8)
+        L, info = orc.cholesky(R)
+        assert info == 0
+        est = orc.cond1_est(R, L)
+        true = np.linalg.cond(R, 1)
+        assert est <= true * (1 + 1e-6)
+        assert est >= true / 3.0
+
+
+# --------------------------------------------------------- invariants -------
+
+def check_invariants(orc, seed=23):
+    g = np.random.default_rng(seed)
+    n, d = 25, 3
+    x = g.random((n, d))
+    y = np.cos(4 * x).sum(axis=1)
+    th = [2.0, 0.5, 7.0]
+    p, delta = 1.95, 1e-6
+    base, st = orc.nll(x, y, th, p, delta)
+    assert st == 0
+    perm = g.permutation(n)
+    o, _ = orc.nll(x[perm], y[perm], th, p, delta)
+    for k in ("nll", "mu", "sigma2", "logdet"):
+        assert _rel(o[k], base[k]) < 1e-10
+    c = -3.5
+    o, _ = orc.nll(x, c * y, th, p, delta)
+    assert _rel(o["mu"], c * base["mu"]) < 1e-10
+    assert _rel(o["sigma2"], c * c * base["sigma2"]) < 1e-10
+    assert abs(o["nll"] - (base["nll"] + 2 * n * math.log(abs(c)))) < 1e-9 * abs(base["nll"]) + 1e-9
+    o, _ = orc.nll(x, y + 10.0, th, p, delta)
+    assert _rel(o["mu"], base["mu"] + 10.0) < 1e-10
+    assert _rel(o["sigma2"], base["sigma2"]) < 1e-8
+    # Hadamard: unit-diagonal SPD matrix has log|R| <= 0
+    o, _ = orc.nll(x, y, th, p, 0.0)
+    assert o["logdet"] <= 0.0
+
+
+def check_table_form(orc):
+    """Eq. (4) read literally: -2logL = log|R| + n log Q with Q = n sigma2.
+    (a) the oracle's outputs have exactly that structure;
+    (b) on the paper's printed rows, that reading implies log|R| <= 0, which
+        Hadamard's inequality requires of a unit-diagonal correlation matrix,
+        while the other readings (n log sigma2, or the full Gaussian form)
+        would imply log|R| > 0 on the n = 4064 single-replication row."""
+    g = np.random.default_rng(29)
+    x = g.random((12, 2))
+    y = g.standard_normal(12)
+    o, st = orc.nll(x, y, [3.0, 4.0], 2.0, 1e-8)
+    assert st == 0
+    assert abs((o["nll"] - o["logdet"]) - 12 * math.log(12 * o["sigma2"])) < 1e-10
+    with open(os.path.join(GOLDEN, "paper_table_rows.json")) as f:
+        rows = json.load(f)["rows"]
+    for row in rows:
+        n, nll, s2 = row["n"], row["nll"], row["sigma2"]
+        assert nll - n * math.log(n * s2) < 0.0, row["cite"]
+    big = rows[0]
+    n, nll, s2 = big["n"], big["nll"], big["sigma2"]
+    assert nll - n * math.log(s2) > 0.0
+    assert nll - n * math.log(s2) - n * (1 + math.log(2 * math.pi)) > 0.0
+
+
+# --------------------------------------------------------- prediction -------
+
+def check_predict(orc, seed=31):
+    g = np.random.default_rng(seed)
+    n, d = 30, 2
+    x = g.random((n, d))
+    y = np.sin(5 * x[:, 0]) + x[:, 1] ** 2
+    th = [4.0, 2.0]
+    p = 1.95
+    # delta = 0: interpolation at the design points, zero variance
+    yh, s2, st = orc.predict(x, y, th, p, 0.0, x[:7])
+    assert st == 0
+    assert np.max(np.abs(yh - y[:7])) < 1e-8
+    assert np.max(np.abs(s2)) < 1e-8
+    # a point far from every design point: r = 0 -> mu_hat, sigma2 (1 + delta + 1/1'R^-1 1)
+    delta = 1e-6
+    o, _ = orc.nll(x, y, th, p, delta)
+    far = np.array([[40.0, 40.0]])
+    R = orc.corr_matrix(x, th, p, delta)
+    A = np.ones(n) @ np.linalg.solve(R, np.ones(n))
+    yh, s2, st = orc.predict(x, y, th, p, delta, far)
+    assert _rel(yh[0], o["mu"]) < 1e-12
+    assert _rel(s2[0], o["sigma2"] * (1 + delta + 1.0 / A)) < 1e-9
+    yh, s2n, _ = orc.predict(x, y, th, p, delta, far, nugget_in_var=False)
+    assert _rel(s2n[0], o["sigma2"] * (1 + 1.0 / A)) < 1e-9
+    # general points against LAPACK solves
+    xs = g.random((9, d))
+    yh, s2, _ = orc.predict(x, y, th, p, delta, xs)
+    one = np.ones(n)
+    Ri1 = np.linalg.solve(R, one)
+    w = np.linalg.solve(R, y - o["mu"])
+    for m in range(9):
+        r = np.array([math.exp(-sum(th[k] * abs(xs[m, k] - x[i, k]) ** p for k in range(d)))
+                      for i in range(n)])
+        Rir = np.linalg.solve(R, r)
+        ref_y = o["mu"] + r @ w
+        ref_s = o["sigma2"] * (1 + delta - r @ Rir + (1 - one @ Rir) ** 2 / (one @ Ri1))
+        assert abs(yh[m] - ref_y) < 1e-9 * max(1, abs(ref_y))
+        assert abs(s2[m] - ref_s) < 1e-9 * o["sigma2"]
+    # the variance is never negative beyond rounding
+    assert np.all(s2 > -1e-12)
+
+
+ALL_CHECKS = [
+    check_corr_hand_values, check_corr_invariants, check_kms, check_n1, check_n2,
+    check_n3, check_eig_logdet, check_solve_estimates, check_cholesky_reconstructs,
+    check_notpd, check_cond_estimate, check_invariants, check_table_form, check_predict,
+]

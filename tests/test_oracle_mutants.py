@@ -1,0 +1,70 @@
+"""CPU test: plant plausible mistakes in copies of the oracle and check that
+the pins catch every one.
+
+Each mutant is the oracle source with one textual change (a dropped term, a
+wrong sign, a wrong index, a transposed operand, the other reading of eq. 4),
+compiled into a temporary directory; the committed oracle is never touched.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "gp_oracle.c")
+
+MUTANTS = {
+    "corr_ignores_p": ("pow(diff, p)", "pow(diff, 2.0)"),
+    "corr_wrong_index": ("fabs(xi[k] - xj[k])", "fabs(xi[k] - xj[0])"),
+    "corr_sign": ("r *= exp(-theta[k] * pow(diff, p));", "r *= exp(theta[k] * pow(diff, p));"),
+    "nugget_everywhere": ("if (i == j) v += delta;", "v += delta;"),
+    "nugget_dropped": ("if (i == j) v += delta;", ";"),
+    "chol_update_sign": ("s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];",
+                         "s += L[(size_t)i * n + k] * L[(size_t)j * n + k];"),
+    "chol_offdiag_mul": ("L[(size_t)i * n + j] = s / L[(size_t)j * n + j];",
+                         "L[(size_t)i * n + j] = s * L[(size_t)j * n + j];"),
+    "forward_transposed": ("for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * z[k];",
+                           "for (int k = 0; k < i; ++k) s -= L[(size_t)k * n + i] * z[k];"),
+    "backward_transposed": ("for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * w[k];",
+                            "for (int k = i + 1; k < n; ++k) s -= L[(size_t)i * n + k] * w[k];"),
+    "mu_inverted": ("double mu = ab / aa;\n    double Q = 0.0, bb", "double mu = aa / ab;\n    double Q = 0.0, bb"),
+    "residual_sign": ("e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; bb", "e[i] = b[i] + mu * a[i]; Q += e[i] * e[i]; bb"),
+    "logdet_not_doubled": ("    logdet *= 2.0;\n    double sigma2", "    double sigma2"),
+    "nll_uses_sigma2": ("out[0] = logdet + n * log(Q);", "out[0] = logdet + n * log(Q / n);"),
+    "nll_drops_n": ("out[0] = logdet + n * log(Q);", "out[0] = logdet + log(Q);"),
+    "sigma2_not_over_n": ("double sigma2 = Q / n;\n    out[1]", "double sigma2 = Q;\n    out[1]"),
+    "predict_drops_mu": ("yhat[m] = mu + yh;", "yhat[m] = yh;"),
+    "predict_var_sign": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 + vv + g * g / aa);"),
+    "predict_var_unsquared": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 - vv + g / aa);"),
+    "predict_nugget_in_r": ("gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p);",
+                            "gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p) + 1e-6;"),
+    "cond_no_anorm": ("return anorm * est;", "return est;"),
+}
+
+
+def _build_mutant(tmpdir, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    cpath = os.path.join(tmpdir, f"m_{name}.c")
+    lib = os.path.join(tmpdir, f"libm_{name}.so")
+    with open(cpath, "w") as f:
+        f.write(mutated)
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                    "-D_DEFAULT_SOURCE", cpath, "-o", lib, "-lm"], check=True)
+    return oracle.Oracle(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    orc = _build_mutant(str(tmp_path), name, old, new)
+    failed = []
+    for check in pins.ALL_CHECKS:
+        try:
+            check(orc)
+        except Exception as exc:  # AssertionError, or a numeric error from nonsense output
+            failed.append((check.__name__, type(exc).__name__))
+    assert failed, f"no pin caught mutant {name}"
