@@ -1,0 +1,390 @@
+"""Benchmark: profile -2logL evaluations per second at n = 4000.
+
+Workload (one "step"): -2logL, mu_hat, sigma2_hat and log|R| at T = 256
+theta candidates (a multi-start population, log10 theta ~ U[-2, 1]^6) on a
+seeded random Latin hypercube of n = 4000 points in d = 6 with the smooth
+synthetic response sum_k sin(2 pi x_k)/k + 0.1 sum_k x_k^2, p = 1.95,
+delta = 1e-7 -- the shape of the paper's Example 2 (Hartman-6, n = 4064,
+p = 1.95, Section 4), whose test function is not used.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+                  [--impl gp|reference]
+
+--impl gp (default) times the CUDA library (inputs resident in HBM, CUDA
+events on the library's stream, max over ranks; each rank evaluates its own
+256 candidates: weak scaling, no collective on the data path).  The line
+also carries the end-to-end number through the host-buffer C entry point,
+the roofline of the dominant kernel, the SM clocks seen during the timed
+region, and the CPU oracle timed on a bounded sample on the host cores.
+--impl reference times the CPU oracle itself, on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1203_1269_gb300 import inputs  # noqa: E402
+
+METRIC = "GP -2logL evals/s at n=4000 (d=6, T=256 theta batch)"
+UNIT = "evals/s"
+NB = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def update_flops(n, nb=NB):
+    """Algorithmic flops of the trailing updates of one Cholesky (real rows
+    only): sum over block steps of nb * m (m + 1), m = rows below the panel."""
+    f = 0
+    J = 0
+    while (J + 1) * nb < n:
+        m = n - (J + 1) * nb
+        f += nb * m * (m + 1)
+        J += 1
+    return float(f)
+
+
+def chol_flops(n):
+    return n ** 3 / 3.0
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_for_rank(rank):
+    w = inputs.hartman_shape()
+    if rank > 0:
+        w.thetas = inputs.log_uniform_thetas(inputs.rng(inputs.BASE_SEED + 1 + 1000 * rank),
+                                             w.T, w.d)
+    return w
+
+
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1203_1269_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, src_files):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except OSError:
+        return None
+    ent = table.get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash(src_files):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def cpu_baseline_sample(w, max_theta=None, timeout_s=60.0):
+    """The oracle, as it stands, on a bounded sample of the workload's
+    candidates, spread over the host cores by its OpenMP loop."""
+    import oracle
+    cores = oracle.num_threads()
+    k = min(w.T, max_theta or cores)
+    t0 = time.perf_counter()
+    out, st = oracle.nll_batch(w.x, w.y, w.thetas[:k], w.p, w.delta)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} of the {w.T} candidates at n={w.n}, d={w.d} "
+                      f"(one single-threaded evaluation per core, {dt:.1f} s)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    w = workload_for_rank(0)
+    import oracle
+    cores = oracle.num_threads()
+    k = max(1, min(w.T, cores))
+    for _ in range(args.warmup):
+        oracle.nll_batch(w.x, w.y, w.thetas[:1], w.p, w.delta)
+    times = []
+    for s in range(args.steps):
+        sel = w.thetas[(s * k) % w.T:(s * k) % w.T + k]
+        t0 = time.perf_counter()
+        oracle.nll_batch(w.x, w.y, sel, w.p, w.delta)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = k * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "T": w.T, "p": w.p,
+                       "delta": w.delta, "sample_per_step": k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{k} candidates per step at n={w.n}, d={w.d}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gp(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1203_1269_gb300 import gp
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = workload_for_rank(rank)
+    prec = args.prec
+    ctx = gp.Context(local)
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, th = f64(w.x), f64(w.y), f64(w.thetas)
+    out = None
+
+    def step():
+        nonlocal out
+        out = ctx.nll_batch(x, y, th, w.p, w.delta, prec, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    ok = int((st == 0).sum())
+
+    # ---- timed region: device-resident inputs --------------------------------
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ctx.set_timing(True)
+    ctx.phase_times()  # reset
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    phases = ctx.phase_times()
+    ctx.set_timing(False)
+    total_ms = t0.elapsed_time(t1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * w.T * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    pk, pk_src = peaks()
+    dom = max(("assemble", "potrf", "trsm", "update", "solve", "split"), key=lambda k: phases[k][0])
+    if prec == "fp64":
+        upd_ms, upd_n = phases["update"]
+        flops = update_flops(w.n) * w.T * args.steps
+        achieved = flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"kernel": "k_update_f64", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None,
+                "traffic": stored_traffic("k_update_f64", ["k_chol_f64.cu"]),
+                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock "
+                               "(unit counts and clock of the profiling recipe)",
+                "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
+                "algorithmic_flops_per_launch": flops / max(upd_n, 1)}
+    else:
+        upd_ms, upd_n = phases["update"]
+        flops = update_flops(w.n) * w.T * args.steps
+        achieved = flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"kernel": "k_update_mixed", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": stored_traffic("k_update_mixed", ["k_mixed.cu"]),
+                "peak_source": f"bf16 dense sustained, {pk_src}",
+                "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
+                "algorithmic_flops_per_launch": flops / max(upd_n, 1)}
+
+    # ---- end to end through the host-buffer entry point ---------------------
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    hx = torch.from_numpy(w.x.copy()).pin_memory()
+    hy = torch.from_numpy(w.y.copy()).pin_memory()
+    hth = torch.from_numpy(w.thetas.copy()).pin_memory()
+    hout = dict(nll=torch.empty(w.T, dtype=torch.float64).pin_memory(),
+                mu=torch.empty(w.T, dtype=torch.float64).pin_memory(),
+                sigma2=torch.empty(w.T, dtype=torch.float64).pin_memory(),
+                logdet=torch.empty(w.T, dtype=torch.float64).pin_memory(),
+                status=torch.empty(w.T, dtype=torch.int32).pin_memory())
+    ctx.nll_batch_host(hx, hy, hth, w.p, w.delta, prec, out=hout)
+    if world > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.nll_batch_host(hx, hy, hth, w.p, w.delta, prec, out=hout)
+    e2e_s = time.perf_counter() - te
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = (w.x.size + w.y.size + w.thetas.size) * 8
+    d2h = w.T * (4 * 8 + 4)
+    e2e = {"value": world * w.T * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    # ---- secondary precision (the other arm of the metric) -------------------
+    other = None
+    if args.compare and prec == "mixed":
+        o = ctx.nll_batch(x, y, th, w.p, w.delta, "fp64")
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.compare_steps):
+            o = ctx.nll_batch(x, y, th, w.p, w.delta, "fp64", out=o)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1)
+        ref = o["nll"].cpu().numpy()
+        got = out["nll"].cpu().numpy()
+        fin = np.isfinite(ref) & np.isfinite(got)
+        rel = np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])
+        other = {"prec": "fp64", "value": world * w.T * args.compare_steps / (ms / 1e3),
+                 "steps": args.compare_steps,
+                 "mixed_vs_fp64_rel_err_nll": {"max": float(rel.max()) if rel.size else None,
+                                               "median": float(np.median(rel)) if rel.size else None}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(w)
+
+    if rank == 0:
+        pct = lambda q: float(np.percentile(step_ms, q))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == "fp64" else "bf16-split/f64",
+                "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "d": w.d, "T": w.T, "p": w.p,
+                           "delta": w.delta, "prec": prec, "parallelism": f"replicas{world}",
+                           "l2": "no flush: the batch's factor storage "
+                                 f"({w.T * (w.n // NB + 1) * (w.n // NB + 2) // 2 * NB * NB * 8 / 1e9:.1f} GB) "
+                                 "exceeds L2 (129 MB)"},
+                "latency_ms": {"p50": pct(50), "p99": pct(99), "unit": "ms per 256-candidate batch"},
+                "statuses_ok": ok,
+                "roofline": roof, "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()
+                                                         if v[1]},
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        if other:
+            line["compare"] = other
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--compare", action="store_true")
+    ap.add_argument("--compare-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

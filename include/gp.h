@@ -1,0 +1,192 @@
+/*
+ * gp.h -- C ABI of libgp: Gaussian-process likelihood and kriging on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of Franey, Ranjan & Chipman, "A Short Note on Gaussian
+ * Process Modeling for Large Datasets using Graphics Processing Units":
+ *   Section 2, eq. (2): power-exponential correlation
+ *       R_ij = prod_k exp(-theta_k |x_ik - x_jk|^p),  p in (0, 2];
+ *   Section 2, eq. (3): mu_hat = (1'R^-1 1)^-1 1'R^-1 Y,
+ *       sigma2_hat = (Y - 1 mu_hat)' R^-1 (Y - 1 mu_hat) / n;
+ *   Section 2, eq. (4): -2 log L = log|R| + n log[(Y-1mu)'R^-1(Y-1mu)];
+ *   Section 3: one evaluation of R, one Cholesky factorisation and a few
+ *       triangular solves per likelihood value; prediction at N points from
+ *       one fit.
+ * A diagonal nugget delta >= 0 is added: R_delta = R + delta I (delta = 0
+ * allowed).  Cross-correlations r(x*) used for prediction carry no nugget.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers unless the name ends in _host.
+ *     The caller owns them; the library never frees caller memory.
+ *   - Matrices are row-major: x is n x d with x[i*d + k]; theta is T x d.
+ *   - Work is enqueued on the context's stream.  Calls that return results
+ *     to the host (gp_fit, gp_predict's status, *_host variants) synchronise
+ *     that stream before returning; the others are asynchronous and report
+ *     only argument and launch errors in their return value.
+ *   - Return value: GP_OK or a negative gp_status.  The message of the last
+ *     failure is available from gp_last_error().
+ *   - Arguments are validated: n >= 1, d >= 1, T >= 1, 0 < p <= 2,
+ *     delta >= 0 and finite.  theta values are checked on the device: a
+ *     theta_k that is negative or not finite makes that candidate's status
+ *     GP_EINVAL and its outputs NaN; the rest of the batch completes.
+ *   - Per-candidate failures never fail the call: a Cholesky pivot that is
+ *     not positive gives status GP_ENOTPD and -2logL = +inf; Q at rounding
+ *     level (Y in the span of 1, e.g. n = 1) gives GP_EDEGENERATE and
+ *     -2logL = -inf.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_ctx gp_ctx;
+typedef struct gp_model gp_model;
+
+/* Arithmetic of the factorisation.
+ * GP_FP64:  assembly, Cholesky and solves in IEEE double.
+ * GP_MIXED: assembly, diagonal-block factorisation and inversion, log-det
+ *           and the iterative-refinement residuals in double; the panel and
+ *           trailing updates of the blocked Cholesky on the tensor cores with
+ *           double operands split into bf16 slices and exact fp32
+ *           accumulation (Ozaki-style), recombined in double-float.
+ * GP_AUTO:  GP_MIXED. */
+typedef enum {
+    GP_FP64 = 0,
+    GP_MIXED = 1,
+    GP_AUTO = 3
+} gp_precision;
+
+typedef enum {
+    GP_OK = 0,
+    GP_EINVAL = -1,       /* bad argument                                  */
+    GP_ENOMEM = -2,       /* device memory or HBM budget exhausted         */
+    GP_ENOTPD = -3,       /* R(theta) not positive definite in arithmetic  */
+    GP_ECUDA = -4,        /* CUDA runtime or launch error                  */
+    GP_ETIMEOUT = -5,     /* a bounded device wait gave up                 */
+    GP_EDEGENERATE = -6,  /* Q = 0 at rounding level: -2logL = -inf        */
+    GP_ENOTSUP = -7       /* configuration not built into this library     */
+} gp_status;
+
+/* Tunables; gp_default_options() fills the defaults. */
+typedef struct {
+    int slices;           /* GP_MIXED: bf16 slices per double operand (2..7), default 5 */
+    int panel_slices;     /* GP_MIXED: slices for the panel solve GEMM (2..8), default 7 */
+    int refine_iters;     /* GP_MIXED: iterative-refinement steps of the solves, default 2 */
+    int nugget_in_var;    /* kriging variance uses 1 + delta (1) or 1 (0), default 1 */
+    int max_batch;        /* instances factored concurrently (0 = from the budget) */
+} gp_options;
+
+void gp_default_options(gp_options* opt);
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  hbm_budget_bytes
+ * bounds the device workspace the context and its models may allocate
+ * (0 = 3/4 of the device's free memory).  Returns GP_OK and *ctx, or an
+ * error with *ctx = NULL. */
+int gp_create(gp_ctx** ctx, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* Free the context's workspace (synchronising its stream first). */
+void gp_destroy(gp_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char* gp_last_error(const gp_ctx* ctx);
+
+/* Switch the stream later calls enqueue on. */
+int gp_set_stream(gp_ctx* ctx, void* cuda_stream);
+
+/* Replace the context's tunables (copied). */
+int gp_set_options(gp_ctx* ctx, const gp_options* opt);
+
+/* Bytes of device workspace currently held by the context. */
+size_t gp_workspace_bytes(const gp_ctx* ctx);
+
+/* Phase timers.  While timing is on, every group of kernel launches is
+ * bracketed by CUDA events on the context's stream; gp_phase_times
+ * synchronises the stream, returns the accumulated milliseconds and kernel
+ * launches per phase (GP_PHASE_*) since the previous call, and resets them.
+ * The launch counts are kept whether or not timing is on. */
+enum {
+    GP_PHASE_ASSEMBLE = 0,   /* theta checks + correlation assembly        */
+    GP_PHASE_POTRF = 1,      /* diagonal-tile factorisation (and inverse)  */
+    GP_PHASE_TRSM = 2,       /* panel solve                                */
+    GP_PHASE_UPDATE = 3,     /* trailing update                            */
+    GP_PHASE_SOLVE = 4,      /* triangular solves, refinement, reductions  */
+    GP_PHASE_SPLIT = 5,      /* bf16 slicing of panels (GP_MIXED)          */
+    GP_PHASE_PREDICT = 6,    /* kriging kernels                            */
+    GP_NUM_PHASES = 8
+};
+int gp_set_timing(gp_ctx* ctx, int on);
+int gp_phase_times(gp_ctx* ctx, double* ms, long long* launches, int nphases);
+
+/* Kernels this context has launched since it was created. */
+long long gp_launch_count(const gp_ctx* ctx);
+
+/* R(theta) + delta I by eq. (2) (Section 2) for ONE theta (length d).
+ * layout 0: dense n x n row-major, both triangles (R[i*n + j]).
+ * layout 1: the factorisation's storage: lower-triangular 128 x 128 tiles,
+ *           tile (I, J) (I >= J) at offset (J*nt - J*(J-1)/2 + I - J)*16384
+ *           doubles with nt = ceil(n/128), column-major inside a tile
+ *           (element (r, c) at r + 128 c); rows and columns >= n hold the
+ *           identity; diagonal tiles hold both triangles.
+ *           R must hold nt(nt+1)/2 * 16384 doubles.
+ * Asynchronous. */
+int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
+                     double p, double delta, double* R, int layout);
+
+/* Profile -2 log-likelihood, eq. (4), at T candidate theta vectors (T x d),
+ * with the profile estimates of eq. (3).  Outputs (length T each):
+ *   nll[t]        -2logL = log|R| + n log Q  (eq. 4 read literally)
+ *   mu_hat[t]     eq. (3)
+ *   sigma2_hat[t] Q / n, eq. (3)
+ *   logdet[t]     log|R| = 2 sum log L_ii   (may be NULL)
+ *   status[t]     GP_OK, GP_ENOTPD, GP_EDEGENERATE or GP_EINVAL
+ * prec selects the factorisation's arithmetic (gp_precision).
+ * The candidates are factored in batches sized by the context's budget.
+ * Asynchronous. */
+int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                 const double* theta, double p, double delta, int prec,
+                 double* nll, double* mu_hat, double* sigma2_hat, double* logdet,
+                 int* status);
+
+/* gp_nll_batch with every array in host memory: the call copies the inputs
+ * to the device, evaluates, copies the outputs back and synchronises.
+ * Host buffers may be pageable or pinned. */
+int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host,
+                      const double* y_host, int T, const double* theta_host, double p,
+                      double delta, int prec, double* nll_host, double* mu_hat_host,
+                      double* sigma2_hat_host, double* logdet_host, int* status_host);
+
+/* Fit at one theta (length d): assemble, factor, solve, and keep on the
+ * device what prediction needs -- the factor L, w = R^-1 (Y - 1 mu_hat),
+ * a = L^-1 1, a copy of x, and the scalars.  Synchronises.  On GP_OK,
+ * *model owns that device memory until gp_model_free.  A fit whose R is
+ * not positive definite returns GP_ENOTPD and no model. */
+int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y,
+           const double* theta, double p, double delta, int prec, gp_model** model);
+
+/* Scalars of a fit: out[0..5] = -2logL, mu_hat, sigma2_hat, log|R|, Q, a'a. */
+int gp_model_scalars(const gp_model* model, double* out_host);
+
+/* Kriging prediction (Section 3: one R, one factorisation, two solves per
+ * test point) at N points xstar (N x d, device):
+ *   yhat[m] = mu_hat + r' R^-1 (Y - 1 mu_hat)
+ *   s2[m]   = sigma2_hat [c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1)]
+ * with r_i = corr(z(x*_m), z(x_i)) by eq. (2), c0 = 1 + delta (or 1 when
+ * the context's nugget_in_var is 0).  s2 may be NULL (mean only).
+ * Asynchronous; the model must outlive the enqueued work. */
+int gp_predict(gp_ctx* ctx, const gp_model* model, int N, const double* xstar,
+               double* yhat, double* s2);
+
+/* Release a model's device memory (synchronising the context's stream). */
+void gp_model_free(gp_model* model);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

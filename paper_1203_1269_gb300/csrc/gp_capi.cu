@@ -1,0 +1,513 @@
+// gp_capi.cu -- the C ABI of libgp (declared in include/gp.h): contexts,
+// argument checks, the device workspace, batching of theta candidates and
+// the sequence of kernel launches for each call.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gp_internal.cuh"
+#include "gp_mixed.cuh"
+
+struct gp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;          // bytes the context and its models may hold
+    size_t models_bytes = 0;    // held by live models
+    gp_options opt;
+    void* ws = nullptr;         // workspace arena
+    size_t ws_bytes = 0;
+    std::string err;
+    // phase timers (CUDA events on the context's stream) and launch counter
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+    double phase_ms[GP_NUM_PHASES] = {0};
+    long long phase_launches[GP_NUM_PHASES] = {0};
+    long long launches = 0;
+};
+
+struct gp_model {
+    gp_ctx* ctx = nullptr;
+    int n = 0, d = 0, nt = 0, prec = 0;
+    double p = 0.0, delta = 0.0;
+    void* mem = nullptr;        // one allocation holding everything below
+    size_t bytes = 0;
+    double* L = nullptr;        // packed factor tiles
+    double* Z = nullptr;        // [a | w], 2 * npad
+    double* x = nullptr;        // n x d
+    double* theta = nullptr;    // d
+    double* scalars = nullptr;  // nll, mu, sigma2, logdet, Q, aa (+2 spare)
+    int* status = nullptr;
+    gp::InstState* st = nullptr;
+    double host_scalars[6];
+};
+
+namespace {
+
+cudaEvent_t take_event(gp_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a group of launches of one phase with events (when timing is on)
+// and count the kernels it launched.
+struct PhaseScope {
+    gp_ctx* ctx;
+    int phase;
+    int kernels;
+    cudaEvent_t e0 = nullptr;
+    PhaseScope(gp_ctx* c, int ph, int k) : ctx(c), phase(ph), kernels(k) {
+        if (ctx->timing) {
+            e0 = take_event(ctx);
+            cudaEventRecord(e0, ctx->stream);
+        }
+    }
+    ~PhaseScope() {
+        ctx->launches += kernels;
+        ctx->phase_launches[phase] += kernels;
+        if (ctx->timing) {
+            cudaEvent_t e1 = take_event(ctx);
+            cudaEventRecord(e1, ctx->stream);
+            ctx->ev_open.push_back({phase, {e0, e1}});
+        }
+    }
+};
+
+int fail(gp_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define GP_CUDA(ctx, call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail((ctx), GP_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+int check_common(gp_ctx* ctx, int n, int d, double p, double delta) {
+    if (!ctx) return GP_EINVAL;
+    if (n < 1 || n > (1 << 20)) return fail(ctx, GP_EINVAL, "n = %d out of range [1, 2^20]", n);
+    if (d < 1 || d > GP_MAX_D) return fail(ctx, GP_EINVAL, "d = %d out of range [1, %d]", d, GP_MAX_D);
+    if (!(p > 0.0 && p <= 2.0)) return fail(ctx, GP_EINVAL, "p = %g outside (0, 2]", p);
+    if (!(delta >= 0.0) || !std::isfinite(delta))
+        return fail(ctx, GP_EINVAL, "delta = %g must be finite and >= 0", delta);
+    return GP_OK;
+}
+
+// Make the workspace at least `bytes` large, within the budget.
+int ensure_ws(gp_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return GP_OK;
+    if (bytes + ctx->models_bytes > ctx->budget)
+        return fail(ctx, GP_ENOMEM, "workspace of %zu bytes exceeds the HBM budget (%zu, %zu held by models)",
+                    bytes, ctx->budget, ctx->models_bytes);
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) {
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return fail(ctx, GP_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = bytes;
+    return GP_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Bytes of workspace per instance of the FP64 path.
+size_t per_instance_bytes_f64(int n) {
+    const int nt = gp::num_tiles(n);
+    return align256(gp::packed_elems(n) * sizeof(double)) +
+           align256((size_t)2 * nt * GP_NB * sizeof(double)) + align256(sizeof(gp::InstState));
+}
+
+// Factor and solve `b.count` instances already assembled in b.A.
+int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
+    for (int J = 0; J < b.nt; ++J) {
+        const int more = (J + 1 < b.nt) ? 1 : 0;
+        {
+            PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
+            GP_CUDA(ctx, gp::launch_potrf_f64(b, J, ctx->stream));
+        }
+        if (more) {
+            PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
+            GP_CUDA(ctx, gp::launch_trsm_f64(b, J, ctx->stream));
+        }
+        if (more) {
+            PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+            GP_CUDA(ctx, gp::launch_update_f64(b, J, ctx->stream));
+        }
+    }
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gp_default_options(gp_options* opt) {
+    if (!opt) return;
+    opt->slices = 5;
+    opt->panel_slices = 7;
+    opt->refine_iters = 2;
+    opt->nugget_in_var = 1;
+    opt->max_batch = 0;
+}
+
+int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+    if (!out) return GP_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return GP_ECUDA;
+    }
+    if (device < 0 || device >= count) return GP_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return GP_ECUDA;
+    gp_ctx* ctx = new gp_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    gp_default_options(&ctx->opt);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete ctx;
+        return GP_ECUDA;
+    }
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (free_b / 4) * 3;
+    *out = ctx;
+    return GP_OK;
+}
+
+void gp_destroy(gp_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto& o : ctx->ev_open) {
+        cudaEventDestroy(o.second.first);
+        cudaEventDestroy(o.second.second);
+    }
+    delete ctx;
+}
+
+const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gp_set_stream(gp_ctx* ctx, void* stream) {
+    if (!ctx) return GP_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return GP_OK;
+}
+
+int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
+    if (!ctx || !opt) return GP_EINVAL;
+    if (opt->slices < 2 || opt->slices > 7) return fail(ctx, GP_EINVAL, "slices = %d outside [2, 7]", opt->slices);
+    if (opt->panel_slices < 2 || opt->panel_slices > 8)
+        return fail(ctx, GP_EINVAL, "panel_slices = %d outside [2, 8]", opt->panel_slices);
+    if (opt->refine_iters < 0 || opt->refine_iters > 10)
+        return fail(ctx, GP_EINVAL, "refine_iters = %d outside [0, 10]", opt->refine_iters);
+    if (opt->max_batch < 0) return fail(ctx, GP_EINVAL, "max_batch must be >= 0");
+    ctx->opt = *opt;
+    return GP_OK;
+}
+
+size_t gp_workspace_bytes(const gp_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int gp_set_timing(gp_ctx* ctx, int on) {
+    if (!ctx) return GP_EINVAL;
+    ctx->timing = (on != 0);
+    return GP_OK;
+}
+
+int gp_phase_times(gp_ctx* ctx, double* ms, long long* launches, int nphases) {
+    if (!ctx || nphases < 0) return GP_EINVAL;
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& o : ctx->ev_open) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, o.second.first, o.second.second) == cudaSuccess)
+            ctx->phase_ms[o.first] += t;
+        ctx->ev_pool.push_back(o.second.first);
+        ctx->ev_pool.push_back(o.second.second);
+    }
+    ctx->ev_open.clear();
+    for (int i = 0; i < nphases && i < GP_NUM_PHASES; ++i) {
+        if (ms) ms[i] = ctx->phase_ms[i];
+        if (launches) launches[i] = ctx->phase_launches[i];
+    }
+    for (int i = 0; i < GP_NUM_PHASES; ++i) {
+        ctx->phase_ms[i] = 0.0;
+        ctx->phase_launches[i] = 0;
+    }
+    return GP_OK;
+}
+
+long long gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* theta, double p,
+                     double delta, double* R, int layout) {
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (!x || !theta || !R) return fail(ctx, GP_EINVAL, "null pointer argument");
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (layout == 0) {
+        if (n > 65535) return fail(ctx, GP_EINVAL, "dense layout limited to n <= 65535");
+        GP_CUDA(ctx, gp::launch_assemble_dense(n, d, x, theta, p, delta, R, ctx->stream));
+        return GP_OK;
+    }
+    if (layout != 1) return fail(ctx, GP_EINVAL, "layout must be 0 or 1");
+    rc = ensure_ws(ctx, align256(sizeof(gp::InstState)));
+    if (rc) return rc;
+    gp::Batch b{};
+    b.n = n; b.d = d; b.nt = gp::num_tiles(n); b.count = 1;
+    b.p = p; b.delta = delta; b.x = x; b.y = nullptr; b.theta = theta;
+    b.A = R; b.inst_stride = gp::packed_elems(n);
+    b.st = (gp::InstState*)ctx->ws;
+    GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+    GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+    return GP_OK;
+}
+
+int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                 const double* theta, double p, double delta, int prec, double* nll,
+                 double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
+        return fail(ctx, GP_EINVAL, "null pointer argument");
+    if (prec == GP_AUTO) prec = GP_MIXED;
+    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (prec == GP_MIXED) return gp::mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat,
+                                                     sigma2_hat, logdet, status);
+    const int nt = gp::num_tiles(n);
+    const size_t per = per_instance_bytes_f64(n);
+    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    long long cap = (long long)(avail / per);
+    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
+    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
+    if (cap > 65535) cap = 65535;  // grid.y bound of the per-instance launches
+    const int Tc = (int)(cap < T ? cap : T);
+    rc = ensure_ws(ctx, per * (size_t)Tc);
+    if (rc) return rc;
+    char* base = (char*)ctx->ws;
+    const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
+    const size_t z_bytes = align256((size_t)2 * nt * GP_NB * sizeof(double));
+    double* A = (double*)base;
+    double* Z = (double*)(base + a_bytes * Tc);
+    gp::InstState* st = (gp::InstState*)(base + (a_bytes + z_bytes) * Tc);
+    for (int c0 = 0; c0 < T; c0 += Tc) {
+        const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
+        gp::Batch b{};
+        b.n = n; b.d = d; b.nt = nt; b.count = cnt;
+        b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
+        b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
+        {
+            PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+            GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+            GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+        }
+        rc = run_factor_f64(ctx, b);
+        if (rc) return rc;
+        const size_t zs = z_bytes / sizeof(double);
+        PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+        GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
+        GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, mu_hat + c0, sigma2_hat + c0,
+                                         logdet ? logdet + c0 : nullptr, status + c0, ctx->stream));
+    }
+    return GP_OK;
+}
+
+int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host, const double* y_host, int T,
+                      const double* theta_host, double p, double delta, int prec, double* nll_host,
+                      double* mu_hat_host, double* sigma2_hat_host, double* logdet_host,
+                      int* status_host) {
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (!x_host || !y_host || !theta_host || !nll_host || !mu_hat_host || !sigma2_hat_host ||
+        !status_host)
+        return fail(ctx, GP_EINVAL, "null pointer argument");
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t bx = (size_t)n * d * sizeof(double), by = (size_t)n * sizeof(double);
+    const size_t bt = (size_t)T * d * sizeof(double), bo = (size_t)T * sizeof(double);
+    const size_t total = align256(bx) + align256(by) + align256(bt) + 4 * align256(bo) +
+                         align256((size_t)T * sizeof(int));
+    // the staging area is its own allocation so the batch can use the workspace
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&dev, total, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GP_ENOMEM, "staging allocation of %zu bytes failed", total);
+    }
+    char* c = (char*)dev;
+    double* dx = (double*)c; c += align256(bx);
+    double* dy = (double*)c; c += align256(by);
+    double* dth = (double*)c; c += align256(bt);
+    double* dnll = (double*)c; c += align256(bo);
+    double* dmu = (double*)c; c += align256(bo);
+    double* ds2 = (double*)c; c += align256(bo);
+    double* dld = (double*)c; c += align256(bo);
+    int* dst = (int*)c;
+    cudaMemcpyAsync(dx, x_host, bx, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dy, y_host, by, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dth, theta_host, bt, cudaMemcpyHostToDevice, ctx->stream);
+    rc = gp_nll_batch(ctx, n, d, dx, dy, T, dth, p, delta, prec, dnll, dmu, ds2, dld, dst);
+    if (rc == GP_OK) {
+        cudaMemcpyAsync(nll_host, dnll, bo, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(mu_hat_host, dmu, bo, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(sigma2_hat_host, ds2, bo, cudaMemcpyDeviceToHost, ctx->stream);
+        if (logdet_host) cudaMemcpyAsync(logdet_host, dld, bo, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(status_host, dst, (size_t)T * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    cudaFreeAsync(dev, ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(ctx, GP_ECUDA, "stream synchronise: %s", cudaGetErrorString(e));
+    return GP_OK;
+}
+
+int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const double* theta,
+           double p, double delta, int prec, gp_model** model) {
+    if (!model) return fail(ctx, GP_EINVAL, "null model pointer");
+    *model = nullptr;
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
+    if (prec == GP_AUTO) prec = GP_MIXED;
+    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int nt = gp::num_tiles(n);
+    const int npad = nt * GP_NB;
+    const size_t bL = align256(gp::packed_elems(n) * sizeof(double));
+    const size_t bZ = align256((size_t)2 * npad * sizeof(double));
+    const size_t bx = align256((size_t)n * d * sizeof(double));
+    const size_t bth = align256((size_t)d * sizeof(double));
+    const size_t bsc = align256(8 * sizeof(double));
+    const size_t bstat = align256(sizeof(int));
+    const size_t bst = align256(sizeof(gp::InstState));
+    const size_t total = bL + bZ + bx + bth + bsc + bstat + bst;
+    if (total + ctx->models_bytes + ctx->ws_bytes > ctx->budget)
+        return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
+    gp_model* m = new gp_model();
+    m->ctx = ctx; m->n = n; m->d = d; m->nt = nt; m->p = p; m->delta = delta; m->prec = prec;
+    cudaError_t e = cudaMalloc(&m->mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return fail(ctx, GP_ENOMEM, "cudaMalloc(%zu) for the model failed", total);
+    }
+    m->bytes = total;
+    char* c = (char*)m->mem;
+    m->L = (double*)c; c += bL;
+    m->Z = (double*)c; c += bZ;
+    m->x = (double*)c; c += bx;
+    m->theta = (double*)c; c += bth;
+    m->scalars = (double*)c; c += bsc;
+    m->status = (int*)c; c += bstat;
+    m->st = (gp::InstState*)c;
+    ctx->models_bytes += total;
+    auto bail = [&](int code) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(m->mem);
+        ctx->models_bytes -= m->bytes;
+        delete m;
+        return code;
+    };
+    if (cudaMemcpyAsync(m->x, x, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) ||
+        cudaMemcpyAsync(m->theta, theta, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream))
+        return bail(fail(ctx, GP_ECUDA, "copy of x/theta into the model failed"));
+    gp::Batch b{};
+    b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta;
+    b.x = m->x; b.y = y; b.theta = m->theta; b.A = m->L; b.inst_stride = bL / sizeof(double);
+    b.st = m->st;
+    if (prec == GP_MIXED) {
+        rc = gp::mixed_fit_factor(ctx, b, m->Z, (size_t)2 * npad);
+        if (rc) return bail(rc);
+    } else {
+        if (gp::launch_validate_theta(b, ctx->stream) || gp::launch_assemble_tiles(b, ctx->stream))
+            return bail(fail(ctx, GP_ECUDA, "assembly launch failed"));
+        rc = run_factor_f64(ctx, b);
+        if (rc) return bail(rc);
+        if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream))
+            return bail(fail(ctx, GP_ECUDA, "forward solve launch failed"));
+    }
+    if (gp::launch_finalize(b, m->Z, (size_t)2 * npad, m->scalars + 0, m->scalars + 1, m->scalars + 2,
+                            m->scalars + 3, m->status, ctx->stream) ||
+        gp::launch_fit_finish(b, m->Z, (size_t)2 * npad, m->scalars, ctx->stream) ||
+        gp::launch_backward_solve(b, m->Z, (size_t)2 * npad, 1, ctx->stream))
+        return bail(fail(ctx, GP_ECUDA, "solve launch failed"));
+    int hstatus = 0;
+    e = cudaMemcpyAsync(&hstatus, m->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->host_scalars, m->scalars, 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, GP_ECUDA, "fit: %s", cudaGetErrorString(e)));
+    if (hstatus == GP_ENOTPD || hstatus == GP_EINVAL)
+        return bail(fail(ctx, hstatus, "fit failed with status %d", hstatus));
+    *model = m;
+    return hstatus;  // GP_OK or GP_EDEGENERATE (model still usable for the mean)
+}
+
+int gp_model_scalars(const gp_model* m, double* out) {
+    if (!m || !out) return GP_EINVAL;
+    for (int i = 0; i < 6; ++i) out[i] = m->host_scalars[i];
+    return GP_OK;
+}
+
+int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, double* yhat, double* s2) {
+    if (!ctx || !m) return GP_EINVAL;
+    if (N < 0) return fail(ctx, GP_EINVAL, "N = %d must be >= 0", N);
+    if (N == 0) return GP_OK;
+    if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int npad = m->nt * GP_NB;
+    const size_t per_cta = (size_t)npad * 32 * sizeof(double);
+    const int blocks_total = (N + 31) / 32;
+    int chunk = blocks_total < 4 * 152 ? blocks_total : 4 * 152;
+    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    while (chunk > 1 && per_cta * chunk > avail) chunk /= 2;
+    int rc = ensure_ws(ctx, s2 ? per_cta * chunk : 256);
+    if (rc) return rc;
+    const double c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
+    GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, m->x, m->theta, m->p, c0, m->L,
+                                    m->Z + npad, m->Z, m->scalars, N, xstar, yhat, s2,
+                                    (double*)ctx->ws, chunk, ctx->stream));
+    return GP_OK;
+}
+
+void gp_model_free(gp_model* m) {
+    if (!m) return;
+    if (m->ctx) {
+        cudaSetDevice(m->ctx->device);
+        cudaStreamSynchronize(m->ctx->stream);
+        m->ctx->models_bytes -= m->bytes;
+    }
+    cudaFree(m->mem);
+    delete m;
+}
+
+}  // extern "C"

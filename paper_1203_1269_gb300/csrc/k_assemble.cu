@@ -1,0 +1,211 @@
+// k_assemble.cu -- the power-exponential correlation matrix (Section 2,
+// eq. 2) with a diagonal nugget, written straight into the factorisation's
+// tile storage for a batch of theta candidates.
+//
+// R_ij = exp(-sum_k theta_k |x_ik - x_jk|^p) + delta [i == j]
+//
+// The d powers |x_ik - x_jk|^p do not depend on theta, so each thread
+// computes them once per matrix entry and reuses them for every candidate of
+// its group; per candidate an entry then costs d FMAs and one exp.  The paper
+// counts d n(n-1)/2 independent terms (Section 3); here the lower triangle of
+// tiles (diagonal tiles in full) is produced.
+#include "gp_internal.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSplit = 4;                       // a CTA covers NB/kSplit columns of a tile
+constexpr int kCols = GP_NB / kSplit;           // 32 columns
+constexpr int kEntries = GP_NB * kCols / kThreads;  // 16 entries per thread
+
+__device__ __forceinline__ double powabs(double diff, double p) {
+    double a = fabs(diff);
+    if (p == 2.0) return a * a;
+    if (p == 1.0) return a;
+    return (a == 0.0) ? 0.0 : pow(a, p);
+}
+
+// Validate theta and reset each instance's record.
+__global__ void k_validate_theta(Batch b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.count) return;
+    int bad = 0;
+    for (int k = 0; k < b.d; ++k) {
+        double th = b.theta[(size_t)t * b.d + k];
+        if (!(th >= 0.0) || !isfinite(th)) bad = 1;
+    }
+    InstState s;
+    s.logdet = 0.0; s.aa = 0.0; s.ab = 0.0; s.mu = 0.0; s.Q = 0.0; s.bb = 0.0;
+    s.status = bad ? GP_EINVAL : GP_OK;
+    s.fail_col = -1;
+    b.st[t] = s;
+}
+
+// grid.x = packed tiles * kSplit, grid.y = candidate groups; DB = bound on d
+template <int DB>
+__global__ void __launch_bounds__(kThreads)
+k_assemble_tiles(Batch b, int group) {
+    __shared__ double xs_r[GP_NB * DB];
+    __shared__ double xs_c[kCols * DB];
+    const int nt = b.nt, n = b.n, d = b.d;
+    const int tile_lin = blockIdx.x / kSplit;
+    const int part = blockIdx.x % kSplit;
+    // decode packed tile index -> (I, J) with column-major tile packing
+    int J = 0;
+    {
+        long long rem = tile_lin;
+        while (rem >= nt - J) { rem -= nt - J; ++J; }
+        // I = J + rem
+        (void)rem;
+    }
+    long long start = tile_index(J, J, nt);
+    const int I = J + (int)(tile_lin - start);
+    const int row0 = I * GP_NB, col0 = J * GP_NB + part * kCols;
+
+    for (int q = threadIdx.x; q < GP_NB * DB; q += kThreads) {
+        int r = q / DB, k = q % DB;
+        int gi = row0 + r;
+        xs_r[q] = (gi < n && k < d) ? b.x[(size_t)gi * d + k] : 0.0;
+    }
+    for (int q = threadIdx.x; q < kCols * DB; q += kThreads) {
+        int c = q / DB, k = q % DB;
+        int gj = col0 + c;
+        xs_c[q] = (gj < n && k < d) ? b.x[(size_t)gj * d + k] : 0.0;
+    }
+    __syncthreads();
+
+    const int t0 = blockIdx.y * group;
+    const int t1 = min(b.count, t0 + group);
+    const size_t tile_off = (size_t)tile_lin * GP_TILE_ELEMS;
+    const int r = threadIdx.x % GP_NB;           // row inside the tile
+    const int cb = threadIdx.x / GP_NB;          // 0..1
+    const int gi = row0 + r;
+
+#pragma unroll 1
+    for (int e = 0; e < kEntries; ++e) {
+        const int c = cb + 2 * e;                // column inside this part
+        const int gj = col0 + c;
+        const size_t off = tile_off + (size_t)(part * kCols + c) * GP_NB + r;
+        const bool pad = (gi >= n) || (gj >= n);
+        const bool diag = (gi == gj);
+        double D[DB];
+#pragma unroll
+        for (int k = 0; k < DB; ++k)
+            D[k] = (k < d && !pad) ? powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p) : 0.0;
+#pragma unroll 1
+        for (int t = t0; t < t1; ++t) {
+            if (b.st[t].status != GP_OK) continue;
+            double v;
+            if (pad) {
+                v = diag ? 1.0 : 0.0;
+            } else {
+                const double* th = b.theta + (size_t)t * d;
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < DB; ++k)
+                    if (k < d) s = fma(__ldg(th + k), D[k], s);
+                v = exp(-s);
+                if (diag) v += b.delta;
+            }
+            b.A[(size_t)t * b.inst_stride + off] = v;
+        }
+    }
+}
+
+// d above the register-bounded variants: recompute the powers per candidate.
+__global__ void __launch_bounds__(kThreads)
+k_assemble_tiles_generic(Batch b, int group) {
+    const int nt = b.nt, n = b.n, d = b.d;
+    const int tile_lin = blockIdx.x / kSplit;
+    const int part = blockIdx.x % kSplit;
+    int J = 0;
+    {
+        long long rem = tile_lin;
+        while (rem >= nt - J) { rem -= nt - J; ++J; }
+    }
+    const int I = J + (int)(tile_lin - tile_index(J, J, nt));
+    const int row0 = I * GP_NB, col0 = J * GP_NB + part * kCols;
+    const int t0 = blockIdx.y * group;
+    const int t1 = min(b.count, t0 + group);
+    const size_t tile_off = (size_t)tile_lin * GP_TILE_ELEMS;
+    const int r = threadIdx.x % GP_NB;
+    const int cb = threadIdx.x / GP_NB;
+    const int gi = row0 + r;
+    for (int e = 0; e < kEntries; ++e) {
+        const int c = cb + 2 * e;
+        const int gj = col0 + c;
+        const size_t off = tile_off + (size_t)(part * kCols + c) * GP_NB + r;
+        const bool pad = (gi >= n) || (gj >= n);
+        const bool diag = (gi == gj);
+        for (int t = t0; t < t1; ++t) {
+            if (b.st[t].status != GP_OK) continue;
+            double v;
+            if (pad) {
+                v = diag ? 1.0 : 0.0;
+            } else {
+                const double* th = b.theta + (size_t)t * d;
+                double s = 0.0;
+                for (int k = 0; k < d; ++k)
+                    s = fma(th[k], powabs(b.x[(size_t)gi * d + k] - b.x[(size_t)gj * d + k], b.p), s);
+                v = exp(-s);
+                if (diag) v += b.delta;
+            }
+            b.A[(size_t)t * b.inst_stride + off] = v;
+        }
+    }
+}
+
+// Dense n x n row-major R (both triangles) for one theta.
+__global__ void k_assemble_dense(int n, int d, const double* __restrict__ x,
+                                 const double* __restrict__ theta, double p, double delta,
+                                 double* __restrict__ R) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k)
+        s = fma(theta[k], powabs(x[(size_t)i * d + k] - x[(size_t)j * d + k], p), s);
+    double v = exp(-s);
+    if (i == j) v += delta;
+    R[(size_t)i * n + j] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_validate_theta(const Batch& b, cudaStream_t s) {
+    k_validate_theta<<<(b.count + 127) / 128, 128, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
+    const long long tiles = packed_tiles(b.nt);
+    const long long ctas_per_group = tiles * kSplit;
+    // enough candidate groups to give ~4 CTAs per SM, but as few as possible
+    // so that the theta-independent powers are shared by many candidates
+    long long groups = (4 * 152 + ctas_per_group - 1) / ctas_per_group;
+    if (groups < 1) groups = 1;
+    if (groups > b.count) groups = b.count;
+    int group = (int)((b.count + groups - 1) / groups);
+    groups = (b.count + group - 1) / group;
+    dim3 grid((unsigned)ctas_per_group, (unsigned)groups);
+    if (b.d <= 4)
+        k_assemble_tiles<4><<<grid, kThreads, 0, s>>>(b, group);
+    else if (b.d <= 8)
+        k_assemble_tiles<8><<<grid, kThreads, 0, s>>>(b, group);
+    else if (b.d <= 16)
+        k_assemble_tiles<16><<<grid, kThreads, 0, s>>>(b, group);
+    else
+        k_assemble_tiles_generic<<<grid, kThreads, 0, s>>>(b, group);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* theta, double p,
+                                  double delta, double* R, cudaStream_t s) {
+    dim3 grid((n + 255) / 256, n);
+    k_assemble_dense<<<grid, 256, 0, s>>>(n, d, x, theta, p, delta, R);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

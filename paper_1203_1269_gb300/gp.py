@@ -1,0 +1,291 @@
+"""Python binding of libgp (the C ABI in include/gp.h).
+
+Argument marshalling only: tensors are checked (device, dtype, layout) and
+their data pointers handed to the C entry points of the same names; every
+step of the computation runs in the library's CUDA kernels.  PyTorch provides
+the device memory and the stream.
+
+The library must have been built (``paper_1203_1269_gb300.build.build()``);
+if it is missing, importing functions from here raises -- there is no CPU or
+PyTorch fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+GP_FP64, GP_MIXED, GP_AUTO = 0, 1, 3
+PRECISIONS = {"fp64": GP_FP64, "mixed": GP_MIXED, "auto": GP_AUTO}
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ENOTPD", -4: "ECUDA", -5: "ETIMEOUT",
+          -6: "EDEGENERATE", -7: "ENOTSUP"}
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_EDEGENERATE, GP_ENOTSUP = \
+    0, -1, -2, -3, -4, -5, -6, -7
+
+_c_int, _c_double, _c_size, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+
+
+class GPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
+                ("nugget_in_var", _c_int), ("max_batch", _c_int)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libgp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgp.so not found at {path}: build it with "
+                           "paper_1203_1269_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P = _vp
+    lib.gp_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.gp_create.argtypes = [ctypes.POINTER(P), _c_int, _c_size, P]
+    lib.gp_destroy.argtypes = [P]
+    lib.gp_destroy.restype = None
+    lib.gp_last_error.argtypes = [P]
+    lib.gp_last_error.restype = ctypes.c_char_p
+    lib.gp_set_stream.argtypes = [P, P]
+    lib.gp_set_options.argtypes = [P, ctypes.POINTER(Options)]
+    lib.gp_workspace_bytes.argtypes = [P]
+    lib.gp_workspace_bytes.restype = _c_size
+    lib.gp_set_timing.argtypes = [P, _c_int]
+    lib.gp_phase_times.argtypes = [P, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong),
+                                   _c_int]
+    lib.gp_launch_count.argtypes = [P]
+    lib.gp_launch_count.restype = ctypes.c_longlong
+    lib.gp_corr_assemble.argtypes = [P, _c_int, _c_int, P, P, _c_double, _c_double, P, _c_int]
+    lib.gp_nll_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
+                                 P, P, P, P, P]
+    lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
+    lib.gp_fit.argtypes = [P, _c_int, _c_int, P, P, P, _c_double, _c_double, _c_int,
+                           ctypes.POINTER(P)]
+    lib.gp_model_scalars.argtypes = [P, ctypes.POINTER(_c_double)]
+    lib.gp_predict.argtypes = [P, P, _c_int, P, P, P]
+    lib.gp_model_free.argtypes = [P]
+    lib.gp_model_free.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _dev_f64(t, name, shape=None, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the context uses {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _prec(prec):
+    if isinstance(prec, str):
+        return PRECISIONS[prec]
+    return int(prec)
+
+
+def packed_elems(n, nb=128):
+    """Doubles in the tile storage of an n x n R (lower tiles, 128 x 128)."""
+    nt = (n + nb - 1) // nb
+    return nt * (nt + 1) // 2 * nb * nb
+
+
+class Model:
+    """A resident fit (device factor and weights) owned by libgp."""
+
+    def __init__(self, ctx, handle, n, d):
+        self._ctx = ctx
+        self._h = handle
+        self.n, self.d = n, d
+        out = (_c_double * 6)()
+        ctx._lib.gp_model_scalars(handle, out)
+        self.nll, self.mu, self.sigma2, self.logdet, self.Q, self.aa = list(out)
+
+    def free(self):
+        if self._h:
+            self._ctx._lib.gp_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A libgp context on one CUDA device, enqueuing on a torch stream."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, stream=None, **options):
+        self._lib = load()
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = _vp()
+        rc = self._lib.gp_create(ctypes.byref(h), device, int(hbm_budget_bytes),
+                                 _vp(stream.cuda_stream))
+        if rc != 0:
+            raise GPError(rc, "gp_create failed")
+        self._h = h
+        opt = Options()
+        self._lib.gp_default_options(ctypes.byref(opt))
+        self._opt = opt
+        if options:
+            self.set_options(**options)
+
+    # -- plumbing ----------------------------------------------------------
+    def _check(self, rc):
+        if rc not in (0,):
+            raise GPError(rc, self._lib.gp_last_error(self._h).decode())
+        return rc
+
+    def options(self):
+        return {f: getattr(self._opt, f) for f, _ in Options._fields_}
+
+    def set_options(self, **kw):
+        opt = Options(**{**self.options(), **kw})
+        self._check(self._lib.gp_set_options(self._h, ctypes.byref(opt)))
+        self._opt = opt
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self._lib.gp_set_stream(self._h, _vp(stream.cuda_stream)))
+
+    PHASES = ("assemble", "potrf", "trsm", "update", "solve", "split", "predict", "spare")
+
+    def set_timing(self, on=True):
+        self._check(self._lib.gp_set_timing(self._h, int(bool(on))))
+
+    def phase_times(self):
+        """{phase: (milliseconds, kernel launches)} since the previous call (synchronises)."""
+        ms = (_c_double * 8)()
+        ln = (ctypes.c_longlong * 8)()
+        self._check(self._lib.gp_phase_times(self._h, ms, ln, 8))
+        return {name: (ms[i], ln[i]) for i, name in enumerate(self.PHASES)}
+
+    def launch_count(self):
+        return int(self._lib.gp_launch_count(self._h))
+
+    def workspace_bytes(self):
+        return int(self._lib.gp_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- gp_corr_assemble --------------------------------------------------
+    def corr_assemble(self, x, theta, p, delta, layout="dense", out=None):
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        theta = _dev_f64(theta, "theta", (d,), self.device)
+        lay = {"dense": 0, "tiles": 1}[layout]
+        size = (n, n) if lay == 0 else (packed_elems(n),)
+        if out is None:
+            out = torch.empty(size, dtype=torch.float64, device=self.device)
+        _dev_f64(out, "out", size, self.device)
+        self._check(self._lib.gp_corr_assemble(self._h, n, d, _ptr(x), _ptr(theta), float(p),
+                                               float(delta), _ptr(out), lay))
+        return out
+
+    # -- gp_nll_batch ------------------------------------------------------
+    def nll_batch(self, x, y, thetas, p, delta, prec="fp64", out=None):
+        """-2logL, mu_hat, sigma2_hat, log|R| and status at each row of thetas."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        if out is None:
+            kw = dict(dtype=torch.float64, device=self.device)
+            out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw),
+                       sigma2=torch.empty(T, **kw), logdet=torch.empty(T, **kw),
+                       status=torch.empty(T, dtype=torch.int32, device=self.device))
+        self._check(self._lib.gp_nll_batch(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
+            _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
+            _ptr(out["status"])))
+        return out
+
+    def nll_batch_host(self, x, y, thetas, p, delta, prec="fp64", out=None):
+        """gp_nll_batch_host: host (CPU, optionally pinned) tensors in and out."""
+        def host(t, name, dtype=torch.float64):
+            if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor")
+            return t
+        x = host(x, "x")
+        n, d = x.shape
+        y = host(y, "y")
+        thetas = host(thetas, "thetas")
+        T = thetas.shape[0]
+        if out is None:
+            out = dict(nll=torch.empty(T, dtype=torch.float64), mu=torch.empty(T, dtype=torch.float64),
+                       sigma2=torch.empty(T, dtype=torch.float64),
+                       logdet=torch.empty(T, dtype=torch.float64),
+                       status=torch.empty(T, dtype=torch.int32))
+        self._check(self._lib.gp_nll_batch_host(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
+            _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
+            _ptr(out["status"])))
+        return out
+
+    # -- gp_fit / gp_predict -----------------------------------------------
+    def fit(self, x, y, theta, p, delta, prec="fp64"):
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        theta = _dev_f64(theta, "theta", (d,), self.device)
+        h = _vp()
+        rc = self._lib.gp_fit(self._h, n, d, _ptr(x), _ptr(y), _ptr(theta), float(p), float(delta),
+                              _prec(prec), ctypes.byref(h))
+        if rc not in (GP_OK, GP_EDEGENERATE):
+            self._check(rc)
+        return Model(self, h, n, d)
+
+    def predict(self, model, xs, want_var=True, yhat=None, s2=None):
+        xs = _dev_f64(xs, "xs", device=self.device)
+        N = xs.shape[0]
+        if xs.dim() != 2 or xs.shape[1] != model.d:
+            raise ValueError("xs must be N x d")
+        if yhat is None:
+            yhat = torch.empty(N, dtype=torch.float64, device=self.device)
+        if want_var and s2 is None:
+            s2 = torch.empty(N, dtype=torch.float64, device=self.device)
+        self._check(self._lib.gp_predict(self._h, model._h, N, _ptr(xs), _ptr(yhat),
+                                         _ptr(s2) if want_var else None))
+        return yhat, (s2 if want_var else None)
