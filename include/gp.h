@@ -73,11 +73,15 @@ typedef enum {
 
 /* Tunables; gp_default_options() fills the defaults. */
 typedef struct {
-    int slices;           /* GP_MIXED: bf16 slices per double operand (2..7), default 5 */
-    int panel_slices;     /* GP_MIXED: slices for the panel solve GEMM (2..8), default 7 */
+    int slices;           /* GP_MIXED: bf16 slices per double operand (2..6), default 5 */
+    int panel_slices;     /* GP_MIXED: slices of the panel-solve GEMM; fixed at 7 (all
+                             product groups exact), other values are rejected */
     int refine_iters;     /* GP_MIXED: iterative-refinement steps of the solves, default 2 */
     int nugget_in_var;    /* kriging variance uses 1 + delta (1) or 1 (0), default 1 */
     int max_batch;        /* instances factored concurrently (0 = from the budget) */
+    int update_groups;    /* GP_MIXED: fp32 accumulators of the trailing update: 3 or 4
+                             (128-wide tiles, the last group rounded) or 7 (64-wide
+                             tiles, every group exact) */
 } gp_options;
 
 void gp_default_options(gp_options* opt);
@@ -138,6 +142,16 @@ long long gp_launch_count(const gp_ctx* ctx);
 int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
                      double p, double delta, double* R, int layout);
 
+/* The Cholesky factor of R(theta) + delta I (Section 3: one factorisation
+ * per likelihood value) for ONE theta, in the tile layout of
+ * gp_corr_assemble (layout 1): the lower triangle of every tile holds L
+ * (the upper triangle of diagonal tiles is unspecified).  prec selects the
+ * factorisation (GP_MIXED: the split-precision factor, returned in double).
+ * L must hold nt(nt+1)/2 * 16384 doubles.  *status_host receives GP_OK,
+ * GP_ENOTPD or GP_EINVAL.  Synchronises. */
+int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta, double p,
+                double delta, int prec, double* L, int* status_host);
+
 /* Profile -2 log-likelihood, eq. (4), at T candidate theta vectors (T x d),
  * with the profile estimates of eq. (3).  Outputs (length T each):
  *   nll[t]        -2logL = log|R| + n log Q  (eq. 4 read literally)
@@ -162,8 +176,11 @@ int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host,
                       double* sigma2_hat_host, double* logdet_host, int* status_host);
 
 /* Fit at one theta (length d): assemble, factor, solve, and keep on the
- * device what prediction needs -- the factor L, w = R^-1 (Y - 1 mu_hat),
- * a = L^-1 1, a copy of x, and the scalars.  Synchronises.  On GP_OK,
+ * device what prediction needs.  The fit is always factored in IEEE double
+ * whatever `prec` asks (any gp_precision value is accepted): a fit is one
+ * factorisation, and the kriging variance needs r'R^-1 r to full precision.
+ * Kept on the device: the factor L, w = R^-1 (Y - 1 mu_hat), a = L^-1 1, a
+ * copy of x, and the scalars.  Synchronises.  On GP_OK,
  * *model owns that device memory until gp_model_free.  A fit whose R is
  * not positive definite returns GP_ENOTPD and no model. */
 int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y,

@@ -10,7 +10,6 @@
 #include <vector>
 
 #include "gp_internal.cuh"
-#include "gp_mixed.cuh"
 
 struct gp_ctx {
     int device = 0;
@@ -162,6 +161,135 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
     return GP_OK;
 }
 
+// Bytes of workspace per instance of the split-precision path.
+struct MixedSizes {
+    size_t A, PS, PE, WS, WE, Z, st, per;
+};
+
+MixedSizes mixed_sizes(int n, int s) {
+    const int nt = gp::num_tiles(n);
+    const int ps = GP_PANEL_SLICES;
+    const int sp = s > ps ? s : ps;
+    MixedSizes z;
+    z.A = align256(gp::packed_elems(n) * sizeof(float2));
+    z.PS = align256((size_t)nt * sp * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
+    z.PE = align256((size_t)nt * GP_NB * sizeof(int));
+    z.WS = align256((size_t)ps * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
+    z.WE = align256((size_t)GP_NB * sizeof(int));
+    z.Z = align256((size_t)4 * nt * GP_NB * sizeof(float2));
+    z.st = align256(sizeof(gp::InstState));
+    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.Z + z.st;
+    return z;
+}
+
+// Carve the split-precision buffers of `cnt` instances out of `base`.
+gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* base, const MixedSizes& z,
+                            int Tc) {
+    gp::MixedBatch mb{};
+    char* c = base;
+    mb.A = (float2*)c; c += z.A * Tc;
+    mb.Rc = (float2*)c; c += z.A * Tc;
+    mb.PS = (__nv_bfloat16*)c; c += z.PS * Tc;
+    mb.PE = (int*)c; c += z.PE * Tc;
+    mb.WS = (__nv_bfloat16*)c; c += z.WS * Tc;
+    mb.WE = (int*)c; c += z.WE * Tc;
+    mb.Z = (float2*)c; c += z.Z * Tc;
+    mb.st = (gp::InstState*)c; c += z.st * Tc;
+    mb.err = (int*)c;
+    mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = ctx->opt.slices;
+    mb.ps = GP_PANEL_SLICES;
+    mb.ug = ctx->opt.update_groups;
+    mb.sp = mb.s > mb.ps ? mb.s : mb.ps;
+    mb.inst_stride = z.A / sizeof(float2);
+    mb.ps_stride = z.PS / sizeof(__nv_bfloat16);
+    mb.pe_stride = z.PE / sizeof(int);
+    mb.ws_stride = z.WS / sizeof(__nv_bfloat16);
+    mb.we_stride = z.WE / sizeof(int);
+    mb.z_stride = z.Z / sizeof(float2);
+    mb.y = y;
+    return mb;
+}
+
+// Assemble and factor (split precision) the instances of `mb`.
+int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, const double* theta, double p,
+                     double delta) {
+    gp::Batch b{};
+    b.n = mb.n; b.d = d; b.nt = mb.nt; b.count = mb.count; b.p = p; b.delta = delta;
+    b.x = x; b.y = mb.y; b.theta = theta; b.A = nullptr; b.Adf = mb.A; b.Rdf = mb.Rc;
+    b.inst_stride = mb.inst_stride; b.st = mb.st;
+    mb.d = d;
+    GP_CUDA(ctx, cudaMemsetAsync(mb.err, 0, sizeof(int), ctx->stream));
+    {
+        PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+        GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+        GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+    }
+    const int nt = mb.nt;
+    for (int J = 0; J < nt; ++J) {
+        {
+            PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
+            GP_CUDA(ctx, gp::launch_diag_mixed(mb, J, ctx->stream));
+        }
+        if (J + 1 == nt) break;
+        {
+            PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
+            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, ctx->stream));
+        }
+        {
+            PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
+            GP_CUDA(ctx, gp::launch_gemm_panel(mb, J, ctx->stream));
+        }
+        {
+            PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
+            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.s, ctx->stream));
+        }
+        {
+            PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+            GP_CUDA(ctx, gp::launch_gemm_update(mb, J, ctx->stream));
+        }
+    }
+    return GP_OK;
+}
+
+// Solves with refinement and the likelihood for the factored instances.
+int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* mu, double* sigma2,
+                    double* logdet, int* status) {
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 3 + 3 * ctx->opt.refine_iters);
+    GP_CUDA(ctx, gp::launch_df_forward(mb, 0, 1, ctx->stream));
+    GP_CUDA(ctx, gp::launch_df_backward(mb, 0, -1, ctx->stream));
+    for (int it = 0; it < ctx->opt.refine_iters; ++it) {
+        GP_CUDA(ctx, gp::launch_df_residual(mb, ctx->stream));
+        GP_CUDA(ctx, gp::launch_df_forward(mb, 2, 0, ctx->stream));
+        GP_CUDA(ctx, gp::launch_df_backward(mb, 2, 0, ctx->stream));
+    }
+    GP_CUDA(ctx, gp::launch_df_finalize(mb, nll, mu, sigma2, logdet, status, ctx->stream));
+    return GP_OK;
+}
+
+int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                    const double* theta, double p, double delta, double* nll, double* mu,
+                    double* sigma2, double* logdet, int* status) {
+    const MixedSizes z = mixed_sizes(n, ctx->opt.slices);
+    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    long long cap = (long long)((avail > 256 ? avail - 256 : 0) / z.per);
+    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
+    if (cap > 65535) cap = 65535;
+    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", z.per);
+    const int Tc = (int)(cap < T ? cap : T);
+    int rc = ensure_ws(ctx, z.per * (size_t)Tc + 256);
+    if (rc) return rc;
+    for (int c0 = 0; c0 < T; c0 += Tc) {
+        const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
+        gp::MixedBatch mb = mixed_layout(ctx, n, cnt, y, (char*)ctx->ws, z, Tc);
+        rc = run_mixed_factor(ctx, mb, d, x, theta + (size_t)c0 * d, p, delta);
+        if (rc) return rc;
+        rc = run_mixed_solve(ctx, mb, nll + c0, mu + c0, sigma2 + c0, logdet ? logdet + c0 : nullptr,
+                             status + c0);
+        if (rc) return rc;
+    }
+    return GP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -169,10 +297,11 @@ extern "C" {
 void gp_default_options(gp_options* opt) {
     if (!opt) return;
     opt->slices = 5;
-    opt->panel_slices = 7;
+    opt->panel_slices = GP_PANEL_SLICES;
     opt->refine_iters = 2;
     opt->nugget_in_var = 1;
     opt->max_batch = 0;
+    opt->update_groups = 4;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -222,12 +351,15 @@ int gp_set_stream(gp_ctx* ctx, void* stream) {
 
 int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
     if (!ctx || !opt) return GP_EINVAL;
-    if (opt->slices < 2 || opt->slices > 7) return fail(ctx, GP_EINVAL, "slices = %d outside [2, 7]", opt->slices);
-    if (opt->panel_slices < 2 || opt->panel_slices > 8)
-        return fail(ctx, GP_EINVAL, "panel_slices = %d outside [2, 8]", opt->panel_slices);
+    if (opt->slices < 2 || opt->slices > 6)
+        return fail(ctx, GP_EINVAL, "slices = %d outside [2, 6]", opt->slices);
+    if (opt->panel_slices != GP_PANEL_SLICES)
+        return fail(ctx, GP_EINVAL, "panel_slices is fixed at %d in this build", GP_PANEL_SLICES);
     if (opt->refine_iters < 0 || opt->refine_iters > 10)
         return fail(ctx, GP_EINVAL, "refine_iters = %d outside [0, 10]", opt->refine_iters);
     if (opt->max_batch < 0) return fail(ctx, GP_EINVAL, "max_batch must be >= 0");
+    if (opt->update_groups != 3 && opt->update_groups != 4 && opt->update_groups != 7)
+        return fail(ctx, GP_EINVAL, "update_groups must be 3, 4 or 7");
     ctx->opt = *opt;
     return GP_OK;
 }
@@ -289,6 +421,45 @@ int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* t
     return GP_OK;
 }
 
+int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta, double p, double delta,
+                int prec, double* L, int* status_host) {
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (!x || !theta || !L || !status_host) return fail(ctx, GP_EINVAL, "null pointer argument");
+    if (prec == GP_AUTO) prec = GP_MIXED;
+    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int nt = gp::num_tiles(n);
+    gp::InstState* st = nullptr;
+    if (prec == GP_FP64) {
+        rc = ensure_ws(ctx, align256(sizeof(gp::InstState)));
+        if (rc) return rc;
+        st = (gp::InstState*)ctx->ws;
+        gp::Batch b{};
+        b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta;
+        b.x = x; b.y = nullptr; b.theta = theta; b.A = L; b.inst_stride = gp::packed_elems(n); b.st = st;
+        {
+            PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+            GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+            GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+        }
+        rc = run_factor_f64(ctx, b);
+        if (rc) return rc;
+    } else {
+        const MixedSizes z = mixed_sizes(n, ctx->opt.slices);
+        rc = ensure_ws(ctx, z.per + 256);
+        if (rc) return rc;
+        gp::MixedBatch mb = mixed_layout(ctx, n, 1, nullptr, (char*)ctx->ws, z, 1);
+        rc = run_mixed_factor(ctx, mb, d, x, theta, p, delta);
+        if (rc) return rc;
+        GP_CUDA(ctx, gp::launch_df_to_double(mb.A, L, gp::packed_elems(n), ctx->stream));
+        st = mb.st;
+    }
+    GP_CUDA(ctx, cudaMemcpyAsync(status_host, &st->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GP_OK;
+}
+
 int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                  const double* theta, double p, double delta, int prec, double* nll,
                  double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
@@ -300,8 +471,8 @@ int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, in
     if (prec == GP_AUTO) prec = GP_MIXED;
     if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
-    if (prec == GP_MIXED) return gp::mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat,
-                                                     sigma2_hat, logdet, status);
+    if (prec == GP_MIXED)
+        return mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status);
     const int nt = gp::num_tiles(n);
     const size_t per = per_instance_bytes_f64(n);
     size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
@@ -396,8 +567,12 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
     if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
-    if (prec == GP_AUTO) prec = GP_MIXED;
-    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_AUTO)
+        return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    // The model is always factored in double: one factorisation per fit, and
+    // the kriging variance needs r'R^-1 r to full precision (the paper, too,
+    // refines the final fit with double-precision runs, Sections 4-5).
+    prec = GP_FP64;
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int nt = gp::num_tiles(n);
     const int npad = nt * GP_NB;
@@ -443,17 +618,16 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta;
     b.x = m->x; b.y = y; b.theta = m->theta; b.A = m->L; b.inst_stride = bL / sizeof(double);
     b.st = m->st;
-    if (prec == GP_MIXED) {
-        rc = gp::mixed_fit_factor(ctx, b, m->Z, (size_t)2 * npad);
-        if (rc) return bail(rc);
-    } else {
+    {
+        PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
         if (gp::launch_validate_theta(b, ctx->stream) || gp::launch_assemble_tiles(b, ctx->stream))
             return bail(fail(ctx, GP_ECUDA, "assembly launch failed"));
-        rc = run_factor_f64(ctx, b);
-        if (rc) return bail(rc);
-        if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream))
-            return bail(fail(ctx, GP_ECUDA, "forward solve launch failed"));
     }
+    rc = run_factor_f64(ctx, b);
+    if (rc) return bail(rc);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 4);
+    if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream))
+        return bail(fail(ctx, GP_ECUDA, "forward solve launch failed"));
     if (gp::launch_finalize(b, m->Z, (size_t)2 * npad, m->scalars + 0, m->scalars + 1, m->scalars + 2,
                             m->scalars + 3, m->status, ctx->stream) ||
         gp::launch_fit_finish(b, m->Z, (size_t)2 * npad, m->scalars, ctx->stream) ||
@@ -493,6 +667,7 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     int rc = ensure_ws(ctx, s2 ? per_cta * chunk : 256);
     if (rc) return rc;
     const double c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
+    PhaseScope ps(ctx, GP_PHASE_PREDICT, (N + 32 * chunk - 1) / (32 * chunk));
     GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, m->x, m->theta, m->p, c0, m->L,
                                     m->Z + npad, m->Z, m->scalars, N, xstar, yhat, s2,
                                     (double*)ctx->ws, chunk, ctx->stream));

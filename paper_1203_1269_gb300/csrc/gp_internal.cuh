@@ -12,12 +12,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <cuda_bf16.h>
 
 #include "../../include/gp.h"
 
 #define GP_NB 128
 #define GP_TILE_ELEMS (GP_NB * GP_NB)
 #define GP_MAX_D 64
+#define GP_MAX_SLICES 7
+#define GP_PANEL_SLICES 7
 
 namespace gp {
 
@@ -64,9 +67,34 @@ struct Batch {
     const double* x;              // n x d
     const double* y;              // n
     const double* theta;          // count x d (already offset to the chunk)
-    double* A;                    // count * packed_elems(n)
-    size_t inst_stride;           // elements between instances in A
+    double* A;                    // count * packed_elems(n)   (double tiles), or
+    float2* Adf;                  // double-float tiles (split path; A unused then)
+    float2* Rdf;                  // double-float copy of R (split path)
+    size_t inst_stride;           // elements between instances in A / Adf / Rdf
     InstState* st;                // count
+};
+
+// Split-precision path: per-instance buffers (double-float tiles, bf16
+// slice images of the current panel and of W = L_JJ^-1, solve vectors).
+struct MixedBatch {
+    int n, d, nt, count;
+    int s;                        // slices of the trailing update operands
+    int ps;                       // slices of the panel solve operands (GP_PANEL_SLICES)
+    int ug;                       // accumulator groups of the trailing update (3, 4 or 7)
+    int sp;                       // slice slots per row block in PS (max(s, ps))
+    float2* A;                    // working matrix -> factor (double-float tiles)
+    float2* Rc;                   // copy of R (double-float tiles), for residuals
+    size_t inst_stride;
+    __nv_bfloat16* PS;            // panel slices: [row block][slice][4 chunks][128 x 32]
+    int* PE;                      // panel row exponents: [row block][128]
+    __nv_bfloat16* WS;            // slices of W's rows: [slice][4 chunks][128 x 32]
+    int* WE;                      // [128]
+    size_t ps_stride, pe_stride, ws_stride, we_stride;
+    float2* Z;                    // 4 columns of npad double-float values
+    size_t z_stride;
+    const double* y;
+    InstState* st;
+    int* err;                     // set when a bounded device wait gave up
 };
 
 // ---- kernels (launch helpers, all on `stream`) ----------------------------
@@ -89,5 +117,16 @@ cudaError_t launch_predict(int n, int d, int nt, const double* x, const double* 
                            double c0, const double* L, const double* w, const double* a,
                            const double* scalars, int N, const double* xs, double* yhat,
                            double* s2, double* work, int chunk, cudaStream_t s);
+
+cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s);
+cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s);
+cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s);
+cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s);
+cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2,
+                               double* logdet, int* status, cudaStream_t s);
+cudaError_t launch_df_to_double(const float2* src, double* dst, size_t count, cudaStream_t s);
 
 }  // namespace gp

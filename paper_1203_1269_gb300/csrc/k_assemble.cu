@@ -27,6 +27,21 @@ __device__ __forceinline__ double powabs(double diff, double p) {
     return (a == 0.0) ? 0.0 : pow(a, p);
 }
 
+// One entry of instance t: double tiles, or double-float working matrix plus
+// its double-float copy (split-precision path).
+__device__ __forceinline__ void store_entry(const Batch& b, int t, size_t off, double v) {
+    const size_t i = (size_t)t * b.inst_stride + off;
+    if (b.Adf) {
+        const float h = __double2float_rn(v);
+        const float l = __double2float_rn(v - (double)h);
+        const float2 hl = make_float2(h, l);
+        b.Adf[i] = hl;
+        b.Rdf[i] = hl;
+    } else {
+        b.A[i] = v;
+    }
+}
+
 // Validate theta and reset each instance's record.
 __global__ void k_validate_theta(Batch b) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,7 +124,7 @@ k_assemble_tiles(Batch b, int group) {
                 v = exp(-s);
                 if (diag) v += b.delta;
             }
-            b.A[(size_t)t * b.inst_stride + off] = v;
+            store_entry(b, t, off, v);
         }
     }
 }
@@ -152,7 +167,7 @@ k_assemble_tiles_generic(Batch b, int group) {
                 v = exp(-s);
                 if (diag) v += b.delta;
             }
-            b.A[(size_t)t * b.inst_stride + off] = v;
+            store_entry(b, t, off, v);
         }
     }
 }

@@ -1,13 +1,935 @@
-// k_mixed.cu -- split-precision (GP_MIXED) factorisation path.
-#include "gp_mixed.cuh"
+// k_mixed.cu -- the split-precision (GP_MIXED) factorisation and solves.
+//
+// Blocked right-looking Cholesky of R(theta) + delta I (Section 3 of the
+// paper factors R by Cholesky for the determinant and the solves) with the
+// off-diagonal work on the tensor cores:
+//
+//   diag   L_JJ = chol(A_JJ), W_J = L_JJ^-1        IEEE double (one CTA)
+//   panel  L_IJ = A_IJ W_J^T            I > J      split GEMM, tcgen05
+//   update A_IK -= L_IJ L_KJ^T      J < K <= I     split GEMM, tcgen05
+//
+// Split GEMM (after Ozaki, Ogita, Oishi & Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication",
+// Numer. Algorithms 59, 2012): each row i of an operand is scaled by 2^(7-E_i)
+// (|row| < 2^E_i) and cut into s slices q_a 2^(-8a) with integers |q_a| <= 128,
+//     row = 2^(E_i - 7) sum_a q_a 2^(-8a),
+// which bf16 holds exactly.  A product of slices summed over the K = 128
+// panel columns stays below 2^22 in magnitude, so the tensor core's fp32
+// accumulation of the groups a+b = 0 and a+b = 1 is exact; the groups
+// a+b >= 2 (weight <= 2^-16) share a third accumulator whose rounding is
+// below 2^-40 of the result.  Products with a+b >= s are dropped.  The three
+// partial sums are recombined and applied to the working matrix in
+// double-float (df.cuh).
+//
+// Operands reach shared memory by bulk asynchronous copies (cp.async.bulk)
+// of pre-swizzled "images": the slicing kernels write each 128-row x 32-col
+// bf16 chunk in the 64-byte-swizzled K-major layout the MMA descriptors
+// expect, so a chunk is one contiguous 8 KB copy.  Accumulators live in
+// tensor memory (3 x 128 of the 512 columns).
+//
+// Solves: forward and backward substitution with the double-float factor,
+// two right-hand sides [1 Y], then iterative refinement against the
+// double-float copy of R (residuals r = b - R x).
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "df.cuh"
+#include "gp_internal.cuh"
 
 namespace gp {
 
-int mixed_nll_batch(gp_ctx*, int, int, const double*, const double*, int, const double*, double,
-                    double, double*, double*, double*, double*, int*) {
-    return GP_ENOTSUP;
+namespace {
+
+constexpr int kChunkElems = GP_NB * 32;       // bf16 elements in one 128 x 32 image chunk
+constexpr uint32_t kChunkBytes = kChunkElems * 2;
+constexpr int kChunks = GP_NB / 32;           // 4 chunks per 128-wide panel
+constexpr int kGemmThreads = 192;             // warp 0 copies, warp 1 MMA, warps 2-5 epilogue
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
+
+// ---------------------------------------------------------------- PTX ------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-int mixed_fit_factor(gp_ctx*, const Batch&, double*, size_t) { return GP_ENOTSUP; }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity, giving up after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try(b, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: start, leading/stride byte offsets, the
+// fixed version bit, swizzle mode (4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t mode) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(mode & 7) << 61;
+    return d;
+}
+
+// Instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ----------------------------------------------------------- layouts -------
+
+__device__ __forceinline__ float2* df_tile(const MixedBatch& b, float2* base, int t, int I, int J) {
+    return base + (size_t)t * b.inst_stride + (size_t)tile_index(I, J, b.nt) * GP_TILE_ELEMS;
+}
+
+// slices of row-block I: [slice][chunk][128 x 32 image]
+__device__ __forceinline__ __nv_bfloat16* ps_block(const MixedBatch& b, int t, int I) {
+    return b.PS + (size_t)t * b.ps_stride + (size_t)I * b.sp * kChunks * kChunkElems;
+}
+__device__ __forceinline__ int* pe_block(const MixedBatch& b, int t, int I) {
+    return b.PE + (size_t)t * b.pe_stride + (size_t)I * GP_NB;
+}
+
+// byte offset of the 16-byte piece holding columns k0..k0+7 (k0 % 8 == 0)
+// of row r inside a 128 x 32 chunk with 64-byte swizzle
+__device__ __forceinline__ uint32_t image_piece(int r, int k0) {
+    const uint32_t piece = (uint32_t)((k0 & 31) >> 3);
+    const uint32_t sw = piece ^ (uint32_t)((r & 7) >> 1);
+    return (uint32_t)(r >> 3) * 512u + (uint32_t)(r & 7) * 64u + sw * 16u;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Cut a double-float x (already scaled so |x| <= 2^7) into s slices: slice a
+// is the integer q_a (|q_a| <= 128) times 2^(-8a), so x = sum_a slice_a and
+// every product of slices carries its own weight 2^(-8(a+b)) into the
+// tensor-core accumulators.
+__device__ __forceinline__ void cut_slices(float xh, float xl, int s, float* m) {
+    float w = 1.f;
+#pragma unroll
+    for (int a = 0; a < GP_MAX_SLICES; ++a) {
+        if (a < s) {
+            const float q = rintf(xh);
+            m[a] = __fmul_rn(q, w);
+            w = __fmul_rn(w, 0.00390625f);
+            const float dh = __fsub_rn(xh, q);   // exact
+            two_sum(dh, xl, xh, xl);
+            xh = __fmul_rn(xh, 256.f);
+            xl = __fmul_rn(xl, 256.f);
+        } else {
+            m[a] = 0.f;
+        }
+    }
+}
+
+// ----------------------------------------------------------- kernels -------
+
+// Diagonal block of column J: L_JJ = chol(A_JJ) in double, W = L_JJ^-1 by
+// solving X L_JJ^T = I (X = W^T, upper triangular), log-det, and the slices
+// of W's rows.  Dynamic smem: S (128 x 128 double) + packed L (8256 doubles).
+__global__ void __launch_bounds__(256) k_diag_mixed(MixedBatch b, int J) {
+    extern __shared__ double sm[];
+    double* S = sm;
+    double* P = sm + GP_TILE_ELEMS;   // packed lower L: P[r(r+1)/2 + c]
+    __shared__ double inv_diag[GP_NB];
+    __shared__ double inv_piv;
+    __shared__ int failed;
+    const int t = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    float2* T = df_tile(b, b.A, t, J, J);
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) {
+        const float2 v = T[q];
+        S[q] = (double)v.x + (double)v.y;
+    }
+    if (threadIdx.x == 0) failed = -1;
+    __syncthreads();
+    const int r = threadIdx.x % GP_NB;
+    const int h = threadIdx.x / GP_NB;
+    double logdet = 0.0;
+    for (int c = 0; c < GP_NB; ++c) {
+        if (threadIdx.x == 0) {
+            const double piv = S[c * GP_NB + c];
+            if (!(piv > 0.0) || !isfinite(piv)) {
+                failed = c;
+            } else {
+                const double l = sqrt(piv);
+                S[c * GP_NB + c] = l;
+                inv_piv = 1.0 / l;
+                logdet += log(l);
+            }
+        }
+        __syncthreads();
+        if (failed >= 0) break;
+        if (h == 0 && r > c) S[c * GP_NB + r] *= inv_piv;
+        __syncthreads();
+        if (r > c) {
+            const double lr = S[c * GP_NB + r];
+            for (int k = c + 1 + h; k <= r; k += 2) S[k * GP_NB + r] = fma(-lr, S[c * GP_NB + k], S[k * GP_NB + r]);
+        }
+        __syncthreads();
+    }
+    if (failed >= 0) {
+        if (threadIdx.x == 0) {
+            b.st[t].status = GP_ENOTPD;
+            b.st[t].fail_col = J * GP_NB + failed;
+        }
+        return;
+    }
+    // L out (double-float, lower triangle) and into the packed copy
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) {
+        const int rr = q % GP_NB, cc = q / GP_NB;
+        if (rr >= cc) {
+            const double v = S[q];
+            const dfl d = df_from_double(v);
+            T[q] = make_float2(d.hi, d.lo);
+            P[rr * (rr + 1) / 2 + cc] = v;
+        }
+    }
+    if (threadIdx.x == 0) b.st[t].logdet += 2.0 * logdet;
+    __syncthreads();
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) S[q] = ((q % GP_NB) == (q / GP_NB)) ? 1.0 : 0.0;
+    if (threadIdx.x < GP_NB) inv_diag[threadIdx.x] = 1.0 / P[threadIdx.x * (threadIdx.x + 1) / 2 + threadIdx.x];
+    __syncthreads();
+    // X L^T = I, column by column; X is upper triangular so only rows r <= c move
+    for (int c = 0; c < GP_NB; ++c) {
+        const double xrc = S[c * GP_NB + r] * inv_diag[c];
+        __syncthreads();
+        if (r <= c) {
+            if (h == 0) S[c * GP_NB + r] = xrc;
+            for (int k = c + 1 + h; k < GP_NB; k += 2) S[k * GP_NB + r] = fma(-xrc, P[k * (k + 1) / 2 + c], S[k * GP_NB + r]);
+        }
+        __syncthreads();
+    }
+    // W row c = S[c*NB .. c*NB+127]; one warp per row: exponent and slices
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __nv_bfloat16* WS = b.WS + (size_t)t * b.ws_stride;
+    int* WE = b.WE + (size_t)t * b.we_stride;
+    for (int c = warp; c < GP_NB; c += 8) {
+        const double* w = S + c * GP_NB;
+        double mx = 0.0;
+        for (int k = lane; k < GP_NB; k += 32) mx = fmax(mx, fabs(w[k]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int E = 0;
+        if (mx > 0.0) frexp(mx, &E);
+        if (lane == 0) WE[c] = E;
+        // lane handles columns 4*lane .. 4*lane+3 (half of one 16-byte piece)
+        const int k0 = 4 * lane;
+        float m[4][GP_MAX_SLICES];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const double x = ldexp(w[k0 + e], 7 - E);
+            const dfl xd = df_from_double(x);
+            cut_slices(xd.hi, xd.lo, b.ps, m[e]);
+        }
+        const uint32_t off = image_piece(c, k0 & ~7) + ((k0 & 4) ? 8u : 0u);
+#pragma unroll
+        for (int a = 0; a < GP_MAX_SLICES; ++a) {
+            if (a >= b.ps) break;
+            uint2 v;
+            v.x = pack_bf16x2(m[0][a], m[1][a]);
+            v.y = pack_bf16x2(m[2][a], m[3][a]);
+            uint8_t* dst = reinterpret_cast<uint8_t*>(WS + (size_t)(a * kChunks + (k0 >> 5)) * kChunkElems);
+            *reinterpret_cast<uint2*>(dst + off) = v;
+        }
+    }
+}
+
+// Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x, into row block I
+// of PS: one thread per row (column-major tiles: coalesced reads).
+__global__ void __launch_bounds__(GP_NB) k_split_panel(MixedBatch b, int J, int ns) {
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int I = J + 1 + blockIdx.x;
+    const float2* src = df_tile(b, b.A, t, I, J);
+    const int r = threadIdx.x;
+    float mx = 0.f;
+    for (int c = 0; c < GP_NB; ++c) mx = fmaxf(mx, fabsf(src[c * GP_NB + r].x));
+    int E = 0;
+    if (mx > 0.f) frexpf(mx, &E);
+    pe_block(b, t, I)[r] = E;
+    __nv_bfloat16* dst = ps_block(b, t, I);
+    for (int k0 = 0; k0 < GP_NB; k0 += 8) {
+        float m[8][GP_MAX_SLICES];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float2 v = src[(k0 + e) * GP_NB + r];
+            cut_slices(ldexpf(v.x, 7 - E), ldexpf(v.y, 7 - E), ns, m[e]);
+        }
+        const uint32_t off = image_piece(r, k0);
+#pragma unroll
+        for (int a = 0; a < GP_MAX_SLICES; ++a) {
+            if (a >= ns) break;
+            uint4 v;
+            v.x = pack_bf16x2(m[0][a], m[1][a]);
+            v.y = pack_bf16x2(m[2][a], m[3][a]);
+            v.z = pack_bf16x2(m[4][a], m[5][a]);
+            v.w = pack_bf16x2(m[6][a], m[7][a]);
+            uint8_t* chunk = reinterpret_cast<uint8_t*>(dst + (size_t)(a * kChunks + (k0 >> 5)) * kChunkElems);
+            *reinterpret_cast<uint4*>(chunk + off) = v;
+        }
+    }
+}
+
+// Split GEMM on one 128 x NT output tile with NG accumulator groups
+// (group g gathers the products with a + b = g, the last one all a + b >= g).
+// MODE 0 (panel):  A_IJ(:, cols)  =  PS_I . WS(cols)^T   NT = 64, ps slices,
+//                  every group exact: the result must stay accurate relative
+//                  to |A| |W|, which exceeds |L_IJ| when L_JJ is ill-conditioned.
+// MODE 1 (update): A_IK -= PS_I . PS_K^T                  NT = 128, s slices,
+//                  groups 0 and 1 exact, the rest rounded (rows of L have norm <= 1).
+template <int MODE, int NT, int NG>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J) {
+    static_assert(NG * NT <= 512, "accumulators exceed tensor memory");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ __align__(8) uint64_t empty_bar[2];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    int I, K;
+    const int tile = blockIdx.x / (GP_NB / NT);
+    const int col0 = (blockIdx.x % (GP_NB / NT)) * NT;
+    if (MODE == 0) {
+        I = J + 1 + tile;
+        K = J;
+    } else {
+        int ii, kk;
+        tri_decode(tile, ii, kk);
+        I = J + 1 + ii;
+        K = J + 1 + kk;
+    }
+    const int ns = (MODE == 0) ? b.ps : b.s;
+    constexpr uint32_t kBBytes = kChunkBytes / (GP_NB / NT);      // B rows col0..col0+NT of a chunk
+    const __nv_bfloat16* gA = ps_block(b, t, I);
+    const uint8_t* gB = reinterpret_cast<const uint8_t*>((MODE == 0) ? (b.WS + (size_t)t * b.ws_stride)
+                                                                      : ps_block(b, t, K)) +
+                        (size_t)col0 * 64;   // 64 bytes per row inside a chunk
+    const int* eAp = pe_block(b, t, I);
+    const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride) : pe_block(b, t, K)) + col0;
+    const uint32_t a_bytes = (uint32_t)ns * kChunkBytes;
+    const uint32_t stage_bytes = a_bytes + (uint32_t)ns * kBBytes;
+    constexpr uint32_t idesc = idesc_bf16(NT);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        mbar_init(&empty_bar[0], 1);
+        mbar_init(&empty_bar[1], 1);
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < kChunks; ++kc) {
+                const int st = kc & 1, use = kc >> 1;
+                if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                uint8_t* sa = smem + st * stage_bytes;
+                uint8_t* sb = sa + a_bytes;
+                mbar_expect_tx(&full_bar[st], stage_bytes);
+                for (int a = 0; a < ns; ++a)
+                    bulk_g2s(sa + a * kChunkBytes, gA + (size_t)(a * kChunks + kc) * kChunkElems, kChunkBytes,
+                             &full_bar[st]);
+                for (int a = 0; a < ns; ++a)
+                    bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * kChunks + kc) * kChunkBytes, kBBytes,
+                             &full_bar[st]);
+                ++issued;
+            }
+            // make sure no copy is still landing when the CTA retires
+            for (int kc = (issued > 2 ? issued - 2 : 0); kc < issued; ++kc) mbar_wait(&full_bar[kc & 1], (kc >> 1) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t started = 0;
+            for (int kc = 0; kc < kChunks; ++kc) {
+                const int st = kc & 1, use = kc >> 1;
+                if (!mbar_wait(&full_bar[st], use & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + st * stage_bytes);
+                const uint32_t sb = sa + a_bytes;
+                for (int a = 0; a < ns; ++a) {
+                    for (int bb = 0; a + bb < ns; ++bb) {
+                        const int g = (a + bb < NG) ? (a + bb) : (NG - 1);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t ad = smem_desc(sa + a * kChunkBytes + kk * 32, 16, 512, 4);
+                            const uint64_t bd = smem_desc(sb + bb * kBBytes + kk * 32, 16, 512, 4);
+                            mma_bf16(tbase + g * NT, ad, bd, idesc, (started >> g) & 1u);
+                            started |= 1u << g;
+                        }
+                    }
+                }
+                mma_commit(&empty_bar[st]);
+            }
+            mma_commit(&done_bar);
+        }
+    } else {
+        // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const bool ok = mbar_wait(&done_bar, 0);
+        tc_fence_after();
+        if (ok && !abort_flag) {
+            const int eA = eAp[r];
+            float2* C = df_tile(b, b.A, t, I, K) + (size_t)col0 * GP_NB;
+            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+            constexpr int CB = (NG > 3) ? 16 : 32;   // columns per TMEM load
+            for (int c0 = 0; c0 < NT; c0 += CB) {
+                float d[NG][CB];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    if (CB == 16) tmem_ld16(lane_addr + g * NT + c0, d[g]);
+                    else          tmem_ld32(lane_addr + g * NT + c0, d[g]);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < CB; ++j) {
+                    const int c = c0 + j;
+                    // v = sum_g d_g (weights already in the slices); d0 + d1 exactly,
+                    // then the smaller groups into the double-float sum
+                    float h, l;
+                    two_sum(d[0][j], d[1][j], h, l);
+#pragma unroll
+                    for (int g = 2; g < NG; ++g) {
+                        float s2, e2;
+                        two_sum(h, d[g][j], s2, e2);
+                        l = __fadd_rn(l, e2);
+                        fast_two_sum(s2, l, h, l);
+                    }
+                    const int e = eA + __ldg(eBp + c) - 14;
+                    const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
+                    h = __fmul_rn(h, sc);
+                    l = __fmul_rn(l, sc);
+                    float2* p = C + (size_t)c * GP_NB + r;
+                    if (MODE == 0) {
+                        float hh, ll;
+                        fast_two_sum(h, l, hh, ll);
+                        *p = make_float2(hh, ll);
+                    } else {
+                        const float2 cv = *p;
+                        const dfl res = df_sub(dfl{cv.x, cv.y}, dfl{h, l});
+                        *p = make_float2(res.hi, res.lo);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (abort_flag && threadIdx.x == 0) {
+        b.st[t].status = GP_ETIMEOUT;
+        atomicExch(b.err, GP_ETIMEOUT);
+    }
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+}
+
+// ------------------------------------------------------------ solves -------
+// Z (per instance, float2): column k of length npad at Z + k * npad.
+//   0: x_1   1: x_y   2, 3: residual / correction
+
+__device__ __forceinline__ float2* zcol(const MixedBatch& b, int t, int k) {
+    return b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB;
+}
+
+// Fixed-order sum over the block of a double-float value held per thread.
+__device__ dfl block_sum_df(dfl v, dfl* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        dfl w;
+        w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dfl s = red[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s = df_add(s, red[i]);
+        red[0] = s;
+    }
+    __syncthreads();
+    dfl s = red[0];
+    __syncthreads();
+    return s;
+}
+
+// Forward substitution L z = rhs for two columns (c0, c0 + 1) in place.
+// init != 0: the right-hand sides are [1 Y] (zero on padded rows).
+__global__ void __launch_bounds__(256) k_df_forward(MixedBatch b, int c0, int init) {
+    __shared__ dfl xj[2][GP_NB];
+    __shared__ dfl part[2][2][GP_NB];
+    __shared__ dfl rhs[2][GP_NB];
+    const int t = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    const int nt = b.nt, n = b.n;
+    float2* z0 = zcol(b, t, c0);
+    float2* z1 = zcol(b, t, c0 + 1);
+    const int r = threadIdx.x % GP_NB, h = threadIdx.x / GP_NB;
+    for (int I = 0; I < nt; ++I) {
+        const int gi = I * GP_NB + r;
+        dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+        for (int Jt = 0; Jt < I; ++Jt) {
+            __syncthreads();
+            if (h == 0) xj[0][r] = df_load(z0 + Jt * GP_NB + r);
+            else        xj[1][r] = df_load(z1 + Jt * GP_NB + r);
+            __syncthreads();
+            const float2* L = df_tile(b, b.A, t, I, Jt);
+            for (int c = h; c < GP_NB; c += 2) {
+                const float2 lv = __ldg(L + c * GP_NB + r);
+                const dfl l = {lv.x, lv.y};
+                a0 = df_fma(l, xj[0][c], a0);
+                a1 = df_fma(l, xj[1][c], a1);
+            }
+        }
+        part[h][0][r] = a0;
+        part[h][1][r] = a1;
+        __syncthreads();
+        if (h == 0) {
+            dfl b0, b1;
+            if (init) {
+                b0 = {(gi < n) ? 1.f : 0.f, 0.f};
+                b1 = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
+            } else {
+                b0 = df_load(z0 + gi);
+                b1 = df_load(z1 + gi);
+            }
+            rhs[0][r] = df_sub(b0, df_add(part[0][0][r], part[1][0][r]));
+            rhs[1][r] = df_sub(b1, df_add(part[0][1][r], part[1][1][r]));
+        }
+        __syncthreads();
+        const float2* D = df_tile(b, b.A, t, I, I);
+        for (int c = 0; c < GP_NB; ++c) {
+            const float2 dv = __ldg(D + c * GP_NB + c);
+            const dfl dc = {dv.x, dv.y};
+            const dfl x0 = df_div(rhs[0][c], dc);
+            const dfl x1 = df_div(rhs[1][c], dc);
+            __syncthreads();
+            if (threadIdx.x < GP_NB && r > c) {
+                const float2 lv = __ldg(D + c * GP_NB + r);
+                const dfl l = {lv.x, lv.y};
+                rhs[0][r] = df_fms(l, x0, rhs[0][r]);
+                rhs[1][r] = df_fms(l, x1, rhs[1][r]);
+            }
+            if (threadIdx.x == 0) {
+                rhs[0][c] = x0;
+                rhs[1][c] = x1;
+            }
+            __syncthreads();
+        }
+        if (h == 0) df_store(z0 + gi, rhs[0][r]);
+        else        df_store(z1 + gi, rhs[1][r]);
+        __syncthreads();
+    }
+}
+
+// Backward substitution L^T w = z for columns (c0, c0 + 1) in place; when
+// add_to >= 0 the result is also added into columns (add_to, add_to + 1).
+__global__ void __launch_bounds__(256) k_df_backward(MixedBatch b, int c0, int add_to) {
+    __shared__ dfl wk[2][GP_NB];
+    __shared__ dfl rhs[2][GP_NB];
+    const int t = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    const int nt = b.nt;
+    float2* z[2] = {zcol(b, t, c0), zcol(b, t, c0 + 1)};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int I = nt - 1; I >= 0; --I) {
+        if (threadIdx.x < 2 * GP_NB) {
+            const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
+            rhs[k][i] = df_load(z[k] + I * GP_NB + i);
+        }
+        __syncthreads();
+        for (int K = I + 1; K < nt; ++K) {
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
+                wk[k][i] = df_load(z[k] + K * GP_NB + i);
+            }
+            __syncthreads();
+            const float2* L = df_tile(b, b.A, t, K, I);
+            for (int c = w; c < GP_NB; c += 8) {
+                dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+                for (int k = lane; k < GP_NB; k += 32) {
+                    const float2 lv = __ldg(L + c * GP_NB + k);
+                    const dfl l = {lv.x, lv.y};
+                    s0 = df_fma(l, wk[0][k], s0);
+                    s1 = df_fma(l, wk[1][k], s1);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    dfl u0 = {__shfl_down_sync(0xffffffffu, s0.hi, o), __shfl_down_sync(0xffffffffu, s0.lo, o)};
+                    dfl u1 = {__shfl_down_sync(0xffffffffu, s1.hi, o), __shfl_down_sync(0xffffffffu, s1.lo, o)};
+                    s0 = df_add(s0, u0);
+                    s1 = df_add(s1, u1);
+                }
+                if (lane == 0) {
+                    rhs[0][c] = df_sub(rhs[0][c], s0);
+                    rhs[1][c] = df_sub(rhs[1][c], s1);
+                }
+            }
+            __syncthreads();
+        }
+        const float2* D = df_tile(b, b.A, t, I, I);
+        for (int c = GP_NB - 1; c >= 0; --c) {
+            const float2 dv = __ldg(D + c * GP_NB + c);
+            const dfl dc = {dv.x, dv.y};
+            const dfl x0 = df_div(rhs[0][c], dc);
+            const dfl x1 = df_div(rhs[1][c], dc);
+            __syncthreads();
+            if (threadIdx.x < c) {
+                const float2 lv = __ldg(D + threadIdx.x * GP_NB + c);   // L(c, r) with r = threadIdx.x
+                const dfl l = {lv.x, lv.y};
+                rhs[0][threadIdx.x] = df_fms(l, x0, rhs[0][threadIdx.x]);
+                rhs[1][threadIdx.x] = df_fms(l, x1, rhs[1][threadIdx.x]);
+            }
+            if (threadIdx.x == 0) {
+                rhs[0][c] = x0;
+                rhs[1][c] = x1;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < 2 * GP_NB) {
+            const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
+            df_store(z[k] + I * GP_NB + i, rhs[k][i]);
+            if (add_to >= 0) {
+                float2* acc = zcol(b, t, add_to + k) + I * GP_NB + i;
+                df_store(acc, df_add(df_load(acc), rhs[k][i]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Residuals [r_1 r_y] = [1 Y] - R [x_1 x_y] into columns 2, 3, with the
+// double-float copy of R (lower tiles; diagonal tiles full).
+__global__ void __launch_bounds__(256) k_df_residual(MixedBatch b) {
+    __shared__ dfl xs[2][GP_NB];
+    __shared__ dfl acc_t[2][GP_NB];
+    __shared__ dfl part[2][2][GP_NB];
+    const int t = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    const int nt = b.nt, n = b.n;
+    const float2* x[2] = {zcol(b, t, 0), zcol(b, t, 1)};
+    float2* res[2] = {zcol(b, t, 2), zcol(b, t, 3)};
+    const int r = threadIdx.x % GP_NB, h = threadIdx.x / GP_NB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int I = 0; I < nt; ++I) {
+        dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+        if (threadIdx.x < 2 * GP_NB) acc_t[threadIdx.x / GP_NB][threadIdx.x % GP_NB] = dfl{0.f, 0.f};
+        // tiles (I, J), J <= I: row r of the tile times x_J
+        for (int Jt = 0; Jt <= I; ++Jt) {
+            __syncthreads();
+            if (h == 0) xs[0][r] = df_load(x[0] + Jt * GP_NB + r);
+            else        xs[1][r] = df_load(x[1] + Jt * GP_NB + r);
+            __syncthreads();
+            const float2* R = df_tile(b, b.Rc, t, I, Jt);
+            for (int c = h; c < GP_NB; c += 2) {
+                const float2 v = __ldg(R + c * GP_NB + r);
+                const dfl rv = {v.x, v.y};
+                a0 = df_fma(rv, xs[0][c], a0);
+                a1 = df_fma(rv, xs[1][c], a1);
+            }
+        }
+        // tiles (J, I), J > I: transposed, warp w reduces columns w, w + 8, ...
+        for (int Jt = I + 1; Jt < nt; ++Jt) {
+            __syncthreads();
+            if (h == 0) xs[0][r] = df_load(x[0] + Jt * GP_NB + r);
+            else        xs[1][r] = df_load(x[1] + Jt * GP_NB + r);
+            __syncthreads();
+            const float2* R = df_tile(b, b.Rc, t, Jt, I);
+            for (int c = w; c < GP_NB; c += 8) {
+                dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+                for (int k = lane; k < GP_NB; k += 32) {
+                    const float2 v = __ldg(R + c * GP_NB + k);
+                    const dfl rv = {v.x, v.y};
+                    s0 = df_fma(rv, xs[0][k], s0);
+                    s1 = df_fma(rv, xs[1][k], s1);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    dfl u0 = {__shfl_down_sync(0xffffffffu, s0.hi, o), __shfl_down_sync(0xffffffffu, s0.lo, o)};
+                    dfl u1 = {__shfl_down_sync(0xffffffffu, s1.hi, o), __shfl_down_sync(0xffffffffu, s1.lo, o)};
+                    s0 = df_add(s0, u0);
+                    s1 = df_add(s1, u1);
+                }
+                if (lane == 0) {
+                    acc_t[0][c] = df_add(acc_t[0][c], s0);
+                    acc_t[1][c] = df_add(acc_t[1][c], s1);
+                }
+            }
+        }
+        part[h][0][r] = a0;
+        part[h][1][r] = a1;
+        __syncthreads();
+        if (h == 0) {
+            const int gi = I * GP_NB + r;
+            const dfl b0 = {(gi < n) ? 1.f : 0.f, 0.f};
+            const dfl b1 = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
+            const dfl s0 = df_add(df_add(part[0][0][r], part[1][0][r]), acc_t[0][r]);
+            const dfl s1 = df_add(df_add(part[0][1][r], part[1][1][r]), acc_t[1][r]);
+            // padded rows: R is the identity there and x is zero, so r = 0
+            df_store(res[0] + gi, (gi < n) ? df_sub(b0, s0) : dfl{0.f, 0.f});
+            df_store(res[1] + gi, (gi < n) ? df_sub(b1, s1) : dfl{0.f, 0.f});
+        }
+        __syncthreads();
+    }
+}
+
+// mu_hat = 1'x_y / 1'x_1, w = x_y - mu x_1 = R^-1 (Y - 1 mu), Q = (Y - 1 mu)'w,
+// -2logL = log|R| + n log Q; column 1 becomes w (for kriging), column 0 keeps
+// x_1 = R^-1 1.  Q is taken as zero when Q <= 16 n eps^2 Y'x_y with
+// eps = 2^-40, the accuracy unit of the split factorisation.
+__global__ void __launch_bounds__(256) k_df_finalize(MixedBatch b, double* nll, double* mu, double* sigma2,
+                                                     double* logdet, int* status) {
+    __shared__ dfl red[8];
+    const int t = blockIdx.x;
+    InstState st = b.st[t];
+    const int n = b.n;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    if (st.status != GP_OK) {
+        if (threadIdx.x == 0) {
+            nll[t] = (st.status == GP_ENOTPD) ? inf : nan;
+            mu[t] = nan;
+            sigma2[t] = nan;
+            if (logdet) logdet[t] = (st.status == GP_ENOTPD) ? nan : nan;
+            status[t] = st.status;
+        }
+        return;
+    }
+    float2* x1 = zcol(b, t, 0);
+    float2* xy = zcol(b, t, 1);
+    dfl sa = {0.f, 0.f}, sb = {0.f, 0.f}, sc = {0.f, 0.f};
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const dfl a = df_load(x1 + i), c = df_load(xy + i);
+        const dfl yi = df_from_double(b.y[i]);
+        sa = df_add(sa, a);
+        sb = df_add(sb, c);
+        sc = df_fma(yi, c, sc);
+    }
+    const double A = df_to_double(block_sum_df(sa, red));
+    const double B = df_to_double(block_sum_df(sb, red));
+    const double C = df_to_double(block_sum_df(sc, red));
+    const double m = B / A;
+    const dfl md = df_from_double(m);
+    dfl sq = {0.f, 0.f};
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const dfl wv = df_fms(md, df_load(x1 + i), df_load(xy + i));
+        df_store(xy + i, wv);
+        const dfl e = df_sub(df_from_double(b.y[i]), md);
+        sq = df_fma(e, wv, sq);
+    }
+    const double Q = df_to_double(block_sum_df(sq, red));
+    if (threadIdx.x == 0) {
+        const double eps = 9.094947017729282e-13;   // 2^-40
+        const bool degenerate = Q <= 16.0 * n * eps * eps * fabs(C);
+        nll[t] = degenerate ? -inf : st.logdet + n * log(Q);
+        mu[t] = m;
+        sigma2[t] = Q / n;
+        if (logdet) logdet[t] = st.logdet;
+        status[t] = degenerate ? GP_EDEGENERATE : GP_OK;
+        st.aa = A;
+        st.ab = B;
+        st.bb = C;
+        st.mu = m;
+        st.Q = Q;
+        b.st[t] = st;
+    }
+}
+
+// Convert the double-float factor and solve vectors of one fitted instance
+// into the double layout that the kriging kernel reads: L (tiles), a = L^-1 1
+// is not needed by the mixed fit, so column 0 of Zd gets x_1 = R^-1 1 and
+// column 1 w; the kriging kernel's a'v term is formed from R^-1 1 instead.
+__global__ void k_df_to_double(const float2* src, double* dst, size_t count) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        const float2 v = src[i];
+        dst[i] = (double)v.x + (double)v.y;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
+    const size_t smem = (GP_TILE_ELEMS + GP_NB * (GP_NB + 1) / 2) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_diag_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_diag_mixed<<<b.count, 256, smem, s>>>(b, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s) {
+    const int m = b.nt - J - 1;
+    if (m <= 0) return cudaSuccess;
+    k_split_panel<<<dim3(m, b.count), GP_NB, 0, s>>>(b, J, ns);
+    return cudaGetLastError();
+}
+
+template <int MODE, int NT, int NG>
+static cudaError_t launch_gemm(const MixedBatch& b, int J, int tiles, int ns, cudaStream_t s) {
+    const size_t smem = (size_t)2 * ns * (kChunkBytes + kChunkBytes / (GP_NB / NT)) + 1024;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_split_gemm<MODE, NT, NG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k_split_gemm<MODE, NT, NG><<<dim3(tiles, b.count), kGemmThreads, smem, s>>>(b, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s) {
+    const int m = b.nt - J - 1;
+    if (m <= 0) return cudaSuccess;
+    return launch_gemm<0, 64, GP_PANEL_SLICES>(b, J, 2 * m, b.ps, s);
+}
+
+cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {
+    const int m = b.nt - J - 1;
+    if (m <= 0) return cudaSuccess;
+    const int tiles = m * (m + 1) / 2;
+    switch (b.ug) {
+        case 7: return launch_gemm<1, 64, 7>(b, J, 2 * tiles, b.s, s);
+        case 3: return launch_gemm<1, 128, 3>(b, J, tiles, b.s, s);
+        default: return launch_gemm<1, 128, 4>(b, J, tiles, b.s, s);
+    }
+}
+
+cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s) {
+    k_df_forward<<<b.count, 256, 0, s>>>(b, c0, init);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s) {
+    k_df_backward<<<b.count, 256, 0, s>>>(b, c0, add_to);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
+    k_df_residual<<<b.count, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2, double* logdet,
+                               int* status, cudaStream_t s) {
+    k_df_finalize<<<b.count, 256, 0, s>>>(b, nll, mu, sigma2, logdet, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_double(const float2* src, double* dst, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    k_df_to_double<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
 
 }  // namespace gp

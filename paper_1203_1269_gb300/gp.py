@@ -34,7 +34,7 @@ class GPError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
-                ("nugget_in_var", _c_int), ("max_batch", _c_int)]
+                ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int)]
 
 
 _lib = None
@@ -71,6 +71,8 @@ def load(path=None):
     lib.gp_launch_count.argtypes = [P]
     lib.gp_launch_count.restype = ctypes.c_longlong
     lib.gp_corr_assemble.argtypes = [P, _c_int, _c_int, P, P, _c_double, _c_double, P, _c_int]
+    lib.gp_cholesky.argtypes = [P, _c_int, _c_int, P, P, _c_double, _c_double, _c_int, P,
+                                ctypes.POINTER(_c_int)]
     lib.gp_nll_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
                                  P, P, P, P, P]
     lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
@@ -220,6 +222,21 @@ class Context:
         self._check(self._lib.gp_corr_assemble(self._h, n, d, _ptr(x), _ptr(theta), float(p),
                                                float(delta), _ptr(out), lay))
         return out
+
+    # -- gp_cholesky -------------------------------------------------------
+    def cholesky(self, x, theta, p, delta, prec="fp64", out=None):
+        """Factor of R(theta) + delta I in the tile layout; returns (L, status)."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        theta = _dev_f64(theta, "theta", (d,), self.device)
+        size = (packed_elems(n),)
+        if out is None:
+            out = torch.zeros(size, dtype=torch.float64, device=self.device)
+        _dev_f64(out, "out", size, self.device)
+        st = _c_int(0)
+        self._check(self._lib.gp_cholesky(self._h, n, d, _ptr(x), _ptr(theta), float(p), float(delta),
+                                          _prec(prec), _ptr(out), ctypes.byref(st)))
+        return out, st.value
 
     # -- gp_nll_batch ------------------------------------------------------
     def nll_batch(self, x, y, thetas, p, delta, prec="fp64", out=None):

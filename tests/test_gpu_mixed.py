@@ -1,0 +1,190 @@
+"""GPU parity of the split-precision path (GP_MIXED) against the CPU oracle.
+
+Tolerance: -2logL within 1e-6 relative, mu_hat and sigma2_hat within 1e-6,
+where the oracle's condition estimate of R is at most 1e8.  Beyond that the
+error of a factorisation accurate to ~2^-40 per entry grows about linearly
+with cond(R); the check there is 1e-6 * cond / 1e8.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1203_1269_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_1269_gb300 import gp
+    return gp.Context(0)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def check_against(ref, st_ref, res, label, tol=TOL):
+    nll = host(res["nll"]); mu = host(res["mu"]); s2 = host(res["sigma2"]); st = host(res["status"])
+    worst_ok, worst_ill = 0.0, 0.0
+    for t in range(len(st_ref)):
+        assert st[t] == st_ref[t], (label, t, st[t], st_ref[t])
+        if st_ref[t] != 0:
+            continue
+        cond = ref[t, 6]
+        bound = tol * max(1.0, cond / 1e8)
+        rel = abs(nll[t] - ref[t, 0]) / abs(ref[t, 0])
+        assert rel <= bound, (label, t, rel, cond)
+        if cond <= 1e8:
+            assert abs(mu[t] - ref[t, 1]) <= tol * max(1.0, abs(ref[t, 1])), (label, t)
+            assert abs(s2[t] - ref[t, 2]) <= tol * abs(ref[t, 2]), (label, t)
+            worst_ok = max(worst_ok, rel)
+        else:
+            worst_ill = max(worst_ill, rel)
+    return worst_ok, worst_ill
+
+
+def unpack_lower(buf, n, nb=128):
+    nt = (n + nb - 1) // nb
+    full = np.zeros((nt * nb, nt * nb))
+    idx = 0
+    for J in range(nt):
+        for I in range(J, nt):
+            full[I * nb:(I + 1) * nb, J * nb:(J + 1) * nb] = buf[idx * nb * nb:(idx + 1) * nb * nb].reshape(nb, nb).T
+            idx += 1
+    return np.tril(full)[:n, :n]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-8)])
+@pytest.mark.parametrize("n", [100, 300])
+def test_factor_matches_oracle(ctx, prec, tol, n):
+    """The factor itself: split-precision L against the oracle's unblocked
+    Cholesky (entries of L are at most 1 in magnitude)."""
+    g = np.random.default_rng(n)
+    d = 3
+    x = g.random((n, d))
+    th = np.array([3.0, 5.0, 7.0])
+    L, st = ctx.cholesky(dev(x), dev(th), 1.95, 1e-6, prec)
+    assert st == 0
+    Lg = unpack_lower(host(L), n)
+    Lo, info = oracle.cholesky(oracle.corr_matrix(x, th, 1.95, 1e-6))
+    assert info == 0
+    err = np.max(np.abs(Lg - Lo))
+    print(f"\n{prec} n={n}: max |L - L_oracle| = {err:.2e}")
+    assert err <= tol
+
+
+def test_mixed_small_grid(ctx):
+    w = inputs.small_grid_fit()
+    ref, st = oracle.nll_batch(w.x, w.y, w.thetas, w.p, w.delta, want_cond=True)
+    res = ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "mixed")
+    ok, ill = check_against(ref, st, res, "grid64")
+    print(f"\nmixed n=200 grid: worst rel err cond<=1e8 {ok:.2e}, cond>1e8 {ill:.2e}")
+
+
+@pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 257, 389])
+def test_mixed_ragged_sizes(ctx, n):
+    g = np.random.default_rng(300 + n)
+    d, p, delta = 3, 1.95, 1e-6
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 12, d, lo=-0.5, hi=1.0)
+    ref, st = oracle.nll_batch(x, y, th, p, delta, want_cond=True)
+    res = ctx.nll_batch(dev(x), dev(y), dev(th), p, delta, "mixed")
+    check_against(ref, st, res, f"n{n}")
+
+
+@pytest.mark.parametrize("n", [1000, 4000])
+def test_mixed_kms_closed_form(ctx, n):
+    h = 1.0 / 1024.0
+    x = (np.arange(n) * h).reshape(n, 1)
+    y = np.random.default_rng(9).standard_normal(n)
+    rhos = [0.3, 0.8, 0.95]
+    th = np.array([[-math.log(r) / h] for r in rhos])
+    res = ctx.nll_batch(dev(x), dev(y), dev(th), 1.0, 0.0, "mixed")
+    one = np.ones(n)
+    for t in range(len(rhos)):
+        rho = math.exp(-th[t, 0] * h)
+        c = 1.0 / (1.0 - rho * rho)
+        diag = np.full(n, 1.0 + rho * rho)
+        diag[0] = diag[-1] = 1.0
+        qf = lambda u, v: c * (np.dot(u * diag, v) - rho * (np.dot(u[1:], v[:-1]) + np.dot(u[:-1], v[1:])))
+        A, B, C = qf(one, one), qf(one, y), qf(y, y)
+        Q = C - B * B / A
+        logdet = (n - 1) * math.log(1.0 - rho * rho)
+        nll = logdet + n * math.log(Q)
+        assert host(res["status"])[t] == 0
+        assert abs(host(res["nll"])[t] - nll) <= TOL * abs(nll)
+        assert abs(host(res["logdet"])[t] - logdet) <= TOL * abs(logdet)
+        assert abs(host(res["mu"])[t] - B / A) <= TOL * max(1.0, abs(B / A))
+        assert abs(host(res["sigma2"])[t] - Q / n) <= TOL * Q / n
+
+
+def test_mixed_status_cases(ctx):
+    res = ctx.nll_batch(dev([[0.3, 0.7]]), dev([2.5]), dev([[1.0, 2.0]]), 1.9, 1e-3, "mixed")
+    assert host(res["status"])[0] == -6 and host(res["nll"])[0] == -math.inf
+    x = np.array([[0.2, 0.3], [0.2, 0.3], [0.7, 0.1], [0.5, 0.9]])
+    y = np.array([1.0, 2.0, 0.5, -1.0])
+    th = np.array([[1.0, 1.0], [-1.0, 1.0], [1.0, float("inf")], [2.0, 3.0]])
+    res = ctx.nll_batch(dev(x), dev(y), dev(th), 2.0, 0.0, "mixed")
+    assert list(host(res["status"])) == [-3, -1, -1, -3]
+
+
+def test_mixed_deterministic_alone_and_in_batch(ctx):
+    w = inputs.small_grid_fit(n=300, N=0)
+    res = ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "mixed")
+    for t in (3, 40):
+        one = ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas[t:t + 1]), w.p, w.delta, "mixed")
+        for k in ("nll", "mu", "sigma2", "logdet"):
+            assert host(one[k])[0] == host(res[k])[t]
+
+
+def test_mixed_more_slices_more_accurate(ctx):
+    g = np.random.default_rng(77)
+    n, d = 600, 4
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 6, d, lo=-0.5, hi=0.5)
+    ref, st = oracle.nll_batch(x, y, th, 1.95, 1e-6, want_cond=True)
+    errs = {}
+    try:
+        for s in (3, 5, 6):
+            ctx.set_options(slices=s)
+            res = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+            errs[s] = float(np.max(np.abs(host(res["nll"]) - ref[:, 0]) / np.abs(ref[:, 0])))
+    finally:
+        ctx.set_options(slices=5)
+    print("\nmixed rel err by slices:", errs)
+    assert errs[5] <= TOL
+    assert errs[3] > errs[5] and errs[6] <= errs[5] * 10
+
+
+def test_mixed_full_size_sampled(ctx):
+    """n = 4000, d = 6, T = 256 as the benchmark runs it: a sample of the
+    candidates against the oracle one by one, all of them against the GPU's
+    FP64 path."""
+    w = inputs.hartman_shape()
+    res = ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "mixed")
+    st = host(res["status"])
+    assert np.all(st == 0)
+    sample = np.linspace(0, w.T - 1, 16).astype(int)
+    ref, st_ref = oracle.nll_batch(w.x, w.y, w.thetas[sample], w.p, w.delta, want_cond=True)
+    sub = {k: v[torch.as_tensor(sample, device="cuda")] for k, v in res.items()}
+    ok, ill = check_against(ref, st_ref, sub, "n4000")
+    f64 = ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "fp64")
+    rel = np.abs(host(res["nll"]) - host(f64["nll"])) / np.abs(host(f64["nll"]))
+    print(f"\nmixed n=4000: oracle sample worst cond<=1e8 {ok:.2e}, cond>1e8 {ill:.2e}; "
+          f"vs GPU FP64 over 256: max {rel.max():.2e} median {np.median(rel):.2e}")
+    assert np.median(rel) <= TOL
