@@ -122,8 +122,8 @@ def dist_setup():
     return world, rank, local
 
 
-def workload_for_rank(rank):
-    w = inputs.hartman_shape()
+def workload_for_rank(rank, n=4000, T=256):
+    w = inputs.hartman_shape(n=n, T=T)
     if rank > 0:
         w.thetas = inputs.log_uniform_thetas(inputs.rng(inputs.BASE_SEED + 1 + 1000 * rank),
                                              w.T, w.d)
@@ -172,7 +172,7 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
-    w = workload_for_rank(0)
+    w = workload_for_rank(0, args.n, args.T)
     import oracle
     cores = oracle.num_threads()
     k = max(1, min(w.T, cores))
@@ -211,7 +211,7 @@ def run_gp(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = workload_for_rank(rank)
+    w = workload_for_rank(rank, args.n, args.T)
     prec = args.prec
     ctx = gp.Context(local)
     f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -280,15 +280,23 @@ def run_gp(args):
                 "algorithmic_flops_per_launch": flops / max(upd_n, 1)}
     else:
         upd_ms, upd_n = phases["update"]
-        flops = update_flops(w.n) * w.T * args.steps
-        achieved = flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+        opts = ctx.options()
+        s = opts["slices"]
+        prods = s * (s + 1) // 2
+        nt = (w.n + NB - 1) // NB
+        tiles = sum(m * (m + 1) // 2 for m in range(1, nt))          # trailing tiles per instance
+        exec_flops = float(tiles) * prods * 2 * NB ** 3 * w.T * args.steps
+        achieved = exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
         peak = pk["bf16_tflops_sustained"]
-        roof = {"kernel": "k_update_mixed", "bound": "tensor", "achieved": achieved,
+        roof = {"kernel": "k_split_gemm<update>", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": stored_traffic("k_update_mixed", ["k_mixed.cu"]),
-                "peak_source": f"bf16 dense sustained, {pk_src}",
+                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"]),
+                "peak_source": f"bf16 dense sustained, {pk_src} (MEASURED_PEAKS.json)",
+                "flops_counted": f"executed bf16 slice products: {tiles} 128x128 tiles per "
+                                 f"instance x {prods} products x 2*128^3",
                 "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
-                "algorithmic_flops_per_launch": flops / max(upd_n, 1)}
+                "flops_per_launch": exec_flops / max(upd_n, 1),
+                "fp64_equivalent_tflops": update_flops(w.n) * w.T * args.steps / (upd_ms / 1e3) / 1e12}
 
     # ---- end to end through the host-buffer entry point ---------------------
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -351,7 +359,7 @@ def run_gp(args):
                 "config": {"workload": w.name, "n": w.n, "d": w.d, "T": w.T, "p": w.p,
                            "delta": w.delta, "prec": prec, "parallelism": f"replicas{world}",
                            "l2": "no flush: the batch's factor storage "
-                                 f"({w.T * (w.n // NB + 1) * (w.n // NB + 2) // 2 * NB * NB * 8 / 1e9:.1f} GB) "
+                                 f"({w.T * ((w.n + NB - 1) // NB) * ((w.n + NB - 1) // NB + 1) // 2 * NB * NB * 8 / 1e9:.1f} GB) "
                                  "exceeds L2 (129 MB)"},
                 "latency_ms": {"p50": pct(50), "p99": pct(99), "unit": "ms per 256-candidate batch"},
                 "statuses_ok": ok,
@@ -373,11 +381,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--compare", action="store_true")
-    ap.add_argument("--compare-steps", type=int, default=2)
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip timing the FP64 arm beside the mixed one")
+    ap.add_argument("--compare-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=4000, help="design size (profiling cases only)")
+    ap.add_argument("--T", type=int, default=256, help="candidates per step (profiling cases only)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

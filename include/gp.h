@@ -76,7 +76,7 @@ typedef struct {
     int slices;           /* GP_MIXED: bf16 slices per double operand (2..6), default 5 */
     int panel_slices;     /* GP_MIXED: slices of the panel-solve GEMM; fixed at 7 (all
                              product groups exact), other values are rejected */
-    int refine_iters;     /* GP_MIXED: iterative-refinement steps of the solves, default 2 */
+    int refine_iters;     /* GP_MIXED: iterative-refinement steps of the solves, default 1 */
     int nugget_in_var;    /* kriging variance uses 1 + delta (1) or 1 (0), default 1 */
     int max_batch;        /* instances factored concurrently (0 = from the budget) */
     int update_groups;    /* GP_MIXED: fp32 accumulators of the trailing update: 3 or 4
@@ -138,6 +138,10 @@ long long gp_launch_count(const gp_ctx* ctx);
  *           (element (r, c) at r + 128 c); rows and columns >= n hold the
  *           identity; diagonal tiles hold both triangles.
  *           R must hold nt(nt+1)/2 * 16384 doubles.
+ * layout 2: the split-precision path's storage: the tiles of layout 1 with
+ *           each entry as a pair of floats (hi, lo), hi + lo ~ R_ij to about
+ *           46 bits (exp evaluated in double-float arithmetic); same size in
+ *           bytes as layout 1.  Entries below 2^-125 are zero.
  * Asynchronous. */
 int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
                      double p, double delta, double* R, int layout);

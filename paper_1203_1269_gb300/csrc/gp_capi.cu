@@ -176,7 +176,7 @@ MixedSizes mixed_sizes(int n, int s) {
     z.PE = align256((size_t)nt * GP_NB * sizeof(int));
     z.WS = align256((size_t)ps * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
     z.WE = align256((size_t)GP_NB * sizeof(int));
-    z.Z = align256((size_t)4 * nt * GP_NB * sizeof(float2));
+    z.Z = align256((size_t)5 * nt * GP_NB * sizeof(float2));
     z.st = align256(sizeof(gp::InstState));
     z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.Z + z.st;
     return z;
@@ -298,7 +298,7 @@ void gp_default_options(gp_options* opt) {
     if (!opt) return;
     opt->slices = 5;
     opt->panel_slices = GP_PANEL_SLICES;
-    opt->refine_iters = 2;
+    opt->refine_iters = 1;
     opt->nugget_in_var = 1;
     opt->max_batch = 0;
     opt->update_groups = 4;
@@ -408,13 +408,20 @@ int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* t
         GP_CUDA(ctx, gp::launch_assemble_dense(n, d, x, theta, p, delta, R, ctx->stream));
         return GP_OK;
     }
-    if (layout != 1) return fail(ctx, GP_EINVAL, "layout must be 0 or 1");
+    if (layout != 1 && layout != 2) return fail(ctx, GP_EINVAL, "layout must be 0, 1 or 2");
     rc = ensure_ws(ctx, align256(sizeof(gp::InstState)));
     if (rc) return rc;
     gp::Batch b{};
     b.n = n; b.d = d; b.nt = gp::num_tiles(n); b.count = 1;
     b.p = p; b.delta = delta; b.x = x; b.y = nullptr; b.theta = theta;
-    b.A = R; b.inst_stride = gp::packed_elems(n);
+    if (layout == 1) {
+        b.A = R;
+    } else {
+        b.A = nullptr;
+        b.Adf = reinterpret_cast<float2*>(R);
+        b.Rdf = reinterpret_cast<float2*>(R);
+    }
+    b.inst_stride = gp::packed_elems(n);
     b.st = (gp::InstState*)ctx->ws;
     GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
     GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));

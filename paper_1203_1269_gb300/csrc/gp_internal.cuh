@@ -90,7 +90,8 @@ struct MixedBatch {
     __nv_bfloat16* WS;            // slices of W's rows: [slice][4 chunks][128 x 32]
     int* WE;                      // [128]
     size_t ps_stride, pe_stride, ws_stride, we_stride;
-    float2* Z;                    // 4 columns of npad double-float values
+    float2* Z;                    // 5 columns of npad double-float values (x_1, x_y, two
+                                  // residual columns, 1 / L_ii)
     size_t z_stride;
     const double* y;
     InstState* st;

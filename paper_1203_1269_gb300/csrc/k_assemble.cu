@@ -9,6 +9,7 @@
 // its group; per candidate an entry then costs d FMAs and one exp.  The paper
 // counts d n(n-1)/2 independent terms (Section 3); here the lower triangle of
 // tiles (diagonal tiles in full) is produced.
+#include "df.cuh"
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -129,6 +130,87 @@ k_assemble_tiles(Batch b, int group) {
     }
 }
 
+// Double-float variant for the split-precision path: the powers in double
+// (once per entry), then per candidate S = sum_k theta_k D_k and exp(-S) in
+// double-float arithmetic on the FP32 pipes.  Writes the working matrix and
+// its copy.  Dynamic smem: x rows/cols (double), theta of the group and the
+// exp table (double-float), the group's status flags.
+template <int DB>
+__global__ void __launch_bounds__(kThreads)
+k_assemble_tiles_df(Batch b, int group) {
+    extern __shared__ double dsm[];
+    double* xs_r = dsm;                                  // GP_NB * DB
+    double* xs_c = xs_r + GP_NB * DB;                    // kCols * DB
+    dfl* th = reinterpret_cast<dfl*>(xs_c + kCols * DB); // group * DB
+    dfl* tab = th + (size_t)group * DB;                  // 64
+    int* live = reinterpret_cast<int*>(tab + 64);        // group
+    const int nt = b.nt, n = b.n, d = b.d;
+    const int tile_lin = blockIdx.x / kSplit;
+    const int part = blockIdx.x % kSplit;
+    int J = 0;
+    {
+        long long rem = tile_lin;
+        while (rem >= nt - J) { rem -= nt - J; ++J; }
+    }
+    const int I = J + (int)(tile_lin - tile_index(J, J, nt));
+    const int row0 = I * GP_NB, col0 = J * GP_NB + part * kCols;
+    const int t0 = blockIdx.y * group;
+    const int t1 = min(b.count, t0 + group);
+    for (int q = threadIdx.x; q < GP_NB * DB; q += kThreads) {
+        const int r = q / DB, k = q % DB, gi = row0 + r;
+        xs_r[q] = (gi < n && k < d) ? b.x[(size_t)gi * d + k] : 0.0;
+    }
+    for (int q = threadIdx.x; q < kCols * DB; q += kThreads) {
+        const int c = q / DB, k = q % DB, gj = col0 + c;
+        xs_c[q] = (gj < n && k < d) ? b.x[(size_t)gj * d + k] : 0.0;
+    }
+    for (int q = threadIdx.x; q < (t1 - t0) * DB; q += kThreads) {
+        const int tt = q / DB, k = q % DB;
+        th[q] = (k < d) ? df_from_double(b.theta[(size_t)(t0 + tt) * d + k]) : dfl{0.f, 0.f};
+    }
+    for (int q = threadIdx.x; q < t1 - t0; q += kThreads) live[q] = (b.st[t0 + q].status == GP_OK);
+    fill_exp2_table(tab);
+    __syncthreads();
+    const dfl delta = df_from_double(b.delta);
+    const size_t tile_off = (size_t)tile_lin * GP_TILE_ELEMS;
+    const int r = threadIdx.x % GP_NB;
+    const int cb = threadIdx.x / GP_NB;
+    const int gi = row0 + r;
+#pragma unroll 1
+    for (int e = 0; e < kEntries; ++e) {
+        const int c = cb + 2 * e;
+        const int gj = col0 + c;
+        const size_t off = tile_off + (size_t)(part * kCols + c) * GP_NB + r;
+        const bool pad = (gi >= n) || (gj >= n);
+        const bool diag = (gi == gj);
+        dfl D[DB];
+#pragma unroll
+        for (int k = 0; k < DB; ++k)
+            D[k] = (k < d && !pad) ? df_from_double(powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p))
+                                   : dfl{0.f, 0.f};
+#pragma unroll 1
+        for (int t = t0; t < t1; ++t) {
+            if (!live[t - t0]) continue;
+            dfl v;
+            if (pad) {
+                v = {diag ? 1.f : 0.f, 0.f};
+            } else {
+                const dfl* tt = th + (size_t)(t - t0) * DB;
+                dfl s = {0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < DB; ++k)
+                    if (k < d) s = df_fma(tt[k], D[k], s);
+                v = df_exp_neg(s, tab);
+                if (diag) v = df_add(v, delta);
+            }
+            const size_t i = (size_t)t * b.inst_stride + off;
+            const float2 hl = make_float2(v.hi, v.lo);
+            b.Adf[i] = hl;
+            b.Rdf[i] = hl;
+        }
+    }
+}
+
 // d above the register-bounded variants: recompute the powers per candidate.
 __global__ void __launch_bounds__(kThreads)
 k_assemble_tiles_generic(Batch b, int group) {
@@ -205,6 +287,24 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
     int group = (int)((b.count + groups - 1) / groups);
     groups = (b.count + group - 1) / group;
     dim3 grid((unsigned)ctas_per_group, (unsigned)groups);
+    if (b.Adf && b.d <= 16) {
+        const int DB = b.d <= 4 ? 4 : (b.d <= 8 ? 8 : 16);
+        const size_t smem = (size_t)(GP_NB + kCols) * DB * sizeof(double) +
+                            ((size_t)group * DB + 64) * sizeof(dfl) + (size_t)group * sizeof(int);
+        cudaError_t e = cudaSuccess;
+        if (DB == 4) {
+            e = cudaFuncSetAttribute(k_assemble_tiles_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assemble_tiles_df<4><<<grid, kThreads, smem, s>>>(b, group);
+        } else if (DB == 8) {
+            e = cudaFuncSetAttribute(k_assemble_tiles_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assemble_tiles_df<8><<<grid, kThreads, smem, s>>>(b, group);
+        } else {
+            e = cudaFuncSetAttribute(k_assemble_tiles_df<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assemble_tiles_df<16><<<grid, kThreads, smem, s>>>(b, group);
+        }
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (b.d <= 4)
         k_assemble_tiles<4><<<grid, kThreads, 0, s>>>(b, group);
     else if (b.d <= 8)

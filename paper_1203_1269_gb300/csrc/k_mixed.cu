@@ -272,6 +272,11 @@ __global__ void __launch_bounds__(256) k_diag_mixed(MixedBatch b, int J) {
         }
     }
     if (threadIdx.x == 0) b.st[t].logdet += 2.0 * logdet;
+    if (threadIdx.x < GP_NB) {
+        float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
+        const dfl ri = df_from_double(1.0 / S[threadIdx.x * GP_NB + threadIdx.x]);
+        rinv[threadIdx.x] = make_float2(ri.hi, ri.lo);
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) S[q] = ((q % GP_NB) == (q / GP_NB)) ? 1.0 : 0.0;
     if (threadIdx.x < GP_NB) inv_diag[threadIdx.x] = 1.0 / P[threadIdx.x * (threadIdx.x + 1) / 2 + threadIdx.x];
@@ -532,7 +537,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
 
 // ------------------------------------------------------------ solves -------
 // Z (per instance, float2): column k of length npad at Z + k * npad.
-//   0: x_1   1: x_y   2, 3: residual / correction
+//   0: x_1   1: x_y   2, 3: residual / correction   4: 1 / L_ii
+// One CTA of 512 threads per instance.  Tiles whose transpose is needed are
+// staged in shared memory as T[c][k] with a row stride of 129 entries, so
+// that thread c walking row c and thread k walking column k both read
+// conflict-free (2-way for the 8-byte entries).
+
+constexpr int kSolveThreads = 512;
+constexpr int kTs = GP_NB + 1;   // staged tile row stride
 
 __device__ __forceinline__ float2* zcol(const MixedBatch& b, int t, int k) {
     return b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB;
@@ -561,144 +573,163 @@ __device__ dfl block_sum_df(dfl v, dfl* red) {
     return s;
 }
 
+// Stage tile `src` (column-major 128 x 128) as T[c * kTs + k] = src(k, c).
+__device__ __forceinline__ void stage_tile(const float2* __restrict__ src, dfl* T) {
+#pragma unroll 8
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kSolveThreads) {
+        const float2 v = __ldg(src + q);
+        T[(q >> 7) * kTs + (q & 127)] = dfl{v.x, v.y};
+    }
+}
+
 // Forward substitution L z = rhs for two columns (c0, c0 + 1) in place.
 // init != 0: the right-hand sides are [1 Y] (zero on padded rows).
-__global__ void __launch_bounds__(256) k_df_forward(MixedBatch b, int c0, int init) {
+__global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int c0, int init) {
     __shared__ dfl xj[2][GP_NB];
-    __shared__ dfl part[2][2][GP_NB];
+    __shared__ dfl part[4][2][GP_NB];
     __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
     const int nt = b.nt, n = b.n;
     float2* z0 = zcol(b, t, c0);
     float2* z1 = zcol(b, t, c0 + 1);
-    const int r = threadIdx.x % GP_NB, h = threadIdx.x / GP_NB;
+    const float2* rinv = zcol(b, t, 4);
+    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
     for (int I = 0; I < nt; ++I) {
         const int gi = I * GP_NB + r;
-        dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+        dfl a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
         for (int Jt = 0; Jt < I; ++Jt) {
             __syncthreads();
-            if (h == 0) xj[0][r] = df_load(z0 + Jt * GP_NB + r);
-            else        xj[1][r] = df_load(z1 + Jt * GP_NB + r);
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x >> 7;
+                xj[k][r] = df_load((k ? z1 : z0) + Jt * GP_NB + r);
+            }
             __syncthreads();
             const float2* L = df_tile(b, b.A, t, I, Jt);
-            for (int c = h; c < GP_NB; c += 2) {
-                const float2 lv = __ldg(L + c * GP_NB + r);
-                const dfl l = {lv.x, lv.y};
-                a0 = df_fma(l, xj[0][c], a0);
-                a1 = df_fma(l, xj[1][c], a1);
+            // thread (r, h) takes columns h, h + 8, ... and h + 4, h + 12, ...: 4 chains
+#pragma unroll 4
+            for (int c = h; c < GP_NB; c += 8) {
+                const float2 u = __ldg(L + c * GP_NB + r);
+                const float2 v = __ldg(L + (c + 4) * GP_NB + r);
+                const dfl l0 = {u.x, u.y}, l1 = {v.x, v.y};
+                a00 = df_fma(l0, xj[0][c], a00);
+                a01 = df_fma(l1, xj[0][c + 4], a01);
+                a10 = df_fma(l0, xj[1][c], a10);
+                a11 = df_fma(l1, xj[1][c + 4], a11);
             }
         }
-        part[h][0][r] = a0;
-        part[h][1][r] = a1;
+        part[h][0][r] = df_add(a00, a01);
+        part[h][1][r] = df_add(a10, a11);
         __syncthreads();
-        if (h == 0) {
-            dfl b0, b1;
+        if (threadIdx.x < 2 * GP_NB) {
+            const int k = threadIdx.x >> 7;
+            dfl bk;
             if (init) {
-                b0 = {(gi < n) ? 1.f : 0.f, 0.f};
-                b1 = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
+                if (k == 0) bk = {(gi < n) ? 1.f : 0.f, 0.f};
+                else        bk = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
             } else {
-                b0 = df_load(z0 + gi);
-                b1 = df_load(z1 + gi);
+                bk = df_load((k ? z1 : z0) + gi);
             }
-            rhs[0][r] = df_sub(b0, df_add(part[0][0][r], part[1][0][r]));
-            rhs[1][r] = df_sub(b1, df_add(part[0][1][r], part[1][1][r]));
+            const dfl sm = df_add(df_add(part[0][k][r], part[1][k][r]), df_add(part[2][k][r], part[3][k][r]));
+            rhs[k][r] = df_sub(bk, sm);
         }
         __syncthreads();
         const float2* D = df_tile(b, b.A, t, I, I);
         for (int c = 0; c < GP_NB; ++c) {
-            const float2 dv = __ldg(D + c * GP_NB + c);
-            const dfl dc = {dv.x, dv.y};
-            const dfl x0 = df_div(rhs[0][c], dc);
-            const dfl x1 = df_div(rhs[1][c], dc);
+            const dfl ri = df_load(rinv + I * GP_NB + c);
+            const dfl x0 = df_mul(rhs[0][c], ri);
+            const dfl x1 = df_mul(rhs[1][c], ri);
             __syncthreads();
             if (threadIdx.x < GP_NB && r > c) {
                 const float2 lv = __ldg(D + c * GP_NB + r);
                 const dfl l = {lv.x, lv.y};
                 rhs[0][r] = df_fms(l, x0, rhs[0][r]);
                 rhs[1][r] = df_fms(l, x1, rhs[1][r]);
-            }
-            if (threadIdx.x == 0) {
+            } else if (threadIdx.x == c) {
                 rhs[0][c] = x0;
                 rhs[1][c] = x1;
             }
             __syncthreads();
         }
-        if (h == 0) df_store(z0 + gi, rhs[0][r]);
-        else        df_store(z1 + gi, rhs[1][r]);
+        if (threadIdx.x < 2 * GP_NB) {
+            const int k = threadIdx.x >> 7;
+            df_store((k ? z1 : z0) + gi, rhs[k][r]);
+        }
         __syncthreads();
     }
 }
 
 // Backward substitution L^T w = z for columns (c0, c0 + 1) in place; when
 // add_to >= 0 the result is also added into columns (add_to, add_to + 1).
-__global__ void __launch_bounds__(256) k_df_backward(MixedBatch b, int c0, int add_to) {
+// Dynamic smem: the staged tile (128 x kTs double-float).
+__global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int c0, int add_to) {
+    extern __shared__ dfl T[];
     __shared__ dfl wk[2][GP_NB];
+    __shared__ dfl part[4][2][GP_NB];
     __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
     const int nt = b.nt;
-    float2* z[2] = {zcol(b, t, c0), zcol(b, t, c0 + 1)};
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2* z0 = zcol(b, t, c0);
+    float2* z1 = zcol(b, t, c0 + 1);
+    const float2* rinv = zcol(b, t, 4);
+    const int c = threadIdx.x & 127, h = threadIdx.x >> 7;
     for (int I = nt - 1; I >= 0; --I) {
         if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
-            rhs[k][i] = df_load(z[k] + I * GP_NB + i);
+            const int k = threadIdx.x >> 7;
+            rhs[k][c] = df_load((k ? z1 : z0) + I * GP_NB + c);
+        }
+        dfl a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
+        for (int K = I + 1; K < nt; ++K) {
+            __syncthreads();
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x >> 7;
+                wk[k][c] = df_load((k ? z1 : z0) + K * GP_NB + c);
+            }
+            stage_tile(df_tile(b, b.A, t, K, I), T);
+            __syncthreads();
+            // (L_KI^T w_K)[c] = sum_k L_KI(k, c) w_K[k] = sum_k T[c][k] w_K[k]; k in [32h, 32h + 32)
+            const dfl* row = T + c * kTs + 32 * h;
+#pragma unroll 4
+            for (int k = 0; k < 32; k += 2) {
+                a00 = df_fma(row[k], wk[0][32 * h + k], a00);
+                a01 = df_fma(row[k + 1], wk[0][32 * h + k + 1], a01);
+                a10 = df_fma(row[k], wk[1][32 * h + k], a10);
+                a11 = df_fma(row[k + 1], wk[1][32 * h + k + 1], a11);
+            }
+        }
+        part[h][0][c] = df_add(a00, a01);
+        part[h][1][c] = df_add(a10, a11);
+        __syncthreads();
+        stage_tile(df_tile(b, b.A, t, I, I), T);   // diagonal tile for the triangular solve
+        if (threadIdx.x < 2 * GP_NB) {
+            const int k = threadIdx.x >> 7;
+            const dfl sm = df_add(df_add(part[0][k][c], part[1][k][c]), df_add(part[2][k][c], part[3][k][c]));
+            rhs[k][c] = df_sub(rhs[k][c], sm);
         }
         __syncthreads();
-        for (int K = I + 1; K < nt; ++K) {
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
-                wk[k][i] = df_load(z[k] + K * GP_NB + i);
-            }
+        // L_II^T w = rhs from the bottom; L_II(c', r) = T[r][c']
+        for (int cc = GP_NB - 1; cc >= 0; --cc) {
+            const dfl ri = df_load(rinv + I * GP_NB + cc);
+            const dfl x0 = df_mul(rhs[0][cc], ri);
+            const dfl x1 = df_mul(rhs[1][cc], ri);
             __syncthreads();
-            const float2* L = df_tile(b, b.A, t, K, I);
-            for (int c = w; c < GP_NB; c += 8) {
-                dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-                for (int k = lane; k < GP_NB; k += 32) {
-                    const float2 lv = __ldg(L + c * GP_NB + k);
-                    const dfl l = {lv.x, lv.y};
-                    s0 = df_fma(l, wk[0][k], s0);
-                    s1 = df_fma(l, wk[1][k], s1);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    dfl u0 = {__shfl_down_sync(0xffffffffu, s0.hi, o), __shfl_down_sync(0xffffffffu, s0.lo, o)};
-                    dfl u1 = {__shfl_down_sync(0xffffffffu, s1.hi, o), __shfl_down_sync(0xffffffffu, s1.lo, o)};
-                    s0 = df_add(s0, u0);
-                    s1 = df_add(s1, u1);
-                }
-                if (lane == 0) {
-                    rhs[0][c] = df_sub(rhs[0][c], s0);
-                    rhs[1][c] = df_sub(rhs[1][c], s1);
-                }
-            }
-            __syncthreads();
-        }
-        const float2* D = df_tile(b, b.A, t, I, I);
-        for (int c = GP_NB - 1; c >= 0; --c) {
-            const float2 dv = __ldg(D + c * GP_NB + c);
-            const dfl dc = {dv.x, dv.y};
-            const dfl x0 = df_div(rhs[0][c], dc);
-            const dfl x1 = df_div(rhs[1][c], dc);
-            __syncthreads();
-            if (threadIdx.x < c) {
-                const float2 lv = __ldg(D + threadIdx.x * GP_NB + c);   // L(c, r) with r = threadIdx.x
-                const dfl l = {lv.x, lv.y};
+            if (threadIdx.x < cc) {
+                const dfl l = T[threadIdx.x * kTs + cc];
                 rhs[0][threadIdx.x] = df_fms(l, x0, rhs[0][threadIdx.x]);
                 rhs[1][threadIdx.x] = df_fms(l, x1, rhs[1][threadIdx.x]);
-            }
-            if (threadIdx.x == 0) {
-                rhs[0][c] = x0;
-                rhs[1][c] = x1;
+            } else if (threadIdx.x == cc) {
+                rhs[0][cc] = x0;
+                rhs[1][cc] = x1;
             }
             __syncthreads();
         }
         if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x / GP_NB, i = threadIdx.x % GP_NB;
-            df_store(z[k] + I * GP_NB + i, rhs[k][i]);
+            const int k = threadIdx.x >> 7;
+            df_store((k ? z1 : z0) + I * GP_NB + c, rhs[k][c]);
             if (add_to >= 0) {
-                float2* acc = zcol(b, t, add_to + k) + I * GP_NB + i;
-                df_store(acc, df_add(df_load(acc), rhs[k][i]));
+                float2* acc = zcol(b, t, add_to + k) + I * GP_NB + c;
+                df_store(acc, df_add(df_load(acc), rhs[k][c]));
             }
         }
         __syncthreads();
@@ -706,76 +737,88 @@ __global__ void __launch_bounds__(256) k_df_backward(MixedBatch b, int c0, int a
 }
 
 // Residuals [r_1 r_y] = [1 Y] - R [x_1 x_y] into columns 2, 3, with the
-// double-float copy of R (lower tiles; diagonal tiles full).
-__global__ void __launch_bounds__(256) k_df_residual(MixedBatch b) {
-    __shared__ dfl xs[2][GP_NB];
-    __shared__ dfl acc_t[2][GP_NB];
-    __shared__ dfl part[2][2][GP_NB];
+// double-float copy of R.  Every stored tile (I, J) is read once and applied
+// both ways: y_I += R_IJ x_J and, off the diagonal, y_J += R_IJ^T x_I.
+// y accumulates in columns 2, 3 (each entry always by the same thread).
+// Dynamic smem: the staged tile.
+__global__ void __launch_bounds__(kSolveThreads) k_df_residual(MixedBatch b) {
+    extern __shared__ dfl T[];
+    __shared__ dfl xa[2][GP_NB];
+    __shared__ dfl xb[2][GP_NB];
+    __shared__ dfl part[4][2][GP_NB];
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
     const int nt = b.nt, n = b.n;
-    const float2* x[2] = {zcol(b, t, 0), zcol(b, t, 1)};
-    float2* res[2] = {zcol(b, t, 2), zcol(b, t, 3)};
-    const int r = threadIdx.x % GP_NB, h = threadIdx.x / GP_NB;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int I = 0; I < nt; ++I) {
-        dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
-        if (threadIdx.x < 2 * GP_NB) acc_t[threadIdx.x / GP_NB][threadIdx.x % GP_NB] = dfl{0.f, 0.f};
-        // tiles (I, J), J <= I: row r of the tile times x_J
-        for (int Jt = 0; Jt <= I; ++Jt) {
+    const float2* x0 = zcol(b, t, 0);
+    const float2* x1 = zcol(b, t, 1);
+    const int i = threadIdx.x & 127, h = threadIdx.x >> 7;
+    float2* y0 = zcol(b, t, 2);
+    float2* y1 = zcol(b, t, 3);
+    if (threadIdx.x < 2 * GP_NB) {
+        float2* y = (threadIdx.x >> 7) ? y1 : y0;
+        for (int I = 0; I < nt; ++I) y[I * GP_NB + i] = make_float2(0.f, 0.f);
+    }
+    for (int J = 0; J < nt; ++J) {
+        for (int I = J; I < nt; ++I) {
             __syncthreads();
-            if (h == 0) xs[0][r] = df_load(x[0] + Jt * GP_NB + r);
-            else        xs[1][r] = df_load(x[1] + Jt * GP_NB + r);
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x >> 7;
+                xa[k][i] = df_load((k ? x1 : x0) + J * GP_NB + i);   // x_J
+                xb[k][i] = df_load((k ? x1 : x0) + I * GP_NB + i);   // x_I
+            }
+            stage_tile(df_tile(b, b.Rc, t, I, J), T);
             __syncthreads();
-            const float2* R = df_tile(b, b.Rc, t, I, Jt);
-            for (int c = h; c < GP_NB; c += 2) {
-                const float2 v = __ldg(R + c * GP_NB + r);
-                const dfl rv = {v.x, v.y};
-                a0 = df_fma(rv, xs[0][c], a0);
-                a1 = df_fma(rv, xs[1][c], a1);
+            // rows: (R_IJ x_J)[i] = sum_c T[c][i] x_J[c], c in [32h, 32h + 32)
+            dfl r0 = {0.f, 0.f}, r1 = {0.f, 0.f};
+#pragma unroll 4
+            for (int c = 32 * h; c < 32 * h + 32; ++c) {
+                const dfl v = T[c * kTs + i];
+                r0 = df_fma(v, xa[0][c], r0);
+                r1 = df_fma(v, xa[1][c], r1);
+            }
+            part[h][0][i] = r0;
+            part[h][1][i] = r1;
+            __syncthreads();
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x >> 7;
+                float2* y = (k ? y1 : y0) + I * GP_NB + i;
+                df_store(y, df_add(df_load(y), df_add(df_add(part[0][k][i], part[1][k][i]),
+                                                      df_add(part[2][k][i], part[3][k][i]))));
+            }
+            if (I == J) continue;
+            __syncthreads();
+            // columns: (R_IJ^T x_I)[c] = sum_k T[c][k] x_I[k], k in [32h, 32h + 32)
+            const int c = i;
+            dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+            const dfl* row = T + c * kTs;
+#pragma unroll 4
+            for (int k = 32 * h; k < 32 * h + 32; ++k) {
+                s0 = df_fma(row[k], xb[0][k], s0);
+                s1 = df_fma(row[k], xb[1][k], s1);
+            }
+            part[h][0][c] = s0;
+            part[h][1][c] = s1;
+            __syncthreads();
+            if (threadIdx.x < 2 * GP_NB) {
+                const int k = threadIdx.x >> 7;
+                float2* y = (k ? y1 : y0) + J * GP_NB + c;
+                df_store(y, df_add(df_load(y), df_add(df_add(part[0][k][c], part[1][k][c]),
+                                                      df_add(part[2][k][c], part[3][k][c]))));
             }
         }
-        // tiles (J, I), J > I: transposed, warp w reduces columns w, w + 8, ...
-        for (int Jt = I + 1; Jt < nt; ++Jt) {
-            __syncthreads();
-            if (h == 0) xs[0][r] = df_load(x[0] + Jt * GP_NB + r);
-            else        xs[1][r] = df_load(x[1] + Jt * GP_NB + r);
-            __syncthreads();
-            const float2* R = df_tile(b, b.Rc, t, Jt, I);
-            for (int c = w; c < GP_NB; c += 8) {
-                dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-                for (int k = lane; k < GP_NB; k += 32) {
-                    const float2 v = __ldg(R + c * GP_NB + k);
-                    const dfl rv = {v.x, v.y};
-                    s0 = df_fma(rv, xs[0][k], s0);
-                    s1 = df_fma(rv, xs[1][k], s1);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    dfl u0 = {__shfl_down_sync(0xffffffffu, s0.hi, o), __shfl_down_sync(0xffffffffu, s0.lo, o)};
-                    dfl u1 = {__shfl_down_sync(0xffffffffu, s1.hi, o), __shfl_down_sync(0xffffffffu, s1.lo, o)};
-                    s0 = df_add(s0, u0);
-                    s1 = df_add(s1, u1);
-                }
-                if (lane == 0) {
-                    acc_t[0][c] = df_add(acc_t[0][c], s0);
-                    acc_t[1][c] = df_add(acc_t[1][c], s1);
-                }
-            }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * GP_NB) {
+        // r = b - y by the owning threads; padded rows: R is the identity there
+        // and x is zero, so r = 0
+        const int k = threadIdx.x >> 7;
+        float2* y = k ? y1 : y0;
+        for (int I = 0; I < nt; ++I) {
+            const int q = I * GP_NB + i;
+            dfl bq = {0.f, 0.f};
+            if (q < n) bq = k ? df_from_double(b.y[q]) : dfl{1.f, 0.f};
+            df_store(y + q, (q < n) ? df_sub(bq, df_load(y + q)) : dfl{0.f, 0.f});
         }
-        part[h][0][r] = a0;
-        part[h][1][r] = a1;
-        __syncthreads();
-        if (h == 0) {
-            const int gi = I * GP_NB + r;
-            const dfl b0 = {(gi < n) ? 1.f : 0.f, 0.f};
-            const dfl b1 = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
-            const dfl s0 = df_add(df_add(part[0][0][r], part[1][0][r]), acc_t[0][r]);
-            const dfl s1 = df_add(df_add(part[0][1][r], part[1][1][r]), acc_t[1][r]);
-            // padded rows: R is the identity there and x is zero, so r = 0
-            df_store(res[0] + gi, (gi < n) ? df_sub(b0, s0) : dfl{0.f, 0.f});
-            df_store(res[1] + gi, (gi < n) ? df_sub(b1, s1) : dfl{0.f, 0.f});
-        }
-        __syncthreads();
     }
 }
 
@@ -783,9 +826,9 @@ __global__ void __launch_bounds__(256) k_df_residual(MixedBatch b) {
 // -2logL = log|R| + n log Q; column 1 becomes w (for kriging), column 0 keeps
 // x_1 = R^-1 1.  Q is taken as zero when Q <= 16 n eps^2 Y'x_y with
 // eps = 2^-40, the accuracy unit of the split factorisation.
-__global__ void __launch_bounds__(256) k_df_finalize(MixedBatch b, double* nll, double* mu, double* sigma2,
-                                                     double* logdet, int* status) {
-    __shared__ dfl red[8];
+__global__ void __launch_bounds__(kSolveThreads) k_df_finalize(MixedBatch b, double* nll, double* mu,
+                                                               double* sigma2, double* logdet, int* status) {
+    __shared__ dfl red[kSolveThreads / 32];
     const int t = blockIdx.x;
     InstState st = b.st[t];
     const int n = b.n;
@@ -804,7 +847,7 @@ __global__ void __launch_bounds__(256) k_df_finalize(MixedBatch b, double* nll, 
     float2* x1 = zcol(b, t, 0);
     float2* xy = zcol(b, t, 1);
     dfl sa = {0.f, 0.f}, sb = {0.f, 0.f}, sc = {0.f, 0.f};
-    for (int i = threadIdx.x; i < n; i += 256) {
+    for (int i = threadIdx.x; i < n; i += kSolveThreads) {
         const dfl a = df_load(x1 + i), c = df_load(xy + i);
         const dfl yi = df_from_double(b.y[i]);
         sa = df_add(sa, a);
@@ -817,7 +860,7 @@ __global__ void __launch_bounds__(256) k_df_finalize(MixedBatch b, double* nll, 
     const double m = B / A;
     const dfl md = df_from_double(m);
     dfl sq = {0.f, 0.f};
-    for (int i = threadIdx.x; i < n; i += 256) {
+    for (int i = threadIdx.x; i < n; i += kSolveThreads) {
         const dfl wv = df_fms(md, df_load(x1 + i), df_load(xy + i));
         df_store(xy + i, wv);
         const dfl e = df_sub(df_from_double(b.y[i]), md);
@@ -906,23 +949,37 @@ cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {
 }
 
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s) {
-    k_df_forward<<<b.count, 256, 0, s>>>(b, c0, init);
+    k_df_forward<<<b.count, kSolveThreads, 0, s>>>(b, c0, init);
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s) {
-    k_df_backward<<<b.count, 256, 0, s>>>(b, c0, add_to);
+    const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_df_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_df_backward<<<b.count, kSolveThreads, smem, s>>>(b, c0, add_to);
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
-    k_df_residual<<<b.count, 256, 0, s>>>(b);
+    const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_df_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_df_residual<<<b.count, kSolveThreads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2, double* logdet,
                                int* status, cudaStream_t s) {
-    k_df_finalize<<<b.count, 256, 0, s>>>(b, nll, mu, sigma2, logdet, status);
+    k_df_finalize<<<b.count, kSolveThreads, 0, s>>>(b, nll, mu, sigma2, logdet, status);
     return cudaGetLastError();
 }
 

@@ -214,7 +214,7 @@ class Context:
         x = _dev_f64(x, "x", device=self.device)
         n, d = x.shape
         theta = _dev_f64(theta, "theta", (d,), self.device)
-        lay = {"dense": 0, "tiles": 1}[layout]
+        lay = {"dense": 0, "tiles": 1, "tiles_df": 2}[layout]
         size = (n, n) if lay == 0 else (packed_elems(n),)
         if out is None:
             out = torch.empty(size, dtype=torch.float64, device=self.device)

@@ -86,6 +86,28 @@ def test_factor_matches_oracle(ctx, prec, tol, n):
     assert err <= tol
 
 
+@pytest.mark.parametrize("p", [2.0, 1.95, 1.0])
+def test_df_assembly_matches_fp64_and_oracle(ctx, p):
+    """Double-float exp(-S) (table-driven, double-float arithmetic) against
+    CUDA's double exp in the FP64 assembly and against the oracle."""
+    g = np.random.default_rng(int(p * 100))
+    n, d = 300, 6
+    x = g.random((n, d))
+    th = 10 ** g.uniform(-2, 1.5, d)
+    f64 = host(ctx.corr_assemble(dev(x), dev(th), p, 1e-7, "tiles"))
+    dfb = host(ctx.corr_assemble(dev(x), dev(th), p, 1e-7, "tiles_df")).view(np.float32)
+    dfv = dfb[0::2].astype(np.float64) + dfb[1::2].astype(np.float64)
+    big = f64 > 2.0 ** -120
+    rel = np.abs(dfv[big] - f64[big]) / f64[big]
+    assert rel.max() < 2e-13, rel.max()
+    assert np.all(np.abs(dfv[~big] - f64[~big]) < 2.0 ** -118)
+    Ro = oracle.corr_matrix(x, th, p, 1e-7)
+    full = unpack_lower(dfv, n)
+    low = np.tril(Ro)
+    m = low > 2.0 ** -120
+    assert np.max(np.abs(full[m] - low[m]) / low[m]) < 2e-13
+
+
 def test_mixed_small_grid(ctx):
     w = inputs.small_grid_fit()
     ref, st = oracle.nll_batch(w.x, w.y, w.thetas, w.p, w.delta, want_cond=True)
