@@ -43,7 +43,8 @@ namespace {
 constexpr int kChunkElems = GP_NB * 32;       // bf16 elements in one 128 x 32 image chunk
 constexpr uint32_t kChunkBytes = kChunkElems * 2;
 constexpr int kChunks = GP_NB / 32;           // 4 chunks per 128-wide panel
-constexpr int kGemmThreads = 192;             // warp 0 copies, warp 1 MMA, warps 2-5 epilogue
+constexpr int kGemmThreads = 320;             // warp 0 copies, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiThreads = 256;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
 
 // ---------------------------------------------------------------- PTX ------
@@ -153,6 +154,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -361,49 +372,67 @@ __global__ void __launch_bounds__(GP_NB) k_split_panel(MixedBatch b, int J, int 
     }
 }
 
-// Split GEMM on one 128 x NT output tile with NG accumulator groups
-// (group g gathers the products with a + b = g, the last one all a + b >= g).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Split GEMM over 128 x NT output tiles with NG accumulator groups (group g
+// gathers the products with a + b = g, the last one all a + b >= g).
 // MODE 0 (panel):  A_IJ(:, cols)  =  PS_I . WS(cols)^T   NT = 64, ps slices,
 //                  every group exact: the result must stay accurate relative
 //                  to |A| |W|, which exceeds |L_IJ| when L_JJ is ill-conditioned.
 // MODE 1 (update): A_IK -= PS_I . PS_K^T                  NT = 128, s slices,
-//                  groups 0 and 1 exact, the rest rounded (rows of L have norm <= 1).
+//                  groups 0..NG-2 exact, the last rounded (rows of L have
+//                  norm <= 1, so nothing amplifies it).
+//
+// Persistent: one CTA per SM walks the work items w = blockIdx.x + k gridDim.x
+// (instance-major).  Warp 0 streams K-chunk stages through a two-slot ring
+// that runs on across tiles, so the next tile's operands land while the
+// current tile's epilogue runs; warp 1 issues the MMAs once the epilogue has
+// drained the accumulators of the previous tile; warps 2-9 read tensor memory
+// and apply the result (two warps per tensor-memory lane quarter, each taking
+// half of the columns, with the loads of a column block issued together).  Every wait is bounded; a timeout marks the instance
+// GP_ETIMEOUT and stops the CTA after its copies and MMAs have landed.
 template <int MODE, int NT, int NG>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J) {
+__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst) {
     static_assert(NG * NT <= 512, "accumulators exceed tensor memory");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ __align__(8) uint64_t empty_bar[2];
-    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ __align__(8) uint64_t tfull_bar;
+    __shared__ __align__(8) uint64_t tempty_bar;
+    __shared__ __align__(8) uint64_t drain_bar;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
+    __shared__ volatile int abort_flag;
 
-    const int t = blockIdx.y;
-    if (b.st[t].status != GP_OK) return;
-    int I, K;
-    const int tile = blockIdx.x / (GP_NB / NT);
-    const int col0 = (blockIdx.x % (GP_NB / NT)) * NT;
-    if (MODE == 0) {
-        I = J + 1 + tile;
-        K = J;
-    } else {
-        int ii, kk;
-        tri_decode(tile, ii, kk);
-        I = J + 1 + ii;
-        K = J + 1 + kk;
-    }
     const int ns = (MODE == 0) ? b.ps : b.s;
     constexpr uint32_t kBBytes = kChunkBytes / (GP_NB / NT);      // B rows col0..col0+NT of a chunk
-    const __nv_bfloat16* gA = ps_block(b, t, I);
-    const uint8_t* gB = reinterpret_cast<const uint8_t*>((MODE == 0) ? (b.WS + (size_t)t * b.ws_stride)
-                                                                      : ps_block(b, t, K)) +
-                        (size_t)col0 * 64;   // 64 bytes per row inside a chunk
-    const int* eAp = pe_block(b, t, I);
-    const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride) : pe_block(b, t, K)) + col0;
     const uint32_t a_bytes = (uint32_t)ns * kChunkBytes;
     const uint32_t stage_bytes = a_bytes + (uint32_t)ns * kBBytes;
     constexpr uint32_t idesc = idesc_bf16(NT);
+    const int total = per_inst * b.count;
+
+    // work item -> (instance, I, K, first column)
+    auto decode = [&](int w, int& t, int& I, int& K, int& col0) {
+        t = w / per_inst;
+        const int q = w - t * per_inst;
+        const int tile = q / (GP_NB / NT);
+        col0 = (q % (GP_NB / NT)) * NT;
+        if (MODE == 0) {
+            I = J + 1 + tile;
+            K = J;
+        } else {
+            int ii, kk;
+            tri_decode(tile, ii, kk);
+            I = J + 1 + ii;
+            K = J + 1 + kk;
+        }
+    };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -411,7 +440,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
         mbar_init(&full_bar[1], 1);
         mbar_init(&empty_bar[0], 1);
         mbar_init(&empty_bar[1], 1);
-        mbar_init(&done_bar, 1);
+        mbar_init(&tfull_bar, 1);
+        mbar_init(&tempty_bar, kEpiThreads);
+        mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -426,86 +457,144 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kc = 0; kc < kChunks; ++kc) {
-                const int st = kc & 1, use = kc >> 1;
-                if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1)) {
-                    abort_flag = 1;
-                    break;
+            int g = 0;   // stages issued so far
+            for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
+                int t, I, K, col0;
+                decode(w, t, I, K, col0);
+                if (b.st[t].status != GP_OK) continue;
+                const __nv_bfloat16* gA = ps_block(b, t, I);
+                const uint8_t* gB = reinterpret_cast<const uint8_t*>((MODE == 0) ? (b.WS + (size_t)t * b.ws_stride)
+                                                                                  : ps_block(b, t, K)) +
+                                    (size_t)col0 * 64;   // 64 bytes per row inside a chunk
+                for (int kc = 0; kc < kChunks; ++kc, ++g) {
+                    const int st = g & 1;
+                    if (g >= 2 && !mbar_wait(&empty_bar[st], ((g >> 1) - 1) & 1)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    uint8_t* sa = smem + st * stage_bytes;
+                    uint8_t* sb = sa + a_bytes;
+                    mbar_expect_tx(&full_bar[st], stage_bytes);
+                    for (int a = 0; a < ns; ++a)
+                        bulk_g2s(sa + a * kChunkBytes, gA + (size_t)(a * kChunks + kc) * kChunkElems, kChunkBytes,
+                                 &full_bar[st]);
+                    for (int a = 0; a < ns; ++a)
+                        bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * kChunks + kc) * kChunkBytes, kBBytes,
+                                 &full_bar[st]);
                 }
-                uint8_t* sa = smem + st * stage_bytes;
-                uint8_t* sb = sa + a_bytes;
-                mbar_expect_tx(&full_bar[st], stage_bytes);
-                for (int a = 0; a < ns; ++a)
-                    bulk_g2s(sa + a * kChunkBytes, gA + (size_t)(a * kChunks + kc) * kChunkElems, kChunkBytes,
-                             &full_bar[st]);
-                for (int a = 0; a < ns; ++a)
-                    bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * kChunks + kc) * kChunkBytes, kBBytes,
-                             &full_bar[st]);
-                ++issued;
             }
-            // make sure no copy is still landing when the CTA retires
-            for (int kc = (issued > 2 ? issued - 2 : 0); kc < issued; ++kc) mbar_wait(&full_bar[kc & 1], (kc >> 1) & 1);
+            // no copy may still be landing when the CTA retires
+            for (int k = (g > 2 ? g - 2 : 0); k < g; ++k) mbar_wait(&full_bar[k & 1], (k >> 1) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            uint32_t started = 0;
-            for (int kc = 0; kc < kChunks; ++kc) {
-                const int st = kc & 1, use = kc >> 1;
-                if (!mbar_wait(&full_bar[st], use & 1)) {
+            int g = 0, i = 0;   // stages consumed, tiles finished
+            for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
+                int t, I, K, col0;
+                decode(w, t, I, K, col0);
+                if (b.st[t].status != GP_OK) continue;
+                if (i >= 1 && !mbar_wait(&tempty_bar, (i - 1) & 1)) {
                     abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem + st * stage_bytes);
-                const uint32_t sb = sa + a_bytes;
-                for (int a = 0; a < ns; ++a) {
-                    for (int bb = 0; a + bb < ns; ++bb) {
-                        const int g = (a + bb < NG) ? (a + bb) : (NG - 1);
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = smem_desc(sa + a * kChunkBytes + kk * 32, 16, 512, 4);
-                            const uint64_t bd = smem_desc(sb + bb * kBBytes + kk * 32, 16, 512, 4);
-                            mma_bf16(tbase + g * NT, ad, bd, idesc, (started >> g) & 1u);
-                            started |= 1u << g;
+                uint32_t started = 0;
+                for (int kc = 0; kc < kChunks; ++kc, ++g) {
+                    const int st = g & 1;
+                    if (!mbar_wait(&full_bar[st], (g >> 1) & 1)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + st * stage_bytes);
+                    const uint32_t sb = sa + a_bytes;
+                    for (int a = 0; a < ns; ++a) {
+                        for (int bb = 0; a + bb < ns; ++bb) {
+                            const int gr = (a + bb < NG) ? (a + bb) : (NG - 1);
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint64_t ad = smem_desc(sa + a * kChunkBytes + kk * 32, 16, 512, 4);
+                                const uint64_t bd = smem_desc(sb + bb * kBBytes + kk * 32, 16, 512, 4);
+                                mma_bf16(tbase + gr * NT, ad, bd, idesc, (started >> gr) & 1u);
+                                started |= 1u << gr;
+                            }
                         }
                     }
+                    mma_commit(&empty_bar[st]);
                 }
-                mma_commit(&empty_bar[st]);
+                if (abort_flag) break;
+                mma_commit(&tfull_bar);
+                ++i;
             }
-            mma_commit(&done_bar);
+            // every MMA issued has completed before tensor memory is released
+            mma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0);
         }
     } else {
-        // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
+        // epilogue: warps 2..9; warp w reads TMEM lane quarter w % 4 and the
+        // column half (w - 2) / 4 of the tile
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int r = q * 32 + lane;
-        const bool ok = mbar_wait(&done_bar, 0);
-        tc_fence_after();
-        if (ok && !abort_flag) {
-            const int eA = eAp[r];
+        const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+        constexpr int CB = (NG > 4) ? 8 : 16;    // columns per TMEM load
+        int i = 0;
+        for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
+            int t, I, K, col0;
+            decode(w, t, I, K, col0);
+            if (b.st[t].status != GP_OK) continue;
             float2* C = df_tile(b, b.A, t, I, K) + (size_t)col0 * GP_NB;
-            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-            constexpr int CB = (NG > 3) ? 16 : 32;   // columns per TMEM load
-            for (int c0 = 0; c0 < NT; c0 += CB) {
+            // the C tile (contiguous) heads for L2 while this tile's MMAs run
+            if (MODE == 1 && threadIdx.x == 64) prefetch_l2(C, (uint32_t)(NT * GP_NB * sizeof(float2)));
+            if (!mbar_wait(&tfull_bar, i & 1)) {
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int* eAp = pe_block(b, t, I);
+            const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride) : pe_block(b, t, K)) + col0;
+            const int eA = eAp[r];
+            for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += CB) {
+                float2 cv[CB];
+                if (MODE == 1) {
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) cv[j] = C[(size_t)(c0 + j) * GP_NB + r];
+                }
                 float d[NG][CB];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
-                    if (CB == 16) tmem_ld16(lane_addr + g * NT + c0, d[g]);
-                    else          tmem_ld32(lane_addr + g * NT + c0, d[g]);
+                    if (CB == 8)       tmem_ld8(lane_addr + g * NT + c0, d[g]);
+                    else               tmem_ld16(lane_addr + g * NT + c0, d[g]);
                 }
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < CB; ++j) {
                     const int c = c0 + j;
-                    // v = sum_g d_g (weights already in the slices); d0 + d1 exactly,
-                    // then the smaller groups into the double-float sum
+                    // v = sum_g d_g (weights already in the slices).  In the update
+                    // the groups 0 .. NG-2 enter exactly and the last (weight
+                    // <= 2^-24 of the result) folds into the low word; the panel
+                    // keeps every group exact in the double-float sum.
                     float h, l;
                     two_sum(d[0][j], d[1][j], h, l);
+                    if (MODE == 1) {
 #pragma unroll
-                    for (int g = 2; g < NG; ++g) {
-                        float s2, e2;
-                        two_sum(h, d[g][j], s2, e2);
-                        l = __fadd_rn(l, e2);
-                        fast_two_sum(s2, l, h, l);
+                        for (int g = 2; g < NG - 1; ++g) {
+                            float s2, e2;
+                            two_sum(h, d[g][j], s2, e2);
+                            h = s2;
+                            l = __fadd_rn(l, e2);
+                        }
+                        if (NG > 2) l = __fadd_rn(l, d[NG - 1][j]);
+                        // h may be tiny under cancellation: normalise without
+                        // assuming |h| >= |l|
+                        two_sum(h, l, h, l);
+                    } else {
+#pragma unroll
+                        for (int g = 2; g < NG; ++g) {
+                            float s2, e2;
+                            two_sum(h, d[g][j], s2, e2);
+                            l = __fadd_rn(l, e2);
+                            fast_two_sum(s2, l, h, l);
+                        }
                     }
                     const int e = eA + __ldg(eBp + c) - 14;
                     const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
@@ -517,21 +606,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                         fast_two_sum(h, l, hh, ll);
                         *p = make_float2(hh, ll);
                     } else {
-                        const float2 cv = *p;
-                        const dfl res = df_sub(dfl{cv.x, cv.y}, dfl{h, l});
-                        *p = make_float2(res.hi, res.lo);
+                        // C - (h + l) to an absolute error of about 2^-47 (|C| + |h|);
+                        // the final normalisation makes no assumption on the
+                        // sizes (the diagonal cancels heavily)
+                        float sh, se;
+                        two_sum(cv[j].x, -h, sh, se);
+                        se = __fadd_rn(se, __fsub_rn(cv[j].y, l));
+                        two_sum(sh, se, sh, se);
+                        *p = make_float2(sh, se);
                     }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&tempty_bar);
+            ++i;
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (abort_flag && threadIdx.x == 0) {
-        b.st[t].status = GP_ETIMEOUT;
-        atomicExch(b.err, GP_ETIMEOUT);
-    }
+    if (abort_flag && threadIdx.x == 0) atomicExch(b.err, GP_ETIMEOUT);
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
 }
 
@@ -917,8 +1011,18 @@ cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t 
     return cudaGetLastError();
 }
 
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
 template <int MODE, int NT, int NG>
-static cudaError_t launch_gemm(const MixedBatch& b, int J, int tiles, int ns, cudaStream_t s) {
+static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s) {
     const size_t smem = (size_t)2 * ns * (kChunkBytes + kChunkBytes / (GP_NB / NT)) + 1024;
     static size_t attr = 0;
     if (smem > attr) {
@@ -927,7 +1031,9 @@ static cudaError_t launch_gemm(const MixedBatch& b, int J, int tiles, int ns, cu
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    k_split_gemm<MODE, NT, NG><<<dim3(tiles, b.count), kGemmThreads, smem, s>>>(b, J);
+    const long long total = (long long)per_inst * b.count;
+    const int grid = (int)(total < sm_count() ? total : sm_count());
+    k_split_gemm<MODE, NT, NG><<<grid, kGemmThreads, smem, s>>>(b, J, per_inst);
     return cudaGetLastError();
 }
 
