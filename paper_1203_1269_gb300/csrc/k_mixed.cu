@@ -221,47 +221,66 @@ __device__ __forceinline__ void cut_slices(float xh, float xl, int s, float* m) 
 
 // ----------------------------------------------------------- kernels -------
 
-// Diagonal block of column J: L_JJ = chol(A_JJ) in double, W = L_JJ^-1 by
-// solving X L_JJ^T = I (X = W^T, upper triangular), log-det, and the slices
-// of W's rows.  Dynamic smem: S (128 x 128 double) + packed L (8256 doubles).
-__global__ void __launch_bounds__(256) k_diag_mixed(MixedBatch b, int J) {
-    extern __shared__ double sm[];
-    double* S = sm;
-    double* P = sm + GP_TILE_ELEMS;   // packed lower L: P[r(r+1)/2 + c]
-    __shared__ double inv_diag[GP_NB];
+// Diagonal block of column J in IEEE double: L_JJ = chol(A_JJ), log-det,
+// the reciprocal diagonal, and W = L_JJ^-1 with the slices of W's rows.
+// The block lives in shared memory as a packed lower triangle (row-major,
+// P[r(r+1)/2 + c]), 66 KB, so that three CTAs share an SM.
+//   factor:  right-looking by columns; column c is copied to a contiguous
+//            buffer after scaling so the rank-1 update reads it conflict-free;
+//   inverse: in place, row by row: row i of W needs row i of L and rows < i
+//            of W (already inverted), W_ij = -(1/L_ii) sum_{k=j}^{i-1} L_ik W_kj;
+//            four threads share each entry's sum.
+constexpr int kDiagThreads = 512;
+constexpr int kPacked = GP_NB * (GP_NB + 1) / 2;
+
+__device__ __forceinline__ int prow(int r) { return r * (r + 1) / 2; }
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J) {
+    extern __shared__ double P[];          // kPacked doubles
+    __shared__ double col[GP_NB];
+    __shared__ double rowtmp[GP_NB];
     __shared__ double inv_piv;
     __shared__ int failed;
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
     float2* T = df_tile(b, b.A, t, J, J);
-    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) {
-        const float2 v = T[q];
-        S[q] = (double)v.x + (double)v.y;
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
+        const int rr = q & 127, cc = q >> 7;
+        if (rr >= cc) {
+            const float2 v = T[q];
+            P[prow(rr) + cc] = (double)v.x + (double)v.y;
+        }
     }
     if (threadIdx.x == 0) failed = -1;
     __syncthreads();
-    const int r = threadIdx.x % GP_NB;
-    const int h = threadIdx.x / GP_NB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kDiagThreads / 32;
     double logdet = 0.0;
     for (int c = 0; c < GP_NB; ++c) {
         if (threadIdx.x == 0) {
-            const double piv = S[c * GP_NB + c];
+            const double piv = P[prow(c) + c];
             if (!(piv > 0.0) || !isfinite(piv)) {
                 failed = c;
             } else {
                 const double l = sqrt(piv);
-                S[c * GP_NB + c] = l;
+                P[prow(c) + c] = l;
                 inv_piv = 1.0 / l;
                 logdet += log(l);
             }
         }
         __syncthreads();
         if (failed >= 0) break;
-        if (h == 0 && r > c) S[c * GP_NB + r] *= inv_piv;
+        if (threadIdx.x > c && threadIdx.x < GP_NB) {
+            const double v = P[prow(threadIdx.x) + c] * inv_piv;
+            P[prow(threadIdx.x) + c] = v;
+            col[threadIdx.x] = v;
+        }
         __syncthreads();
-        if (r > c) {
-            const double lr = S[c * GP_NB + r];
-            for (int k = c + 1 + h; k <= r; k += 2) S[k * GP_NB + r] = fma(-lr, S[c * GP_NB + k], S[k * GP_NB + r]);
+        // A(r, k) -= L(r, c) L(k, c) for c < k <= r: warp per row, lanes along k
+        for (int r = c + 1 + warp; r < GP_NB; r += kWarps) {
+            const double lr = col[r];
+            double* row = P + prow(r);
+            for (int k = c + 1 + lane; k <= r; k += 32) row[k] = fma(-lr, col[k], row[k]);
         }
         __syncthreads();
     }
@@ -272,44 +291,44 @@ __global__ void __launch_bounds__(256) k_diag_mixed(MixedBatch b, int J) {
         }
         return;
     }
-    // L out (double-float, lower triangle) and into the packed copy
-    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) {
-        const int rr = q % GP_NB, cc = q / GP_NB;
+    // L out (double-float, lower triangle), log-det, reciprocal diagonal
+    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
+        const int rr = q & 127, cc = q >> 7;
         if (rr >= cc) {
-            const double v = S[q];
-            const dfl d = df_from_double(v);
+            const dfl d = df_from_double(P[prow(rr) + cc]);
             T[q] = make_float2(d.hi, d.lo);
-            P[rr * (rr + 1) / 2 + cc] = v;
         }
     }
     if (threadIdx.x == 0) b.st[t].logdet += 2.0 * logdet;
     if (threadIdx.x < GP_NB) {
         float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
-        const dfl ri = df_from_double(1.0 / S[threadIdx.x * GP_NB + threadIdx.x]);
-        rinv[threadIdx.x] = make_float2(ri.hi, ri.lo);
+        const double ri = 1.0 / P[prow(threadIdx.x) + threadIdx.x];
+        const dfl d = df_from_double(ri);
+        rinv[threadIdx.x] = make_float2(d.hi, d.lo);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += 256) S[q] = ((q % GP_NB) == (q / GP_NB)) ? 1.0 : 0.0;
-    if (threadIdx.x < GP_NB) inv_diag[threadIdx.x] = 1.0 / P[threadIdx.x * (threadIdx.x + 1) / 2 + threadIdx.x];
-    __syncthreads();
-    // X L^T = I, column by column; X is upper triangular so only rows r <= c move
-    for (int c = 0; c < GP_NB; ++c) {
-        const double xrc = S[c * GP_NB + r] * inv_diag[c];
+    // W = L^-1 in place, row by row; thread (j, part) sums k = j + part, j + part + 4, ...
+    const int j = threadIdx.x >> 2, part = threadIdx.x & 3;
+    for (int i = 0; i < GP_NB; ++i) {
+        const double* Li = P + prow(i);
+        double sum = 0.0;
+        if (j < i)
+            for (int k = j + part; k < i; k += 4) sum = fma(Li[k], P[prow(k) + j], sum);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        const double rinv_i = 1.0 / Li[i];
+        if (part == 0 && j <= i) rowtmp[j] = (j == i) ? rinv_i : -rinv_i * sum;
         __syncthreads();
-        if (r <= c) {
-            if (h == 0) S[c * GP_NB + r] = xrc;
-            for (int k = c + 1 + h; k < GP_NB; k += 2) S[k * GP_NB + r] = fma(-xrc, P[k * (k + 1) / 2 + c], S[k * GP_NB + r]);
-        }
+        if (threadIdx.x <= i) P[prow(i) + threadIdx.x] = rowtmp[threadIdx.x];
         __syncthreads();
     }
-    // W row c = S[c*NB .. c*NB+127]; one warp per row: exponent and slices
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // row c of W: exponent and slices; one warp per row
     __nv_bfloat16* WS = b.WS + (size_t)t * b.ws_stride;
     int* WE = b.WE + (size_t)t * b.we_stride;
-    for (int c = warp; c < GP_NB; c += 8) {
-        const double* w = S + c * GP_NB;
+    for (int c = warp; c < GP_NB; c += kWarps) {
+        const double* w = P + prow(c);
         double mx = 0.0;
-        for (int k = lane; k < GP_NB; k += 32) mx = fmax(mx, fabs(w[k]));
+        for (int k = lane; k <= c; k += 32) mx = fmax(mx, fabs(w[k]));
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         int E = 0;
         if (mx > 0.0) frexp(mx, &E);
@@ -319,7 +338,7 @@ __global__ void __launch_bounds__(256) k_diag_mixed(MixedBatch b, int J) {
         float m[4][GP_MAX_SLICES];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const double x = ldexp(w[k0 + e], 7 - E);
+            const double x = (k0 + e <= c) ? ldexp(w[k0 + e], 7 - E) : 0.0;
             const dfl xd = df_from_double(x);
             cut_slices(xd.hi, xd.lo, b.ps, m[e]);
         }
@@ -993,14 +1012,14 @@ __global__ void k_df_to_double(const float2* src, double* dst, size_t count) {
 }  // namespace
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
-    const size_t smem = (GP_TILE_ELEMS + GP_NB * (GP_NB + 1) / 2) * sizeof(double);
+    const size_t smem = (size_t)kPacked * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_diag_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_diag_mixed<<<b.count, 256, smem, s>>>(b, J);
+    k_diag_mixed<<<b.count, kDiagThreads, smem, s>>>(b, J);
     return cudaGetLastError();
 }
 
