@@ -179,6 +179,32 @@ int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host,
                       double delta, int prec, double* nll_host, double* mu_hat_host,
                       double* sigma2_hat_host, double* logdet_host, int* status_host);
 
+/* gp_nll_batch in IEEE double (GP_FP64) for callers that cannot let the
+ * library allocate device memory -- services that reserve their whole device
+ * budget at start-up, hosts whose allocator must account for every byte, or
+ * callers that cannot afford the device-wide synchronisation of cudaMalloc
+ * and cudaFree.  The paper has no counterpart: it is an interface variant,
+ * not part of the method.
+ *   - Working memory is one fixed array of GP_NOALLOC_SCRATCH_BYTES inside
+ *     the library (reserved on every GPU that loads the library, until the
+ *     process exits); the call allocates nothing.  Candidates are processed
+ *     in as many rounds as the array needs; n above GP_NOALLOC_MAX_N does not
+ *     fit one candidate and is rejected with GP_ENOMEM and a message.
+ *   - The first call on a device looks up the array's device address (a
+ *     runtime query, done once per device, with the context's device made
+ *     current); make that first call before any stream capture.
+ *   - Every call on a device shares the array: calls whose work overlaps on
+ *     the GPU (other streams, other contexts, other threads) race and corrupt
+ *     each other's results.  Calls in order on one stream are safe; nothing
+ *     needs clearing between calls (every buffer is written before it is
+ *     read).
+ * Arguments, outputs and asynchrony are those of gp_nll_batch. */
+#define GP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+#define GP_NOALLOC_MAX_N 2816
+int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                         const double* theta, double p, double delta, double* nll,
+                         double* mu_hat, double* sigma2_hat, double* logdet, int* status);
+
 /* Fit at one theta (length d): assemble, factor, solve, and keep on the
  * device what prediction needs.  The fit is always factored in IEEE double
  * whatever `prec` asks (any gp_precision value is accepted): a fit is one

@@ -292,6 +292,25 @@ int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y,
 
 }  // namespace
 
+namespace gp {
+
+// Accessors for the entry points defined in other translation units.
+int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+int ctx_device(const gp_ctx* ctx) { return ctx->device; }
+
+cudaStream_t ctx_stream(const gp_ctx* ctx) { return ctx->stream; }
+
+}  // namespace gp
+
 extern "C" {
 
 void gp_default_options(gp_options* opt) {

@@ -98,6 +98,11 @@ struct MixedBatch {
     int* err;                     // set when a bounded device wait gave up
 };
 
+// ---- context accessors (gp_capi.cu) ----------------------------------------
+int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...);
+int ctx_device(const gp_ctx* ctx);
+cudaStream_t ctx_stream(const gp_ctx* ctx);
+
 // ---- kernels (launch helpers, all on `stream`) ----------------------------
 cudaError_t launch_validate_theta(const Batch& b, cudaStream_t s);
 cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s);

@@ -76,6 +76,8 @@ def load(path=None):
     lib.gp_nll_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
                                  P, P, P, P, P]
     lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
+    lib.gp_nll_batch_noalloc.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double,
+                                         P, P, P, P, P]
     lib.gp_fit.argtypes = [P, _c_int, _c_int, P, P, P, _c_double, _c_double, _c_int,
                            ctypes.POINTER(P)]
     lib.gp_model_scalars.argtypes = [P, ctypes.POINTER(_c_double)]
@@ -255,6 +257,28 @@ class Context:
                        status=torch.empty(T, dtype=torch.int32, device=self.device))
         self._check(self._lib.gp_nll_batch(
             self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
+            _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
+            _ptr(out["status"])))
+        return out
+
+    def nll_batch_noalloc(self, x, y, thetas, p, delta, out=None):
+        """gp_nll_batch_noalloc: the double-precision batch with the library's
+        fixed scratch array (no device allocation by the library).  Pass
+        preallocated `out` tensors to keep the call itself allocation-free."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        if out is None:
+            kw = dict(dtype=torch.float64, device=self.device)
+            out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw),
+                       sigma2=torch.empty(T, **kw), logdet=torch.empty(T, **kw),
+                       status=torch.empty(T, dtype=torch.int32, device=self.device))
+        self._check(self._lib.gp_nll_batch_noalloc(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta),
             _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
             _ptr(out["status"])))
         return out
