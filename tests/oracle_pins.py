@@ -372,8 +372,27 @@ def check_predict(orc, seed=31):
     assert np.all(s2 > -1e-12)
 
 
+def check_fit_parts(orc, seed=37):
+    """The intermediate vectors of one fit against LAPACK: L L' = R,
+    a = L^-1 1, b = L^-1 Y, w = R^-1 (Y - 1 mu_hat)."""
+    g = np.random.default_rng(seed)
+    n = 20
+    x = g.random((n, 3))
+    y = g.standard_normal(n)
+    th = [2.0, 3.0, 1.5]
+    R, L, a, b, w, st = orc.fit_parts(x, y, th, 1.95, 1e-6)
+    assert st == 0
+    assert np.max(np.abs(L @ L.T - R)) < 1e-13
+    assert np.max(np.abs(L @ a - 1.0)) < 1e-10
+    assert np.max(np.abs(L @ b - y)) < 1e-10
+    one = np.ones(n)
+    mu = (one @ np.linalg.solve(R, y)) / (one @ np.linalg.solve(R, one))
+    assert np.max(np.abs(w - np.linalg.solve(R, y - mu))) < 1e-8 * max(1.0, np.max(np.abs(w)))
+
+
 ALL_CHECKS = [
     check_corr_hand_values, check_corr_invariants, check_kms, check_n1, check_n2,
     check_n3, check_eig_logdet, check_solve_estimates, check_cholesky_reconstructs,
     check_notpd, check_cond_estimate, check_invariants, check_table_form, check_predict,
+    check_fit_parts,
 ]
