@@ -138,9 +138,10 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, src_files):
-    """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current source of that kernel (else None)."""
+def stored_traffic(kernel, src_files, units_per_launch=None):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current source of that kernel (else None).  A capture of a smaller
+    case stores bytes per tile, scaled here by the tiles one launch updates."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -150,7 +151,11 @@ def stored_traffic(kernel, src_files):
     ent = table.get(kernel)
     if not ent or ent.get("source_hash") != kernel_source_hash(src_files):
         return None
-    return ent.get("bytes_per_launch")
+    if "bytes_per_launch" in ent:
+        return ent["bytes_per_launch"]
+    if "bytes_per_tile" in ent and units_per_launch:
+        return ent["bytes_per_tile"] * units_per_launch
+    return None
 
 
 def cpu_baseline_sample(w, max_theta=None, timeout_s=60.0):
@@ -290,7 +295,9 @@ def run_gp(args):
         peak = pk["bf16_tflops_sustained"]
         roof = {"kernel": "k_split_gemm<update>", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"]),
+                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"],
+                                          tiles * w.T / max(nt - 1, 1)),
+                "algorithmic_bytes_per_launch": tiles * w.T / max(nt - 1, 1) * 2 * NB * NB * 8,
                 "peak_source": f"bf16 dense sustained, {pk_src} (MEASURED_PEAKS.json)",
                 "flops_counted": f"executed bf16 slice products: {tiles} 128x128 tiles per "
                                  f"instance x {prods} products x 2*128^3",
