@@ -356,37 +356,77 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
 }
 
 // Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x, into row block I
-// of PS: one thread per row (column-major tiles: coalesced reads).
-__global__ void __launch_bounds__(GP_NB) k_split_panel(MixedBatch b, int J, int ns) {
+// of PS.  512 threads per tile: thread (r, q) owns row r's columns
+// 32q .. 32q + 31, which form exactly image chunk q, so it loads its values
+// once (coalesced along r) and writes only its own 16-byte pieces.  The four
+// owners of a row agree on the row's exponent through shared memory.
+constexpr int kSplitThreads = 512;
+
+__device__ __forceinline__ int exponent_of(float mx) {
+    // mx = f 2^E with f in [0.5, 1); 0 for mx == 0
+    if (mx == 0.f) return 0;
+    const int bits = __float_as_int(mx);
+    const int be = (bits >> 23) & 0xff;
+    if (be != 0) return be - 126;
+    int E;
+    frexpf(mx, &E);
+    return E;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns) {
+    __shared__ float pmax[4][GP_NB];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     const int I = J + 1 + blockIdx.x;
     const float2* src = df_tile(b, b.A, t, I, J);
-    const int r = threadIdx.x;
+    const int r = threadIdx.x & 127, q = threadIdx.x >> 7;
+    float2 v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
     float mx = 0.f;
-    for (int c = 0; c < GP_NB; ++c) mx = fmaxf(mx, fabsf(src[c * GP_NB + r].x));
-    int E = 0;
-    if (mx > 0.f) frexpf(mx, &E);
-    pe_block(b, t, I)[r] = E;
-    __nv_bfloat16* dst = ps_block(b, t, I);
-    for (int k0 = 0; k0 < GP_NB; k0 += 8) {
-        float m[8][GP_MAX_SLICES];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fabsf(v[j].x));
+    pmax[q][r] = mx;
+    __syncthreads();
+    mx = fmaxf(fmaxf(pmax[0][r], pmax[1][r]), fmaxf(pmax[2][r], pmax[3][r]));
+    const int E = exponent_of(mx);
+    if (q == 0) pe_block(b, t, I)[r] = E;
+    // scale by 2^(7 - E) exactly (two factors when 7 - E leaves the float range)
+    const int e2 = 7 - E;
+    const int ea = e2 > 127 ? 127 : (e2 < -126 ? -126 : e2);
+    const int eb = e2 - ea;
+    const float sa = __int_as_float((ea + 127) << 23);
+    const float sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
+    uint8_t* chunk0 = reinterpret_cast<uint8_t*>(ps_block(b, t, I) + (size_t)q * kChunkElems);
+#pragma unroll
+    for (int pc = 0; pc < 4; ++pc) {
+        float xh[8], xl[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const float2 v = src[(k0 + e) * GP_NB + r];
-            cut_slices(ldexpf(v.x, 7 - E), ldexpf(v.y, 7 - E), ns, m[e]);
+            xh[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].x, sa), sb);
+            xl[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].y, sa), sb);
         }
-        const uint32_t off = image_piece(r, k0);
+        const uint32_t off = image_piece(r, 8 * pc);
+        float w = 1.f;
 #pragma unroll
         for (int a = 0; a < GP_MAX_SLICES; ++a) {
             if (a >= ns) break;
-            uint4 v;
-            v.x = pack_bf16x2(m[0][a], m[1][a]);
-            v.y = pack_bf16x2(m[2][a], m[3][a]);
-            v.z = pack_bf16x2(m[4][a], m[5][a]);
-            v.w = pack_bf16x2(m[6][a], m[7][a]);
-            uint8_t* chunk = reinterpret_cast<uint8_t*>(dst + (size_t)(a * kChunks + (k0 >> 5)) * kChunkElems);
-            *reinterpret_cast<uint4*>(chunk + off) = v;
+            float m[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float qv = rintf(xh[e]);
+                m[e] = __fmul_rn(qv, w);
+                two_sum(__fsub_rn(xh[e], qv), xl[e], xh[e], xl[e]);
+                xh[e] = __fmul_rn(xh[e], 256.f);
+                xl[e] = __fmul_rn(xl[e], 256.f);
+            }
+            w = __fmul_rn(w, 0.00390625f);
+            uint4 u;
+            u.x = pack_bf16x2(m[0], m[1]);
+            u.y = pack_bf16x2(m[2], m[3]);
+            u.z = pack_bf16x2(m[4], m[5]);
+            u.w = pack_bf16x2(m[6], m[7]);
+            *reinterpret_cast<uint4*>(chunk0 + (size_t)a * kChunks * kChunkBytes + off) = u;
         }
     }
 }
@@ -1026,7 +1066,7 @@ cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
 cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
-    k_split_panel<<<dim3(m, b.count), GP_NB, 0, s>>>(b, J, ns);
+    k_split_panel<<<dim3(m, b.count), kSplitThreads, 0, s>>>(b, J, ns);
     return cudaGetLastError();
 }
 
