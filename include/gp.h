@@ -82,6 +82,11 @@ typedef struct {
     int update_groups;    /* GP_MIXED: fp32 accumulators of the trailing update: 3 or 4
                              (128-wide tiles, the last group rounded) or 7 (64-wide
                              tiles, every group exact) */
+    int inject_timeout;   /* test hook, default 0: when 1, the first CTA of the first
+                             trailing-update launch of each GP_MIXED batch waits 5 ms on
+                             a barrier nothing signals, gives up, and the instances it
+                             would have updated come back GP_ETIMEOUT (the bounded-wait
+                             failure path, exercised without faulting the GPU) */
 } gp_options;
 
 void gp_default_options(gp_options* opt);

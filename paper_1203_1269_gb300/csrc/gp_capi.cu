@@ -199,6 +199,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = ctx->opt.slices;
     mb.ps = GP_PANEL_SLICES;
     mb.ug = ctx->opt.update_groups;
+    mb.inject_timeout = ctx->opt.inject_timeout;
     mb.sp = mb.s > mb.ps ? mb.s : mb.ps;
     mb.inst_stride = z.A / sizeof(float2);
     mb.ps_stride = z.PS / sizeof(__nv_bfloat16);
@@ -321,6 +322,7 @@ void gp_default_options(gp_options* opt) {
     opt->nugget_in_var = 1;
     opt->max_batch = 0;
     opt->update_groups = 4;
+    opt->inject_timeout = 0;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {

@@ -81,6 +81,7 @@ struct MixedBatch {
     int s;                        // slices of the trailing update operands
     int ps;                       // slices of the panel solve operands (GP_PANEL_SLICES)
     int ug;                       // accumulator groups of the trailing update (3, 4 or 7)
+    int inject_timeout;           // test hook: one split-GEMM CTA waits on a barrier nothing signals
     int sp;                       // slice slots per row block in PS (max(s, ps))
     float2* A;                    // working matrix -> factor (double-float tiles)
     float2* Rc;                   // copy of R (double-float tiles), for residuals

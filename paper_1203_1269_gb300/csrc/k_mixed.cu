@@ -79,13 +79,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity, giving up after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// Wait for the phase with the given parity, giving up after `limit_ns`, or
+// as soon as *abort is set (another role of the CTA gave up).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, const volatile int* abort = nullptr,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         if (mbar_try(b, parity)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (abort && *abort) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
     __shared__ __align__(8) uint64_t tfull_bar;
     __shared__ __align__(8) uint64_t tempty_bar;
     __shared__ __align__(8) uint64_t drain_bar;
+    __shared__ __align__(8) uint64_t never_bar;   // never signalled: the timeout test waits on it
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -502,6 +506,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
         mbar_init(&tfull_bar, 1);
         mbar_init(&tempty_bar, kEpiThreads);
         mbar_init(&drain_bar, 1);
+        mbar_init(&never_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -527,7 +532,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                                     (size_t)col0 * 64;   // 64 bytes per row inside a chunk
                 for (int kc = 0; kc < kChunks; ++kc, ++g) {
                     const int st = g & 1;
-                    if (g >= 2 && !mbar_wait(&empty_bar[st], ((g >> 1) - 1) & 1)) {
+                    if (g >= 2 && !mbar_wait(&empty_bar[st], ((g >> 1) - 1) & 1, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
@@ -552,7 +557,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 int t, I, K, col0;
                 decode(w, t, I, K, col0);
                 if (b.st[t].status != GP_OK) continue;
-                if (i >= 1 && !mbar_wait(&tempty_bar, (i - 1) & 1)) {
+                if (i >= 1 && !mbar_wait(&tempty_bar, (i - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                // test hook: a wait that nothing ends, limited to 5 ms
+                if (b.inject_timeout && J == 0 && blockIdx.x == 0 && i == 0 &&
+                    !mbar_wait(&never_bar, 0, &abort_flag, 5000000ull)) {
                     abort_flag = 1;
                     break;
                 }
@@ -560,7 +571,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 uint32_t started = 0;
                 for (int kc = 0; kc < kChunks; ++kc, ++g) {
                     const int st = g & 1;
-                    if (!mbar_wait(&full_bar[st], (g >> 1) & 1)) {
+                    if (!mbar_wait(&full_bar[st], (g >> 1) & 1, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
@@ -604,7 +615,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             float2* C = df_tile(b, b.A, t, I, K) + (size_t)col0 * GP_NB;
             // the C tile (contiguous) heads for L2 while this tile's MMAs run
             if (MODE == 1 && threadIdx.x == 64) prefetch_l2(C, (uint32_t)(NT * GP_NB * sizeof(float2)));
-            if (!mbar_wait(&tfull_bar, i & 1)) {
+            if (!mbar_wait(&tfull_bar, i & 1, &abort_flag)) {
                 abort_flag = 1;
                 break;
             }
@@ -684,7 +695,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (abort_flag && threadIdx.x == 0) atomicExch(b.err, GP_ETIMEOUT);
+    if (abort_flag && threadIdx.x == 0) {
+        // every instance this CTA touches is incomplete: later kernels skip
+        // them and their outputs read GP_ETIMEOUT
+        atomicExch(b.err, GP_ETIMEOUT);
+        for (int w = blockIdx.x; w < total; w += gridDim.x) b.st[w / per_inst].status = GP_ETIMEOUT;
+    }
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
 }
 

@@ -210,3 +210,50 @@ def test_mixed_full_size_sampled(ctx):
     print(f"\nmixed n=4000: oracle sample worst cond<=1e8 {ok:.2e}, cond>1e8 {ill:.2e}; "
           f"vs GPU FP64 over 256: max {rel.max():.2e} median {np.median(rel):.2e}")
     assert np.median(rel) <= TOL
+
+
+def test_timeout_path_reports_and_context_recovers(ctx):
+    """A wait that nothing ends (the inject_timeout hook, 5 ms limit) makes
+    the affected instances come back GP_ETIMEOUT with NaN outputs while the
+    others are right; the next call on the same context is normal."""
+    g = np.random.default_rng(5)
+    n, d = 300, 3
+    x = g.random((n, d))
+    y = np.sin(4 * x).sum(axis=1)
+    th = 10 ** g.uniform(0, 1, (8, d))
+    good = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+    try:
+        ctx.set_options(inject_timeout=1)
+        bad = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+        st = host(bad["status"])
+    finally:
+        ctx.set_options(inject_timeout=0)
+    assert (st == -5).sum() >= 1
+    assert np.all(np.isnan(host(bad["nll"])[st == -5]))
+    ok = st == 0
+    assert np.array_equal(host(bad["nll"])[ok], host(good["nll"])[ok])
+    again = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+    assert np.all(host(again["status"]) == 0)
+    assert np.array_equal(host(again["nll"]), host(good["nll"]))
+
+
+def test_batched_split_workload_sampled():
+    """n = 2048, d = 8, T = 1024, p = 2, delta = 1e-6 in one call: a sample
+    of candidates against the oracle, all of them against the FP64 path."""
+    from paper_1203_1269_gb300 import gp
+    ctx2 = gp.Context(0)
+    w = inputs.batched_split()
+    res = ctx2.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "mixed")
+    st = host(res["status"])
+    assert np.all((st == 0) | (st == -3))
+    sample = np.linspace(0, w.T - 1, 16).astype(int)
+    ref, st_ref = oracle.nll_batch(w.x, w.y, w.thetas[sample], w.p, w.delta, want_cond=True)
+    sub = {k: v[torch.as_tensor(sample, device="cuda")] for k, v in res.items()}
+    ok, ill = check_against(ref, st_ref, sub, "n2048_T1024")
+    f64 = ctx2.nll_batch(dev(w.x), dev(w.y), dev(w.thetas), w.p, w.delta, "fp64")
+    both = (st == 0) & (host(f64["status"]) == 0)
+    rel = np.abs(host(res["nll"])[both] - host(f64["nll"])[both]) / np.abs(host(f64["nll"])[both])
+    print(f"\nn=2048 T=1024: oracle sample worst cond<=1e8 {ok:.2e}, cond>1e8 {ill:.2e}; "
+          f"vs FP64 over {both.sum()}: median {np.median(rel):.2e} max {rel.max():.2e}")
+    assert np.median(rel) <= TOL
+    ctx2.close()
