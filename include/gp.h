@@ -98,7 +98,9 @@ void gp_default_options(gp_options* opt);
  * error with *ctx = NULL. */
 int gp_create(gp_ctx** ctx, int device, size_t hbm_budget_bytes, void* cuda_stream);
 
-/* Free the context's workspace (synchronising its stream first). */
+/* Free the context's workspace and synchronise its stream.  Workspace and
+ * models come from the stream-ordered allocator (cudaMallocAsync), so a
+ * context growing its workspace does not stall contexts on other streams. */
 void gp_destroy(gp_ctx* ctx);
 
 /* Message of the last failure on this context ("" if none).  Valid until
@@ -234,8 +236,12 @@ int gp_model_scalars(const gp_model* model, double* out_host);
 int gp_predict(gp_ctx* ctx, const gp_model* model, int N, const double* xstar,
                double* yhat, double* s2);
 
-/* Release a model's device memory (synchronising the context's stream). */
+/* Release a model's device memory (stream-ordered on the context's stream,
+ * which is then synchronised). */
 void gp_model_free(gp_model* model);
+
+/* Device bytes a model holds (0 for NULL). */
+size_t gp_model_bytes(const gp_model* model);
 
 #ifdef __cplusplus
 }

@@ -116,17 +116,18 @@ int ensure_ws(gp_ctx* ctx, size_t bytes) {
     if (bytes + ctx->models_bytes > ctx->budget)
         return fail(ctx, GP_ENOMEM, "workspace of %zu bytes exceeds the HBM budget (%zu, %zu held by models)",
                     bytes, ctx->budget, ctx->models_bytes);
-    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    // stream-ordered: no device-wide synchronisation, so contexts on other
+    // streams keep running while this one grows its workspace
     if (ctx->ws) {
-        cudaFree(ctx->ws);
+        cudaFreeAsync(ctx->ws, ctx->stream);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+    cudaError_t e = cudaMallocAsync(&ctx->ws, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx->ws = nullptr;
-        return fail(ctx, GP_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return fail(ctx, GP_ENOMEM, "workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     ctx->ws_bytes = bytes;
     return GP_OK;
@@ -352,8 +353,8 @@ int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stre
 void gp_destroy(gp_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->ws) cudaFree(ctx->ws);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (auto& o : ctx->ev_open) {
         cudaEventDestroy(o.second.first);
@@ -616,11 +617,11 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
         return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
     gp_model* m = new gp_model();
     m->ctx = ctx; m->n = n; m->d = d; m->nt = nt; m->p = p; m->delta = delta; m->prec = prec;
-    cudaError_t e = cudaMalloc(&m->mem, total);
+    cudaError_t e = cudaMallocAsync(&m->mem, total, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete m;
-        return fail(ctx, GP_ENOMEM, "cudaMalloc(%zu) for the model failed", total);
+        return fail(ctx, GP_ENOMEM, "allocation of %zu bytes for the model failed", total);
     }
     m->bytes = total;
     char* c = (char*)m->mem;
@@ -633,8 +634,8 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     m->st = (gp::InstState*)c;
     ctx->models_bytes += total;
     auto bail = [&](int code) {
+        cudaFreeAsync(m->mem, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
-        cudaFree(m->mem);
         ctx->models_bytes -= m->bytes;
         delete m;
         return code;
@@ -706,11 +707,15 @@ void gp_model_free(gp_model* m) {
     if (!m) return;
     if (m->ctx) {
         cudaSetDevice(m->ctx->device);
-        cudaStreamSynchronize(m->ctx->stream);
         m->ctx->models_bytes -= m->bytes;
+        cudaFreeAsync(m->mem, m->ctx->stream);
+        cudaStreamSynchronize(m->ctx->stream);
+    } else {
+        cudaFree(m->mem);
     }
-    cudaFree(m->mem);
     delete m;
 }
+
+size_t gp_model_bytes(const gp_model* m) { return m ? m->bytes : 0; }
 
 }  // extern "C"

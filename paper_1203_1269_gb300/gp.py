@@ -85,6 +85,8 @@ def load(path=None):
     lib.gp_predict.argtypes = [P, P, _c_int, P, P, P]
     lib.gp_model_free.argtypes = [P]
     lib.gp_model_free.restype = None
+    lib.gp_model_bytes.argtypes = [P]
+    lib.gp_model_bytes.restype = _c_size
     _lib = lib
     return lib
 
@@ -131,6 +133,7 @@ class Model:
         out = (_c_double * 6)()
         ctx._lib.gp_model_scalars(handle, out)
         self.nll, self.mu, self.sigma2, self.logdet, self.Q, self.aa = list(out)
+        self.bytes = int(ctx._lib.gp_model_bytes(handle))
 
     def free(self):
         if self._h:

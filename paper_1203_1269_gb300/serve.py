@@ -1,0 +1,287 @@
+"""Continuous-batching request server over libgp.
+
+Requests are fits (the -2logL of a request's 32 theta candidates through
+gp_nll_batch, then gp_fit at the best one, whose factor stays resident on the
+device) and predictions (gp_predict against a resident fit).  Work runs on
+`workers` CUDA streams at once, one libgp context per stream, so requests of
+different n and d overlap on the GPU.  A request is admitted as soon as a
+stream is free and its device memory fits the HBM budget next to what is
+already held (workspaces of the contexts plus resident factors); otherwise it
+waits, and later requests that fit go ahead of it.  A prediction waits for
+its fit.  When resident factors would exceed the budget, the least recently
+used ones are released; a prediction against a released fit refits it at its
+chosen theta first.
+
+Every result depends only on its own request: each candidate's factorisation
+and reductions run in a fixed order whatever else shares the GPU, so results
+are identical alone and in the mix (tests/test_gpu_serve.py checks this).
+
+    python -m paper_1203_1269_gb300.serve [--requests 2000] [--rate 200]
+           [--workers 4] [--budget-gb 120] [--prec mixed]
+"""
+import argparse
+import collections
+import json
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import gp, inputs
+
+_MB = 1 << 20
+
+
+def mixed_bytes(n, T=32, slices=5):
+    """Workspace gp_nll_batch(GP_MIXED) asks for T candidates of size n."""
+    nt = (n + 127) // 128
+    tiles = nt * (nt + 1) // 2
+    a = tiles * 16384 * 8
+    per = 2 * a + nt * 7 * 16384 * 2 + nt * 128 * 4 + 7 * 16384 * 2 + 512 + 5 * nt * 128 * 8 + 256
+    return T * per + 256
+
+
+def model_bytes(n, d):
+    nt = (n + 127) // 128
+    return nt * (nt + 1) // 2 * 16384 * 8 + 2 * nt * 128 * 8 + n * d * 8 + 4096
+
+
+def predict_bytes(n, N):
+    nt = (n + 127) // 128
+    blocks = min((N + 31) // 32, 4 * 152)
+    return blocks * nt * 128 * 32 * 8
+
+
+class Result:
+    __slots__ = ("rid", "kind", "arrival", "start", "done", "theta", "nll", "mu", "sigma2",
+                 "best", "yhat", "s2", "status", "refit")
+
+    def __init__(self, rid, kind):
+        self.rid, self.kind = rid, kind
+        self.arrival = self.start = self.done = None
+        self.theta = self.nll = self.mu = self.sigma2 = self.best = None
+        self.yhat = self.s2 = None
+        self.status = None
+        self.refit = False
+
+
+class Server:
+    def __init__(self, workers=4, budget_bytes=120 * 1024 * _MB, prec="mixed", device=0, N_pred=1000):
+        self.device = device
+        self.prec = prec
+        self.budget = budget_bytes
+        self.N_pred = N_pred
+        self.lock = threading.Condition()
+        self.queue = collections.deque()
+        self.results = {}
+        self.models = collections.OrderedDict()   # rid -> (Model, theta, p, delta) in LRU order
+        self.fit_done = {}                        # rid -> threading.Event
+        self.worker_ws = [0] * workers
+        self.in_flight = [0] * workers
+        self.model_held = 0
+        self.closed = False
+        self.requests = {}                        # rid -> Request
+        self.busy = [False] * workers
+        self.ctxs = []
+        self.streams = []
+        for _ in range(workers):
+            s = torch.cuda.Stream(device=device)
+            self.streams.append(s)
+            # the server admits by its own budget; each context may size its workspace freely
+            self.ctxs.append(gp.Context(device, hbm_budget_bytes=0, stream=s))
+        self.threads = [threading.Thread(target=self._work, args=(i,), daemon=True) for i in range(workers)]
+        for t in self.threads:
+            t.start()
+
+    # -- accounting ----------------------------------------------------------
+    def _held(self):
+        return sum(self.worker_ws) + sum(self.in_flight) + self.model_held
+
+    def _need(self, req):
+        if req.kind == "fit":
+            return mixed_bytes(req.n) + model_bytes(req.n, req.d)
+        tgt = self.requests[req.target]
+        return predict_bytes(tgt.n, self.N_pred) + model_bytes(tgt.n, tgt.d)
+
+    # -- submission ----------------------------------------------------------
+    def submit(self, req):
+        with self.lock:
+            self.requests[req.rid] = req
+            r = Result(req.rid, req.kind)
+            r.arrival = time.perf_counter()
+            self.results[req.rid] = r
+            if req.kind == "fit":
+                self.fit_done[req.rid] = threading.Event()
+            self.queue.append(req)
+            self.lock.notify_all()
+
+    def _pick(self, i):
+        """Next admissible request for worker i (caller holds the lock)."""
+        for k, req in enumerate(self.queue):
+            if req.kind == "predict":
+                ev = self.fit_done.get(req.target)
+                if ev is None or not ev.is_set():
+                    continue
+            need = self._need(req)
+            held_other = self._held() - self.worker_ws[i]
+            if held_other + max(need, self.worker_ws[i]) <= self.budget or not any(self.busy):
+                del self.queue[k]
+                return req, need
+        return None, 0
+
+    def _evict_for(self, need, keep):
+        """Release least recently used factors until `need` more bytes fit."""
+        while self.models and self._held() + need > self.budget:
+            rid, entry = next(iter(self.models.items()))
+            if rid == keep:
+                break
+            self.models.pop(rid)
+            self.model_held -= entry[0].bytes
+            entry[0].free()
+
+    # -- execution -----------------------------------------------------------
+    def _work(self, i):
+        ctx, stream = self.ctxs[i], self.streams[i]
+        while True:
+            with self.lock:
+                while True:
+                    if self.closed and not self.queue:
+                        return
+                    req, need = self._pick(i)
+                    if req is not None:
+                        break
+                    self.lock.wait(timeout=0.05)
+                self.busy[i] = True
+                self.in_flight[i] = need
+                self._evict_for(0, keep=req.target if req.kind == "predict" else -1)
+            res = self.results[req.rid]
+            res.start = time.perf_counter()
+            try:
+                with torch.cuda.stream(stream):
+                    if req.kind == "fit":
+                        self._fit(ctx, req, res)
+                    else:
+                        self._predict(ctx, req, res)
+            except gp.GPError as e:
+                res.status = e.code
+            res.done = time.perf_counter()
+            with self.lock:
+                self.busy[i] = False
+                self.in_flight[i] = 0
+                self.worker_ws[i] = ctx.workspace_bytes()
+                if req.kind == "fit":
+                    self.fit_done[req.rid].set()
+                self.lock.notify_all()
+
+    def _device(self, a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).to(
+            torch.device("cuda", self.device), non_blocking=False)
+
+    def _fit(self, ctx, req, res):
+        x, y, th, _ = inputs.request_data(req, self.N_pred)
+        xd, yd, thd = self._device(x), self._device(y), self._device(th)
+        out = ctx.nll_batch(xd, yd, thd, req.p, req.delta, self.prec)
+        nll = out["nll"].cpu().numpy()
+        st = out["status"].cpu().numpy()
+        ok = np.where(st == 0)[0]
+        res.nll = nll
+        res.status = int(0 if ok.size else st[0])
+        if not ok.size:
+            return
+        best = int(ok[np.argmin(nll[ok])])
+        res.best, res.theta = best, th[best]
+        model = ctx.fit(xd, yd, thd[best].contiguous(), req.p, req.delta, "fp64")
+        res.mu, res.sigma2 = model.mu, model.sigma2
+        with self.lock:
+            self._evict_for(model.bytes, keep=req.rid)
+            self.models[req.rid] = (model, th[best], req.p, req.delta)
+            self.model_held += model.bytes
+
+    def _predict(self, ctx, req, res):
+        fit = self.results[req.target]
+        src = self.requests[req.target]
+        with self.lock:
+            entry = self.models.get(req.target)
+            if entry is not None:
+                self.models.move_to_end(req.target)
+        if fit.theta is None:
+            res.status = fit.status if fit.status is not None else gp.GP_EINVAL
+            return
+        if entry is None:
+            # released: refit at the chosen theta (same factor, same result)
+            x, y, _, _ = inputs.request_data(src, self.N_pred)
+            model = ctx.fit(self._device(x), self._device(y), self._device(fit.theta), src.p, src.delta, "fp64")
+            res.refit = True
+            with self.lock:
+                self._evict_for(model.bytes, keep=req.target)
+                entry = (model, fit.theta, src.p, src.delta)
+                self.models[req.target] = entry
+                self.model_held += model.bytes
+        model = entry[0]
+        xs = inputs.uniform_design(inputs.rng(req.seed), self.N_pred, src.d)
+        yhat, s2 = ctx.predict(model, self._device(xs))
+        res.yhat = yhat.cpu().numpy()
+        res.s2 = s2.cpu().numpy()
+        res.status = 0
+
+    # -- driving a trace -----------------------------------------------------
+    def run(self, requests, realtime=True):
+        """Replay `requests` (arrival times in seconds) and wait for all of them."""
+        t0 = time.perf_counter()
+        for req in requests:
+            if realtime:
+                delay = t0 + req.arrival_s - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            self.submit(req)
+        with self.lock:
+            self.closed = True
+            self.lock.notify_all()
+        for t in self.threads:
+            t.join()
+        torch.cuda.synchronize(self.device)
+        return self.results
+
+    def close(self):
+        for m in list(self.models.values()):
+            m[0].free()
+        self.models.clear()
+        for c in self.ctxs:
+            c.close()
+
+
+def summarize(results, requests):
+    lat = np.array([r.done - r.arrival for r in results.values() if r.done is not None])
+    span = max(r.done for r in results.values()) - min(r.arrival for r in results.values())
+    fits = [r for r in results.values() if r.kind == "fit"]
+    evals = sum(len(r.nll) for r in fits if r.nll is not None)
+    return {"requests": len(results), "seconds": span, "req_per_s": len(results) / span,
+            "evals_per_s": evals / span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "mean": float(lat.mean() * 1e3)},
+            "refits": sum(r.refit for r in results.values()),
+            "failed": sum(1 for r in results.values() if r.status not in (0, None))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    args = ap.parse_args()
+    reqs = inputs.serving_stream(count=args.requests, rate=args.rate)
+    srv = Server(workers=args.workers, budget_bytes=int(args.budget_gb * (1 << 30)), prec=args.prec)
+    res = srv.run(reqs)
+    out = summarize(res, reqs)
+    out.update({"workload": f"serving stream, {args.requests} requests, Poisson {args.rate}/s, "
+                            "n log-uniform [256, 8192], d 2..12",
+                "workers": args.workers, "prec": args.prec, "budget_gb": args.budget_gb})
+    srv.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
