@@ -87,6 +87,10 @@ typedef struct {
                              a barrier nothing signals, gives up, and the instances it
                              would have updated come back GP_ETIMEOUT (the bounded-wait
                              failure path, exercised without faulting the GPU) */
+    int fuse_panels;      /* GP_MIXED, default 1: panels are factored in pairs with a
+                             one-panel look-ahead and both applied to the trailing tiles
+                             in one 256-wide pass (half the passes over the trailing
+                             matrix); 0: one pass per panel.  Needs update_groups = 4 */
 } gp_options;
 
 void gp_default_options(gp_options* opt);

@@ -164,7 +164,7 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
 
 // Bytes of workspace per instance of the split-precision path.
 struct MixedSizes {
-    size_t A, PS, PE, WS, WE, Z, st, per;
+    size_t A, PS, PE, WS, WE, PF, FE, Z, st, per;
 };
 
 MixedSizes mixed_sizes(int n, int s) {
@@ -177,9 +177,11 @@ MixedSizes mixed_sizes(int n, int s) {
     z.PE = align256((size_t)nt * GP_NB * sizeof(int));
     z.WS = align256((size_t)ps * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
     z.WE = align256((size_t)GP_NB * sizeof(int));
+    z.PF = align256((size_t)nt * s * 2 * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
+    z.FE = align256((size_t)nt * GP_NB * sizeof(int));
     z.Z = align256((size_t)5 * nt * GP_NB * sizeof(float2));
     z.st = align256(sizeof(gp::InstState));
-    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.Z + z.st;
+    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + z.Z + z.st;
     return z;
 }
 
@@ -194,6 +196,8 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.PE = (int*)c; c += z.PE * Tc;
     mb.WS = (__nv_bfloat16*)c; c += z.WS * Tc;
     mb.WE = (int*)c; c += z.WE * Tc;
+    mb.PF = (__nv_bfloat16*)c; c += z.PF * Tc;
+    mb.FE = (int*)c; c += z.FE * Tc;
     mb.Z = (float2*)c; c += z.Z * Tc;
     mb.st = (gp::InstState*)c; c += z.st * Tc;
     mb.err = (int*)c;
@@ -207,6 +211,9 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.pe_stride = z.PE / sizeof(int);
     mb.ws_stride = z.WS / sizeof(__nv_bfloat16);
     mb.we_stride = z.WE / sizeof(int);
+    mb.pf_stride = z.PF / sizeof(__nv_bfloat16);
+    mb.fe_stride = z.FE / sizeof(int);
+    mb.fuse = ctx->opt.fuse_panels;
     mb.z_stride = z.Z / sizeof(float2);
     mb.y = y;
     return mb;
@@ -227,27 +234,56 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
         GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
     }
     const int nt = mb.nt;
-    for (int J = 0; J < nt; ++J) {
-        {
-            PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
-            GP_CUDA(ctx, gp::launch_diag_mixed(mb, J, ctx->stream));
-        }
-        if (J + 1 == nt) break;
+    auto diag = [&](int J) -> int {
+        PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
+        GP_CUDA(ctx, gp::launch_diag_mixed(mb, J, ctx->stream));
+        return GP_OK;
+    };
+    auto panel = [&](int J) -> int {
         {
             PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
             GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, ctx->stream));
         }
-        {
-            PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
-            GP_CUDA(ctx, gp::launch_gemm_panel(mb, J, ctx->stream));
-        }
+        PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
+        GP_CUDA(ctx, gp::launch_gemm_panel(mb, J, ctx->stream));
+        return GP_OK;
+    };
+    int J = 0;
+    while (J < nt) {
+        int rc = diag(J);
+        if (rc) return rc;
+        if (J + 1 == nt) break;
+        rc = panel(J);
+        if (rc) return rc;
         {
             PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
             GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.s, ctx->stream));
         }
-        {
+        if (mb.fuse && J + 2 < nt) {
+            // panel pair (J, J + 1): update column J + 1 from panel J, factor and
+            // solve panel J + 1, then apply both panels to the trailing tiles in
+            // one K = 256 pass
+            {
+                PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+                GP_CUDA(ctx, gp::launch_gemm_update_column(mb, J, ctx->stream));
+            }
+            rc = diag(J + 1);
+            if (rc) return rc;
+            rc = panel(J + 1);
+            if (rc) return rc;
+            {
+                PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
+                GP_CUDA(ctx, gp::launch_split_fused(mb, J, ctx->stream));
+            }
+            {
+                PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+                GP_CUDA(ctx, gp::launch_gemm_update_fused(mb, J, ctx->stream));
+            }
+            J += 2;
+        } else {
             PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
             GP_CUDA(ctx, gp::launch_gemm_update(mb, J, ctx->stream));
+            J += 1;
         }
     }
     return GP_OK;
@@ -324,6 +360,7 @@ void gp_default_options(gp_options* opt) {
     opt->max_batch = 0;
     opt->update_groups = 4;
     opt->inject_timeout = 0;
+    opt->fuse_panels = 1;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -382,6 +419,8 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
     if (opt->max_batch < 0) return fail(ctx, GP_EINVAL, "max_batch must be >= 0");
     if (opt->update_groups != 3 && opt->update_groups != 4 && opt->update_groups != 7)
         return fail(ctx, GP_EINVAL, "update_groups must be 3, 4 or 7");
+    if (opt->fuse_panels && opt->update_groups != 4)
+        return fail(ctx, GP_EINVAL, "fuse_panels needs update_groups = 4");
     ctx->opt = *opt;
     return GP_OK;
 }

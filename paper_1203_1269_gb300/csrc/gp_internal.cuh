@@ -90,6 +90,10 @@ struct MixedBatch {
     int* PE;                      // panel row exponents: [row block][128]
     __nv_bfloat16* WS;            // slices of W's rows: [slice][4 chunks][128 x 32]
     int* WE;                      // [128]
+    __nv_bfloat16* PF;            // two-panel slices for the fused update: [row block][slice][8 chunks][128 x 32]
+    int* FE;                      // their row exponents: [row block][128]
+    size_t pf_stride, fe_stride;
+    int fuse;                     // 1: trailing updates of panel pairs fused (K = 256)
     size_t ps_stride, pe_stride, ws_stride, we_stride;
     float2* Z;                    // 5 columns of npad double-float values (x_1, x_y, two
                                   // residual columns, 1 / L_ii)
@@ -129,6 +133,9 @@ cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s);
 cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s);
+cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s);
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s);
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s);

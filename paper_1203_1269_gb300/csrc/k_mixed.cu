@@ -187,6 +187,14 @@ __device__ __forceinline__ int* pe_block(const MixedBatch& b, int t, int I) {
     return b.PE + (size_t)t * b.pe_stride + (size_t)I * GP_NB;
 }
 
+// slices of row block I over two panels (256 columns): [slice][8 chunks][128 x 32]
+__device__ __forceinline__ __nv_bfloat16* pf_block(const MixedBatch& b, int t, int I) {
+    return b.PF + (size_t)t * b.pf_stride + (size_t)I * b.s * 2 * kChunks * kChunkElems;
+}
+__device__ __forceinline__ int* fe_block(const MixedBatch& b, int t, int I) {
+    return b.FE + (size_t)t * b.fe_stride + (size_t)I * GP_NB;
+}
+
 // byte offset of the 16-byte piece holding columns k0..k0+7 (k0 % 8 == 0)
 // of row r inside a 128 x 32 chunk with 64-byte swizzle
 __device__ __forceinline__ uint32_t image_piece(int r, int k0) {
@@ -434,6 +442,76 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
     }
 }
 
+// Slices of two adjacent panels at once, for the fused (K = 256) trailing
+// update: row r of row block I = J + 2 + blockIdx.x spans tiles (I, J) and
+// (I, J + 1) and gets one exponent for all 256 columns, so the products of
+// both panels accumulate in the same tensor-memory groups.  Thread (r, q)
+// owns image chunk q of each panel; the row maximum is taken in a first pass
+// and the values are read again for slicing.
+__global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int J) {
+    __shared__ float pmax[4][GP_NB];
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int I = J + 2 + blockIdx.x;
+    const int r = threadIdx.x & 127, q = threadIdx.x >> 7;
+    const float2* src0 = df_tile(b, b.A, t, I, J);
+    const float2* src1 = df_tile(b, b.A, t, I, J + 1);
+    float mx = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+        mx = fmaxf(mx, fabsf(src0[(32 * q + j) * GP_NB + r].x));
+        mx = fmaxf(mx, fabsf(src1[(32 * q + j) * GP_NB + r].x));
+    }
+    pmax[q][r] = mx;
+    __syncthreads();
+    mx = fmaxf(fmaxf(pmax[0][r], pmax[1][r]), fmaxf(pmax[2][r], pmax[3][r]));
+    const int E = exponent_of(mx);
+    if (q == 0) fe_block(b, t, I)[r] = E;
+    const int e2 = 7 - E;
+    const int ea = e2 > 127 ? 127 : (e2 < -126 ? -126 : e2);
+    const int eb = e2 - ea;
+    const float sa = __int_as_float((ea + 127) << 23);
+    const float sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
+    for (int half = 0; half < 2; ++half) {
+        const float2* src = half ? src1 : src0;
+        float2 v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
+        uint8_t* chunk0 = reinterpret_cast<uint8_t*>(pf_block(b, t, I) + (size_t)(4 * half + q) * kChunkElems);
+#pragma unroll
+        for (int pc = 0; pc < 4; ++pc) {
+            float xh[8], xl[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                xh[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].x, sa), sb);
+                xl[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].y, sa), sb);
+            }
+            const uint32_t off = image_piece(r, 8 * pc);
+            float w = 1.f;
+#pragma unroll
+            for (int a = 0; a < GP_MAX_SLICES; ++a) {
+                if (a >= b.s) break;
+                float m[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float qv = rintf(xh[e]);
+                    m[e] = __fmul_rn(qv, w);
+                    two_sum(__fsub_rn(xh[e], qv), xl[e], xh[e], xl[e]);
+                    xh[e] = __fmul_rn(xh[e], 256.f);
+                    xl[e] = __fmul_rn(xl[e], 256.f);
+                }
+                w = __fmul_rn(w, 0.00390625f);
+                uint4 u;
+                u.x = pack_bf16x2(m[0], m[1]);
+                u.y = pack_bf16x2(m[2], m[3]);
+                u.z = pack_bf16x2(m[4], m[5]);
+                u.w = pack_bf16x2(m[6], m[7]);
+                *reinterpret_cast<uint4*>(chunk0 + (size_t)a * 2 * kChunks * kChunkBytes + off) = u;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
@@ -460,7 +538,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // half of the columns, with the loads of a column block issued together).  Every wait is bounded; a timeout marks the instance
 // GP_ETIMEOUT and stops the CTA after its copies and MMAs have landed.
 template <int MODE, int NT, int NG>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst) {
+__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
     static_assert(NG * NT <= 512, "accumulators exceed tensor memory");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -473,7 +551,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
+    // kind (MODE 1): 0 trailing tiles from J + 1 (K = 128), 1 the single
+    // column J + 1 (look-ahead, K = 128), 2 trailing tiles from J + 2 with
+    // the two panels J, J + 1 fused (K = 256)
     const int ns = (MODE == 0) ? b.ps : b.s;
+    const bool fused = (MODE == 1 && kind == 2);
+    const int nch = fused ? 2 * kChunks : kChunks;
     constexpr uint32_t kBBytes = kChunkBytes / (GP_NB / NT);      // B rows col0..col0+NT of a chunk
     const uint32_t a_bytes = (uint32_t)ns * kChunkBytes;
     const uint32_t stage_bytes = a_bytes + (uint32_t)ns * kBBytes;
@@ -489,11 +572,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
         if (MODE == 0) {
             I = J + 1 + tile;
             K = J;
+        } else if (kind == 1) {
+            I = J + 1 + tile;
+            K = J + 1;
         } else {
             int ii, kk;
             tri_decode(tile, ii, kk);
-            I = J + 1 + ii;
-            K = J + 1 + kk;
+            const int base = (kind == 2) ? J + 2 : J + 1;
+            I = base + ii;
+            K = base + kk;
         }
     };
 
@@ -526,11 +613,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 int t, I, K, col0;
                 decode(w, t, I, K, col0);
                 if (b.st[t].status != GP_OK) continue;
-                const __nv_bfloat16* gA = ps_block(b, t, I);
-                const uint8_t* gB = reinterpret_cast<const uint8_t*>((MODE == 0) ? (b.WS + (size_t)t * b.ws_stride)
-                                                                                  : ps_block(b, t, K)) +
-                                    (size_t)col0 * 64;   // 64 bytes per row inside a chunk
-                for (int kc = 0; kc < kChunks; ++kc, ++g) {
+                const __nv_bfloat16* gA = fused ? pf_block(b, t, I) : ps_block(b, t, I);
+                const __nv_bfloat16* gBb = (MODE == 0) ? (b.WS + (size_t)t * b.ws_stride)
+                                                       : (fused ? pf_block(b, t, K) : ps_block(b, t, K));
+                const uint8_t* gB = reinterpret_cast<const uint8_t*>(gBb) + (size_t)col0 * 64;   // 64 B per row in a chunk
+                for (int kc = 0; kc < nch; ++kc, ++g) {
                     const int st = g & 1;
                     if (g >= 2 && !mbar_wait(&empty_bar[st], ((g >> 1) - 1) & 1, &abort_flag)) {
                         abort_flag = 1;
@@ -540,10 +627,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                     uint8_t* sb = sa + a_bytes;
                     mbar_expect_tx(&full_bar[st], stage_bytes);
                     for (int a = 0; a < ns; ++a)
-                        bulk_g2s(sa + a * kChunkBytes, gA + (size_t)(a * kChunks + kc) * kChunkElems, kChunkBytes,
+                        bulk_g2s(sa + a * kChunkBytes, gA + (size_t)(a * nch + kc) * kChunkElems, kChunkBytes,
                                  &full_bar[st]);
                     for (int a = 0; a < ns; ++a)
-                        bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * kChunks + kc) * kChunkBytes, kBBytes,
+                        bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * nch + kc) * kChunkBytes, kBBytes,
                                  &full_bar[st]);
                 }
             }
@@ -569,7 +656,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 }
                 tc_fence_after();
                 uint32_t started = 0;
-                for (int kc = 0; kc < kChunks; ++kc, ++g) {
+                for (int kc = 0; kc < nch; ++kc, ++g) {
                     const int st = g & 1;
                     if (!mbar_wait(&full_bar[st], (g >> 1) & 1, &abort_flag)) {
                         abort_flag = 1;
@@ -620,8 +707,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 break;
             }
             tc_fence_after();
-            const int* eAp = pe_block(b, t, I);
-            const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride) : pe_block(b, t, K)) + col0;
+            const int* eAp = fused ? fe_block(b, t, I) : pe_block(b, t, I);
+            const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride)
+                                          : (fused ? fe_block(b, t, K) : pe_block(b, t, K))) + col0;
             const int eA = eAp[r];
             for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += CB) {
                 float2 cv[CB];
@@ -1097,7 +1185,7 @@ static int sm_count() {
 }
 
 template <int MODE, int NT, int NG>
-static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s) {
+static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s, int kind = 0) {
     const size_t smem = (size_t)2 * ns * (kChunkBytes + kChunkBytes / (GP_NB / NT)) + 1024;
     static size_t attr = 0;
     if (smem > attr) {
@@ -1108,7 +1196,7 @@ static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns,
     }
     const long long total = (long long)per_inst * b.count;
     const int grid = (int)(total < sm_count() ? total : sm_count());
-    k_split_gemm<MODE, NT, NG><<<grid, kGemmThreads, smem, s>>>(b, J, per_inst);
+    k_split_gemm<MODE, NT, NG><<<grid, kGemmThreads, smem, s>>>(b, J, per_inst, kind);
     return cudaGetLastError();
 }
 
@@ -1116,6 +1204,25 @@ cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
     return launch_gemm<0, 64, GP_PANEL_SLICES>(b, J, 2 * m, b.ps, s);
+}
+
+cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s) {
+    const int m = b.nt - J - 1;
+    if (m <= 0) return cudaSuccess;
+    return launch_gemm<1, 128, 4>(b, J, m, b.s, s, 1);
+}
+
+cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s) {
+    const int m = b.nt - J - 2;
+    if (m <= 0) return cudaSuccess;
+    return launch_gemm<1, 128, 4>(b, J, m * (m + 1) / 2, b.s, s, 2);
+}
+
+cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s) {
+    const int m = b.nt - J - 2;
+    if (m <= 0) return cudaSuccess;
+    k_split_fused<<<dim3(m, b.count), kSplitThreads, 0, s>>>(b, J);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {

@@ -35,7 +35,7 @@ class GPError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
                 ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int),
-                ("inject_timeout", _c_int)]
+                ("inject_timeout", _c_int), ("fuse_panels", _c_int)]
 
 
 _lib = None

@@ -257,3 +257,24 @@ def test_batched_split_workload_sampled():
           f"vs FP64 over {both.sum()}: median {np.median(rel):.2e} max {rel.max():.2e}")
     assert np.median(rel) <= TOL
     ctx2.close()
+
+
+def test_fused_panel_pairs_match_single_panels(ctx):
+    """The fused two-panel update (default) and one pass per panel give the
+    same -2logL to the split path's tolerance, and both match the oracle."""
+    g = np.random.default_rng(91)
+    n, d = 777, 4          # nt = 7: three pairs, then an odd final panel
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 6, d, lo=-0.5, hi=1.0)
+    ref, st = oracle.nll_batch(x, y, th, 1.95, 1e-6, want_cond=True)
+    fused = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+    try:
+        ctx.set_options(fuse_panels=0)
+        single = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, "mixed")
+    finally:
+        ctx.set_options(fuse_panels=1)
+    check_against(ref, st, fused, "fused")
+    check_against(ref, st, single, "single")
+    a, b = host(fused["nll"]), host(single["nll"])
+    assert np.max(np.abs(a - b) / np.abs(b)) <= TOL
