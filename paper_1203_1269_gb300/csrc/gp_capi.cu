@@ -164,7 +164,7 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
 
 // Bytes of workspace per instance of the split-precision path.
 struct MixedSizes {
-    size_t A, PS, PE, WS, WE, PF, FE, Z, st, per;
+    size_t A, PS, PE, WS, WE, PF, FE, WT, Z, st, per;
 };
 
 MixedSizes mixed_sizes(int n, int s) {
@@ -179,9 +179,10 @@ MixedSizes mixed_sizes(int n, int s) {
     z.WE = align256((size_t)GP_NB * sizeof(int));
     z.PF = align256((size_t)nt * s * 2 * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
     z.FE = align256((size_t)nt * GP_NB * sizeof(int));
+    z.WT = align256((size_t)nt * GP_TILE_ELEMS * sizeof(float2));
     z.Z = align256((size_t)5 * nt * GP_NB * sizeof(float2));
     z.st = align256(sizeof(gp::InstState));
-    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + z.Z + z.st;
+    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + z.WT + z.Z + z.st;
     return z;
 }
 
@@ -198,6 +199,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.WE = (int*)c; c += z.WE * Tc;
     mb.PF = (__nv_bfloat16*)c; c += z.PF * Tc;
     mb.FE = (int*)c; c += z.FE * Tc;
+    mb.WT = (float2*)c; c += z.WT * Tc;
     mb.Z = (float2*)c; c += z.Z * Tc;
     mb.st = (gp::InstState*)c; c += z.st * Tc;
     mb.err = (int*)c;
@@ -213,6 +215,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.we_stride = z.WE / sizeof(int);
     mb.pf_stride = z.PF / sizeof(__nv_bfloat16);
     mb.fe_stride = z.FE / sizeof(int);
+    mb.wt_stride = z.WT / sizeof(float2);
     mb.fuse = ctx->opt.fuse_panels;
     mb.z_stride = z.Z / sizeof(float2);
     mb.y = y;

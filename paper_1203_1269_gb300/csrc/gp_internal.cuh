@@ -94,6 +94,8 @@ struct MixedBatch {
     int* FE;                      // their row exponents: [row block][128]
     size_t pf_stride, fe_stride;
     int fuse;                     // 1: trailing updates of panel pairs fused (K = 256)
+    float2* WT;                   // L_JJ^-1 per diagonal block, double-float tiles: [J][128 x 128]
+    size_t wt_stride;
     size_t ps_stride, pe_stride, ws_stride, we_stride;
     float2* Z;                    // 5 columns of npad double-float values (x_1, x_y, two
                                   // residual columns, 1 / L_ii)

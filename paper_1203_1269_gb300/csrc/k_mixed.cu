@@ -333,6 +333,20 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         if (threadIdx.x <= i) P[prow(i) + threadIdx.x] = rowtmp[threadIdx.x];
         __syncthreads();
     }
+    // W as a double-float tile (column-major, zeros above the diagonal) for
+    // the diagonal-block products of the solves
+    {
+        float2* Wt = b.WT + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
+        for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
+            const int rr = q & 127, cc = q >> 7;
+            float2 v = make_float2(0.f, 0.f);
+            if (rr >= cc) {
+                const dfl d = df_from_double(P[prow(rr) + cc]);
+                v = make_float2(d.hi, d.lo);
+            }
+            Wt[q] = v;
+        }
+    }
     // row c of W: exponent and slices; one warp per row
     __nv_bfloat16* WS = b.WS + (size_t)t * b.ws_stride;
     int* WE = b.WE + (size_t)t * b.we_stride;
@@ -850,7 +864,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int 
     const int nt = b.nt, n = b.n;
     float2* z0 = zcol(b, t, c0);
     float2* z1 = zcol(b, t, c0 + 1);
-    const float2* rinv = zcol(b, t, 4);
     const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
     for (int I = 0; I < nt; ++I) {
         const int gi = I * GP_NB + r;
@@ -891,26 +904,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int 
             rhs[k][r] = df_sub(bk, sm);
         }
         __syncthreads();
-        const float2* D = df_tile(b, b.A, t, I, I);
-        for (int c = 0; c < GP_NB; ++c) {
-            const dfl ri = df_load(rinv + I * GP_NB + c);
-            const dfl x0 = df_mul(rhs[0][c], ri);
-            const dfl x1 = df_mul(rhs[1][c], ri);
-            __syncthreads();
-            if (threadIdx.x < GP_NB && r > c) {
-                const float2 lv = __ldg(D + c * GP_NB + r);
-                const dfl l = {lv.x, lv.y};
-                rhs[0][r] = df_fms(l, x0, rhs[0][r]);
-                rhs[1][r] = df_fms(l, x1, rhs[1][r]);
-            } else if (threadIdx.x == c) {
-                rhs[0][c] = x0;
-                rhs[1][c] = x1;
+        // x_I = W_I rhs_I with W_I = L_II^-1 (lower): thread (r, h) sums columns
+        // c <= r of its parity classes, four chains
+        {
+            const float2* W = b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS;
+            dfl s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
+#pragma unroll 4
+            for (int c = h; c < GP_NB; c += 8) {
+                const float2 u = __ldg(W + c * GP_NB + r);
+                const float2 v = __ldg(W + (c + 4) * GP_NB + r);
+                const dfl w0 = {u.x, u.y}, w1 = {v.x, v.y};
+                s00 = df_fma(w0, rhs[0][c], s00);
+                s01 = df_fma(w1, rhs[0][c + 4], s01);
+                s10 = df_fma(w0, rhs[1][c], s10);
+                s11 = df_fma(w1, rhs[1][c + 4], s11);
             }
-            __syncthreads();
+            part[h][0][r] = df_add(s00, s01);
+            part[h][1][r] = df_add(s10, s11);
         }
+        __syncthreads();
         if (threadIdx.x < 2 * GP_NB) {
             const int k = threadIdx.x >> 7;
-            df_store((k ? z1 : z0) + gi, rhs[k][r]);
+            const dfl x = df_add(df_add(part[0][k][r], part[1][k][r]), df_add(part[2][k][r], part[3][k][r]));
+            df_store((k ? z1 : z0) + gi, x);
         }
         __syncthreads();
     }
@@ -929,7 +945,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int
     const int nt = b.nt;
     float2* z0 = zcol(b, t, c0);
     float2* z1 = zcol(b, t, c0 + 1);
-    const float2* rinv = zcol(b, t, 4);
     const int c = threadIdx.x & 127, h = threadIdx.x >> 7;
     for (int I = nt - 1; I >= 0; --I) {
         if (threadIdx.x < 2 * GP_NB) {
@@ -958,35 +973,35 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int
         part[h][0][c] = df_add(a00, a01);
         part[h][1][c] = df_add(a10, a11);
         __syncthreads();
-        stage_tile(df_tile(b, b.A, t, I, I), T);   // diagonal tile for the triangular solve
+        // W_I = L_II^-1 staged; w_I = W_I^T rhs: w[c] = sum_k W(k, c) rhs[k] = sum_k T[c][k] rhs[k]
+        stage_tile(b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS, T);
         if (threadIdx.x < 2 * GP_NB) {
             const int k = threadIdx.x >> 7;
             const dfl sm = df_add(df_add(part[0][k][c], part[1][k][c]), df_add(part[2][k][c], part[3][k][c]));
             rhs[k][c] = df_sub(rhs[k][c], sm);
         }
         __syncthreads();
-        // L_II^T w = rhs from the bottom; L_II(c', r) = T[r][c']
-        for (int cc = GP_NB - 1; cc >= 0; --cc) {
-            const dfl ri = df_load(rinv + I * GP_NB + cc);
-            const dfl x0 = df_mul(rhs[0][cc], ri);
-            const dfl x1 = df_mul(rhs[1][cc], ri);
-            __syncthreads();
-            if (threadIdx.x < cc) {
-                const dfl l = T[threadIdx.x * kTs + cc];
-                rhs[0][threadIdx.x] = df_fms(l, x0, rhs[0][threadIdx.x]);
-                rhs[1][threadIdx.x] = df_fms(l, x1, rhs[1][threadIdx.x]);
-            } else if (threadIdx.x == cc) {
-                rhs[0][cc] = x0;
-                rhs[1][cc] = x1;
+        {
+            const dfl* row = T + c * kTs + 32 * h;
+            dfl s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
+#pragma unroll 4
+            for (int k = 0; k < 32; k += 2) {
+                s00 = df_fma(row[k], rhs[0][32 * h + k], s00);
+                s01 = df_fma(row[k + 1], rhs[0][32 * h + k + 1], s01);
+                s10 = df_fma(row[k], rhs[1][32 * h + k], s10);
+                s11 = df_fma(row[k + 1], rhs[1][32 * h + k + 1], s11);
             }
-            __syncthreads();
+            part[h][0][c] = df_add(s00, s01);
+            part[h][1][c] = df_add(s10, s11);
         }
+        __syncthreads();
         if (threadIdx.x < 2 * GP_NB) {
             const int k = threadIdx.x >> 7;
-            df_store((k ? z1 : z0) + I * GP_NB + c, rhs[k][c]);
+            const dfl x = df_add(df_add(part[0][k][c], part[1][k][c]), df_add(part[2][k][c], part[3][k][c]));
+            df_store((k ? z1 : z0) + I * GP_NB + c, x);
             if (add_to >= 0) {
                 float2* acc = zcol(b, t, add_to + k) + I * GP_NB + c;
-                df_store(acc, df_add(df_load(acc), rhs[k][c]));
+                df_store(acc, df_add(df_load(acc), x));
             }
         }
         __syncthreads();

@@ -39,7 +39,7 @@ def mixed_bytes(n, T=32, slices=5):
     tiles = nt * (nt + 1) // 2
     a = tiles * 16384 * 8
     per = (2 * a + nt * 7 * 16384 * 2 + nt * 128 * 4 + 7 * 16384 * 2 + 512 + nt * slices * 2 * 16384 * 2
-           + nt * 128 * 4 + 5 * nt * 128 * 8 + 256)
+           + nt * 128 * 4 + nt * 16384 * 8 + 5 * nt * 128 * 8 + 256)
     return T * per + 256
 
 
