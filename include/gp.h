@@ -220,8 +220,9 @@ int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, const doubl
  * device what prediction needs.  The fit is always factored in IEEE double
  * whatever `prec` asks (any gp_precision value is accepted): a fit is one
  * factorisation, and the kriging variance needs r'R^-1 r to full precision.
- * Kept on the device: the factor L, w = R^-1 (Y - 1 mu_hat), a = L^-1 1, a
- * copy of x, and the scalars.  Synchronises.  On GP_OK,
+ * Kept on the device: the factor L, w = R^-1 (Y - 1 mu_hat), a = L^-1 1 and a
+ * copy of x, converted after the solves to double-float pairs (hi + lo floats,
+ * ~48 bits) for the kriging kernel, and the scalars.  Synchronises.  On GP_OK,
  * *model owns that device memory until gp_model_free.  A fit whose R is
  * not positive definite returns GP_ENOTPD and no model. */
 int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y,
@@ -241,7 +242,8 @@ int gp_predict(gp_ctx* ctx, const gp_model* model, int N, const double* xstar,
                double* yhat, double* s2);
 
 /* Release a model's device memory (stream-ordered on the context's stream,
- * which is then synchronised). */
+ * which is then synchronised).  A model may outlive its context: gp_destroy
+ * detaches it, and gp_model_free then releases it synchronously. */
 void gp_model_free(gp_model* model);
 
 /* Device bytes a model holds (0 for NULL). */

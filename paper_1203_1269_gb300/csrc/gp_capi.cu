@@ -25,6 +25,7 @@ struct gp_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
     double phase_ms[GP_NUM_PHASES] = {0};
+    std::vector<gp_model*> models;   // live models (detached when the context goes first)
     long long phase_launches[GP_NUM_PHASES] = {0};
     long long launches = 0;
 };
@@ -393,6 +394,9 @@ int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stre
 void gp_destroy(gp_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    // models outlive their context safely: they are detached and freed on
+    // their own later (synchronously)
+    for (gp_model* m : ctx->models) m->ctx = nullptr;
     if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -704,6 +708,11 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
         gp::launch_fit_finish(b, m->Z, (size_t)2 * npad, m->scalars, ctx->stream) ||
         gp::launch_backward_solve(b, m->Z, (size_t)2 * npad, 1, ctx->stream))
         return bail(fail(ctx, GP_ECUDA, "solve launch failed"));
+    // the kriging kernel reads the factor, [a | w] and x as double-float pairs
+    if (gp::launch_to_df_inplace(m->L, gp::packed_elems(n), ctx->stream) ||
+        gp::launch_to_df_inplace(m->Z, (size_t)2 * npad, ctx->stream) ||
+        gp::launch_to_df_inplace(m->x, (size_t)n * d, ctx->stream))
+        return bail(fail(ctx, GP_ECUDA, "model conversion launch failed"));
     int hstatus = 0;
     e = cudaMemcpyAsync(&hstatus, m->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess)
@@ -713,6 +722,7 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     if (e != cudaSuccess) return bail(fail(ctx, GP_ECUDA, "fit: %s", cudaGetErrorString(e)));
     if (hstatus == GP_ENOTPD || hstatus == GP_EINVAL)
         return bail(fail(ctx, hstatus, "fit failed with status %d", hstatus));
+    ctx->models.push_back(m);
     *model = m;
     return hstatus;  // GP_OK or GP_EDEGENERATE (model still usable for the mean)
 }
@@ -730,18 +740,21 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int npad = m->nt * GP_NB;
-    const size_t per_cta = (size_t)npad * 32 * sizeof(double);
-    const int blocks_total = (N + 31) / 32;
+    const size_t per_cta = gp::predict_work_per_cta(m->nt);
+    const int ppc = gp::predict_points_per_cta();
+    const int blocks_total = (N + ppc - 1) / ppc;
     int chunk = blocks_total < 4 * 152 ? blocks_total : 4 * 152;
     size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
     while (chunk > 1 && per_cta * chunk > avail) chunk /= 2;
     int rc = ensure_ws(ctx, s2 ? per_cta * chunk : 256);
     if (rc) return rc;
     const double c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
-    PhaseScope ps(ctx, GP_PHASE_PREDICT, (N + 32 * chunk - 1) / (32 * chunk));
-    GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, m->x, m->theta, m->p, c0, m->L,
-                                    m->Z + npad, m->Z, m->scalars, N, xstar, yhat, s2,
-                                    (double*)ctx->ws, chunk, ctx->stream));
+    const float2* Ldf = reinterpret_cast<const float2*>(m->L);
+    const float2* Zdf = reinterpret_cast<const float2*>(m->Z);
+    PhaseScope ps(ctx, GP_PHASE_PREDICT, (blocks_total + chunk - 1) / chunk);
+    GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, reinterpret_cast<const float2*>(m->x), m->theta, m->p,
+                                    c0, Ldf, Zdf + npad, Zdf, m->scalars, N, xstar, yhat, s2,
+                                    (float2*)ctx->ws, chunk, ctx->stream));
     return GP_OK;
 }
 
@@ -750,6 +763,13 @@ void gp_model_free(gp_model* m) {
     if (m->ctx) {
         cudaSetDevice(m->ctx->device);
         m->ctx->models_bytes -= m->bytes;
+        auto& v = m->ctx->models;
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i] == m) {
+                v[i] = v.back();
+                v.pop_back();
+                break;
+            }
         cudaFreeAsync(m->mem, m->ctx->stream);
         cudaStreamSynchronize(m->ctx->stream);
     } else {

@@ -126,10 +126,12 @@ cudaError_t launch_fit_finish(const Batch& b, double* Z, size_t z_stride, double
                               cudaStream_t s);
 cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t z_stride, int col,
                                   cudaStream_t s);
-cudaError_t launch_predict(int n, int d, int nt, const double* x, const double* theta, double p,
-                           double c0, const double* L, const double* w, const double* a,
-                           const double* scalars, int N, const double* xs, double* yhat,
-                           double* s2, double* work, int chunk, cudaStream_t s);
+cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, double c0,
+                           const float2* L, const float2* w, const float2* a, const double* scalars, int N,
+                           const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s);
+cudaError_t launch_to_df_inplace(double* p, size_t count, cudaStream_t s);
+size_t predict_work_per_cta(int nt);
+int predict_points_per_cta();
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s);

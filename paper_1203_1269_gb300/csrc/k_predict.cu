@@ -1,17 +1,23 @@
 // k_predict.cu -- kriging mean and variance from a resident fit.
 //
-// For a test point x*:  r_i = prod_k exp(-theta_k |x*_k - x_ik|^p)  (eq. 2,
+// For a test point x*:  r_i = exp(-sum_k theta_k |x*_k - x_ik|^p)  (eq. 2,
 // no nugget), yhat = mu_hat + r'w with w = R^-1 (Y - 1 mu_hat), and, with
 // v = L^-1 r and a = L^-1 1,
 //   s2 = sigma2_hat [c0 - v'v + (1 - a'v)^2 / a'a].
 // The paper prices prediction at one R, one factorisation and 2N + 6
 // back-solves for N points (Section 3): two triangular solves per point.
 //
-// One CTA takes NR = 32 test points as right-hand sides and walks the tile
+// The fit is factored in double and its factor, w, a and x are then held as
+// double-float pairs (hi + lo floats), so that everything here runs on the
+// FP32 pipes: |dx|^p = exp(p ln|dx|) and exp(-S) in double-float arithmetic,
+// and the forward solve v = L^-1 r in double-float.
+//
+// One CTA takes NR = 16 test points as right-hand sides and walks the tile
 // rows of L: it forms the r block of the tile row on the fly, removes the
-// solved blocks above it (a 128 x 128 by 128 x 32 product per tile), solves
+// solved blocks above it (a 128 x 128 by 128 x 16 product per tile), solves
 // with the diagonal tile and folds the finished block into v'v and a'v.
-// Solved blocks are kept in a per-CTA slice of `work` (npad x NR doubles).
+// Solved blocks are kept in a per-CTA slice of `work` (npad x NR pairs).
+#include "df.cuh"
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -19,137 +25,169 @@ namespace gp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int NR = 32;
+constexpr int NR = 16;          // test points per CTA
+constexpr int PT = NR / 2;      // points per thread (two threads per row)
 
-__device__ __forceinline__ double powabs_p(double diff, double p) {
-    double a = fabs(diff);
-    if (p == 2.0) return a * a;
-    if (p == 1.0) return a;
-    return (a == 0.0) ? 0.0 : pow(a, p);
+// ln x for x > 0: a float seed and one Newton step y += x exp(-y) - 1 in
+// double-float (doubles the seed's ~22 correct bits).
+__device__ __forceinline__ dfl df_log(dfl x, const dfl* tab) {
+    const float y0 = logf(x.hi);
+    const dfl e = df_exp_neg(dfl{y0, 0.f}, tab);          // exp(-y0)
+    const dfl t = df_fma(x, e, dfl{-1.f, 0.f});            // x exp(-y0) - 1
+    return df_add(dfl{y0, 0.f}, t);
+}
+
+// |d|^p for the double-float d (p = 2 and p = 1 exactly)
+__device__ __forceinline__ dfl df_powabs(dfl d, double p, dfl pd, const dfl* tab) {
+    if (d.hi < 0.f) d = df_neg(d);
+    if (d.hi < 1e-30f) return {0.f, 0.f};    // |d|^p below 1e-30 p: negligible beside 1
+    if (p == 2.0) return df_mul(d, d);
+    if (p == 1.0) return d;
+    const dfl l = df_log(d, tab);
+    return df_exp_neg(df_neg(df_mul(pd, l)), tab);       // exp(p ln d)
 }
 
 struct PredArgs {
     int n, d, nt, N, m0;   // m0: first test point of this launch
-    const double* x;       // n x d
+    const float2* x;       // n x d (double-float)
     const double* theta;   // d
     double p, c0;
-    const double* L;       // packed tiles
-    const double* w;       // npad
-    const double* a;       // npad
+    const float2* L;       // packed tiles (double-float)
+    const float2* w;       // npad
+    const float2* a;       // npad
     const double* sc;      // scalars: nll, mu, sigma2, logdet, Q, aa
     const double* xs;      // N x d
     double* yhat;
     double* s2;
-    double* work;          // per CTA: npad * NR
+    float2* work;          // per CTA: npad * NR
 };
 
-// dynamic shared memory: rhs[NR][NB] + vs[NB][NR] + xs[NR][d] + th[d]
+// dynamic shared memory: rhs[NR][NB] + vs[NB][NR] (dfl) + xs[NR][d] + th[d] (dfl) + tab[64]
 __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
-    extern __shared__ double sm[];
-    double* rhs = sm;                              // [NR][NB]
-    double* vs = rhs + NR * GP_NB;                 // [NB][NR]
-    double* xsm = vs + GP_NB * NR;                 // [NR][d]
-    double* th = xsm + NR * g.d;                   // [d]
-    __shared__ double red[2][NR][4];
+    extern __shared__ dfl sm[];
+    dfl* rhs = sm;                                 // [NR][NB]
+    dfl* vs = rhs + NR * GP_NB;                    // [NB][NR]
+    dfl* xsm = vs + GP_NB * NR;                    // [NR][d]
+    dfl* th = xsm + NR * g.d;                      // [d]
+    dfl* tab = th + g.d;                           // [64]
+    __shared__ dfl red[3][NR][4];
     const int d = g.d, n = g.n, nt = g.nt;
     const int npad = nt * GP_NB;
     const int mbase = g.m0 + blockIdx.x * NR;
     const int r = threadIdx.x % GP_NB;
-    const int hh = threadIdx.x / GP_NB;           // 0..1 -> points hh*16 .. hh*16+15
+    const int hh = threadIdx.x / GP_NB;            // points hh*PT .. hh*PT+PT-1
     const bool want_var = (g.s2 != nullptr);
-    double* V = g.work + (size_t)blockIdx.x * npad * NR;   // V[i * NR + m]
+    float2* V = g.work + (size_t)blockIdx.x * npad * NR;   // V[i * NR + m]
 
     for (int q = threadIdx.x; q < NR * d; q += kThreads) {
         const int m = q / d, k = q % d;
-        xsm[q] = (mbase + m < g.N) ? g.xs[(size_t)(mbase + m) * d + k] : 0.0;
+        xsm[q] = (mbase + m < g.N) ? df_from_double(g.xs[(size_t)(mbase + m) * d + k]) : dfl{0.f, 0.f};
     }
-    for (int q = threadIdx.x; q < d; q += kThreads) th[q] = g.theta[q];
+    for (int q = threadIdx.x; q < d; q += kThreads) th[q] = df_from_double(g.theta[q]);
+    fill_exp2_table(tab);
+    const dfl pd = df_from_double(g.p);
     __syncthreads();
 
-    double mean_p[16], vv_p[16], av_p[16];
+    dfl mean_p[PT], vv_p[PT], av_p[PT];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) { mean_p[u] = 0.0; vv_p[u] = 0.0; av_p[u] = 0.0; }
+    for (int u = 0; u < PT; ++u) {
+        mean_p[u] = {0.f, 0.f};
+        vv_p[u] = {0.f, 0.f};
+        av_p[u] = {0.f, 0.f};
+    }
 
     for (int I = 0; I < nt; ++I) {
         const int gi = I * GP_NB + r;
-        const double wi = g.w[gi];
+        const dfl wi = df_load(g.w + gi);
         // r block of this tile row (zero on padded rows)
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int m = hh * 16 + u;
-            double v = 0.0;
+        for (int u = 0; u < PT; ++u) {
+            const int m = hh * PT + u;
+            dfl v = {0.f, 0.f};
             if (gi < n && mbase + m < g.N) {
-                double s = 0.0;
-                for (int k = 0; k < d; ++k)
-                    s = fma(th[k], powabs_p(xsm[m * d + k] - g.x[(size_t)gi * d + k], g.p), s);
-                v = exp(-s);
+                dfl s = {0.f, 0.f};
+                for (int k = 0; k < d; ++k) {
+                    const dfl dx = df_sub(xsm[m * d + k], df_load(g.x + (size_t)gi * d + k));
+                    s = df_fma(th[k], df_powabs(dx, g.p, pd, tab), s);
+                }
+                v = df_exp_neg(s, tab);
             }
-            mean_p[u] = fma(v, wi, mean_p[u]);
+            mean_p[u] = df_fma(v, wi, mean_p[u]);
             rhs[m * GP_NB + r] = v;
         }
         if (!want_var) continue;
         // remove the solved blocks above: rhs -= L_IJ V_J
-        double acc[16];
+        dfl acc[PT];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+        for (int u = 0; u < PT; ++u) acc[u] = {0.f, 0.f};
         for (int J = 0; J < I; ++J) {
             __syncthreads();
-            for (int q = threadIdx.x; q < GP_NB * NR; q += kThreads) vs[q] = V[(size_t)J * GP_NB * NR + q];
+            for (int q = threadIdx.x; q < GP_NB * NR; q += kThreads) {
+                const float2 v = V[(size_t)J * GP_NB * NR + q];
+                vs[q] = dfl{v.x, v.y};
+            }
             __syncthreads();
-            const double* Lt = g.L + (size_t)tile_index(I, J, nt) * GP_TILE_ELEMS;
+            const float2* Lt = g.L + (size_t)tile_index(I, J, nt) * GP_TILE_ELEMS;
+#pragma unroll 2
             for (int c = 0; c < GP_NB; ++c) {
-                const double l = __ldg(Lt + c * GP_NB + r);
+                const float2 lv = __ldg(Lt + c * GP_NB + r);
+                const dfl l = {lv.x, lv.y};
 #pragma unroll
-                for (int u = 0; u < 16; ++u) acc[u] = fma(l, vs[c * NR + hh * 16 + u], acc[u]);
+                for (int u = 0; u < PT; ++u) acc[u] = df_fma(l, vs[c * NR + hh * PT + u], acc[u]);
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 16; ++u) rhs[(hh * 16 + u) * GP_NB + r] -= acc[u];
+        for (int u = 0; u < PT; ++u) rhs[(hh * PT + u) * GP_NB + r] = df_sub(rhs[(hh * PT + u) * GP_NB + r], acc[u]);
         __syncthreads();
-        // solve with the diagonal tile: thread (r, hh) owns points hh*16..+15 of row r
-        const double* D = g.L + (size_t)tile_index(I, I, nt) * GP_TILE_ELEMS;
+        // solve with the diagonal tile: thread (r, hh) owns points hh*PT.. of row r
+        const float2* D = g.L + (size_t)tile_index(I, I, nt) * GP_TILE_ELEMS;
         for (int c = 0; c < GP_NB; ++c) {
-            const double inv = 1.0 / __ldg(D + c * GP_NB + c);
-            const double lrc = (r > c) ? __ldg(D + c * GP_NB + r) : 0.0;
-            double xc[16];
+            const float2 dv = __ldg(D + c * GP_NB + c);
+            const dfl dc = {dv.x, dv.y};
+            dfl lrc = {0.f, 0.f};
+            if (r > c) {
+                const float2 lv = __ldg(D + c * GP_NB + r);
+                lrc = dfl{lv.x, lv.y};
+            }
+            dfl xc[PT];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) xc[u] = rhs[(hh * 16 + u) * GP_NB + c] * inv;
+            for (int u = 0; u < PT; ++u) xc[u] = df_div(rhs[(hh * PT + u) * GP_NB + c], dc);
             __syncthreads();
             if (r > c) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) rhs[(hh * 16 + u) * GP_NB + r] = fma(-lrc, xc[u], rhs[(hh * 16 + u) * GP_NB + r]);
+                for (int u = 0; u < PT; ++u)
+                    rhs[(hh * PT + u) * GP_NB + r] = df_fms(lrc, xc[u], rhs[(hh * PT + u) * GP_NB + r]);
             } else if (r == c) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) rhs[(hh * 16 + u) * GP_NB + c] = xc[u];
+                for (int u = 0; u < PT; ++u) rhs[(hh * PT + u) * GP_NB + c] = xc[u];
             }
             __syncthreads();
         }
-        const double ai = g.a[gi];
+        const dfl ai = df_load(g.a + gi);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const double v = rhs[(hh * 16 + u) * GP_NB + r];
-            V[(size_t)gi * NR + hh * 16 + u] = v;
-            vv_p[u] = fma(v, v, vv_p[u]);
-            av_p[u] = fma(ai, v, av_p[u]);
+        for (int u = 0; u < PT; ++u) {
+            const dfl v = rhs[(hh * PT + u) * GP_NB + r];
+            V[(size_t)gi * NR + hh * PT + u] = make_float2(v.hi, v.lo);
+            vv_p[u] = df_fma(v, v, vv_p[u]);
+            av_p[u] = df_fma(ai, v, av_p[u]);
         }
         __syncthreads();
     }
-    // reduce over the 128 rows for each point: warp shuffles then 4 warps
+    // reduce over the 128 rows for each point: warp shuffles, then 4 warps
     const int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) & 3;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        double m1 = mean_p[u], m2 = vv_p[u], m3 = av_p[u];
-        for (int o = 16; o > 0; o >>= 1) {
-            m1 += __shfl_down_sync(0xffffffffu, m1, o);
-            m2 += __shfl_down_sync(0xffffffffu, m2, o);
-            m3 += __shfl_down_sync(0xffffffffu, m3, o);
-        }
-        if (lane == 0) {
-            red[0][hh * 16 + u][wq] = m1;
-            red[1][hh * 16 + u][wq] = m2;
-            // a'v partials reuse rhs (free now) to keep `red` small
-            rhs[(hh * 16 + u) * 4 + wq] = m3;
+    for (int u = 0; u < PT; ++u) {
+        dfl t3[3] = {mean_p[u], vv_p[u], av_p[u]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            for (int o = 16; o > 0; o >>= 1) {
+                dfl w2;
+                w2.hi = __shfl_down_sync(0xffffffffu, t3[k].hi, o);
+                w2.lo = __shfl_down_sync(0xffffffffu, t3[k].lo, o);
+                t3[k] = df_add(t3[k], w2);
+            }
+            if (lane == 0) red[k][hh * PT + u][wq] = t3[k];
         }
     }
     __syncthreads();
@@ -157,29 +195,49 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
         const int m = threadIdx.x;
         if (mbase + m < g.N) {
             const double mu = g.sc[1], sigma2 = g.sc[2], aa = g.sc[5];
-            const double mean = red[0][m][0] + red[0][m][1] + red[0][m][2] + red[0][m][3];
-            g.yhat[mbase + m] = mu + mean;
+            dfl s3[3];
+            for (int k = 0; k < 3; ++k)
+                s3[k] = df_add(df_add(red[k][m][0], red[k][m][1]), df_add(red[k][m][2], red[k][m][3]));
+            g.yhat[mbase + m] = mu + df_to_double(s3[0]);
             if (want_var) {
-                const double vv = red[1][m][0] + red[1][m][1] + red[1][m][2] + red[1][m][3];
-                const double av = rhs[m * 4 + 0] + rhs[m * 4 + 1] + rhs[m * 4 + 2] + rhs[m * 4 + 3];
-                const double gg = 1.0 - av;
+                const double vv = df_to_double(s3[1]);
+                const double gg = 1.0 - df_to_double(s3[2]);
                 g.s2[mbase + m] = sigma2 * (g.c0 - vv + gg * gg / aa);
             }
         }
     }
 }
 
+// In-place double -> double-float conversion of a fitted model's arrays.
+__global__ void k_to_df_inplace(double* p, size_t count) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        const double v = p[i];
+        const float h = __double2float_rn(v);
+        const float l = __double2float_rn(v - (double)h);
+        reinterpret_cast<float2*>(p)[i] = make_float2(h, l);
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_predict(int n, int d, int nt, const double* x, const double* theta, double p,
-                           double c0, const double* L, const double* w, const double* a,
-                           const double* scalars, int N, const double* xs, double* yhat,
-                           double* s2, double* work, int chunk, cudaStream_t s) {
-    const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d) * sizeof(double);
+cudaError_t launch_to_df_inplace(double* p, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    k_to_df_inplace<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(p, count);
+    return cudaGetLastError();
+}
+
+size_t predict_work_per_cta(int nt) { return (size_t)nt * GP_NB * NR * sizeof(float2); }
+
+int predict_points_per_cta() { return NR; }
+
+cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, double c0,
+                           const float2* L, const float2* w, const float2* a, const double* scalars, int N,
+                           const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s) {
+    const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + 64) * sizeof(dfl);
     static size_t attr = 0;
     if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = smem;
     }

@@ -11,6 +11,7 @@ PyTorch fallback.
 """
 import ctypes
 import os
+import sys
 
 import torch
 
@@ -141,6 +142,9 @@ class Model:
             self._h = None
 
     def __del__(self):
+        # at interpreter shutdown the CUDA runtime may already be gone
+        if sys.is_finalizing():
+            return
         try:
             self.free()
         except Exception:
@@ -210,6 +214,8 @@ class Context:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

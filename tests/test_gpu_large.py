@@ -1,0 +1,117 @@
+"""GPU checks at the large-instance scale (n = 16384) against closed forms.
+
+d = 1, x_i = i h, p = 1, delta = 0 gives R_ij = rho^|i-j| (Kac-Murdock-Szego):
+log|R|, 1'R^-1 1 and the quadratic forms follow from the tridiagonal inverse.
+For kriging, the exponential correlation in one dimension is Markov: for
+x_j < x* < x_j+1 the weights R^-1 r are zero except
+    lam_j = (rho1 - rho rho2) / (1 - rho^2),  lam_j+1 = (rho2 - rho rho1) / (1 - rho^2),
+rho1 = exp(-theta (x* - x_j)), rho2 = exp(-theta (x_j+1 - x*)), so the mean
+and variance are O(1) per point at any n (checked against LAPACK at small n).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 1024.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_1269_gb300 import gp
+    return gp.Context(0)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def kms(n, rho, y):
+    c = 1.0 / (1.0 - rho * rho)
+    one = np.ones(n)
+    diag = np.full(n, 1.0 + rho * rho)
+    diag[0] = diag[-1] = 1.0
+    qf = lambda u, v: c * (np.dot(u * diag, v) - rho * (np.dot(u[1:], v[:-1]) + np.dot(u[:-1], v[1:])))
+    A, B, C = qf(one, one), qf(one, y), qf(y, y)
+    mu = B / A
+    Q = C - B * B / A
+    logdet = (n - 1) * math.log(1.0 - rho * rho)
+    return dict(A=A, mu=mu, Q=Q, sigma2=Q / n, logdet=logdet, nll=logdet + n * math.log(Q))
+
+
+def ou_predict(theta, y, xs, f):
+    """Closed-form ordinary kriging for x* = (j + f) h, 0 < f < 1."""
+    n = len(y)
+    rho = math.exp(-theta * H)
+    yh = np.empty(len(xs)); s2 = np.empty(len(xs))
+    for m, x in enumerate(xs):
+        j = int(math.floor(x / H))
+        r1 = math.exp(-theta * (x - j * H))
+        r2 = math.exp(-theta * ((j + 1) * H - x))
+        l1 = (r1 - rho * r2) / (1 - rho * rho)
+        l2 = (r2 - rho * r1) / (1 - rho * rho)
+        yh[m] = f["mu"] + l1 * (y[j] - f["mu"]) + l2 * (y[j + 1] - f["mu"])
+        s2[m] = f["sigma2"] * (1.0 - (l1 * r1 + l2 * r2) + (1 - l1 - l2) ** 2 / f["A"])
+    return yh, s2
+
+
+def test_ou_closed_form_matches_lapack_small():
+    n, theta = 40, 30.0
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(n)
+    x = np.arange(n) * H
+    rho = math.exp(-theta * H)
+    R = rho ** np.abs(np.subtract.outer(np.arange(n), np.arange(n)))
+    f = kms(n, rho, y)
+    xs = (np.arange(3, 30) + 0.37) * H
+    yh, s2 = ou_predict(theta, y, xs, f)
+    one = np.ones(n)
+    for m, xv in enumerate(xs):
+        r = np.exp(-theta * np.abs(xv - x))
+        lam = np.linalg.solve(R, r)
+        ref_y = f["mu"] + lam @ (y - f["mu"])
+        ref_s = f["sigma2"] * (1 - r @ lam + (1 - one @ lam) ** 2 / f["A"])
+        assert abs(yh[m] - ref_y) < 1e-12 and abs(s2[m] - ref_s) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_kms_nll_at_n16384(ctx, prec):
+    n = 16384
+    x = (np.arange(n) * H).reshape(n, 1)
+    y = np.random.default_rng(3).standard_normal(n)
+    rhos = [0.5, 0.9]
+    th = np.array([[-math.log(r) / H] for r in rhos])
+    res = ctx.nll_batch(dev(x), dev(y), dev(th), 1.0, 0.0, prec)
+    tol = 1e-6 if prec == "mixed" else 1e-9
+    for t in range(len(rhos)):
+        rho = math.exp(-th[t, 0] * H)
+        f = kms(n, rho, y)
+        assert int(res["status"][t]) == 0
+        assert abs(float(res["nll"][t]) - f["nll"]) <= tol * abs(f["nll"])
+        assert abs(float(res["mu"][t]) - f["mu"]) <= tol * max(1, abs(f["mu"]))
+        assert abs(float(res["sigma2"][t]) - f["sigma2"]) <= tol * f["sigma2"]
+
+
+def test_kriging_at_n16384_closed_form(ctx):
+    n = 16384
+    theta = -math.log(0.9) / H
+    x = (np.arange(n) * H).reshape(n, 1)
+    y = np.random.default_rng(4).standard_normal(n)
+    model = ctx.fit(dev(x), dev(y), dev([theta]), 1.0, 0.0, "fp64")
+    f = kms(n, math.exp(-theta * H), y)
+    assert abs(model.nll - f["nll"]) <= 1e-9 * abs(f["nll"])
+    rng = np.random.default_rng(5)
+    js = rng.integers(0, n - 1, 1000)
+    xs = (js + rng.uniform(0.05, 0.95, 1000)) * H
+    yh, s2 = ctx.predict(model, dev(xs.reshape(-1, 1)))
+    ry, rs = ou_predict(theta, y, xs, f)
+    yh, s2 = yh.cpu().numpy(), s2.cpu().numpy()
+    assert np.max(np.abs(yh - ry)) <= 1e-8 * np.max(np.abs(y))
+    assert np.max(np.abs(s2 - rs)) <= 1e-8 * f["sigma2"]
+    model.free()

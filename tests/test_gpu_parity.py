@@ -276,3 +276,28 @@ def test_full_size_sampled_against_oracle(ctx):
     worst = compare_batch(w, sub, ref, st_ref, label="n4000")
     print(f"\nn=4000 sample: worst rel err (cond<=1e8) {worst:.3e}; cond "
           f"{ref[:, 6].min():.2e}..{ref[:, 6].max():.2e}")
+
+
+def test_model_outlives_context_and_clean_exit():
+    """A model freed after its context, and a process that exits holding a
+    context and a model, both end cleanly."""
+    import subprocess
+    import sys
+    from paper_1203_1269_gb300 import gp
+    c2 = gp.Context(0)
+    w = inputs.small_grid_fit(n=150, N=10)
+    m = c2.fit(dev(w.x), dev(w.y), dev([3.0, 5.0]), w.p, w.delta, "fp64")
+    c2.close()
+    m.free()
+    code = ("import numpy as np, torch\n"
+            "from paper_1203_1269_gb300 import gp, inputs\n"
+            "c = gp.Context(0)\n"
+            "w = inputs.small_grid_fit(n=150, N=10)\n"
+            "d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device='cuda')\n"
+            "m = c.fit(d(w.x), d(w.y), d([3.0, 5.0]), w.p, w.delta, 'fp64')\n"
+            "print('ok')\n")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "ok" in r.stdout
