@@ -56,7 +56,7 @@ def predict_bytes(n, N):
 
 class Result:
     __slots__ = ("rid", "kind", "arrival", "start", "done", "theta", "nll", "mu", "sigma2",
-                 "best", "yhat", "s2", "status", "refit")
+                 "best", "yhat", "s2", "status", "refit", "t_eval", "t_fit", "t_pred")
 
     def __init__(self, rid, kind):
         self.rid, self.kind = rid, kind
@@ -65,6 +65,7 @@ class Result:
         self.yhat = self.s2 = None
         self.status = None
         self.refit = False
+        self.t_eval = self.t_fit = self.t_pred = 0.0
 
 
 class Server:
@@ -182,8 +183,10 @@ class Server:
     def _fit(self, ctx, req, res):
         x, y, th, _ = inputs.request_data(req, self.N_pred)
         xd, yd, thd = self._device(x), self._device(y), self._device(th)
+        t0 = time.perf_counter()
         out = ctx.nll_batch(xd, yd, thd, req.p, req.delta, self.prec)
         nll = out["nll"].cpu().numpy()
+        res.t_eval = time.perf_counter() - t0
         st = out["status"].cpu().numpy()
         ok = np.where(st == 0)[0]
         res.nll = nll
@@ -192,7 +195,9 @@ class Server:
             return
         best = int(ok[np.argmin(nll[ok])])
         res.best, res.theta = best, th[best]
+        t0 = time.perf_counter()
         model = ctx.fit(xd, yd, thd[best].contiguous(), req.p, req.delta, "fp64")
+        res.t_fit = time.perf_counter() - t0
         res.mu, res.sigma2 = model.mu, model.sigma2
         with self.lock:
             self._evict_for(model.bytes, keep=req.rid)
@@ -221,8 +226,10 @@ class Server:
                 self.model_held += model.bytes
         model = entry[0]
         xs = inputs.uniform_design(inputs.rng(req.seed), self.N_pred, src.d)
+        t0 = time.perf_counter()
         yhat, s2 = ctx.predict(model, self._device(xs))
         res.yhat = yhat.cpu().numpy()
+        res.t_pred = time.perf_counter() - t0
         res.s2 = s2.cpu().numpy()
         res.status = 0
 
@@ -262,6 +269,9 @@ def summarize(results, requests):
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
             "refits": sum(r.refit for r in results.values()),
+            "busy_s": {"evals": sum(r.t_eval for r in results.values()),
+                       "final_fits": sum(r.t_fit for r in results.values()),
+                       "predicts": sum(r.t_pred for r in results.values())},
             "failed": sum(1 for r in results.values() if r.status not in (0, None))}
 
 

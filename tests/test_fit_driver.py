@@ -1,0 +1,60 @@
+"""The end-to-end fit driver (genetic search + double refinement + fit +
+SSPE).  CPU: the search logic on a stand-in objective.  GPU: a small fit
+whose final -2logL and SSPE match the oracle at the chosen theta."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1203_1269_gb300 import fit
+
+
+class _Bowl:
+    """Stand-in for gp.Context.nll_batch: a smooth bowl in log10 theta."""
+    target = np.array([-0.7, 0.4])
+
+    def nll_batch(self, x, y, th, p, delta, prec="mixed", out=None):
+        z = np.log10(th.cpu().numpy())
+        f = np.sum((z - self.target) ** 2, axis=1)
+        return {"nll": torch.as_tensor(f), "status": torch.zeros(len(f), dtype=torch.int32)}
+
+
+def test_genetic_search_and_refinement_on_a_bowl():
+    ctx = _Bowl()
+    x = torch.zeros((5, 2), dtype=torch.float64)
+    y = torch.zeros(5, dtype=torch.float64)
+    z, f, evals, hist = fit.genetic_search(ctx, x, y, 2.0, 0.0, generations=20, population=100, seed=3)
+    assert evals == 2000
+    assert all(a >= b for a, b in zip(hist, hist[1:]))          # best never gets worse
+    assert f < 1e-3 and np.max(np.abs(z - _Bowl.target)) < 0.05
+    z2, f2, used = fit.refine_double(ctx, x, y, 2.0, 0.0, z, f, evaluations=16)
+    assert used <= 16 and f2 <= f
+    z3, f3, _, _ = fit.genetic_search(ctx, x, y, 2.0, 0.0, generations=20, population=100, seed=3)
+    assert np.array_equal(z3, z) and f3 == f                     # seeded: reproducible
+
+
+@pytest.mark.gpu
+def test_fit_driver_matches_oracle_at_chosen_theta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1203_1269_gb300 import gp, inputs
+    ctx = gp.Context(0)
+    g = inputs.rng(77)
+    x = inputs.random_lhd(g, 200, 2)
+    y = inputs.y_trig2(x)
+    xs = inputs.uniform_design(g, 300, 2)
+    ys = inputs.y_trig2(xs)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    res = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50)
+    res2 = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50)
+    assert res["log10_theta"] == res2["log10_theta"] and res["nll"] == res2["nll"]
+    th = 10.0 ** np.array(res["log10_theta"])
+    o, st = oracle.nll(x, y, th, 2.0, 1e-8)
+    assert st == 0
+    assert abs(res["nll"] - o["nll"]) <= 1e-9 * abs(o["nll"]) + 1e-9
+    assert res["nll"] <= res["nll_ga"] + 1e-6 * abs(res["nll_ga"])
+    yo, _, _ = oracle.predict(x, y, th, 2.0, 1e-8, xs, want_var=False)
+    sspe_o = float(np.sum((ys - yo) ** 2))
+    assert abs(res["sspe"] - sspe_o) <= 1e-8 * max(1.0, sspe_o)
+    ctx.close()
