@@ -138,6 +138,40 @@ __device__ __forceinline__ dfl df_exp_neg(dfl S, const dfl* tab) {
     return e;
 }
 
+// ln x for x > 0 (x in [2^-60, 2^60]): a float seed y0 = logf(x) and one
+// Newton step y = y0 + x exp(-y0) - 1 in double-float, which doubles the
+// seed's ~22 correct bits.
+__device__ __forceinline__ dfl df_log(dfl x, const dfl* tab) {
+    const float y0 = logf(x.hi);
+    const dfl e = df_exp_neg(dfl{y0, 0.f}, tab);          // exp(-y0)
+    const dfl t = df_fma(x, e, dfl{-1.f, 0.f});            // x exp(-y0) - 1
+    return df_add(dfl{y0, 0.f}, t);
+}
+
+// Exponent modes of |d|^p: the two exact cases and the general one.
+enum : int { kPowGeneral = 0, kPowOne = 1, kPowTwo = 2 };
+
+__host__ __device__ __forceinline__ int pow_mode(double p) {
+    return p == 2.0 ? kPowTwo : (p == 1.0 ? kPowOne : kPowGeneral);
+}
+
+// |d|^p for p in (0, 2] as exp(p ln |d|) in double-float (pd = p as
+// double-float).  |d| outside [2^-60, 2^60] (far from any realistic
+// coordinate difference) takes the double pow instead, with the result
+// clamped to [0, 2^120] so that a zero theta still gives a zero term.
+__device__ __forceinline__ dfl df_powabs(dfl d, int mode, double p, dfl pd, const dfl* tab) {
+    if (d.hi < 0.f) d = df_neg(d);
+    if (d.hi == 0.f) return {0.f, 0.f};
+    if (!(d.hi >= 0x1p-60f && d.hi <= 0x1p60f)) {
+        const double a = df_to_double(d);
+        const double v = (mode == kPowTwo) ? a * a : (mode == kPowOne ? a : pow(a, p));
+        return df_from_double(fmin(v, 0x1p120));
+    }
+    if (mode == kPowTwo) return df_mul(d, d);
+    if (mode == kPowOne) return d;
+    return df_exp_neg(df_neg(df_mul(pd, df_log(d, tab))), tab);
+}
+
 // tab[j] = 2^(-j/64), j = 0..63, as double-float (threads 0..63 of a block).
 __device__ __forceinline__ void fill_exp2_table(dfl* tab) {
     if (threadIdx.x < 64) tab[threadIdx.x] = df_from_double(exp2(-(double)threadIdx.x / 64.0));

@@ -9,6 +9,10 @@
 // its group; per candidate an entry then costs d FMAs and one exp.  The paper
 // counts d n(n-1)/2 independent terms (Section 3); here the lower triangle of
 // tiles (diagonal tiles in full) is produced.
+//
+// The double-float variant (split-precision path) keeps everything on the
+// FP32 pipes: on this GPU one FP64 pow costs as much as thousands of FP32
+// instructions, so the powers are exp(p ln|dx|) in double-float too.
 #include "df.cuh"
 #include "gp_internal.cuh"
 
@@ -20,12 +24,26 @@ constexpr int kThreads = 256;
 constexpr int kSplit = 4;                       // a CTA covers NB/kSplit columns of a tile
 constexpr int kCols = GP_NB / kSplit;           // 32 columns
 constexpr int kEntries = GP_NB * kCols / kThreads;  // 16 entries per thread
+// double-float variant: finer column parts, so that the last wave of CTAs is
+// nearly full
+constexpr int kSplitDf = 8;
+constexpr int kColsDf = GP_NB / kSplitDf;       // 16 columns
+constexpr int kEntriesDf = GP_NB * kColsDf / kThreads;  // 8 entries per thread
 
 __device__ __forceinline__ double powabs(double diff, double p) {
     double a = fabs(diff);
     if (p == 2.0) return a * a;
     if (p == 1.0) return a;
     return (a == 0.0) ? 0.0 : pow(a, p);
+}
+
+// |dx|^p as double-float: p = 2 and p = 1 exactly in double (one FP64
+// multiply), any other p as exp(p ln|dx|) in double-float arithmetic.
+// Values are clamped to 2^120 so that the float range holds them.
+__device__ __forceinline__ dfl power_term(double dx, int pmode, double p, dfl pd, const dfl* tab) {
+    if (pmode == kPowTwo) return df_from_double(fmin(dx * dx, 0x1p120));
+    if (pmode == kPowOne) return df_from_double(fmin(fabs(dx), 0x1p120));
+    return df_powabs(df_from_double(dx), kPowGeneral, p, pd, tab);
 }
 
 // One entry of instance t: double tiles, or double-float working matrix plus
@@ -130,37 +148,41 @@ k_assemble_tiles(Batch b, int group) {
     }
 }
 
-// Double-float variant for the split-precision path: the powers in double
-// (once per entry), then per candidate S = sum_k theta_k D_k and exp(-S) in
-// double-float arithmetic on the FP32 pipes.  Writes the working matrix and
-// its copy.  Dynamic smem: x rows/cols (double), theta of the group and the
-// exp table (double-float), the group's status flags.
+// Double-float variant for the split-precision path: the powers once per
+// entry, then per candidate S = sum_k theta_k D_k and exp(-S), all in
+// double-float arithmetic on the FP32 pipes.  Every term of S is >= 0, so S
+// is summed with one TwoSum per term on the high parts, the rounding errors
+// of the products and the cross terms gathered in one float and folded in at
+// the end (about 2^-46 relative, the accuracy of a double-float FMA chain at
+// two thirds of its instructions).  Writes the working matrix and its copy.
+// Dynamic smem: x rows/cols (double), theta of the group and the exp table
+// (double-float), the group's status flags.
 template <int DB>
 __global__ void __launch_bounds__(kThreads)
 k_assemble_tiles_df(Batch b, int group) {
     extern __shared__ double dsm[];
     double* xs_r = dsm;                                  // GP_NB * DB
-    double* xs_c = xs_r + GP_NB * DB;                    // kCols * DB
-    dfl* th = reinterpret_cast<dfl*>(xs_c + kCols * DB); // group * DB
+    double* xs_c = xs_r + GP_NB * DB;                    // kColsDf * DB
+    dfl* th = reinterpret_cast<dfl*>(xs_c + kColsDf * DB); // group * DB
     dfl* tab = th + (size_t)group * DB;                  // 64
     int* live = reinterpret_cast<int*>(tab + 64);        // group
     const int nt = b.nt, n = b.n, d = b.d;
-    const int tile_lin = blockIdx.x / kSplit;
-    const int part = blockIdx.x % kSplit;
+    const int tile_lin = blockIdx.x / kSplitDf;
+    const int part = blockIdx.x % kSplitDf;
     int J = 0;
     {
         long long rem = tile_lin;
         while (rem >= nt - J) { rem -= nt - J; ++J; }
     }
     const int I = J + (int)(tile_lin - tile_index(J, J, nt));
-    const int row0 = I * GP_NB, col0 = J * GP_NB + part * kCols;
+    const int row0 = I * GP_NB, col0 = J * GP_NB + part * kColsDf;
     const int t0 = blockIdx.y * group;
     const int t1 = min(b.count, t0 + group);
     for (int q = threadIdx.x; q < GP_NB * DB; q += kThreads) {
         const int r = q / DB, k = q % DB, gi = row0 + r;
         xs_r[q] = (gi < n && k < d) ? b.x[(size_t)gi * d + k] : 0.0;
     }
-    for (int q = threadIdx.x; q < kCols * DB; q += kThreads) {
+    for (int q = threadIdx.x; q < kColsDf * DB; q += kThreads) {
         const int c = q / DB, k = q % DB, gj = col0 + c;
         xs_c[q] = (gj < n && k < d) ? b.x[(size_t)gj * d + k] : 0.0;
     }
@@ -172,21 +194,23 @@ k_assemble_tiles_df(Batch b, int group) {
     fill_exp2_table(tab);
     __syncthreads();
     const dfl delta = df_from_double(b.delta);
+    const int pmode = pow_mode(b.p);
+    const dfl pd = df_from_double(b.p);
     const size_t tile_off = (size_t)tile_lin * GP_TILE_ELEMS;
     const int r = threadIdx.x % GP_NB;
     const int cb = threadIdx.x / GP_NB;
     const int gi = row0 + r;
 #pragma unroll 1
-    for (int e = 0; e < kEntries; ++e) {
+    for (int e = 0; e < kEntriesDf; ++e) {
         const int c = cb + 2 * e;
         const int gj = col0 + c;
-        const size_t off = tile_off + (size_t)(part * kCols + c) * GP_NB + r;
+        const size_t off = tile_off + (size_t)(part * kColsDf + c) * GP_NB + r;
         const bool pad = (gi >= n) || (gj >= n);
         const bool diag = (gi == gj);
         dfl D[DB];
 #pragma unroll
         for (int k = 0; k < DB; ++k)
-            D[k] = (k < d && !pad) ? df_from_double(powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p))
+            D[k] = (k < d && !pad) ? power_term(xs_r[r * DB + k] - xs_c[c * DB + k], pmode, b.p, pd, tab)
                                    : dfl{0.f, 0.f};
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
@@ -196,11 +220,24 @@ k_assemble_tiles_df(Batch b, int group) {
                 v = {diag ? 1.f : 0.f, 0.f};
             } else {
                 const dfl* tt = th + (size_t)(t - t0) * DB;
-                dfl s = {0.f, 0.f};
+                float sh = 0.f, sl = 0.f;
 #pragma unroll
-                for (int k = 0; k < DB; ++k)
-                    if (k < d) s = df_fma(tt[k], D[k], s);
-                v = df_exp_neg(s, tab);
+                for (int k = 0; k < DB; ++k) {
+                    if (k < d) {
+                        const dfl a = tt[k];
+                        const float ph = __fmul_rn(a.hi, D[k].hi);
+                        sl = __fadd_rn(sl, __fmaf_rn(a.hi, D[k].hi, -ph));
+                        sl = __fmaf_rn(a.hi, D[k].lo, sl);
+                        sl = __fmaf_rn(a.lo, D[k].hi, sl);
+                        float s2, e2;
+                        two_sum(sh, ph, s2, e2);
+                        sh = s2;
+                        sl = __fadd_rn(sl, e2);
+                    }
+                }
+                dfl S;
+                fast_two_sum(sh, sl, S.hi, S.lo);   // |sl| << sh: every term is >= 0
+                v = df_exp_neg(S, tab);
                 if (diag) v = df_add(v, delta);
             }
             const size_t i = (size_t)t * b.inst_stride + off;
@@ -288,8 +325,14 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
     groups = (b.count + group - 1) / group;
     dim3 grid((unsigned)ctas_per_group, (unsigned)groups);
     if (b.Adf && b.d <= 16) {
+        long long g_df = (4 * 152 + tiles * kSplitDf - 1) / (tiles * kSplitDf);
+        if (g_df < 1) g_df = 1;
+        if (g_df > b.count) g_df = b.count;
+        group = (int)((b.count + g_df - 1) / g_df);
+        g_df = (b.count + group - 1) / group;
+        grid = dim3((unsigned)(tiles * kSplitDf), (unsigned)g_df);
         const int DB = b.d <= 4 ? 4 : (b.d <= 8 ? 8 : 16);
-        const size_t smem = (size_t)(GP_NB + kCols) * DB * sizeof(double) +
+        const size_t smem = (size_t)(GP_NB + kColsDf) * DB * sizeof(double) +
                             ((size_t)group * DB + 64) * sizeof(dfl) + (size_t)group * sizeof(int);
         cudaError_t e = cudaSuccess;
         if (DB == 4) {

@@ -250,6 +250,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     extern __shared__ double P[];          // kPacked doubles
     __shared__ double col[GP_NB];
     __shared__ double rowtmp[GP_NB];
+    __shared__ double dinv[GP_NB];         // 1 / L_cc, reused by the inverse and the solves
+    __shared__ double lsum[GP_NB / 32];
     __shared__ double inv_piv;
     __shared__ int failed;
     const int t = blockIdx.x;
@@ -266,7 +268,9 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kDiagThreads / 32;
-    double logdet = 0.0;
+    // FP64 instructions are scarce on this GPU (2 DFMA per clock per SM), so
+    // the one square root and division per column run once, on thread 0, and
+    // the logarithms of the pivots wait for the parallel reduction below
     for (int c = 0; c < GP_NB; ++c) {
         if (threadIdx.x == 0) {
             const double piv = P[prow(c) + c];
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
                 const double l = sqrt(piv);
                 P[prow(c) + c] = l;
                 inv_piv = 1.0 / l;
-                logdet += log(l);
+                dinv[c] = inv_piv;
             }
         }
         __syncthreads();
@@ -310,14 +314,22 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             T[q] = make_float2(d.hi, d.lo);
         }
     }
-    if (threadIdx.x == 0) b.st[t].logdet += 2.0 * logdet;
+    // log-det: sum of log L_cc over the block in a fixed order (warp trees,
+    // then the four warp sums in turn)
     if (threadIdx.x < GP_NB) {
+        double v = log(P[prow(threadIdx.x) + threadIdx.x]);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) lsum[warp] = v;
         float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
-        const double ri = 1.0 / P[prow(threadIdx.x) + threadIdx.x];
-        const dfl d = df_from_double(ri);
+        const dfl d = df_from_double(dinv[threadIdx.x]);
         rinv[threadIdx.x] = make_float2(d.hi, d.lo);
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        double ld = 0.0;
+        for (int w = 0; w < GP_NB / 32; ++w) ld += lsum[w];
+        b.st[t].logdet += 2.0 * ld;
+    }
     // W = L^-1 in place, row by row; thread (j, part) sums k = j + part, j + part + 4, ...
     const int j = threadIdx.x >> 2, part = threadIdx.x & 3;
     for (int i = 0; i < GP_NB; ++i) {
@@ -327,7 +339,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             for (int k = j + part; k < i; k += 4) sum = fma(Li[k], P[prow(k) + j], sum);
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
         sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        const double rinv_i = 1.0 / Li[i];
+        const double rinv_i = dinv[i];
         if (part == 0 && j <= i) rowtmp[j] = (j == i) ? rinv_i : -rinv_i * sum;
         __syncthreads();
         if (threadIdx.x <= i) P[prow(i) + threadIdx.x] = rowtmp[threadIdx.x];
@@ -708,6 +720,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
         const int r = q * 32 + lane;
         const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
         constexpr int CB = (NG > 4) ? 8 : 16;    // columns per TMEM load
+        // products a + b <= ns - 1 exist, so with ns < NG slices the groups
+        // from ns on are never written and read as zero
+        const int ng_used = ns < NG ? ns : NG;
         int i = 0;
         for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
             int t, I, K, col0;
@@ -734,8 +749,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 float d[NG][CB];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
-                    if (CB == 8)       tmem_ld8(lane_addr + g * NT + c0, d[g]);
-                    else               tmem_ld16(lane_addr + g * NT + c0, d[g]);
+                    if (g < ng_used) {
+                        if (CB == 8) tmem_ld8(lane_addr + g * NT + c0, d[g]);
+                        else         tmem_ld16(lane_addr + g * NT + c0, d[g]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CB; ++j) d[g][j] = 0.f;
+                    }
                 }
                 tmem_wait_ld();
 #pragma unroll
@@ -815,6 +835,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
 // conflict-free (2-way for the 8-byte entries).
 
 constexpr int kSolveThreads = 512;
+constexpr uint32_t kTileDfBytes = GP_TILE_ELEMS * sizeof(float2);   // one double-float tile, 128 KB
 constexpr int kTs = GP_NB + 1;   // staged tile row stride
 
 __device__ __forceinline__ float2* zcol(const MixedBatch& b, int t, int k) {
@@ -874,6 +895,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int 
                 const int k = threadIdx.x >> 7;
                 xj[k][r] = df_load((k ? z1 : z0) + Jt * GP_NB + r);
             }
+            // the next tile of the walk heads for L2 while this one is used
+            if (threadIdx.x == 0)
+                prefetch_l2(Jt + 1 < I ? df_tile(b, b.A, t, I, Jt + 1)
+                                       : b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS,
+                            kTileDfBytes);
             __syncthreads();
             const float2* L = df_tile(b, b.A, t, I, Jt);
             // thread (r, h) takes columns h, h + 8, ... and h + 4, h + 12, ...: 4 chains
@@ -906,6 +932,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int 
         __syncthreads();
         // x_I = W_I rhs_I with W_I = L_II^-1 (lower): thread (r, h) sums columns
         // c <= r of its parity classes, four chains
+        if (threadIdx.x == 0 && I + 1 < nt) prefetch_l2(df_tile(b, b.A, t, I + 1, 0), kTileDfBytes);
         {
             const float2* W = b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS;
             dfl s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
@@ -958,6 +985,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int
                 const int k = threadIdx.x >> 7;
                 wk[k][c] = df_load((k ? z1 : z0) + K * GP_NB + c);
             }
+            if (threadIdx.x == 0)
+                prefetch_l2(K + 1 < nt ? df_tile(b, b.A, t, K + 1, I)
+                                       : b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS,
+                            kTileDfBytes);
             stage_tile(df_tile(b, b.A, t, K, I), T);
             __syncthreads();
             // (L_KI^T w_K)[c] = sum_k L_KI(k, c) w_K[k] = sum_k T[c][k] w_K[k]; k in [32h, 32h + 32)
@@ -974,6 +1005,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int
         part[h][1][c] = df_add(a10, a11);
         __syncthreads();
         // W_I = L_II^-1 staged; w_I = W_I^T rhs: w[c] = sum_k W(k, c) rhs[k] = sum_k T[c][k] rhs[k]
+        if (threadIdx.x == 0 && I > 0)
+            prefetch_l2(df_tile(b, b.A, t, I, I - 1), kTileDfBytes);
         stage_tile(b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS, T);
         if (threadIdx.x < 2 * GP_NB) {
             const int k = threadIdx.x >> 7;
@@ -1038,6 +1071,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_residual(MixedBatch b) {
                 xa[k][i] = df_load((k ? x1 : x0) + J * GP_NB + i);   // x_J
                 xb[k][i] = df_load((k ? x1 : x0) + I * GP_NB + i);   // x_I
             }
+            // stored tiles are walked in packed order: the next one is adjacent
+            if (threadIdx.x == 0 && !(I + 1 == nt && J + 1 == nt))
+                prefetch_l2(df_tile(b, b.Rc, t, I, J) + GP_TILE_ELEMS, kTileDfBytes);
             stage_tile(df_tile(b, b.Rc, t, I, J), T);
             __syncthreads();
             // rows: (R_IJ x_J)[i] = sum_c T[c][i] x_J[c], c in [32h, 32h + 32)

@@ -28,25 +28,6 @@ constexpr int kThreads = 256;
 constexpr int NR = 16;          // test points per CTA
 constexpr int PT = NR / 2;      // points per thread (two threads per row)
 
-// ln x for x > 0: a float seed and one Newton step y += x exp(-y) - 1 in
-// double-float (doubles the seed's ~22 correct bits).
-__device__ __forceinline__ dfl df_log(dfl x, const dfl* tab) {
-    const float y0 = logf(x.hi);
-    const dfl e = df_exp_neg(dfl{y0, 0.f}, tab);          // exp(-y0)
-    const dfl t = df_fma(x, e, dfl{-1.f, 0.f});            // x exp(-y0) - 1
-    return df_add(dfl{y0, 0.f}, t);
-}
-
-// |d|^p for the double-float d (p = 2 and p = 1 exactly)
-__device__ __forceinline__ dfl df_powabs(dfl d, double p, dfl pd, const dfl* tab) {
-    if (d.hi < 0.f) d = df_neg(d);
-    if (d.hi < 1e-30f) return {0.f, 0.f};    // |d|^p below 1e-30 p: negligible beside 1
-    if (p == 2.0) return df_mul(d, d);
-    if (p == 1.0) return d;
-    const dfl l = df_log(d, tab);
-    return df_exp_neg(df_neg(df_mul(pd, l)), tab);       // exp(p ln d)
-}
-
 struct PredArgs {
     int n, d, nt, N, m0;   // m0: first test point of this launch
     const float2* x;       // n x d (double-float)
@@ -86,6 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
     for (int q = threadIdx.x; q < d; q += kThreads) th[q] = df_from_double(g.theta[q]);
     fill_exp2_table(tab);
     const dfl pd = df_from_double(g.p);
+    const int pmode = pow_mode(g.p);
     __syncthreads();
 
     dfl mean_p[PT], vv_p[PT], av_p[PT];
@@ -108,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
                 dfl s = {0.f, 0.f};
                 for (int k = 0; k < d; ++k) {
                     const dfl dx = df_sub(xsm[m * d + k], df_load(g.x + (size_t)gi * d + k));
-                    s = df_fma(th[k], df_powabs(dx, g.p, pd, tab), s);
+                    s = df_fma(th[k], df_powabs(dx, pmode, g.p, pd, tab), s);
                 }
                 v = df_exp_neg(s, tab);
             }
