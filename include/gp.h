@@ -45,6 +45,7 @@ extern "C" {
 
 typedef struct gp_ctx gp_ctx;
 typedef struct gp_model gp_model;
+typedef struct gp_plan gp_plan;
 
 /* Arithmetic of the factorisation.
  * GP_FP64:  assembly, Cholesky and solves in IEEE double.
@@ -53,10 +54,19 @@ typedef struct gp_model gp_model;
  *           trailing updates of the blocked Cholesky on the tensor cores with
  *           double operands split into bf16 slices and exact fp32
  *           accumulation (Ozaki-style), recombined in double-float.
- * GP_AUTO:  GP_MIXED. */
+ * GP_FP32:  the GP_MIXED factorisation with 3 slices in the trailing
+ *           updates: 24 significant bits, the precision of an FP32 factor,
+ *           at 6 tensor-core products per tile update instead of 15.  Meant
+ *           for well-conditioned R: the error of -2logL grows like
+ *           cond_1(R) 2^-30 (see gp_nll_batch_ex).
+ * GP_AUTO:  per candidate, the cheapest of GP_FP32, GP_MIXED and GP_FP64
+ *           whose error bound, from a condition estimate, meets the
+ *           context's auto_tol (gp_nll_batch_ex); synchronises.  In
+ *           gp_cholesky, which has no candidates to route, GP_MIXED. */
 typedef enum {
     GP_FP64 = 0,
     GP_MIXED = 1,
+    GP_FP32 = 2,
     GP_AUTO = 3
 } gp_precision;
 
@@ -91,6 +101,8 @@ typedef struct {
                              one-panel look-ahead and both applied to the trailing tiles
                              in one 256-wide pass (half the passes over the trailing
                              matrix); 0: one pass per panel.  Needs update_groups = 4 */
+    double auto_tol;      /* GP_AUTO: relative error of -2logL each candidate must meet,
+                             default 1e-6 */
 } gp_options;
 
 void gp_default_options(gp_options* opt);
@@ -181,6 +193,62 @@ int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, in
                  const double* theta, double p, double delta, int prec,
                  double* nll, double* mu_hat, double* sigma2_hat, double* logdet,
                  int* status);
+
+/* gp_nll_batch with two more outputs (length T, each may be NULL):
+ *   cond1[t]     1-norm condition estimate of R(theta_t) + delta I: ||R||_1
+ *                times Hager's estimate of ||R^-1||_1 (W. W. Hager, SIAM J.
+ *                Sci. Stat. Comput. 5, 1984; the iteration LAPACK's
+ *                condition estimators refine).  It is taken with the candidate's own split-precision factor
+ *                after the likelihood: up to five rounds of two solves, all
+ *                candidates in step.  A lower bound of the true value up to
+ *                the factor's error, in practice within a small factor.  NaN
+ *                where the status is GP_EINVAL or GP_ENOTPD.  Not available
+ *                with GP_FP64: cond1 must then be NULL (GP_ENOTSUP).
+ *   prec_used[t] the arithmetic the candidate's outputs come from: GP_FP32,
+ *                GP_MIXED or GP_FP64 (prec itself unless prec is GP_AUTO).
+ * GP_AUTO evaluates every candidate with GP_FP32 and its estimate.  One whose
+ * status is not GP_OK, or whose cond1 * 2^-30 exceeds the context's auto_tol,
+ * is evaluated again with GP_MIXED, whose bound is cond1 * 2^-(8 s + 6) for s
+ * slices; one that fails that test as well is evaluated with GP_FP64.  The
+ * bounds are the largest error of -2logL per unit of cond_1 measured on the
+ * n = 4000 benchmark batch (cond_1 from 2e7 to 4e11), with a margin of 10 or
+ * more.  cond1 then holds each candidate's last split-precision estimate.
+ * GP_AUTO synchronises the stream (the routing reads the estimates on the
+ * host) and takes its staging buffers from the stream-ordered allocator.
+ * Other precisions are asynchronous like gp_nll_batch. */
+int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                    const double* theta, double p, double delta, int prec,
+                    double* nll, double* mu_hat, double* sigma2_hat, double* logdet,
+                    int* status, double* cond1, int* prec_used);
+
+/* A batch recorded as one CUDA graph.  gp_plan_nll_batch evaluates the call
+ * once (eagerly, so that its outputs are also valid on return), then records
+ * the same call's kernel sequence on a private stream and instantiates it;
+ * gp_plan_launch replays it on the context's current stream as a single
+ * graph launch.  The paper evaluates candidates one after another (Section 3);
+ * the graph removes the per-kernel launch cost of a batch, which dominates
+ * for small n.
+ *   - The plan binds the argument ADDRESSES: every replay reads the current
+ *     contents of x, y and theta and overwrites the outputs.  The caller
+ *     keeps those buffers alive, and n, d, T, p, delta and prec fixed, for
+ *     the plan's lifetime.
+ *   - The plan owns its workspace (counted against the context's budget like
+ *     a model), so other calls on the context do not disturb it; replays of
+ *     one plan must not overlap each other on the GPU.
+ *   - prec: GP_FP64, GP_MIXED or GP_FP32 (GP_AUTO routes on the host and is
+ *     rejected with GP_ENOTSUP).  cond1 may be NULL.
+ *   - The context's options at creation are baked in.
+ * gp_plan_nll_batch synchronises; gp_plan_launch is asynchronous and adds
+ * the plan's kernels to the context's launch count.  A plan may outlive its
+ * context (gp_plan_destroy then frees it synchronously). */
+int gp_plan_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                      const double* theta, double p, double delta, int prec, double* nll,
+                      double* mu_hat, double* sigma2_hat, double* logdet, int* status,
+                      double* cond1, gp_plan** plan);
+int gp_plan_launch(gp_plan* plan);
+long long gp_plan_kernels(const gp_plan* plan);   /* kernels in one replay */
+size_t gp_plan_bytes(const gp_plan* plan);        /* device bytes the plan holds */
+void gp_plan_destroy(gp_plan* plan);
 
 /* gp_nll_batch with every array in host memory: the call copies the inputs
  * to the device, evaluates, copies the outputs back and synchronises.

@@ -26,6 +26,7 @@ struct gp_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
     double phase_ms[GP_NUM_PHASES] = {0};
     std::vector<gp_model*> models;   // live models (detached when the context goes first)
+    std::vector<gp_plan*> plans;     // live plans (likewise)
     long long phase_launches[GP_NUM_PHASES] = {0};
     long long launches = 0;
 };
@@ -44,6 +45,15 @@ struct gp_model {
     int* status = nullptr;
     gp::InstState* st = nullptr;
     double host_scalars[6];
+};
+
+struct gp_plan {
+    gp_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* ws = nullptr;         // the plan's own workspace
+    size_t ws_bytes = 0;
+    long long kernels = 0;
 };
 
 namespace {
@@ -181,7 +191,7 @@ MixedSizes mixed_sizes(int n, int s) {
     z.PF = align256((size_t)nt * s * 2 * GP_TILE_ELEMS * sizeof(__nv_bfloat16));
     z.FE = align256((size_t)nt * GP_NB * sizeof(int));
     z.WT = align256((size_t)nt * GP_TILE_ELEMS * sizeof(float2));
-    z.Z = align256((size_t)5 * nt * GP_NB * sizeof(float2));
+    z.Z = align256((size_t)gp::kZCols * nt * GP_NB * sizeof(float2));
     z.st = align256(sizeof(gp::InstState));
     z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + z.WT + z.Z + z.st;
     return z;
@@ -189,7 +199,7 @@ MixedSizes mixed_sizes(int n, int s) {
 
 // Carve the split-precision buffers of `cnt` instances out of `base`.
 gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* base, const MixedSizes& z,
-                            int Tc) {
+                            int Tc, int slices) {
     gp::MixedBatch mb{};
     char* c = base;
     mb.A = (float2*)c; c += z.A * Tc;
@@ -204,7 +214,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.Z = (float2*)c; c += z.Z * Tc;
     mb.st = (gp::InstState*)c; c += z.st * Tc;
     mb.err = (int*)c;
-    mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = ctx->opt.slices;
+    mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = slices;
     mb.ps = GP_PANEL_SLICES;
     mb.ug = ctx->opt.update_groups;
     mb.inject_timeout = ctx->opt.inject_timeout;
@@ -308,10 +318,30 @@ int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* 
     return GP_OK;
 }
 
+// 1-norm condition estimates of the factored instances (k_cond.cu): ||R||_1,
+// then Hager's iteration, all instances in step, at most five rounds.
+int run_mixed_cond(gp_ctx* ctx, const gp::MixedBatch& mb, double* cond) {
+    constexpr int kRounds = 5;
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 3 + kRounds * 3 + (kRounds - 1) * 3);
+    GP_CUDA(ctx, gp::launch_norm1(mb, ctx->stream));
+    GP_CUDA(ctx, gp::launch_hager(mb, 0, nullptr, ctx->stream));
+    for (int it = 0; it < kRounds; ++it) {
+        GP_CUDA(ctx, gp::launch_df_forward(mb, 5, 0, ctx->stream));      // z = R^-1 sign(y)
+        GP_CUDA(ctx, gp::launch_df_backward(mb, 5, -1, ctx->stream));
+        GP_CUDA(ctx, gp::launch_hager(mb, 2, nullptr, ctx->stream));
+        if (it + 1 == kRounds) break;
+        GP_CUDA(ctx, gp::launch_df_forward(mb, 5, 0, ctx->stream));      // y = R^-1 e_j
+        GP_CUDA(ctx, gp::launch_df_backward(mb, 5, -1, ctx->stream));
+        GP_CUDA(ctx, gp::launch_hager(mb, 1, nullptr, ctx->stream));
+    }
+    GP_CUDA(ctx, gp::launch_hager(mb, 3, cond, ctx->stream));
+    return GP_OK;
+}
+
 int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                     const double* theta, double p, double delta, double* nll, double* mu,
-                    double* sigma2, double* logdet, int* status) {
-    const MixedSizes z = mixed_sizes(n, ctx->opt.slices);
+                    double* sigma2, double* logdet, int* status, int slices, double* cond) {
+    const MixedSizes z = mixed_sizes(n, slices);
     size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
     long long cap = (long long)((avail > 256 ? avail - 256 : 0) / z.per);
     if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
@@ -322,14 +352,159 @@ int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y,
     if (rc) return rc;
     for (int c0 = 0; c0 < T; c0 += Tc) {
         const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
-        gp::MixedBatch mb = mixed_layout(ctx, n, cnt, y, (char*)ctx->ws, z, Tc);
+        gp::MixedBatch mb = mixed_layout(ctx, n, cnt, y, (char*)ctx->ws, z, Tc, slices);
         rc = run_mixed_factor(ctx, mb, d, x, theta + (size_t)c0 * d, p, delta);
         if (rc) return rc;
         rc = run_mixed_solve(ctx, mb, nll + c0, mu + c0, sigma2 + c0, logdet ? logdet + c0 : nullptr,
                              status + c0);
         if (rc) return rc;
+        if (cond) {
+            rc = run_mixed_cond(ctx, mb, cond + c0);
+            if (rc) return rc;
+        }
     }
     return GP_OK;
+}
+
+// -2logL in IEEE double for T candidates (batches sized by the budget).
+int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                   const double* theta, double p, double delta, double* nll, double* mu_hat,
+                   double* sigma2_hat, double* logdet, int* status) {
+    const int nt = gp::num_tiles(n);
+    const size_t per = per_instance_bytes_f64(n);
+    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    long long cap = (long long)(avail / per);
+    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
+    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
+    if (cap > 65535) cap = 65535;  // grid.y bound of the per-instance launches
+    const int Tc = (int)(cap < T ? cap : T);
+    int rc = ensure_ws(ctx, per * (size_t)Tc);
+    if (rc) return rc;
+    char* base = (char*)ctx->ws;
+    const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
+    const size_t z_bytes = align256((size_t)2 * nt * GP_NB * sizeof(double));
+    double* A = (double*)base;
+    double* Z = (double*)(base + a_bytes * Tc);
+    gp::InstState* st = (gp::InstState*)(base + (a_bytes + z_bytes) * Tc);
+    for (int c0 = 0; c0 < T; c0 += Tc) {
+        const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
+        gp::Batch b{};
+        b.n = n; b.d = d; b.nt = nt; b.count = cnt;
+        b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
+        b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
+        {
+            PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+            GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+            GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+        }
+        rc = run_factor_f64(ctx, b);
+        if (rc) return rc;
+        const size_t zs = z_bytes / sizeof(double);
+        PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+        GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
+        GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, mu_hat + c0, sigma2_hat + c0,
+                                         logdet ? logdet + c0 : nullptr, status + c0, ctx->stream));
+    }
+    return GP_OK;
+}
+
+// Error of -2logL per unit of cond_1(R) allowed for a split factorisation
+// with s slices in the trailing updates: 2^-(8 s + 6).  The largest ratio
+// measured on the 256 candidates of the n = 4000 benchmark batch (cond_1
+// from 2e7 to 4e11) was 9.5e-11 with 3 slices and 5.4e-16 with 5; the
+// bound leaves a margin of 10 or more.
+double split_error_per_cond(int s) { return std::ldexp(1.0, -(8 * s + 6)); }
+
+// GP_AUTO: route every candidate to the cheapest arithmetic whose bound
+// meets auto_tol (GP_FP32, then GP_MIXED, then GP_FP64); see gp.h.
+int auto_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                   const double* theta, double p, double delta, double* nll, double* mu,
+                   double* sigma2, double* logdet, int* status, double* cond, int* prec_used) {
+    const double tol = ctx->opt.auto_tol;
+    // staging: compacted theta and outputs of a re-evaluated subset, indices,
+    // and cond / prec_used when the caller passed none
+    const size_t bT = align256((size_t)T * sizeof(double));
+    const size_t bI = align256((size_t)T * sizeof(int));
+    const size_t total = align256((size_t)T * d * sizeof(double)) + 6 * bT + 4 * bI;
+    void* dev = nullptr;
+    if (cudaMallocAsync(&dev, total, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GP_ENOMEM, "GP_AUTO staging allocation of %zu bytes failed", total);
+    }
+    char* c = (char*)dev;
+    double* th_c = (double*)c; c += align256((size_t)T * d * sizeof(double));
+    double* nll_c = (double*)c; c += bT;
+    double* mu_c = (double*)c; c += bT;
+    double* s2_c = (double*)c; c += bT;
+    double* ld_c = (double*)c; c += bT;
+    double* cond_c = (double*)c; c += bT;
+    double* cond_all = cond ? cond : (double*)c; c += bT;
+    int* st_c = (int*)c; c += bI;
+    int* idx_d = (int*)c; c += bI;
+    int* pu = prec_used ? prec_used : (int*)c; c += bI;
+    auto done = [&](int rc) {
+        cudaFreeAsync(dev, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (rc == GP_OK && e != cudaSuccess) return fail(ctx, GP_ECUDA, "GP_AUTO: %s", cudaGetErrorString(e));
+        return rc;
+    };
+    int rc = mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu, sigma2, logdet, status, 3, cond_all);
+    if (rc) return done(rc);
+    if (gp::launch_fill_int(pu, T, GP_FP32, ctx->stream) != cudaSuccess)
+        return done(fail(ctx, GP_ECUDA, "GP_AUTO: fill launch failed"));
+    std::vector<int> hst(T);
+    std::vector<double> hc(T), hth((size_t)T * d);
+    if (cudaMemcpyAsync(hst.data(), status, (size_t)T * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaMemcpyAsync(hc.data(), cond_all, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaMemcpyAsync(hth.data(), theta, (size_t)T * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaStreamSynchronize(ctx->stream))
+        return done(fail(ctx, GP_ECUDA, "GP_AUTO: reading the estimates failed"));
+    // a candidate moves on unless it factored and its bound meets the tolerance
+    auto needs_more = [&](int st, double cnd, int s) {
+        if (st == GP_EINVAL || st == GP_ETIMEOUT) return false;
+        if (st != GP_OK) return true;
+        return !(cnd * split_error_per_cond(s) <= tol);
+    };
+    std::vector<int> idx;
+    for (int t = 0; t < T; ++t)
+        if (needs_more(hst[t], hc[t], 3)) idx.push_back(t);
+    for (int tier = 0; tier < 2 && !idx.empty(); ++tier) {
+        const int m = (int)idx.size();
+        const int prec = tier == 0 ? GP_MIXED : GP_FP64;
+        std::vector<double> thc((size_t)m * d);
+        for (int i = 0; i < m; ++i)
+            std::memcpy(&thc[(size_t)i * d], &hth[(size_t)idx[i] * d], d * sizeof(double));
+        if (cudaMemcpyAsync(th_c, thc.data(), thc.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) ||
+            cudaMemcpyAsync(idx_d, idx.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream))
+            return done(fail(ctx, GP_ECUDA, "GP_AUTO: staging copy failed"));
+        if (prec == GP_MIXED)
+            rc = mixed_nll_batch(ctx, n, d, x, y, m, th_c, p, delta, nll_c, mu_c, s2_c, ld_c, st_c,
+                                 ctx->opt.slices, cond_c);
+        else
+            rc = fp64_nll_batch(ctx, n, d, x, y, m, th_c, p, delta, nll_c, mu_c, s2_c, ld_c, st_c);
+        if (rc) return done(rc);
+        cudaStream_t s = ctx->stream;
+        if (gp::launch_scatter(m, idx_d, nll_c, nll, s) || gp::launch_scatter(m, idx_d, mu_c, mu, s) ||
+            gp::launch_scatter(m, idx_d, s2_c, sigma2, s) ||
+            (logdet && gp::launch_scatter(m, idx_d, ld_c, logdet, s)) ||
+            gp::launch_scatter_int(m, idx_d, st_c, status, s) ||
+            (prec == GP_MIXED && gp::launch_scatter(m, idx_d, cond_c, cond_all, s)) ||
+            gp::launch_fill_int(st_c, m, prec, s) || gp::launch_scatter_int(m, idx_d, st_c, pu, s))
+            return done(fail(ctx, GP_ECUDA, "GP_AUTO: scatter launch failed"));
+        if (prec == GP_FP64) break;
+        // statuses of the subset are in `status` now; the estimates in cond_c
+        std::vector<int> sst(m);
+        std::vector<double> sc(m);
+        if (cudaMemcpyAsync(sc.data(), cond_c, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, s) ||
+            cudaMemcpyAsync(hst.data(), status, (size_t)T * sizeof(int), cudaMemcpyDeviceToHost, s) ||
+            cudaStreamSynchronize(s))
+            return done(fail(ctx, GP_ECUDA, "GP_AUTO: reading the estimates failed"));
+        std::vector<int> next;
+        for (int i = 0; i < m; ++i)
+            if (needs_more(hst[idx[i]], sc[i], ctx->opt.slices)) next.push_back(idx[i]);
+        idx.swap(next);
+    }
+    return done(GP_OK);
 }
 
 }  // namespace
@@ -365,6 +540,7 @@ void gp_default_options(gp_options* opt) {
     opt->update_groups = 4;
     opt->inject_timeout = 0;
     opt->fuse_panels = 1;
+    opt->auto_tol = 1e-6;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -397,6 +573,7 @@ void gp_destroy(gp_ctx* ctx) {
     // models outlive their context safely: they are detached and freed on
     // their own later (synchronously)
     for (gp_model* m : ctx->models) m->ctx = nullptr;
+    for (gp_plan* q : ctx->plans) q->ctx = nullptr;
     if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -428,6 +605,8 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
         return fail(ctx, GP_EINVAL, "update_groups must be 3, 4 or 7");
     if (opt->fuse_panels && opt->update_groups != 4)
         return fail(ctx, GP_EINVAL, "fuse_panels needs update_groups = 4");
+    if (!(opt->auto_tol > 0.0) || !std::isfinite(opt->auto_tol))
+        return fail(ctx, GP_EINVAL, "auto_tol = %g must be positive and finite", opt->auto_tol);
     ctx->opt = *opt;
     return GP_OK;
 }
@@ -502,7 +681,8 @@ int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
     if (rc) return rc;
     if (!x || !theta || !L || !status_host) return fail(ctx, GP_EINVAL, "null pointer argument");
     if (prec == GP_AUTO) prec = GP_MIXED;
-    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32)
+        return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int nt = gp::num_tiles(n);
     gp::InstState* st = nullptr;
@@ -521,10 +701,11 @@ int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
         rc = run_factor_f64(ctx, b);
         if (rc) return rc;
     } else {
-        const MixedSizes z = mixed_sizes(n, ctx->opt.slices);
+        const int slices = prec == GP_FP32 ? 3 : ctx->opt.slices;
+        const MixedSizes z = mixed_sizes(n, slices);
         rc = ensure_ws(ctx, z.per + 256);
         if (rc) return rc;
-        gp::MixedBatch mb = mixed_layout(ctx, n, 1, nullptr, (char*)ctx->ws, z, 1);
+        gp::MixedBatch mb = mixed_layout(ctx, n, 1, nullptr, (char*)ctx->ws, z, 1, slices);
         rc = run_mixed_factor(ctx, mb, d, x, theta, p, delta);
         if (rc) return rc;
         GP_CUDA(ctx, gp::launch_df_to_double(mb.A, L, gp::packed_elems(n), ctx->stream));
@@ -535,55 +716,163 @@ int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
     return GP_OK;
 }
 
-int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
-                 const double* theta, double p, double delta, int prec, double* nll,
-                 double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
+int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                    const double* theta, double p, double delta, int prec, double* nll,
+                    double* mu_hat, double* sigma2_hat, double* logdet, int* status, double* cond1,
+                    int* prec_used) {
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
     if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
     if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
         return fail(ctx, GP_EINVAL, "null pointer argument");
-    if (prec == GP_AUTO) prec = GP_MIXED;
-    if (prec != GP_FP64 && prec != GP_MIXED) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32 && prec != GP_AUTO)
+        return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+    if (prec == GP_FP64 && cond1)
+        return fail(ctx, GP_ENOTSUP, "the condition estimate comes with the split-precision factor only");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
-    if (prec == GP_MIXED)
-        return mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status);
-    const int nt = gp::num_tiles(n);
-    const size_t per = per_instance_bytes_f64(n);
-    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
-    long long cap = (long long)(avail / per);
-    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
-    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
-    if (cap > 65535) cap = 65535;  // grid.y bound of the per-instance launches
-    const int Tc = (int)(cap < T ? cap : T);
-    rc = ensure_ws(ctx, per * (size_t)Tc);
-    if (rc) return rc;
-    char* base = (char*)ctx->ws;
-    const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
-    const size_t z_bytes = align256((size_t)2 * nt * GP_NB * sizeof(double));
-    double* A = (double*)base;
-    double* Z = (double*)(base + a_bytes * Tc);
-    gp::InstState* st = (gp::InstState*)(base + (a_bytes + z_bytes) * Tc);
-    for (int c0 = 0; c0 < T; c0 += Tc) {
-        const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
-        gp::Batch b{};
-        b.n = n; b.d = d; b.nt = nt; b.count = cnt;
-        b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
-        b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
-        {
-            PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
-            GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
-            GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
-        }
-        rc = run_factor_f64(ctx, b);
-        if (rc) return rc;
-        const size_t zs = z_bytes / sizeof(double);
-        PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
-        GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
-        GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, mu_hat + c0, sigma2_hat + c0,
-                                         logdet ? logdet + c0 : nullptr, status + c0, ctx->stream));
+    if (prec == GP_AUTO)
+        return auto_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status,
+                              cond1, prec_used);
+    if (prec == GP_FP64)
+        rc = fp64_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status);
+    else
+        rc = mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status,
+                             prec == GP_FP32 ? 3 : ctx->opt.slices, cond1);
+    if (rc == GP_OK && prec_used) GP_CUDA(ctx, gp::launch_fill_int(prec_used, T, prec, ctx->stream));
+    return rc;
+}
+
+int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                 const double* theta, double p, double delta, int prec, double* nll,
+                 double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
+    return gp_nll_batch_ex(ctx, n, d, x, y, T, theta, p, delta, prec, nll, mu_hat, sigma2_hat, logdet,
+                           status, nullptr, nullptr);
+}
+
+int gp_plan_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                      const double* theta, double p, double delta, int prec, double* nll,
+                      double* mu_hat, double* sigma2_hat, double* logdet, int* status, double* cond1,
+                      gp_plan** out) {
+    if (!out) return fail(ctx, GP_EINVAL, "null plan pointer");
+    *out = nullptr;
+    if (!ctx) return GP_EINVAL;
+    if (prec == GP_AUTO)
+        return fail(ctx, GP_ENOTSUP, "GP_AUTO routes candidates on the host and cannot be recorded");
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    // the plan gets a workspace of its own: the context's arena is set aside
+    // (still counted against the budget) while the call runs and is recorded
+    void* saved_ws = ctx->ws;
+    const size_t saved_bytes = ctx->ws_bytes;
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    ctx->models_bytes += saved_bytes;
+    auto restore = [&]() {
+        ctx->models_bytes -= saved_bytes;
+        ctx->ws = saved_ws;
+        ctx->ws_bytes = saved_bytes;
+    };
+    auto release_own = [&]() {
+        if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    };
+    // eager run: outputs valid, workspace sized, kernel attributes set
+    int rc = gp_nll_batch_ex(ctx, n, d, x, y, T, theta, p, delta, prec, nll, mu_hat, sigma2_hat, logdet,
+                             status, cond1, nullptr);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (rc == GP_OK && e != cudaSuccess) rc = fail(ctx, GP_ECUDA, "plan: %s", cudaGetErrorString(e));
+    if (rc) {
+        release_own();
+        restore();
+        return rc;
     }
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        release_own();
+        restore();
+        return fail(ctx, GP_ECUDA, "plan: stream creation failed");
+    }
+    cudaStream_t saved_stream = ctx->stream;
+    const bool saved_timing = ctx->timing;
+    const long long l0 = ctx->launches;
+    long long ph0[GP_NUM_PHASES];
+    std::memcpy(ph0, ctx->phase_launches, sizeof ph0);
+    ctx->stream = cs;
+    ctx->timing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = gp_nll_batch_ex(ctx, n, d, x, y, T, theta, p, delta, prec, nll, mu_hat, sigma2_hat, logdet,
+                             status, cond1, nullptr);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    const long long kernels = ctx->launches - l0;
+    ctx->launches = l0;   // recorded, not run
+    std::memcpy(ctx->phase_launches, ph0, sizeof ph0);
+    ctx->stream = saved_stream;
+    ctx->timing = saved_timing;
+    cudaStreamDestroy(cs);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == GP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (rc || e != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        release_own();
+        restore();
+        return rc ? rc : fail(ctx, GP_ECUDA, "plan: recording failed: %s", cudaGetErrorString(e));
+    }
+    gp_plan* q = new gp_plan();
+    q->ctx = ctx;
+    q->graph = graph;
+    q->exec = exec;
+    q->ws = ctx->ws;
+    q->ws_bytes = ctx->ws_bytes;
+    q->kernels = kernels;
+    restore();
+    ctx->models_bytes += q->ws_bytes;
+    ctx->plans.push_back(q);
+    *out = q;
     return GP_OK;
+}
+
+int gp_plan_launch(gp_plan* q) {
+    if (!q) return GP_EINVAL;
+    if (!q->ctx) return GP_EINVAL;   // its context is gone
+    gp_ctx* ctx = q->ctx;
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    GP_CUDA(ctx, cudaGraphLaunch(q->exec, ctx->stream));
+    ctx->launches += q->kernels;
+    return GP_OK;
+}
+
+long long gp_plan_kernels(const gp_plan* q) { return q ? q->kernels : -1; }
+
+size_t gp_plan_bytes(const gp_plan* q) { return q ? q->ws_bytes : 0; }
+
+void gp_plan_destroy(gp_plan* q) {
+    if (!q) return;
+    if (q->ctx) {
+        gp_ctx* ctx = q->ctx;
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        ctx->models_bytes -= q->ws_bytes;
+        auto& v = ctx->plans;
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i] == q) {
+                v[i] = v.back();
+                v.pop_back();
+                break;
+            }
+        cudaGraphExecDestroy(q->exec);
+        cudaGraphDestroy(q->graph);
+        cudaFreeAsync(q->ws, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    } else {
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(q->exec);
+        cudaGraphDestroy(q->graph);
+        cudaFree(q->ws);
+    }
+    delete q;
 }
 
 int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host, const double* y_host, int T,
@@ -642,7 +931,7 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
     if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
-    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_AUTO)
+    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32 && prec != GP_AUTO)
         return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
     // The model is always factored in double: one factorisation per fit, and
     // the kriging variance needs r'R^-1 r to full precision (the paper, too,

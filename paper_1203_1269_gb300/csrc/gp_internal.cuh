@@ -58,6 +58,13 @@ struct InstState {
     double bb;
     int status;
     int fail_col;
+    // 1-norm condition estimate (split path, k_cond.cu): ||R||_1, Hager's
+    // estimate of ||R^-1||_1 and the iteration's state
+    double anorm;
+    double est;
+    int hager_iter;
+    int hager_jprev;
+    int hager_done;   // 1: the estimate has stopped; the solve kernels skip the instance
 };
 
 // Batched problem description handed to the kernels (by value).
@@ -97,13 +104,16 @@ struct MixedBatch {
     float2* WT;                   // L_JJ^-1 per diagonal block, double-float tiles: [J][128 x 128]
     size_t wt_stride;
     size_t ps_stride, pe_stride, ws_stride, we_stride;
-    float2* Z;                    // 5 columns of npad double-float values (x_1, x_y, two
-                                  // residual columns, 1 / L_ii)
+    float2* Z;                    // 8 columns of npad double-float values: x_1, x_y, two
+                                  // residual columns, 1 / L_ii, two condition-estimate
+                                  // columns, |R| row sums
     size_t z_stride;
     const double* y;
     InstState* st;
     int* err;                     // set when a bounded device wait gave up
 };
+
+constexpr int kZCols = 8;
 
 // ---- context accessors (gp_capi.cu) ----------------------------------------
 int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...);
@@ -143,6 +153,11 @@ cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s);
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s);
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s);
+cudaError_t launch_norm1(const MixedBatch& b, cudaStream_t s);
+cudaError_t launch_hager(const MixedBatch& b, int phase, double* cond, cudaStream_t s);
+cudaError_t launch_fill_int(int* dst, int count, int value, cudaStream_t s);
+cudaError_t launch_scatter(int m, const int* idx, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_scatter_int(int m, const int* idx, const int* src, int* dst, cudaStream_t s);
 cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2,
                                double* logdet, int* status, cudaStream_t s);
 cudaError_t launch_df_to_double(const float2* src, double* dst, size_t count, cudaStream_t s);

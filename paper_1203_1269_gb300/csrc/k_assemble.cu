@@ -74,6 +74,8 @@ __global__ void k_validate_theta(Batch b) {
     s.logdet = 0.0; s.aa = 0.0; s.ab = 0.0; s.mu = 0.0; s.Q = 0.0; s.bb = 0.0;
     s.status = bad ? GP_EINVAL : GP_OK;
     s.fail_col = -1;
+    s.anorm = 0.0; s.est = 0.0;
+    s.hager_iter = 0; s.hager_jprev = -1; s.hager_done = 0;
     b.st[t] = s;
 }
 

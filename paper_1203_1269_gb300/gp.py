@@ -17,8 +17,9 @@ import torch
 
 from . import build as _build
 
-GP_FP64, GP_MIXED, GP_AUTO = 0, 1, 3
-PRECISIONS = {"fp64": GP_FP64, "mixed": GP_MIXED, "auto": GP_AUTO}
+GP_FP64, GP_MIXED, GP_FP32, GP_AUTO = 0, 1, 2, 3
+PRECISIONS = {"fp64": GP_FP64, "mixed": GP_MIXED, "fp32": GP_FP32, "auto": GP_AUTO}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ENOTPD", -4: "ECUDA", -5: "ETIMEOUT",
           -6: "EDEGENERATE", -7: "ENOTSUP"}
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_EDEGENERATE, GP_ENOTSUP = \
@@ -36,7 +37,7 @@ class GPError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
                 ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int),
-                ("inject_timeout", _c_int), ("fuse_panels", _c_int)]
+                ("inject_timeout", _c_int), ("fuse_panels", _c_int), ("auto_tol", _c_double)]
 
 
 _lib = None
@@ -77,7 +78,16 @@ def load(path=None):
                                 ctypes.POINTER(_c_int)]
     lib.gp_nll_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
                                  P, P, P, P, P]
+    lib.gp_nll_batch_ex.argtypes = lib.gp_nll_batch.argtypes + [P, P]
     lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
+    lib.gp_plan_nll_batch.argtypes = lib.gp_nll_batch.argtypes + [P, ctypes.POINTER(P)]
+    lib.gp_plan_launch.argtypes = [P]
+    lib.gp_plan_kernels.argtypes = [P]
+    lib.gp_plan_kernels.restype = ctypes.c_longlong
+    lib.gp_plan_bytes.argtypes = [P]
+    lib.gp_plan_bytes.restype = _c_size
+    lib.gp_plan_destroy.argtypes = [P]
+    lib.gp_plan_destroy.restype = None
     lib.gp_nll_batch_noalloc.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double,
                                          P, P, P, P, P]
     lib.gp_fit.argtypes = [P, _c_int, _c_int, P, P, P, _c_double, _c_double, _c_int,
@@ -143,6 +153,37 @@ class Model:
 
     def __del__(self):
         # at interpreter shutdown the CUDA runtime may already be gone
+        if sys.is_finalizing():
+            return
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A gp_nll_batch call recorded as one CUDA graph (gp_plan_nll_batch).
+    launch() replays it: it re-reads the bound x, y and thetas tensors and
+    overwrites `out`.  Keep those tensors alive while the plan lives."""
+
+    def __init__(self, ctx, handle, inputs, out):
+        self._ctx = ctx
+        self._h = handle
+        self._keep = inputs           # the bound tensors stay referenced
+        self.out = out
+        self.kernels = int(ctx._lib.gp_plan_kernels(handle))
+        self.bytes = int(ctx._lib.gp_plan_bytes(handle))
+
+    def launch(self):
+        self._ctx._check(self._ctx._lib.gp_plan_launch(self._h))
+        return self.out
+
+    def free(self):
+        if self._h:
+            self._ctx._lib.gp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
         if sys.is_finalizing():
             return
         try:
@@ -251,8 +292,11 @@ class Context:
         return out, st.value
 
     # -- gp_nll_batch ------------------------------------------------------
-    def nll_batch(self, x, y, thetas, p, delta, prec="fp64", out=None):
-        """-2logL, mu_hat, sigma2_hat, log|R| and status at each row of thetas."""
+    def nll_batch(self, x, y, thetas, p, delta, prec="fp64", out=None, cond=False):
+        """-2logL, mu_hat, sigma2_hat, log|R| and status at each row of thetas.
+        cond=True adds out["cond"], the 1-norm condition estimate of each R
+        (split precisions only); prec="auto" adds out["prec_used"] (the
+        arithmetic each candidate's values come from, a GP_* code)."""
         x = _dev_f64(x, "x", device=self.device)
         n, d = x.shape
         y = _dev_f64(y, "y", (n,), self.device)
@@ -265,11 +309,38 @@ class Context:
             out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw),
                        sigma2=torch.empty(T, **kw), logdet=torch.empty(T, **kw),
                        status=torch.empty(T, dtype=torch.int32, device=self.device))
-        self._check(self._lib.gp_nll_batch(
-            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
+        pc = _prec(prec)
+        if cond and "cond" not in out:
+            out["cond"] = torch.empty(T, dtype=torch.float64, device=self.device)
+        if pc == GP_AUTO and "prec_used" not in out:
+            out["prec_used"] = torch.empty(T, dtype=torch.int32, device=self.device)
+        self._check(self._lib.gp_nll_batch_ex(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), pc,
             _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
-            _ptr(out["status"])))
+            _ptr(out["status"]), _ptr(out.get("cond") if cond else None), _ptr(out.get("prec_used"))))
         return out
+
+    def plan_nll_batch(self, x, y, thetas, p, delta, prec="mixed", cond=False):
+        """Record nll_batch(x, y, thetas, ...) as a CUDA graph; returns a Plan
+        whose launch() replays it into plan.out (also valid on return)."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        kw = dict(dtype=torch.float64, device=self.device)
+        out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw), sigma2=torch.empty(T, **kw),
+                   logdet=torch.empty(T, **kw), status=torch.empty(T, dtype=torch.int32, device=self.device))
+        if cond:
+            out["cond"] = torch.empty(T, **kw)
+        h = _vp()
+        self._check(self._lib.gp_plan_nll_batch(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
+            _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out["logdet"]), _ptr(out["status"]),
+            _ptr(out.get("cond")), ctypes.byref(h)))
+        return Plan(self, h, (x, y, thetas), out)
 
     def nll_batch_noalloc(self, x, y, thetas, p, delta, out=None):
         """gp_nll_batch_noalloc: the double-precision batch with the library's
