@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int 
     __shared__ dfl part[4][2][GP_NB];
     __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK) return;
+    if (b.st[t].status != GP_OK || b.st[t].hager_done) return;
     const int nt = b.nt, n = b.n;
     float2* z0 = zcol(b, t, c0);
     float2* z1 = zcol(b, t, c0 + 1);
@@ -968,7 +968,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int
     __shared__ dfl part[4][2][GP_NB];
     __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK) return;
+    if (b.st[t].status != GP_OK || b.st[t].hager_done) return;
     const int nt = b.nt;
     float2* z0 = zcol(b, t, c0);
     float2* z1 = zcol(b, t, c0 + 1);
