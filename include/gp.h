@@ -103,6 +103,12 @@ typedef struct {
                              matrix); 0: one pass per panel.  Needs update_groups = 4 */
     double auto_tol;      /* GP_AUTO: relative error of -2logL each candidate must meet,
                              default 1e-6 */
+    int update_tile;      /* split path: columns of a trailing-update output tile, 128
+                             (default) or 64 (twice the work items, for small problems;
+                             same products in the same order, so the same results).
+                             64 needs update_groups = 4 */
+    int assemble_cols;    /* split path: tile columns per CTA of the double-float
+                             assembly, 16 (default) or 32; same results */
 } gp_options;
 
 void gp_default_options(gp_options* opt);
@@ -128,6 +134,9 @@ int gp_set_stream(gp_ctx* ctx, void* cuda_stream);
 
 /* Replace the context's tunables (copied). */
 int gp_set_options(gp_ctx* ctx, const gp_options* opt);
+
+/* Copy the context's current tunables into *opt (gp_autotune may change them). */
+int gp_get_options(const gp_ctx* ctx, gp_options* opt);
 
 /* Bytes of device workspace currently held by the context. */
 size_t gp_workspace_bytes(const gp_ctx* ctx);
@@ -220,6 +229,26 @@ int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y,
                     const double* theta, double p, double delta, int prec,
                     double* nll, double* mu_hat, double* sigma2_hat, double* logdet,
                     int* status, double* cond1, int* prec_used);
+
+/* Launch-shape autotuner.  Times gp_nll_batch(prec) on the caller's batch
+ * for every combination of update_tile (128, 64), fuse_panels (1, 0) and
+ * assemble_cols (16, 32) -- one untimed call, then `reps` calls timed with
+ * CUDA events on the context's stream, median -- and keeps the fastest as
+ * the context's options.  update_tile and assemble_cols never change
+ * results; fuse_panels changes the rounding of the trailing updates (both
+ * settings meet the split path's accuracy).  trials (may be NULL) receives
+ * up to max_trials entries and *ntrials the number of combinations timed.
+ * prec: GP_MIXED or GP_FP32 (GP_ENOTSUP otherwise: the FP64 path has no
+ * shape choices).  Outputs go to a staging area; synchronises. */
+typedef struct {
+    int update_tile;
+    int fuse_panels;
+    int assemble_cols;
+    double ms;            /* median device time of one gp_nll_batch call */
+} gp_tune_trial;
+int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                const double* theta, double p, double delta, int prec, int reps,
+                gp_tune_trial* trials, int max_trials, int* ntrials);
 
 /* A batch recorded as one CUDA graph.  gp_plan_nll_batch evaluates the call
  * once (eagerly, so that its outputs are also valid on return), then records

@@ -1,6 +1,7 @@
 // gp_capi.cu -- the C ABI of libgp (declared in include/gp.h): contexts,
 // argument checks, the device workspace, batching of theta candidates and
 // the sequence of kernel launches for each call.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -218,6 +219,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.ps = GP_PANEL_SLICES;
     mb.ug = ctx->opt.update_groups;
     mb.inject_timeout = ctx->opt.inject_timeout;
+    mb.update_tile = ctx->opt.update_tile;
     mb.sp = mb.s > mb.ps ? mb.s : mb.ps;
     mb.inst_stride = z.A / sizeof(float2);
     mb.ps_stride = z.PS / sizeof(__nv_bfloat16);
@@ -240,6 +242,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
     b.n = mb.n; b.d = d; b.nt = mb.nt; b.count = mb.count; b.p = p; b.delta = delta;
     b.x = x; b.y = mb.y; b.theta = theta; b.A = nullptr; b.Adf = mb.A; b.Rdf = mb.Rc;
     b.inst_stride = mb.inst_stride; b.st = mb.st;
+    b.asm_cols = ctx->opt.assemble_cols;
     mb.d = d;
     GP_CUDA(ctx, cudaMemsetAsync(mb.err, 0, sizeof(int), ctx->stream));
     {
@@ -541,6 +544,8 @@ void gp_default_options(gp_options* opt) {
     opt->inject_timeout = 0;
     opt->fuse_panels = 1;
     opt->auto_tol = 1e-6;
+    opt->update_tile = 128;
+    opt->assemble_cols = 16;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -607,7 +612,19 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
         return fail(ctx, GP_EINVAL, "fuse_panels needs update_groups = 4");
     if (!(opt->auto_tol > 0.0) || !std::isfinite(opt->auto_tol))
         return fail(ctx, GP_EINVAL, "auto_tol = %g must be positive and finite", opt->auto_tol);
+    if (opt->update_tile != 128 && opt->update_tile != 64)
+        return fail(ctx, GP_EINVAL, "update_tile must be 128 or 64");
+    if (opt->update_tile == 64 && opt->update_groups != 4)
+        return fail(ctx, GP_EINVAL, "update_tile = 64 needs update_groups = 4");
+    if (opt->assemble_cols != 16 && opt->assemble_cols != 32)
+        return fail(ctx, GP_EINVAL, "assemble_cols must be 16 or 32");
     ctx->opt = *opt;
+    return GP_OK;
+}
+
+int gp_get_options(const gp_ctx* ctx, gp_options* opt) {
+    if (!ctx || !opt) return GP_EINVAL;
+    *opt = ctx->opt;
     return GP_OK;
 }
 
@@ -747,6 +764,78 @@ int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, in
                  double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
     return gp_nll_batch_ex(ctx, n, d, x, y, T, theta, p, delta, prec, nll, mu_hat, sigma2_hat, logdet,
                            status, nullptr, nullptr);
+}
+
+int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T, const double* theta,
+                double p, double delta, int prec, int reps, gp_tune_trial* trials, int max_trials, int* ntrials) {
+    if (ntrials) *ntrials = 0;
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
+    if (prec != GP_MIXED && prec != GP_FP32)
+        return fail(ctx, GP_ENOTSUP, "the autotuner chooses split-precision launch shapes only");
+    if (reps < 1) reps = 1;
+    if (reps > 20) reps = 20;
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t bT = align256((size_t)T * sizeof(double));
+    void* dev = nullptr;
+    if (cudaMallocAsync(&dev, 4 * bT + align256((size_t)T * sizeof(int)), ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GP_ENOMEM, "autotuner staging allocation failed");
+    }
+    char* c = (char*)dev;
+    double* o_nll = (double*)c;
+    double* o_mu = (double*)(c + bT);
+    double* o_s2 = (double*)(c + 2 * bT);
+    double* o_ld = (double*)(c + 3 * bT);
+    int* o_st = (int*)(c + 4 * bT);
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    const gp_options base = ctx->opt;
+    gp_options best = base;
+    double best_ms = INFINITY;
+    int count = 0;
+    for (int ut : {128, 64}) {
+        for (int fuse : {1, 0}) {
+            for (int ac : {16, 32}) {
+                if (base.update_groups != 4 && (fuse || ut == 64)) continue;
+                gp_options o = base;
+                o.update_tile = ut;
+                o.fuse_panels = fuse;
+                o.assemble_cols = ac;
+                ctx->opt = o;
+                std::vector<float> ms;
+                for (int r = 0; r <= reps && rc == GP_OK; ++r) {
+                    cudaEventRecord(e0, ctx->stream);
+                    rc = gp_nll_batch(ctx, n, d, x, y, T, theta, p, delta, prec, o_nll, o_mu, o_s2, o_ld, o_st);
+                    cudaEventRecord(e1, ctx->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess && rc == GP_OK)
+                        rc = fail(ctx, GP_ECUDA, "autotuner: timing failed");
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (r > 0) ms.push_back(t);   // the first call is the warm-up
+                }
+                if (rc) break;
+                std::sort(ms.begin(), ms.end());
+                const double med = ms[ms.size() / 2];
+                if (trials && count < max_trials) trials[count] = gp_tune_trial{ut, fuse, ac, med};
+                ++count;
+                if (med < best_ms) {
+                    best_ms = med;
+                    best = o;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    ctx->ev_pool.push_back(e0);
+    ctx->ev_pool.push_back(e1);
+    ctx->opt = rc ? base : best;
+    cudaFreeAsync(dev, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (ntrials) *ntrials = count;
+    return rc;
 }
 
 int gp_plan_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,

@@ -9,6 +9,8 @@
 // lower triangle holds L.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -40,8 +42,10 @@ __host__ __device__ inline size_t packed_elems(int n) {
 }
 
 // lower-triangle linear index q -> (i, k), k <= i, over an m x m triangle
+// (a float square root seeds r, the integer loops make it exact: FP64 is
+// scarce on this GPU and this runs once per work item in every warp role)
 __device__ inline void tri_decode(int q, int& i, int& k) {
-    int r = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    int r = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
     while ((long long)(r + 1) * (r + 2) / 2 <= q) ++r;
     while ((long long)r * (r + 1) / 2 > q) --r;
     i = r;
@@ -79,6 +83,7 @@ struct Batch {
     float2* Rdf;                  // double-float copy of R (split path)
     size_t inst_stride;           // elements between instances in A / Adf / Rdf
     InstState* st;                // count
+    int asm_cols;                 // double-float assembly: tile columns per CTA (16 or 32)
 };
 
 // Split-precision path: per-instance buffers (double-float tiles, bf16
@@ -89,6 +94,7 @@ struct MixedBatch {
     int ps;                       // slices of the panel solve operands (GP_PANEL_SLICES)
     int ug;                       // accumulator groups of the trailing update (3, 4 or 7)
     int inject_timeout;           // test hook: one split-GEMM CTA waits on a barrier nothing signals
+    int update_tile;              // columns of a trailing-update output tile (128 or 64)
     int sp;                       // slice slots per row block in PS (max(s, ps))
     float2* A;                    // working matrix -> factor (double-float tiles)
     float2* Rc;                   // copy of R (double-float tiles), for residuals
@@ -114,6 +120,25 @@ struct MixedBatch {
 };
 
 constexpr int kZCols = 8;
+
+// A kernel's dynamic shared-memory limit is a per-device attribute: each
+// launcher keeps the largest size it has set on every device ordinal and
+// raises the limit once per device (and again when it needs more).
+constexpr int kMaxDevices = 64;
+template <typename Kernel>
+inline cudaError_t raise_smem_limit(Kernel* kernel, size_t bytes, std::atomic<size_t> (&done)[kMaxDevices]) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && bytes <= done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) {
+        size_t cur = done[dev].load(std::memory_order_relaxed);
+        while (cur < bytes && !done[dev].compare_exchange_weak(cur, bytes)) {
+        }
+    }
+    return e;
+}
 
 // ---- context accessors (gp_capi.cu) ----------------------------------------
 int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...);

@@ -24,11 +24,9 @@ constexpr int kThreads = 256;
 constexpr int kSplit = 4;                       // a CTA covers NB/kSplit columns of a tile
 constexpr int kCols = GP_NB / kSplit;           // 32 columns
 constexpr int kEntries = GP_NB * kCols / kThreads;  // 16 entries per thread
-// double-float variant: finer column parts, so that the last wave of CTAs is
-// nearly full
-constexpr int kSplitDf = 8;
-constexpr int kColsDf = GP_NB / kSplitDf;       // 16 columns
-constexpr int kEntriesDf = GP_NB * kColsDf / kThreads;  // 8 entries per thread
+// double-float variant: COLS (16 or 32) tile columns per CTA -- narrower
+// parts fill the last wave of CTAs better, wider ones share each theta
+// load over more entries
 
 __device__ __forceinline__ double powabs(double diff, double p) {
     double a = fabs(diff);
@@ -159,9 +157,12 @@ k_assemble_tiles(Batch b, int group) {
 // two thirds of its instructions).  Writes the working matrix and its copy.
 // Dynamic smem: x rows/cols (double), theta of the group and the exp table
 // (double-float), the group's status flags.
-template <int DB>
+template <int DB, int COLS>
 __global__ void __launch_bounds__(kThreads)
 k_assemble_tiles_df(Batch b, int group) {
+    constexpr int kSplitDf = GP_NB / COLS;
+    constexpr int kColsDf = COLS;
+    constexpr int kEntriesDf = GP_NB * COLS / kThreads;
     extern __shared__ double dsm[];
     double* xs_r = dsm;                                  // GP_NB * DB
     double* xs_c = xs_r + GP_NB * DB;                    // kColsDf * DB
@@ -327,25 +328,30 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
     groups = (b.count + group - 1) / group;
     dim3 grid((unsigned)ctas_per_group, (unsigned)groups);
     if (b.Adf && b.d <= 16) {
-        long long g_df = (4 * 152 + tiles * kSplitDf - 1) / (tiles * kSplitDf);
+        const int cols = (b.asm_cols == 32) ? 32 : 16;
+        const int split = GP_NB / cols;
+        long long g_df = (4 * 152 + tiles * split - 1) / (tiles * split);
         if (g_df < 1) g_df = 1;
         if (g_df > b.count) g_df = b.count;
         group = (int)((b.count + g_df - 1) / g_df);
         g_df = (b.count + group - 1) / group;
-        grid = dim3((unsigned)(tiles * kSplitDf), (unsigned)g_df);
+        grid = dim3((unsigned)(tiles * split), (unsigned)g_df);
         const int DB = b.d <= 4 ? 4 : (b.d <= 8 ? 8 : 16);
-        const size_t smem = (size_t)(GP_NB + kColsDf) * DB * sizeof(double) +
+        const size_t smem = (size_t)(GP_NB + cols) * DB * sizeof(double) +
                             ((size_t)group * DB + 64) * sizeof(dfl) + (size_t)group * sizeof(int);
         cudaError_t e = cudaSuccess;
-        if (DB == 4) {
-            e = cudaFuncSetAttribute(k_assemble_tiles_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assemble_tiles_df<4><<<grid, kThreads, smem, s>>>(b, group);
-        } else if (DB == 8) {
-            e = cudaFuncSetAttribute(k_assemble_tiles_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assemble_tiles_df<8><<<grid, kThreads, smem, s>>>(b, group);
+        auto go = [&](auto kern) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) kern<<<grid, kThreads, smem, s>>>(b, group);
+        };
+        if (cols == 16) {
+            if (DB == 4) go(k_assemble_tiles_df<4, 16>);
+            else if (DB == 8) go(k_assemble_tiles_df<8, 16>);
+            else go(k_assemble_tiles_df<16, 16>);
         } else {
-            e = cudaFuncSetAttribute(k_assemble_tiles_df<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assemble_tiles_df<16><<<grid, kThreads, smem, s>>>(b, group);
+            if (DB == 4) go(k_assemble_tiles_df<4, 32>);
+            else if (DB == 8) go(k_assemble_tiles_df<8, 32>);
+            else go(k_assemble_tiles_df<16, 32>);
         }
         if (e != cudaSuccess) return e;
         return cudaGetLastError();

@@ -159,13 +159,9 @@ __global__ void __launch_bounds__(kThreads) k_update_f64(Batch b, int J) {
 
 cudaError_t launch_potrf_f64(const Batch& b, int J, cudaStream_t s) {
     const size_t smem = GP_TILE_ELEMS * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_potrf_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_potrf_f64, smem, attr);
+    if (e != cudaSuccess) return e;
     k_potrf_f64<<<b.count, kThreads, smem, s>>>(b, J);
     return cudaGetLastError();
 }
@@ -174,13 +170,9 @@ cudaError_t launch_trsm_f64(const Batch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
     const size_t smem = GP_TILE_ELEMS * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_trsm_f64, smem, attr);
+    if (e != cudaSuccess) return e;
     k_trsm_f64<<<dim3(m, b.count), kThreads, smem, s>>>(b, J);
     return cudaGetLastError();
 }

@@ -251,12 +251,9 @@ cudaError_t launch_scatter_int(int m, const int* idx, const int* src, int* dst, 
 
 cudaError_t launch_norm1(const MixedBatch& b, cudaStream_t s) {
     const size_t smem = (size_t)GP_NB * kStage * sizeof(dfl);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_norm1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_norm1, smem, attr);
+    if (e != cudaSuccess) return e;
     k_norm1<<<b.count, kThreads, smem, s>>>(b);
     return cudaGetLastError();
 }

@@ -392,12 +392,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     }
 }
 
-// Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x, into row block I
-// of PS.  512 threads per tile: thread (r, q) owns row r's columns
-// 32q .. 32q + 31, which form exactly image chunk q, so it loads its values
-// once (coalesced along r) and writes only its own 16-byte pieces.  The four
-// owners of a row agree on the row's exponent through shared memory.
-constexpr int kSplitThreads = 512;
+// Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x / 2, into row
+// block I of PS.  A CTA of 256 threads takes one half (64 rows) of a tile,
+// so that two CTAs share an SM and one's loads overlap the other's slicing:
+// thread (r, q) owns row r's columns 32q .. 32q + 31, which form exactly
+// image chunk q, so it loads its values once (coalesced along r) and writes
+// only its own 16-byte pieces.  The four owners of a row agree on the row's
+// exponent through shared memory.
+constexpr int kSplitThreads = 256;
+constexpr int kSplitRows = kSplitThreads / 4;   // rows of a tile per CTA
 
 __device__ __forceinline__ int exponent_of(float mx) {
     // mx = f 2^E with f in [0.5, 1); 0 for mx == 0
@@ -411,21 +414,22 @@ __device__ __forceinline__ int exponent_of(float mx) {
 }
 
 __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns) {
-    __shared__ float pmax[4][GP_NB];
+    __shared__ float pmax[4][kSplitRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
-    const int I = J + 1 + blockIdx.x;
+    const int I = J + 1 + blockIdx.x / 2;
     const float2* src = df_tile(b, b.A, t, I, J);
-    const int r = threadIdx.x & 127, q = threadIdx.x >> 7;
+    const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
+    const int r = (blockIdx.x & 1) * kSplitRows + rl;
     float2 v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
     float mx = 0.f;
 #pragma unroll
     for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fabsf(v[j].x));
-    pmax[q][r] = mx;
+    pmax[q][rl] = mx;
     __syncthreads();
-    mx = fmaxf(fmaxf(pmax[0][r], pmax[1][r]), fmaxf(pmax[2][r], pmax[3][r]));
+    mx = fmaxf(fmaxf(pmax[0][rl], pmax[1][rl]), fmaxf(pmax[2][rl], pmax[3][rl]));
     const int E = exponent_of(mx);
     if (q == 0) pe_block(b, t, I)[r] = E;
     // scale by 2^(7 - E) exactly (two factors when 7 - E leaves the float range)
@@ -469,17 +473,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
 }
 
 // Slices of two adjacent panels at once, for the fused (K = 256) trailing
-// update: row r of row block I = J + 2 + blockIdx.x spans tiles (I, J) and
+// update: row r of row block I = J + 2 + blockIdx.x / 2 (one half of its rows
+// per CTA, as in k_split_panel) spans tiles (I, J) and
 // (I, J + 1) and gets one exponent for all 256 columns, so the products of
 // both panels accumulate in the same tensor-memory groups.  Thread (r, q)
 // owns image chunk q of each panel; the row maximum is taken in a first pass
 // and the values are read again for slicing.
 __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int J) {
-    __shared__ float pmax[4][GP_NB];
+    __shared__ float pmax[4][kSplitRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
-    const int I = J + 2 + blockIdx.x;
-    const int r = threadIdx.x & 127, q = threadIdx.x >> 7;
+    const int I = J + 2 + blockIdx.x / 2;
+    const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
+    const int r = (blockIdx.x & 1) * kSplitRows + rl;
     const float2* src0 = df_tile(b, b.A, t, I, J);
     const float2* src1 = df_tile(b, b.A, t, I, J + 1);
     float mx = 0.f;
@@ -488,9 +494,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
         mx = fmaxf(mx, fabsf(src0[(32 * q + j) * GP_NB + r].x));
         mx = fmaxf(mx, fabsf(src1[(32 * q + j) * GP_NB + r].x));
     }
-    pmax[q][r] = mx;
+    pmax[q][rl] = mx;
     __syncthreads();
-    mx = fmaxf(fmaxf(pmax[0][r], pmax[1][r]), fmaxf(pmax[2][r], pmax[3][r]));
+    mx = fmaxf(fmaxf(pmax[0][rl], pmax[1][rl]), fmaxf(pmax[2][rl], pmax[3][rl]));
     const int E = exponent_of(mx);
     if (q == 0) fe_block(b, t, I)[r] = E;
     const int e2 = 7 - E;
@@ -1208,12 +1214,9 @@ __global__ void k_df_to_double(const float2* src, double* dst, size_t count) {
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
     const size_t smem = (size_t)kPacked * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_diag_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_diag_mixed, smem, attr);
+    if (e != cudaSuccess) return e;
     k_diag_mixed<<<b.count, kDiagThreads, smem, s>>>(b, J);
     return cudaGetLastError();
 }
@@ -1221,16 +1224,20 @@ cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
 cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
-    k_split_panel<<<dim3(m, b.count), kSplitThreads, 0, s>>>(b, J, ns);
+    k_split_panel<<<dim3(2 * m, b.count), kSplitThreads, 0, s>>>(b, J, ns);
     return cudaGetLastError();
 }
 
+// SMs of the current device (looked up once per device ordinal)
 static int sm_count() {
-    static int n = 0;
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    int n = cached ? cache[dev].load(std::memory_order_relaxed) : 0;
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        if (cached) cache[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -1238,13 +1245,9 @@ static int sm_count() {
 template <int MODE, int NT, int NG>
 static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s, int kind = 0) {
     const size_t smem = (size_t)2 * ns * (kChunkBytes + kChunkBytes / (GP_NB / NT)) + 1024;
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_split_gemm<MODE, NT, NG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_split_gemm<MODE, NT, NG>, smem, attr);
+    if (e != cudaSuccess) return e;
     const long long total = (long long)per_inst * b.count;
     const int grid = (int)(total < sm_count() ? total : sm_count());
     k_split_gemm<MODE, NT, NG><<<grid, kGemmThreads, smem, s>>>(b, J, per_inst, kind);
@@ -1257,22 +1260,27 @@ cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s) {
     return launch_gemm<0, 64, GP_PANEL_SLICES>(b, J, 2 * m, b.ps, s);
 }
 
+// Trailing updates with 128-column output tiles, or 64-column ones (twice the
+// work items: better load balance for small problems, each output element
+// computed by the same products in the same order).
 cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
+    if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, 2 * m, b.s, s, 1);
     return launch_gemm<1, 128, 4>(b, J, m, b.s, s, 1);
 }
 
 cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 2;
     if (m <= 0) return cudaSuccess;
+    if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, m * (m + 1), b.s, s, 2);
     return launch_gemm<1, 128, 4>(b, J, m * (m + 1) / 2, b.s, s, 2);
 }
 
 cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 2;
     if (m <= 0) return cudaSuccess;
-    k_split_fused<<<dim3(m, b.count), kSplitThreads, 0, s>>>(b, J);
+    k_split_fused<<<dim3(2 * m, b.count), kSplitThreads, 0, s>>>(b, J);
     return cudaGetLastError();
 }
 
@@ -1283,7 +1291,9 @@ cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {
     switch (b.ug) {
         case 7: return launch_gemm<1, 64, 7>(b, J, 2 * tiles, b.s, s);
         case 3: return launch_gemm<1, 128, 3>(b, J, tiles, b.s, s);
-        default: return launch_gemm<1, 128, 4>(b, J, tiles, b.s, s);
+        default:
+            if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, 2 * tiles, b.s, s);
+            return launch_gemm<1, 128, 4>(b, J, tiles, b.s, s);
     }
 }
 
@@ -1294,24 +1304,18 @@ cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_
 
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s) {
     const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_df_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_df_backward, smem, attr);
+    if (e != cudaSuccess) return e;
     k_df_backward<<<b.count, kSolveThreads, smem, s>>>(b, c0, add_to);
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
     const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_df_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_df_residual, smem, attr);
+    if (e != cudaSuccess) return e;
     k_df_residual<<<b.count, kSolveThreads, smem, s>>>(b);
     return cudaGetLastError();
 }

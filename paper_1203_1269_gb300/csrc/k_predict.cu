@@ -217,12 +217,9 @@ cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* 
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
                            const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s) {
     const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + 64) * sizeof(dfl);
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_predict, smem, attr);
+    if (e != cudaSuccess) return e;
     PredArgs g;
     g.n = n; g.d = d; g.nt = nt; g.N = N;
     g.x = x; g.theta = theta; g.p = p; g.c0 = c0;

@@ -37,7 +37,13 @@ class GPError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
                 ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int),
-                ("inject_timeout", _c_int), ("fuse_panels", _c_int), ("auto_tol", _c_double)]
+                ("inject_timeout", _c_int), ("fuse_panels", _c_int), ("auto_tol", _c_double),
+                ("update_tile", _c_int), ("assemble_cols", _c_int)]
+
+
+class TuneTrial(ctypes.Structure):
+    _fields_ = [("update_tile", _c_int), ("fuse_panels", _c_int), ("assemble_cols", _c_int),
+                ("ms", _c_double)]
 
 
 _lib = None
@@ -66,6 +72,7 @@ def load(path=None):
     lib.gp_last_error.restype = ctypes.c_char_p
     lib.gp_set_stream.argtypes = [P, P]
     lib.gp_set_options.argtypes = [P, ctypes.POINTER(Options)]
+    lib.gp_get_options.argtypes = [P, ctypes.POINTER(Options)]
     lib.gp_workspace_bytes.argtypes = [P]
     lib.gp_workspace_bytes.restype = _c_size
     lib.gp_set_timing.argtypes = [P, _c_int]
@@ -81,6 +88,8 @@ def load(path=None):
     lib.gp_nll_batch_ex.argtypes = lib.gp_nll_batch.argtypes + [P, P]
     lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
     lib.gp_plan_nll_batch.argtypes = lib.gp_nll_batch.argtypes + [P, ctypes.POINTER(P)]
+    lib.gp_autotune.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int, _c_int,
+                                ctypes.POINTER(TuneTrial), _c_int, ctypes.POINTER(_c_int)]
     lib.gp_plan_launch.argtypes = [P]
     lib.gp_plan_kernels.argtypes = [P]
     lib.gp_plan_kernels.restype = ctypes.c_longlong
@@ -319,6 +328,28 @@ class Context:
             _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
             _ptr(out["status"]), _ptr(out.get("cond") if cond else None), _ptr(out.get("prec_used"))))
         return out
+
+    def autotune(self, x, y, thetas, p, delta, prec="mixed", reps=2):
+        """gp_autotune: time every launch-shape combination on this batch and
+        keep the fastest as the context's options.  Returns the trials (list
+        of dicts, in the order timed) and the chosen options."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        buf = (TuneTrial * 16)()
+        cnt = _c_int(0)
+        self._check(self._lib.gp_autotune(self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p),
+                                          float(delta), _prec(prec), int(reps), buf, 16, ctypes.byref(cnt)))
+        trials = [{f: getattr(buf[i], f) for f, _ in TuneTrial._fields_} for i in range(cnt.value)]
+        # the library changed the context's options: read them back
+        opt = Options()
+        self._check(self._lib.gp_get_options(self._h, ctypes.byref(opt)))
+        self._opt = opt
+        return trials, self.options()
 
     def plan_nll_batch(self, x, y, thetas, p, delta, prec="mixed", cond=False):
         """Record nll_batch(x, y, thetas, ...) as a CUDA graph; returns a Plan
