@@ -293,11 +293,15 @@ def run_gp(args):
         exec_flops = float(tiles) * prods * 2 * NB ** 3 * w.T * args.steps
         achieved = exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
         peak = pk["bf16_tflops_sustained"]
+        # one unit = one 128 x 128 tile updated by one 128-wide panel; a launch
+        # updates tiles * T * steps / launches of them on average (the fused
+        # launches apply two panels per tile)
+        units = tiles * w.T * args.steps / max(upd_n, 1)
         roof = {"kernel": "k_split_gemm<update>", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"],
-                                          tiles * w.T / max(nt - 1, 1)),
-                "algorithmic_bytes_per_launch": tiles * w.T / max(nt - 1, 1) * 2 * NB * NB * 8,
+                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"], units),
+                "units_per_launch": units,
+                "algorithmic_bytes_per_launch": units * NB * NB * 8,
                 "peak_source": f"bf16 dense sustained, {pk_src} (MEASURED_PEAKS.json)",
                 "flops_counted": f"executed bf16 slice products: {tiles} 128x128 tiles per "
                                  f"instance x {prods} products x 2*128^3",
