@@ -594,6 +594,32 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
+// The MMAs of one stage: every slice product (a, bb), a + bb < NS, over the
+// stage's two K = 16 steps, into accumulator group min(a + bb, NG - 1).  The
+// loops unroll for a compile-time slice count, so each MMA costs its issue
+// and two 64-bit adds to descriptors built once per stage (their address
+// field, bits 0-13, holds the byte address / 16 and does not overflow inside
+// shared memory).
+template <int NS, int NG, int NT, uint32_t kBBytes>
+__device__ __forceinline__ void issue_stage(uint32_t tacc, uint64_t ad0, uint64_t bd0, uint32_t idesc,
+                                            uint32_t& started) {
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+#pragma unroll
+        for (int bb = 0; a + bb < NS; ++bb) {
+            constexpr int kLast = NG - 1;
+            const int gr = (a + bb < kLast) ? (a + bb) : kLast;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = ad0 + (uint64_t)((a * kChunkBytes + kk * 32) >> 4);
+                const uint64_t bd = bd0 + (uint64_t)((bb * kBBytes + kk * 32) >> 4);
+                mma_bf16(tacc + gr * NT, ad, bd, idesc, (started >> gr) & 1u);
+                started |= 1u << gr;
+            }
+        }
+    }
+}
+
 // Split GEMM over 128 x NT output tiles with NG accumulator groups (group g
 // gathers the products with a + b = g, the last one all a + b >= g).
 // MODE 0 (panel):  A_IJ(:, cols)  =  PS_I . WS(cols)^T   NT = 64, ps slices,
@@ -614,12 +640,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 template <int MODE, int NT, int NG>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
     static_assert(NG * NT <= 512, "accumulators exceed tensor memory");
+    // two accumulator sets when they fit (64-column update tiles): the MMAs of
+    // tile i + 1 then run while the epilogue drains tile i
+    constexpr int NBUF = (2 * NG * NT <= 512) ? 2 : 1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ __align__(8) uint64_t empty_bar[2];
-    __shared__ __align__(8) uint64_t tfull_bar;
-    __shared__ __align__(8) uint64_t tempty_bar;
+    __shared__ __align__(8) uint64_t tfull_bar[NBUF];
+    __shared__ __align__(8) uint64_t tempty_bar[NBUF];
     __shared__ __align__(8) uint64_t drain_bar;
     __shared__ __align__(8) uint64_t never_bar;   // never signalled: the timeout test waits on it
     __shared__ uint32_t tmem_base;
@@ -664,8 +693,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
         mbar_init(&full_bar[1], 1);
         mbar_init(&empty_bar[0], 1);
         mbar_init(&empty_bar[1], 1);
-        mbar_init(&tfull_bar, 1);
-        mbar_init(&tempty_bar, kEpiThreads);
+        for (int u = 0; u < NBUF; ++u) {
+            mbar_init(&tfull_bar[u], 1);
+            mbar_init(&tempty_bar[u], kEpiThreads);
+        }
         mbar_init(&drain_bar, 1);
         mbar_init(&never_bar, 1);
         abort_flag = 0;
@@ -718,7 +749,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 int t, I, K, col0;
                 decode(w, t, I, K, col0);
                 if (b.st[t].status != GP_OK) continue;
-                if (i >= 1 && !mbar_wait(&tempty_bar, (i - 1) & 1, &abort_flag)) {
+                // accumulator set i % NBUF is free once the epilogue has drained
+                // tile i - NBUF
+                const int buf = i % NBUF;
+                if (i >= NBUF && !mbar_wait(&tempty_bar[buf], ((i / NBUF) - 1) & 1, &abort_flag)) {
                     abort_flag = 1;
                     break;
                 }
@@ -739,21 +773,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + st * stage_bytes);
                     const uint32_t sb = sa + a_bytes;
-                    for (int a = 0; a < ns; ++a) {
-                        for (int bb = 0; a + bb < ns; ++bb) {
-                            const int gr = (a + bb < NG) ? (a + bb) : (NG - 1);
-                            for (int kk = 0; kk < 2; ++kk) {
-                                const uint64_t ad = smem_desc(sa + a * kChunkBytes + kk * 32, 16, 512, 4);
-                                const uint64_t bd = smem_desc(sb + bb * kBBytes + kk * 32, 16, 512, 4);
-                                mma_bf16(tbase + gr * NT, ad, bd, idesc, (started >> gr) & 1u);
-                                started |= 1u << gr;
-                            }
-                        }
+                    const uint64_t ad0 = smem_desc(sa, 16, 512, 4), bd0 = smem_desc(sb, 16, 512, 4);
+                    const uint32_t tacc = tbase + buf * NG * NT;
+                    switch (ns) {
+                        case 2: issue_stage<2, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
+                        case 3: issue_stage<3, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
+                        case 4: issue_stage<4, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
+                        case 5: issue_stage<5, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
+                        case 6: issue_stage<6, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
+                        default: issue_stage<7, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
                     }
                     mma_commit(&empty_bar[st]);
                 }
                 if (abort_flag) break;
-                mma_commit(&tfull_bar);
+                mma_commit(&tfull_bar[buf]);
                 ++i;
             }
             // every MMA issued has completed before tensor memory is released
@@ -779,7 +812,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             float2* C = df_tile(b, b.A, t, I, K) + (size_t)col0 * GP_NB;
             // the C tile (contiguous) heads for L2 while this tile's MMAs run
             if (MODE == 1 && threadIdx.x == 64) prefetch_l2(C, (uint32_t)(NT * GP_NB * sizeof(float2)));
-            if (!mbar_wait(&tfull_bar, i & 1, &abort_flag)) {
+            const int buf = i % NBUF;
+            if (!mbar_wait(&tfull_bar[buf], (i / NBUF) & 1, &abort_flag)) {
                 abort_flag = 1;
                 break;
             }
@@ -798,8 +832,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     if (g < ng_used) {
-                        if (CB == 8) tmem_ld8(lane_addr + g * NT + c0, d[g]);
-                        else         tmem_ld16(lane_addr + g * NT + c0, d[g]);
+                        if (CB == 8) tmem_ld8(lane_addr + buf * NG * NT + g * NT + c0, d[g]);
+                        else         tmem_ld16(lane_addr + buf * NG * NT + g * NT + c0, d[g]);
                     } else {
 #pragma unroll
                         for (int j = 0; j < CB; ++j) d[g][j] = 0.f;
@@ -858,7 +892,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                 }
             }
             tc_fence_before();
-            mbar_arrive(&tempty_bar);
+            mbar_arrive(&tempty_bar[buf]);
             ++i;
         }
     }
@@ -1022,16 +1056,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
                     if (valid) {
                         const uint32_t sa = smem_u32(smem + st * stage_bytes);
                         const uint32_t sb = sa + a_bytes;
-                        for (int a = 0; a < ns; ++a) {
-                            for (int bb = 0; a + bb < ns; ++bb) {
-                                const int gr = (a + bb < NG) ? (a + bb) : (NG - 1);
-                                for (int kk = 0; kk < 2; ++kk) {
-                                    const uint64_t ad = smem_desc(sa + a * kChunkBytes + kk * 32, 16, 512, 4);
-                                    const uint64_t bd = smem_desc(sb + bb * kBBytes + kk * 32, 16, 512, 4);
-                                    mma_bf16(tbase + gr * NT, ad, bd, idesc, (started >> gr) & 1u);
-                                    started |= 1u << gr;
-                                }
-                            }
+                        const uint64_t ad0 = smem_desc(sa, 16, 512, 4), bd0 = smem_desc(sb, 16, 512, 4);
+                        switch (ns) {
+                            case 2: issue_stage<2, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
+                            case 3: issue_stage<3, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
+                            case 4: issue_stage<4, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
+                            case 5: issue_stage<5, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
+                            default: issue_stage<6, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
                         }
                     }
                     // this stage may be refilled in both CTAs once both have read it
