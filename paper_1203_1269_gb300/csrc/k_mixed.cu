@@ -43,8 +43,11 @@ namespace {
 constexpr int kChunkElems = GP_NB * 32;       // bf16 elements in one 128 x 32 image chunk
 constexpr uint32_t kChunkBytes = kChunkElems * 2;
 constexpr int kChunks = GP_NB / 32;           // 4 chunks per 128-wide panel
-constexpr int kGemmThreads = 320;             // warp 0 copies, warp 1 MMA, warps 2-9 epilogue
-constexpr int kEpiThreads = 256;
+constexpr int kEpiWarps = 8;                  // epilogue warps: kEpiWarps / 4 per tensor-memory lane quarter
+                                               // (16 measured 2% slower on the update)
+constexpr int kEpiParts = kEpiWarps / 4;       // column parts of a tile
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 MMA, then the epilogue
+constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
 
 // ---------------------------------------------------------------- PTX ------
@@ -302,9 +305,21 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     // evenly, and the square root and reciprocal of the next pivot are taken
     // by the thread that finishes that pivot's update, while the others work
     // on; the logarithms of the pivots wait for the reduction below.
+    // The pivot chain is the critical path: 1 / sqrt(piv) by a float seed and
+    // three Newton-Raphson steps y <- y (3/2 - piv y^2 / 2) in double (22, 44,
+    // then rounding-limited correct bits), sqrt(piv) = piv y: ten dependent
+    // FP64 instructions, within a few ulps; pivots outside the float range
+    // take the library square root and division.
     auto take_pivot = [&](int c, double piv) {
         if (!(piv > 0.0) || !isfinite(piv)) {
             failed = c;
+        } else if (piv > 1e-30 && piv < 1e30) {
+            double y = (double)rsqrtf((float)piv);
+            const double h = -0.5 * piv;
+#pragma unroll
+            for (int it = 0; it < 3; ++it) y = y * fma(h, y * y, 1.5);
+            P[prow(c) + c] = piv * y;
+            dinv[c] = y;
         } else {
             const double l = sqrt(piv);
             P[prow(c) + c] = l;
@@ -599,10 +614,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // loops unroll for a compile-time slice count, so each MMA costs its issue
 // and two 64-bit adds to descriptors built once per stage (their address
 // field, bits 0-13, holds the byte address / 16 and does not overflow inside
-// shared memory).
-template <int NS, int NG, int NT, uint32_t kBBytes>
-__device__ __forceinline__ void issue_stage(uint32_t tacc, uint64_t ad0, uint64_t bd0, uint32_t idesc,
-                                            uint32_t& started) {
+// shared memory).  In the first stage of a tile (FIRST) the first product of
+// each group -- (0, g), K step 0, in this order -- overwrites the group.
+template <int NS, int NG, int NT, uint32_t kBBytes, bool FIRST>
+__device__ __forceinline__ void issue_stage(uint32_t tacc, uint64_t ad0, uint64_t bd0, uint32_t idesc) {
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
 #pragma unroll
@@ -613,11 +628,30 @@ __device__ __forceinline__ void issue_stage(uint32_t tacc, uint64_t ad0, uint64_
             for (int kk = 0; kk < 2; ++kk) {
                 const uint64_t ad = ad0 + (uint64_t)((a * kChunkBytes + kk * 32) >> 4);
                 const uint64_t bd = bd0 + (uint64_t)((bb * kBBytes + kk * 32) >> 4);
-                mma_bf16(tacc + gr * NT, ad, bd, idesc, (started >> gr) & 1u);
-                started |= 1u << gr;
+                const bool overwrite = FIRST && a == 0 && kk == 0 && bb <= kLast;
+                mma_bf16(tacc + gr * NT, ad, bd, idesc, overwrite ? 0u : 1u);
             }
         }
     }
+}
+
+// issue_stage for the runtime slice count (2 .. 7)
+template <int NG, int NT, uint32_t kBBytes>
+__device__ __forceinline__ void issue_stage_ns(int ns, bool first, uint32_t tacc, uint64_t ad0, uint64_t bd0,
+                                               uint32_t idesc) {
+#define GP_ISSUE(N)                                                                     \
+    if (first) issue_stage<N, NG, NT, kBBytes, true>(tacc, ad0, bd0, idesc);             \
+    else       issue_stage<N, NG, NT, kBBytes, false>(tacc, ad0, bd0, idesc);            \
+    return
+    switch (ns) {
+        case 2: GP_ISSUE(2);
+        case 3: GP_ISSUE(3);
+        case 4: GP_ISSUE(4);
+        case 5: GP_ISSUE(5);
+        case 6: GP_ISSUE(6);
+        default: GP_ISSUE(7);
+    }
+#undef GP_ISSUE
 }
 
 // Split GEMM over 128 x NT output tiles with NG accumulator groups (group g
@@ -633,9 +667,11 @@ __device__ __forceinline__ void issue_stage(uint32_t tacc, uint64_t ad0, uint64_
 // (instance-major).  Warp 0 streams K-chunk stages through a two-slot ring
 // that runs on across tiles, so the next tile's operands land while the
 // current tile's epilogue runs; warp 1 issues the MMAs once the epilogue has
-// drained the accumulators of the previous tile; warps 2-9 read tensor memory
-// and apply the result (two warps per tensor-memory lane quarter, each taking
-// half of the columns, with the loads of a column block issued together).  Every wait is bounded; a timeout marks the instance
+// drained the accumulators of the previous tile (or, when two accumulator
+// sets fit, of the tile before it); the kEpiWarps epilogue warps read tensor
+// memory and apply the result (kEpiWarps / 4 warps per tensor-memory lane
+// quarter, each taking one column part, with the loads of a column block
+// issued together).  Every wait is bounded; a timeout marks the instance
 // GP_ETIMEOUT and stops the CTA after its copies and MMAs have landed.
 template <int MODE, int NT, int NG>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
@@ -763,7 +799,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                     break;
                 }
                 tc_fence_after();
-                uint32_t started = 0;
                 for (int kc = 0; kc < nch; ++kc, ++g) {
                     const int st = g & 1;
                     if (!mbar_wait(&full_bar[st], (g >> 1) & 1, &abort_flag)) {
@@ -774,15 +809,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
                     const uint32_t sa = smem_u32(smem + st * stage_bytes);
                     const uint32_t sb = sa + a_bytes;
                     const uint64_t ad0 = smem_desc(sa, 16, 512, 4), bd0 = smem_desc(sb, 16, 512, 4);
-                    const uint32_t tacc = tbase + buf * NG * NT;
-                    switch (ns) {
-                        case 2: issue_stage<2, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                        case 3: issue_stage<3, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                        case 4: issue_stage<4, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                        case 5: issue_stage<5, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                        case 6: issue_stage<6, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                        default: issue_stage<7, NG, NT, kBBytes>(tacc, ad0, bd0, idesc, started); break;
-                    }
+                    issue_stage_ns<NG, NT, kBBytes>(ns, kc == 0, tbase + buf * NG * NT, ad0, bd0, idesc);
                     mma_commit(&empty_bar[st]);
                 }
                 if (abort_flag) break;
@@ -794,13 +821,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             mbar_wait(&drain_bar, 0);
         }
     } else {
-        // epilogue: warps 2..9; warp w reads TMEM lane quarter w % 4 and the
-        // column half (w - 2) / 4 of the tile
+        // epilogue: warps 2 .. 1 + kEpiWarps; warp w reads TMEM lane quarter
+        // w % 4 and the column part (w - 2) / 4 of the tile
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;       // column part: NT / kEpiParts columns
         const int r = q * 32 + lane;
         const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-        constexpr int CB = (NG > 4) ? 8 : 16;    // columns per TMEM load
+        constexpr int kPartCols = NT / kEpiParts;
+        constexpr int CB = (NG > 4) ? 8 : 16;               // columns per TMEM load
+        static_assert(kPartCols % CB == 0, "column part not a multiple of the TMEM load width");
         // products a + b <= ns - 1 exist, so with ns < NG slices the groups
         // from ns on are never written and read as zero
         const int ng_used = ns < NG ? ns : NG;
@@ -822,7 +851,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride)
                                           : (fused ? fe_block(b, t, K) : pe_block(b, t, K))) + col0;
             const int eA = eAp[r];
-            for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += CB) {
+            for (int c0 = part * kPartCols; c0 < (part + 1) * kPartCols; c0 += CB) {
                 float2 cv[CB];
                 if (MODE == 1) {
 #pragma unroll
@@ -1045,7 +1074,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
                     break;
                 }
                 tc_fence_after();
-                uint32_t started = 0;
                 for (int kc = 0; kc < nch; ++kc, ++g) {
                     const int st = g & 1;
                     if (!mbar_wait(&full_bar[st], (g >> 1) & 1, &abort_flag)) {
@@ -1057,13 +1085,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
                         const uint32_t sa = smem_u32(smem + st * stage_bytes);
                         const uint32_t sb = sa + a_bytes;
                         const uint64_t ad0 = smem_desc(sa, 16, 512, 4), bd0 = smem_desc(sb, 16, 512, 4);
-                        switch (ns) {
-                            case 2: issue_stage<2, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
-                            case 3: issue_stage<3, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
-                            case 4: issue_stage<4, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
-                            case 5: issue_stage<5, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
-                            default: issue_stage<6, NG, NT, kBBytes>(tbase, ad0, bd0, idesc, started); break;
-                        }
+                        issue_stage_ns<NG, NT, kBBytes>(ns, kc == 0, tbase, ad0, bd0, idesc);
                     }
                     // this stage may be refilled in both CTAs once both have read it
                     mma_commit_mc(&empty_bar[st], kPair);
@@ -1079,9 +1101,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
         }
     } else {
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+        constexpr int kPartCols = NT / kEpiParts;
         constexpr int CB = 16;
         const int ng_used = ns < NG ? ns : NG;
         int i = 0;
@@ -1099,7 +1122,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
             tc_fence_after();
             const int eA = fe_block(b, t, I)[r];
             const int* eBp = fe_block(b, t, K);
-            for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += CB) {
+            for (int c0 = part * kPartCols; c0 < (part + 1) * kPartCols; c0 += CB) {
                 float2 cv[CB];
 #pragma unroll
                 for (int j = 0; j < CB; ++j) cv[j] = C[(size_t)(c0 + j) * GP_NB + r];
