@@ -30,6 +30,13 @@ STATUS_DEGENERATE = -6
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 NLL_FIELDS = ("nll", "mu", "sigma2", "logdet", "Q", "nll_full", "cond1")
+# correlation families of gp_oracle.c (eq. 2's power-exponential, and the
+# Matern family Section 2 names as an alternative, product form)
+CORR = {"powexp": 0, "matern12": 1, "matern32": 2, "matern52": 3}
+
+
+def _fam(corr):
+    return CORR[corr] if isinstance(corr, str) else int(corr)
 
 
 def _f64(a):
@@ -47,22 +54,22 @@ class Oracle:
     def __init__(self, libpath):
         lib = ctypes.CDLL(libpath)
         c_int, c_double = ctypes.c_int, ctypes.c_double
-        lib.gpo_corr_matrix.argtypes = [c_int, c_int, _dp, _dp, c_double, c_double, _dp]
-        lib.gpo_cross_corr.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, _dp]
+        lib.gpo_corr_matrix.argtypes = [c_int, c_int, _dp, _dp, c_double, c_int, c_double, _dp]
+        lib.gpo_cross_corr.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, _dp]
         lib.gpo_cholesky.argtypes = [c_int, _dp, _dp]
         lib.gpo_cholesky.restype = c_int
         lib.gpo_forward.argtypes = [c_int, _dp, _dp, _dp]
         lib.gpo_backward.argtypes = [c_int, _dp, _dp, _dp]
         lib.gpo_cond1_est.argtypes = [c_int, _dp, _dp]
         lib.gpo_cond1_est.restype = c_double
-        lib.gpo_nll.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_double, c_int, _dp]
+        lib.gpo_nll.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, c_double, c_int, _dp]
         lib.gpo_nll.restype = c_int
-        lib.gpo_nll_batch.argtypes = [c_int, c_int, _dp, _dp, c_int, _dp, c_double, c_double,
+        lib.gpo_nll_batch.argtypes = [c_int, c_int, _dp, _dp, c_int, _dp, c_double, c_int, c_double,
                                       c_int, _dp, _ip]
-        lib.gpo_predict.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_double, c_int,
+        lib.gpo_predict.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, c_double, c_int,
                                     _dp, c_int, _dp, _dp]
         lib.gpo_predict.restype = c_int
-        lib.gpo_fit_parts.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_double,
+        lib.gpo_fit_parts.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, c_double,
                                       _dp, _dp, _dp, _dp, _dp]
         lib.gpo_fit_parts.restype = c_int
         lib.gpo_num_threads.restype = c_int
@@ -72,23 +79,23 @@ class Oracle:
         """Host threads the batched oracle uses (OpenMP)."""
         return int(self.lib.gpo_num_threads())
 
-    def corr_matrix(self, x, theta, p, delta=0.0):
-        """Full n x n R(theta) + delta I by eq. (2)."""
+    def corr_matrix(self, x, theta, p, delta=0.0, corr="powexp"):
+        """Full n x n R(theta) + delta I (eq. 2 for the power-exponential family)."""
         x = _f64(x)
         n, d = x.shape
         th = _f64(theta).reshape(d)
         R = np.empty((n, n))
-        self.lib.gpo_corr_matrix(n, d, _p(x), _p(th), float(p), float(delta), _p(R))
+        self.lib.gpo_corr_matrix(n, d, _p(x), _p(th), float(p), _fam(corr), float(delta), _p(R))
         return R
 
-    def cross_corr(self, x, xs, theta, p):
+    def cross_corr(self, x, xs, theta, p, corr="powexp"):
         """r(x*) for one point xs (length d): r_i = corr(z(x*), z(x_i)), no nugget."""
         x = _f64(x)
         n, d = x.shape
         xs = _f64(xs).reshape(d)
         th = _f64(theta).reshape(d)
         r = np.empty(n)
-        self.lib.gpo_cross_corr(n, d, _p(x), _p(xs), _p(th), float(p), _p(r))
+        self.lib.gpo_cross_corr(n, d, _p(x), _p(xs), _p(th), float(p), _fam(corr), _p(r))
         return r
 
     def cholesky(self, R):
@@ -118,18 +125,18 @@ class Oracle:
         L = _f64(L)
         return float(self.lib.gpo_cond1_est(R.shape[0], _p(R), _p(L)))
 
-    def nll(self, x, y, theta, p, delta=0.0, want_cond=False):
+    def nll(self, x, y, theta, p, delta=0.0, want_cond=False, corr="powexp"):
         """Profile -2 log L at one theta.  Returns (dict of NLL_FIELDS, status)."""
         x = _f64(x)
         n, d = x.shape
         y = _f64(y).reshape(n)
         th = _f64(theta).reshape(d)
         out = np.empty(7)
-        st = self.lib.gpo_nll(n, d, _p(x), _p(y), _p(th), float(p), float(delta),
+        st = self.lib.gpo_nll(n, d, _p(x), _p(y), _p(th), float(p), _fam(corr), float(delta),
                               int(bool(want_cond)), _p(out))
         return dict(zip(NLL_FIELDS, out.tolist())), int(st)
 
-    def nll_batch(self, x, y, thetas, p, delta=0.0, want_cond=False):
+    def nll_batch(self, x, y, thetas, p, delta=0.0, want_cond=False, corr="powexp"):
         """-2 log L at T candidates (thetas T x d), spread over host threads.
         Returns (out T x 7 in NLL_FIELDS order, status T)."""
         x = _f64(x)
@@ -139,11 +146,11 @@ class Oracle:
         T = th.shape[0]
         out = np.empty((T, 7))
         st = np.empty(T, dtype=np.int32)
-        self.lib.gpo_nll_batch(n, d, _p(x), _p(y), T, _p(th), float(p), float(delta),
+        self.lib.gpo_nll_batch(n, d, _p(x), _p(y), T, _p(th), float(p), _fam(corr), float(delta),
                                int(bool(want_cond)), _p(out), st.ctypes.data_as(_ip))
         return out, st
 
-    def predict(self, x, y, theta, p, delta, xs, nugget_in_var=True, want_var=True):
+    def predict(self, x, y, theta, p, delta, xs, nugget_in_var=True, want_var=True, corr="powexp"):
         """Kriging mean and variance at the rows of xs.  Returns (yhat, s2|None, status)."""
         x = _f64(x)
         n, d = x.shape
@@ -153,12 +160,12 @@ class Oracle:
         N = xs.shape[0]
         yhat = np.empty(N)
         s2 = np.empty(N) if want_var else None
-        st = self.lib.gpo_predict(n, d, _p(x), _p(y), _p(th), float(p), float(delta), N,
+        st = self.lib.gpo_predict(n, d, _p(x), _p(y), _p(th), float(p), _fam(corr), float(delta), N,
                                   _p(xs), int(bool(nugget_in_var)), _p(yhat),
                                   _p(s2) if want_var else None)
         return yhat, s2, int(st)
 
-    def fit_parts(self, x, y, theta, p, delta=0.0):
+    def fit_parts(self, x, y, theta, p, delta=0.0, corr="powexp"):
         """R, L, a = L^-1 1, b = L^-1 Y, w = R^-1 (Y - 1 mu_hat), status."""
         x = _f64(x)
         n, d = x.shape
@@ -166,7 +173,7 @@ class Oracle:
         th = _f64(theta).reshape(d)
         R = np.empty((n, n)); L = np.empty((n, n))
         a = np.empty(n); b = np.empty(n); w = np.empty(n)
-        st = self.lib.gpo_fit_parts(n, d, _p(x), _p(y), _p(th), float(p), float(delta),
+        st = self.lib.gpo_fit_parts(n, d, _p(x), _p(y), _p(th), float(p), _fam(corr), float(delta),
                                     _p(R), _p(L), _p(a), _p(b), _p(w))
         return R, L, a, b, w, int(st)
 

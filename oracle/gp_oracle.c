@@ -37,24 +37,53 @@
 #define GPO_DEGENERATE (-6)
 #define GPO_ENOMEM (-2)
 
-/* Correlation between two points, eq. (2) of Section 2: the product over
- * the d input dimensions of exp(-theta_k |x_ik - x_jk|^p). */
-static double gpo_corr_pair(int d, const double* xi, const double* xj,
-                            const double* theta, double p) {
-    double r = 1.0;
-    for (int k = 0; k < d; ++k) {
-        double diff = fabs(xi[k] - xj[k]);
-        r *= exp(-theta[k] * pow(diff, p));
+/* Correlation families (argument fam of every function below).
+ *   GPO_POWEXP:   eq. (2) of Section 2, exp(-theta_k |x_ik - x_jk|^p) per
+ *                 input dimension.
+ *   GPO_MATERN*:  the Matern family Section 2 names as an alternative (it
+ *                 cites Stein 1999 and Santner et al. 2003 and gives no
+ *                 formula), read in the same product form over dimensions,
+ *                 with h = theta_k |x_ik - x_jk| and the closed forms of the
+ *                 Matern correlation for half-integer smoothness nu:
+ *                   nu = 1/2: exp(-h)
+ *                   nu = 3/2: (1 + sqrt(3) h) exp(-sqrt(3) h)
+ *                   nu = 5/2: (1 + sqrt(5) h + 5 h^2 / 3) exp(-sqrt(5) h)
+ *                 p is not used. */
+#define GPO_POWEXP 0
+#define GPO_MATERN12 1
+#define GPO_MATERN32 2
+#define GPO_MATERN52 3
+
+/* One dimension's factor of the correlation. */
+static double gpo_corr_1d(double diff, double theta, double p, int fam) {
+    double a = fabs(diff);
+    if (fam == GPO_MATERN12) return exp(-theta * a);
+    if (fam == GPO_MATERN32) {
+        double h = sqrt(3.0) * theta * a;
+        return (1.0 + h) * exp(-h);
     }
+    if (fam == GPO_MATERN52) {
+        double h = sqrt(5.0) * theta * a;
+        return (1.0 + h + h * h / 3.0) * exp(-h);
+    }
+    return exp(-theta * pow(a, p));
+}
+
+/* Correlation between two points: the product over the d input dimensions
+ * (eq. 2 for the power-exponential family). */
+static double gpo_corr_pair(int d, const double* xi, const double* xj,
+                            const double* theta, double p, int fam) {
+    double r = 1.0;
+    for (int k = 0; k < d; ++k) r *= gpo_corr_1d(xi[k] - xj[k], theta[k], p, fam);
     return r;
 }
 
-/* R(theta) by eq. (2), full n x n, plus the nugget delta on the diagonal. */
+/* R(theta), full n x n, plus the nugget delta on the diagonal. */
 void gpo_corr_matrix(int n, int d, const double* x, const double* theta,
-                     double p, double delta, double* R) {
+                     double p, int fam, double delta, double* R) {
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j < n; ++j) {
-            double v = gpo_corr_pair(d, x + (size_t)i * d, x + (size_t)j * d, theta, p);
+            double v = gpo_corr_pair(d, x + (size_t)i * d, x + (size_t)j * d, theta, p, fam);
             if (i == j) v += delta;
             R[(size_t)i * n + j] = v;
         }
@@ -63,9 +92,9 @@ void gpo_corr_matrix(int n, int d, const double* x, const double* theta,
 
 /* Cross-correlations r_i(x*) = corr(z(x*), z(x_i)) by eq. (2); no nugget. */
 void gpo_cross_corr(int n, int d, const double* x, const double* xs,
-                    const double* theta, double p, double* r) {
+                    const double* theta, double p, int fam, double* r) {
     for (int i = 0; i < n; ++i)
-        r[i] = gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p);
+        r[i] = gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam);
 }
 
 /* Unblocked Cholesky (Cholesky-Banachiewicz, row by row): R = L L'.
@@ -177,7 +206,7 @@ static int gpo_q_is_zero(int n, double Q, double bb) {
  * 1'R^-1 1 = a'a and 1'R^-1 Y = a'b; e = b - mu a = L^-1 (Y - 1 mu) and
  * Q = e'e. */
 int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
-            double p, double delta, int want_cond, double* out) {
+            double p, int fam, double delta, int want_cond, double* out) {
     const double nan = NAN;
     for (int i = 0; i < 7; ++i) out[i] = nan;
     out[6] = 0.0;
@@ -190,7 +219,7 @@ int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
     int status = GPO_OK;
     if (!R || !L || !ones || !a || !b || !e) { status = GPO_ENOMEM; goto done; }
 
-    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    gpo_corr_matrix(n, d, x, theta, p, fam, delta, R);
     if (gpo_cholesky(n, R, L) != 0) {
         status = GPO_NOTPD;
         out[0] = INFINITY;
@@ -231,11 +260,11 @@ done:
  * candidates are independent, so they are spread over host threads.  Each
  * evaluation is the single-threaded gpo_nll above.  out is T x 7. */
 void gpo_nll_batch(int n, int d, const double* x, const double* y, int T,
-                   const double* theta, double p, double delta, int want_cond,
+                   const double* theta, double p, int fam, double delta, int want_cond,
                    double* out, int* status) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < T; ++t)
-        status[t] = gpo_nll(n, d, x, y, theta + (size_t)t * d, p, delta,
+        status[t] = gpo_nll(n, d, x, y, theta + (size_t)t * d, p, fam, delta,
                             want_cond, out + (size_t)t * 7);
 }
 
@@ -246,7 +275,7 @@ void gpo_nll_batch(int n, int d, const double* x, const double* y, int T,
  * c0 = 1 + delta if nugget_in_var else 1.  s2 may be NULL.
  * Returns the status of the fit. */
 int gpo_predict(int n, int d, const double* x, const double* y, const double* theta,
-                double p, double delta, int N, const double* xs, int nugget_in_var,
+                double p, int fam, double delta, int N, const double* xs, int nugget_in_var,
                 double* yhat, double* s2) {
     double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
     double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
@@ -257,7 +286,7 @@ int gpo_predict(int n, int d, const double* x, const double* y, const double* th
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
     int status = GPO_OK;
     if (!R || !L || !ones || !a || !b || !e || !w) { status = GPO_ENOMEM; goto done; }
-    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    gpo_corr_matrix(n, d, x, theta, p, fam, delta, R);
     if (gpo_cholesky(n, R, L) != 0) {
         status = GPO_NOTPD;
         for (int m = 0; m < N; ++m) { yhat[m] = NAN; if (s2) s2[m] = NAN; }
@@ -281,7 +310,7 @@ int gpo_predict(int n, int d, const double* x, const double* y, const double* th
 #pragma omp for schedule(static)
         for (int m = 0; m < N; ++m) {
             if (!r || !v) { yhat[m] = NAN; if (s2) s2[m] = NAN; continue; }
-            gpo_cross_corr(n, d, x, xs + (size_t)m * d, theta, p, r);
+            gpo_cross_corr(n, d, x, xs + (size_t)m * d, theta, p, fam, r);
             double yh = 0.0;
             for (int i = 0; i < n; ++i) yh += r[i] * w[i];
             yhat[m] = mu + yh;
@@ -304,9 +333,9 @@ done:
  * intermediate quantities: L (n x n), a = L^-1 1, b = L^-1 Y, w = R^-1(Y-1mu).
  * Returns the status. */
 int gpo_fit_parts(int n, int d, const double* x, const double* y, const double* theta,
-                  double p, double delta, double* R, double* L, double* a, double* b,
+                  double p, int fam, double delta, double* R, double* L, double* a, double* b,
                   double* w) {
-    gpo_corr_matrix(n, d, x, theta, p, delta, R);
+    gpo_corr_matrix(n, d, x, theta, p, fam, delta, R);
     if (gpo_cholesky(n, R, L) != 0) return GPO_NOTPD;
     double* ones = (double*)malloc(sizeof(double) * (size_t)n);
     double* e = (double*)malloc(sizeof(double) * (size_t)n);

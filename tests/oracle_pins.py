@@ -390,9 +390,101 @@ def check_fit_parts(orc, seed=37):
     assert np.max(np.abs(w - np.linalg.solve(R, y - mu))) < 1e-8 * max(1.0, np.max(np.abs(w)))
 
 
+# ----------------------------------------------------------------- Matern --
+# The Matern family (Section 2 names it as an alternative, without a formula)
+# in product form over dimensions with h = theta_k |dx_k|.  The pins below do
+# not retype the closed forms: nu = 1/2 must equal eq. (2) with p = 1, and
+# nu = 3/2, 5/2 must equal the general Matern correlation
+#   rho(h) = 2^(1-nu) / Gamma(nu) (sqrt(2 nu) h)^nu K_nu(sqrt(2 nu) h),
+# evaluated with SciPy's modified Bessel function K_nu.
+
+def _matern_bessel(nu, h):
+    from scipy.special import gamma, kv
+    h = np.asarray(h, dtype=np.float64)
+    z = np.sqrt(2.0 * nu) * h
+    out = np.ones_like(z)
+    nz = z > 0
+    out[nz] = 2.0 ** (1.0 - nu) / gamma(nu) * z[nz] ** nu * kv(nu, z[nz])
+    return out
+
+
+def check_matern_half_is_exponential(orc, seed=41):
+    """nu = 1/2 is the exponential correlation: eq. (2) with p = 1."""
+    g = np.random.default_rng(seed)
+    x = g.random((25, 3))
+    th = 10 ** g.uniform(-1, 1, 3)
+    Rm = orc.corr_matrix(x, th, 1.7, 1e-3, corr="matern12")
+    Rp = orc.corr_matrix(x, th, 1.0, 1e-3, corr="powexp")
+    assert np.max(np.abs(Rm - Rp)) <= 1e-15
+    y = g.standard_normal(25)
+    om, sm = orc.nll(x, y, th, 1.7, 1e-3, corr="matern12")
+    op, sp = orc.nll(x, y, th, 1.0, 1e-3, corr="powexp")
+    assert sm == sp == 0 and _rel(om["nll"], op["nll"]) < 1e-13
+
+
+def check_matern_bessel(orc):
+    """nu = 3/2 and 5/2 against the Bessel-function definition, in one and
+    two dimensions (product form), p ignored."""
+    for fam, nu in (("matern32", 1.5), ("matern52", 2.5)):
+        for a in (1e-3, 0.05, 0.3, 0.9):
+            for th in (0.2, 1.0, 6.0):
+                x = np.array([[0.0], [a]])
+                R = orc.corr_matrix(x, [th], 0.5, 0.0, corr=fam)
+                ref = float(_matern_bessel(nu, th * a))
+                assert abs(R[0, 1] - ref) <= 1e-12 * max(ref, 1e-300) + 1e-300, (fam, a, th, R[0, 1], ref)
+                assert R[0, 0] == 1.0 and R[1, 0] == R[0, 1]
+        x = np.array([[0.1, 0.7], [0.45, 0.2]])
+        th = np.array([2.0, 0.8])
+        R = orc.corr_matrix(x, th, 2.0, 0.0, corr=fam)
+        ref = float(_matern_bessel(nu, 2.0 * 0.35) * _matern_bessel(nu, 0.8 * 0.5))
+        assert _rel(R[0, 1], ref) < 1e-12
+
+
+def check_matern_n2(orc):
+    """The n = 2 hand derivation of -2logL with a Matern correlation (rho from
+    the Bessel form): mu_hat, Q, log|R| and eq. (4)."""
+    x = np.array([[0.2, 0.3], [0.5, 0.1]])
+    th = np.array([1.2, 3.0])
+    y = np.array([0.3, 1.9])
+    for fam, nu in (("matern32", 1.5), ("matern52", 2.5)):
+        rho = float(_matern_bessel(nu, 1.2 * 0.3) * _matern_bessel(nu, 3.0 * 0.2))
+        out, st = orc.nll(x, y, th, 2.0, 0.0, corr=fam)
+        assert st == 0
+        Q = (y[0] - y[1]) ** 2 / (2.0 * (1.0 - rho))
+        logdet = math.log(1.0 - rho * rho)
+        assert _rel(out["mu"], 1.1) < 1e-14
+        assert _rel(out["Q"], Q) < 1e-11
+        assert _rel(out["nll"], logdet + 2 * math.log(Q)) < 1e-11
+
+
+def check_matern_predict(orc, seed=43):
+    """Kriging with a Matern correlation against LAPACK solves of the
+    oracle's own R (the family only enters through R and r)."""
+    g = np.random.default_rng(seed)
+    n, d = 30, 2
+    x = g.random((n, d))
+    y = np.sin(4 * x[:, 0]) + x[:, 1]
+    th = np.array([3.0, 1.5])
+    xs = g.random((5, d))
+    R = orc.corr_matrix(x, th, 2.0, 1e-6, corr="matern52")
+    one = np.ones(n)
+    a = np.linalg.solve(R, one)
+    mu = one @ np.linalg.solve(R, y) / (one @ a)
+    w = np.linalg.solve(R, y - mu)
+    yhat, s2, st = orc.predict(x, y, th, 2.0, 1e-6, xs, corr="matern52")
+    assert st == 0
+    for m in range(len(xs)):
+        r = orc.cross_corr(x, xs[m], th, 2.0, corr="matern52")
+        assert _rel(yhat[m], mu + r @ w) < 1e-9
+        # r from the Bessel form, dimension by dimension
+        rb = np.prod([_matern_bessel(2.5, th[k] * np.abs(x[:, k] - xs[m, k])) for k in range(d)], axis=0)
+        assert np.max(np.abs(r - rb)) < 1e-12
+
+
 ALL_CHECKS = [
     check_corr_hand_values, check_corr_invariants, check_kms, check_n1, check_n2,
     check_n3, check_eig_logdet, check_solve_estimates, check_cholesky_reconstructs,
     check_notpd, check_cond_estimate, check_invariants, check_table_form, check_predict,
-    check_fit_parts,
+    check_fit_parts, check_matern_half_is_exponential, check_matern_bessel, check_matern_n2,
+    check_matern_predict,
 ]

@@ -16,9 +16,15 @@ import oracle_pins as pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "gp_oracle.c")
 
 MUTANTS = {
-    "corr_ignores_p": ("pow(diff, p)", "pow(diff, 2.0)"),
-    "corr_wrong_index": ("fabs(xi[k] - xj[k])", "fabs(xi[k] - xj[0])"),
-    "corr_sign": ("r *= exp(-theta[k] * pow(diff, p));", "r *= exp(theta[k] * pow(diff, p));"),
+    "corr_ignores_p": ("return exp(-theta * pow(a, p));", "return exp(-theta * pow(a, 2.0));"),
+    "corr_wrong_index": ("gpo_corr_1d(xi[k] - xj[k], theta[k], p, fam)", "gpo_corr_1d(xi[k] - xj[0], theta[k], p, fam)"),
+    "corr_sign": ("return exp(-theta * pow(a, p));", "return exp(theta * pow(a, p));"),
+    "matern12_squares": ("if (fam == GPO_MATERN12) return exp(-theta * a);",
+                         "if (fam == GPO_MATERN12) return exp(-theta * a * a);"),
+    "matern32_constant": ("double h = sqrt(3.0) * theta * a;", "double h = sqrt(5.0) * theta * a;"),
+    "matern52_drops_quadratic": ("return (1.0 + h + h * h / 3.0) * exp(-h);", "return (1.0 + h) * exp(-h);"),
+    "matern52_quadratic_coeff": ("return (1.0 + h + h * h / 3.0) * exp(-h);",
+                                 "return (1.0 + h + h * h / 2.0) * exp(-h);"),
     "nugget_everywhere": ("if (i == j) v += delta;", "v += delta;"),
     "nugget_dropped": ("if (i == j) v += delta;", ";"),
     "chol_update_sign": ("s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];",
@@ -38,8 +44,8 @@ MUTANTS = {
     "predict_drops_mu": ("yhat[m] = mu + yh;", "yhat[m] = yh;"),
     "predict_var_sign": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 + vv + g * g / aa);"),
     "predict_var_unsquared": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 - vv + g / aa);"),
-    "predict_nugget_in_r": ("gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p);",
-                            "gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p) + 1e-6;"),
+    "predict_nugget_in_r": ("gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam);",
+                            "gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam) + 1e-6;"),
     "cond_no_anorm": ("return anorm * est;", "return est;"),
 }
 
