@@ -25,8 +25,9 @@
  *     only argument and launch errors in their return value.
  *   - Return value: GP_OK or a negative gp_status.  The message of the last
  *     failure is available from gp_last_error().
- *   - Arguments are validated: n >= 1, d >= 1, T >= 1, 0 < p <= 2,
- *     delta >= 0 and finite.  theta values are checked on the device: a
+ *   - Arguments are validated: n >= 1, d >= 1, T >= 1, 0 < p <= 2 (for the
+ *     power-exponential family; Matern families ignore p), delta >= 0 and
+ *     finite.  theta values are checked on the device: a
  *     theta_k that is negative or not finite makes that candidate's status
  *     GP_EINVAL and its outputs NaN; the rest of the batch completes.
  *   - Per-candidate failures never fail the call: a Cholesky pivot that is
@@ -70,6 +71,22 @@ typedef enum {
     GP_AUTO = 3
 } gp_precision;
 
+/* Correlation families (gp_options.correlation).
+ * GP_CORR_POWEXP:   eq. (2), prod_k exp(-theta_k |x_ik - x_jk|^p), p in (0, 2].
+ * GP_CORR_MATERN*:  the Matern family Section 2 names as a numerically more
+ *                   stable alternative (it gives no formula), taken in the
+ *                   same product form with h = theta_k |x_ik - x_jk| and the
+ *                   closed forms for smoothness nu = 1/2, 3/2, 5/2:
+ *                   exp(-h), (1 + sqrt3 h) exp(-sqrt3 h),
+ *                   (1 + sqrt5 h + 5 h^2/3) exp(-sqrt5 h).  p is ignored.
+ * The nugget and every other convention are the same for all families. */
+typedef enum {
+    GP_CORR_POWEXP = 0,
+    GP_CORR_MATERN12 = 1,
+    GP_CORR_MATERN32 = 2,
+    GP_CORR_MATERN52 = 3
+} gp_correlation;
+
 typedef enum {
     GP_OK = 0,
     GP_EINVAL = -1,       /* bad argument                                  */
@@ -109,6 +126,9 @@ typedef struct {
                              64 needs update_groups = 4 */
     int assemble_cols;    /* split path: tile columns per CTA of the double-float
                              assembly, 16 (default) or 32; same results */
+    int correlation;      /* gp_correlation of every call that builds R or r, default
+                             GP_CORR_POWEXP; a fit keeps the family it was made with,
+                             and its predictions use that one */
     int pair_update;      /* split path, default 0: 1 runs the fused trailing updates
                              on clusters of two CTAs that share their row panel (each
                              copies half of it, multicast to both: a quarter less

@@ -35,6 +35,7 @@ struct gp_ctx {
 struct gp_model {
     gp_ctx* ctx = nullptr;
     int n = 0, d = 0, nt = 0, prec = 0;
+    int corr = 0;               // gp_correlation the fit was made with
     double p = 0.0, delta = 0.0;
     void* mem = nullptr;        // one allocation holding everything below
     size_t bytes = 0;
@@ -116,7 +117,8 @@ int check_common(gp_ctx* ctx, int n, int d, double p, double delta) {
     if (!ctx) return GP_EINVAL;
     if (n < 1 || n > (1 << 20)) return fail(ctx, GP_EINVAL, "n = %d out of range [1, 2^20]", n);
     if (d < 1 || d > GP_MAX_D) return fail(ctx, GP_EINVAL, "d = %d out of range [1, %d]", d, GP_MAX_D);
-    if (!(p > 0.0 && p <= 2.0)) return fail(ctx, GP_EINVAL, "p = %g outside (0, 2]", p);
+    if (ctx->opt.correlation == GP_CORR_POWEXP && !(p > 0.0 && p <= 2.0))
+        return fail(ctx, GP_EINVAL, "p = %g outside (0, 2]", p);
     if (!(delta >= 0.0) || !std::isfinite(delta))
         return fail(ctx, GP_EINVAL, "delta = %g must be finite and >= 0", delta);
     return GP_OK;
@@ -241,6 +243,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
                      double delta) {
     gp::Batch b{};
     b.n = mb.n; b.d = d; b.nt = mb.nt; b.count = mb.count; b.p = p; b.delta = delta;
+    b.corr = ctx->opt.correlation;
     b.x = x; b.y = mb.y; b.theta = theta; b.A = nullptr; b.Adf = mb.A; b.Rdf = mb.Rc;
     b.inst_stride = mb.inst_stride; b.st = mb.st;
     b.asm_cols = ctx->opt.assemble_cols;
@@ -393,7 +396,7 @@ int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
     for (int c0 = 0; c0 < T; c0 += Tc) {
         const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
         gp::Batch b{};
-        b.n = n; b.d = d; b.nt = nt; b.count = cnt;
+        b.n = n; b.d = d; b.nt = nt; b.count = cnt; b.corr = ctx->opt.correlation;
         b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
         b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
         {
@@ -528,6 +531,8 @@ int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...) {
 
 int ctx_device(const gp_ctx* ctx) { return ctx->device; }
 
+int ctx_correlation(const gp_ctx* ctx) { return ctx->opt.correlation; }
+
 cudaStream_t ctx_stream(const gp_ctx* ctx) { return ctx->stream; }
 
 }  // namespace gp
@@ -548,6 +553,7 @@ void gp_default_options(gp_options* opt) {
     opt->update_tile = 128;
     opt->assemble_cols = 16;
     opt->pair_update = 0;
+    opt->correlation = GP_CORR_POWEXP;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -622,6 +628,8 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
         return fail(ctx, GP_EINVAL, "assemble_cols must be 16 or 32");
     if (opt->pair_update != 0 && opt->pair_update != 1)
         return fail(ctx, GP_EINVAL, "pair_update must be 0 or 1");
+    if (opt->correlation < GP_CORR_POWEXP || opt->correlation > GP_CORR_MATERN52)
+        return fail(ctx, GP_EINVAL, "correlation = %d is not a gp_correlation", opt->correlation);
     ctx->opt = *opt;
     return GP_OK;
 }
@@ -673,14 +681,14 @@ int gp_corr_assemble(gp_ctx* ctx, int n, int d, const double* x, const double* t
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     if (layout == 0) {
         if (n > 65535) return fail(ctx, GP_EINVAL, "dense layout limited to n <= 65535");
-        GP_CUDA(ctx, gp::launch_assemble_dense(n, d, x, theta, p, delta, R, ctx->stream));
+        GP_CUDA(ctx, gp::launch_assemble_dense(n, d, x, theta, p, ctx->opt.correlation, delta, R, ctx->stream));
         return GP_OK;
     }
     if (layout != 1 && layout != 2) return fail(ctx, GP_EINVAL, "layout must be 0, 1 or 2");
     rc = ensure_ws(ctx, align256(sizeof(gp::InstState)));
     if (rc) return rc;
     gp::Batch b{};
-    b.n = n; b.d = d; b.nt = gp::num_tiles(n); b.count = 1;
+    b.n = n; b.d = d; b.nt = gp::num_tiles(n); b.count = 1; b.corr = ctx->opt.correlation;
     b.p = p; b.delta = delta; b.x = x; b.y = nullptr; b.theta = theta;
     if (layout == 1) {
         b.A = R;
@@ -712,7 +720,7 @@ int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
         if (rc) return rc;
         st = (gp::InstState*)ctx->ws;
         gp::Batch b{};
-        b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta;
+        b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta; b.corr = ctx->opt.correlation;
         b.x = x; b.y = nullptr; b.theta = theta; b.A = L; b.inst_stride = gp::packed_elems(n); b.st = st;
         {
             PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
@@ -1050,6 +1058,7 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
         return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
     gp_model* m = new gp_model();
     m->ctx = ctx; m->n = n; m->d = d; m->nt = nt; m->p = p; m->delta = delta; m->prec = prec;
+    m->corr = ctx->opt.correlation;
     cudaError_t e = cudaMallocAsync(&m->mem, total, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1077,7 +1086,7 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
         cudaMemcpyAsync(m->theta, theta, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream))
         return bail(fail(ctx, GP_ECUDA, "copy of x/theta into the model failed"));
     gp::Batch b{};
-    b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta;
+    b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta; b.corr = m->corr;
     b.x = m->x; b.y = y; b.theta = m->theta; b.A = m->L; b.inst_stride = bL / sizeof(double);
     b.st = m->st;
     {
@@ -1139,7 +1148,7 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     const float2* Ldf = reinterpret_cast<const float2*>(m->L);
     const float2* Zdf = reinterpret_cast<const float2*>(m->Z);
     PhaseScope ps(ctx, GP_PHASE_PREDICT, (blocks_total + chunk - 1) / chunk);
-    GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, reinterpret_cast<const float2*>(m->x), m->theta, m->p,
+    GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, reinterpret_cast<const float2*>(m->x), m->theta, m->p, m->corr,
                                     c0, Ldf, Zdf + npad, Zdf, m->scalars, N, xstar, yhat, s2,
                                     (float2*)ctx->ws, chunk, ctx->stream));
     return GP_OK;

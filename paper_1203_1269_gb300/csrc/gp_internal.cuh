@@ -84,6 +84,7 @@ struct Batch {
     size_t inst_stride;           // elements between instances in A / Adf / Rdf
     InstState* st;                // count
     int asm_cols;                 // double-float assembly: tile columns per CTA (16 or 32)
+    int corr;                     // gp_correlation
 };
 
 // Split-precision path: per-instance buffers (double-float tiles, bf16
@@ -144,12 +145,13 @@ inline cudaError_t raise_smem_limit(Kernel* kernel, size_t bytes, std::atomic<si
 // ---- context accessors (gp_capi.cu) ----------------------------------------
 int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...);
 int ctx_device(const gp_ctx* ctx);
+int ctx_correlation(const gp_ctx* ctx);
 cudaStream_t ctx_stream(const gp_ctx* ctx);
 
 // ---- kernels (launch helpers, all on `stream`) ----------------------------
 cudaError_t launch_validate_theta(const Batch& b, cudaStream_t s);
 cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s);
-cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* theta, double p,
+cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* theta, double p, int corr,
                                   double delta, double* R, cudaStream_t s);
 cudaError_t launch_potrf_f64(const Batch& b, int J, cudaStream_t s);
 cudaError_t launch_trsm_f64(const Batch& b, int J, cudaStream_t s);
@@ -162,7 +164,7 @@ cudaError_t launch_fit_finish(const Batch& b, double* Z, size_t z_stride, double
                               cudaStream_t s);
 cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t z_stride, int col,
                                   cudaStream_t s);
-cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, double c0,
+cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
                            const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s);
 cudaError_t launch_to_df_inplace(double* p, size_t count, cudaStream_t s);

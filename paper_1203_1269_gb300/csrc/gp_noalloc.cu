@@ -46,7 +46,8 @@ extern "C" int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, 
     if (!ctx) return GP_EINVAL;
     if (n < 1 || d < 1 || d > GP_MAX_D || T < 1)
         return gp::ctx_fail(ctx, GP_EINVAL, "n, d and T must be >= 1 (d <= 64)");
-    if (!(p > 0.0 && p <= 2.0)) return gp::ctx_fail(ctx, GP_EINVAL, "p outside (0, 2]");
+    if (gp::ctx_correlation(ctx) == GP_CORR_POWEXP && !(p > 0.0 && p <= 2.0))
+        return gp::ctx_fail(ctx, GP_EINVAL, "p outside (0, 2]");
     if (!(delta >= 0.0) || !(delta <= 1e300)) return gp::ctx_fail(ctx, GP_EINVAL, "delta must be finite and >= 0");
     if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
         return gp::ctx_fail(ctx, GP_EINVAL, "null pointer argument");
@@ -78,7 +79,7 @@ extern "C" int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, 
     for (int c0 = 0; c0 < T; c0 += Tc) {
         const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
         gp::Batch b{};
-        b.n = n; b.d = d; b.nt = nt; b.count = cnt;
+        b.n = n; b.d = d; b.nt = nt; b.count = cnt; b.corr = gp::ctx_correlation(ctx);
         b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
         b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
         // every buffer the kernels read is written first: the theta check

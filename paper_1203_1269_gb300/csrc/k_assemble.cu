@@ -13,6 +13,7 @@
 // The double-float variant (split-precision path) keeps everything on the
 // FP32 pipes: on this GPU one FP64 pow costs as much as thousands of FP32
 // instructions, so the powers are exp(p ln|dx|) in double-float too.
+#include "corr.cuh"
 #include "df.cuh"
 #include "gp_internal.cuh"
 
@@ -116,6 +117,8 @@ k_assemble_tiles(Batch b, int group) {
     const int r = threadIdx.x % GP_NB;           // row inside the tile
     const int cb = threadIdx.x / GP_NB;          // 0..1
     const int gi = row0 + r;
+    const bool matern = corr_is_matern(b.corr);
+    const double cm = corr_theta_scale(b.corr);
 
 #pragma unroll 1
     for (int e = 0; e < kEntries; ++e) {
@@ -127,7 +130,9 @@ k_assemble_tiles(Batch b, int group) {
         double D[DB];
 #pragma unroll
         for (int k = 0; k < DB; ++k)
-            D[k] = (k < d && !pad) ? powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p) : 0.0;
+            D[k] = (k < d && !pad) ? (matern ? fabs(xs_r[r * DB + k] - xs_c[c * DB + k])
+                                             : powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p))
+                                   : 0.0;
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
             if (b.st[t].status != GP_OK) continue;
@@ -136,11 +141,16 @@ k_assemble_tiles(Batch b, int group) {
                 v = diag ? 1.0 : 0.0;
             } else {
                 const double* th = b.theta + (size_t)t * d;
-                double s = 0.0;
+                double s = 0.0, q = 1.0;
 #pragma unroll
-                for (int k = 0; k < DB; ++k)
-                    if (k < d) s = fma(__ldg(th + k), D[k], s);
-                v = exp(-s);
+                for (int k = 0; k < DB; ++k) {
+                    if (k < d) {
+                        const double h = cm * __ldg(th + k) * D[k];
+                        s += h;
+                        if (matern) q *= matern_q(h, b.corr);
+                    }
+                }
+                v = q * exp(-s);
                 if (diag) v += b.delta;
             }
             store_entry(b, t, off, v);
@@ -157,7 +167,7 @@ k_assemble_tiles(Batch b, int group) {
 // two thirds of its instructions).  Writes the working matrix and its copy.
 // Dynamic smem: x rows/cols (double), theta of the group and the exp table
 // (double-float), the group's status flags.
-template <int DB, int COLS>
+template <int DB, int COLS, bool MATERN>
 __global__ void __launch_bounds__(kThreads)
 k_assemble_tiles_df(Batch b, int group) {
     constexpr int kSplitDf = GP_NB / COLS;
@@ -191,14 +201,17 @@ k_assemble_tiles_df(Batch b, int group) {
     }
     for (int q = threadIdx.x; q < (t1 - t0) * DB; q += kThreads) {
         const int tt = q / DB, k = q % DB;
-        th[q] = (k < d) ? df_from_double(b.theta[(size_t)(t0 + tt) * d + k]) : dfl{0.f, 0.f};
+        th[q] = (k < d) ? df_from_double(corr_theta_scale(b.corr) * b.theta[(size_t)(t0 + tt) * d + k])
+                        : dfl{0.f, 0.f};
     }
     for (int q = threadIdx.x; q < t1 - t0; q += kThreads) live[q] = (b.st[t0 + q].status == GP_OK);
     fill_exp2_table(tab);
     __syncthreads();
     const dfl delta = df_from_double(b.delta);
-    const int pmode = pow_mode(b.p);
+    constexpr bool matern = MATERN;                          // the family is a template argument
+    const int pmode = matern ? kPowOne : pow_mode(b.p);      // Matern: h = c theta |dx|
     const dfl pd = df_from_double(b.p);
+    const dfl third = df_from_double(1.0 / 3.0);
     const size_t tile_off = (size_t)tile_lin * GP_TILE_ELEMS;
     const int r = threadIdx.x % GP_NB;
     const int cb = threadIdx.x / GP_NB;
@@ -224,14 +237,27 @@ k_assemble_tiles_df(Batch b, int group) {
             } else {
                 const dfl* tt = th + (size_t)(t - t0) * DB;
                 float sh = 0.f, sl = 0.f;
+                dfl qp = {1.f, 0.f};                // Matern: prod_k q(h_k)
 #pragma unroll
                 for (int k = 0; k < DB; ++k) {
                     if (k < d) {
                         const dfl a = tt[k];
-                        const float ph = __fmul_rn(a.hi, D[k].hi);
-                        sl = __fadd_rn(sl, __fmaf_rn(a.hi, D[k].hi, -ph));
-                        sl = __fmaf_rn(a.hi, D[k].lo, sl);
-                        sl = __fmaf_rn(a.lo, D[k].hi, sl);
+                        float ph = __fmul_rn(a.hi, D[k].hi);
+                        if (matern) {
+                            // h_k = a D_k itself is needed for q(h_k): its high
+                            // word enters the TwoSum, its low word sl
+                            const float pe = __fmaf_rn(a.hi, D[k].hi, -ph);
+                            const float pl = __fmaf_rn(a.hi, D[k].lo, __fmul_rn(a.lo, D[k].hi));
+                            dfl h;
+                            fast_two_sum(ph, __fadd_rn(pe, pl), h.hi, h.lo);
+                            qp = df_mul(qp, matern_q_df(h, b.corr, third));
+                            ph = h.hi;
+                            sl = __fadd_rn(sl, h.lo);
+                        } else {
+                            sl = __fadd_rn(sl, __fmaf_rn(a.hi, D[k].hi, -ph));
+                            sl = __fmaf_rn(a.hi, D[k].lo, sl);
+                            sl = __fmaf_rn(a.lo, D[k].hi, sl);
+                        }
                         float s2, e2;
                         two_sum(sh, ph, s2, e2);
                         sh = s2;
@@ -241,6 +267,7 @@ k_assemble_tiles_df(Batch b, int group) {
                 dfl S;
                 fast_two_sum(sh, sl, S.hi, S.lo);   // |sl| << sh: every term is >= 0
                 v = df_exp_neg(S, tab);
+                if (matern) v = df_mul(v, qp);
                 if (diag) v = df_add(v, delta);
             }
             const size_t i = (size_t)t * b.inst_stride + off;
@@ -283,10 +310,16 @@ k_assemble_tiles_generic(Batch b, int group) {
                 v = diag ? 1.0 : 0.0;
             } else {
                 const double* th = b.theta + (size_t)t * d;
-                double s = 0.0;
-                for (int k = 0; k < d; ++k)
-                    s = fma(th[k], powabs(b.x[(size_t)gi * d + k] - b.x[(size_t)gj * d + k], b.p), s);
-                v = exp(-s);
+                const bool matern = corr_is_matern(b.corr);
+                const double cm = corr_theta_scale(b.corr);
+                double s = 0.0, q = 1.0;
+                for (int k = 0; k < d; ++k) {
+                    const double dx = b.x[(size_t)gi * d + k] - b.x[(size_t)gj * d + k];
+                    const double h = cm * th[k] * (matern ? fabs(dx) : powabs(dx, b.p));
+                    s += h;
+                    if (matern) q *= matern_q(h, b.corr);
+                }
+                v = q * exp(-s);
                 if (diag) v += b.delta;
             }
             store_entry(b, t, off, v);
@@ -296,15 +329,21 @@ k_assemble_tiles_generic(Batch b, int group) {
 
 // Dense n x n row-major R (both triangles) for one theta.
 __global__ void k_assemble_dense(int n, int d, const double* __restrict__ x,
-                                 const double* __restrict__ theta, double p, double delta,
+                                 const double* __restrict__ theta, double p, int corr, double delta,
                                  double* __restrict__ R) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= n) return;
-    double s = 0.0;
-    for (int k = 0; k < d; ++k)
-        s = fma(theta[k], powabs(x[(size_t)i * d + k] - x[(size_t)j * d + k], p), s);
-    double v = exp(-s);
+    const bool matern = corr_is_matern(corr);
+    const double cm = corr_theta_scale(corr);
+    double s = 0.0, q = 1.0;
+    for (int k = 0; k < d; ++k) {
+        const double dx = x[(size_t)i * d + k] - x[(size_t)j * d + k];
+        const double h = cm * theta[k] * (matern ? fabs(dx) : powabs(dx, p));
+        s += h;
+        if (matern) q *= matern_q(h, corr);
+    }
+    double v = q * exp(-s);
     if (i == j) v += delta;
     R[(size_t)i * n + j] = v;
 }
@@ -344,14 +383,15 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess) kern<<<grid, kThreads, smem, s>>>(b, group);
         };
+        const bool m = corr_is_matern(b.corr);
         if (cols == 16) {
-            if (DB == 4) go(k_assemble_tiles_df<4, 16>);
-            else if (DB == 8) go(k_assemble_tiles_df<8, 16>);
-            else go(k_assemble_tiles_df<16, 16>);
+            if (DB == 4) m ? go(k_assemble_tiles_df<4, 16, true>) : go(k_assemble_tiles_df<4, 16, false>);
+            else if (DB == 8) m ? go(k_assemble_tiles_df<8, 16, true>) : go(k_assemble_tiles_df<8, 16, false>);
+            else m ? go(k_assemble_tiles_df<16, 16, true>) : go(k_assemble_tiles_df<16, 16, false>);
         } else {
-            if (DB == 4) go(k_assemble_tiles_df<4, 32>);
-            else if (DB == 8) go(k_assemble_tiles_df<8, 32>);
-            else go(k_assemble_tiles_df<16, 32>);
+            if (DB == 4) m ? go(k_assemble_tiles_df<4, 32, true>) : go(k_assemble_tiles_df<4, 32, false>);
+            else if (DB == 8) m ? go(k_assemble_tiles_df<8, 32, true>) : go(k_assemble_tiles_df<8, 32, false>);
+            else m ? go(k_assemble_tiles_df<16, 32, true>) : go(k_assemble_tiles_df<16, 32, false>);
         }
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
@@ -367,10 +407,10 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* theta, double p,
+cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* theta, double p, int corr,
                                   double delta, double* R, cudaStream_t s) {
     dim3 grid((n + 255) / 256, n);
-    k_assemble_dense<<<grid, 256, 0, s>>>(n, d, x, theta, p, delta, R);
+    k_assemble_dense<<<grid, 256, 0, s>>>(n, d, x, theta, p, corr, delta, R);
     return cudaGetLastError();
 }
 

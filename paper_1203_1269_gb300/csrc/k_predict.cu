@@ -17,6 +17,7 @@
 // solved blocks above it (a 128 x 128 by 128 x 16 product per tile), solves
 // with the diagonal tile and folds the finished block into v'v and a'v.
 // Solved blocks are kept in a per-CTA slice of `work` (npad x NR pairs).
+#include "corr.cuh"
 #include "df.cuh"
 #include "gp_internal.cuh"
 
@@ -33,6 +34,7 @@ struct PredArgs {
     const float2* x;       // n x d (double-float)
     const double* theta;   // d
     double p, c0;
+    int corr;              // gp_correlation of the fit
     const float2* L;       // packed tiles (double-float)
     const float2* w;       // npad
     const float2* a;       // npad
@@ -64,10 +66,13 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
         const int m = q / d, k = q % d;
         xsm[q] = (mbase + m < g.N) ? df_from_double(g.xs[(size_t)(mbase + m) * d + k]) : dfl{0.f, 0.f};
     }
-    for (int q = threadIdx.x; q < d; q += kThreads) th[q] = df_from_double(g.theta[q]);
+    // Matern families: theta pre-multiplied by c, powers with p = 1 (corr.cuh)
+    for (int q = threadIdx.x; q < d; q += kThreads) th[q] = df_from_double(corr_theta_scale(g.corr) * g.theta[q]);
     fill_exp2_table(tab);
     const dfl pd = df_from_double(g.p);
-    const int pmode = pow_mode(g.p);
+    const bool matern = corr_is_matern(g.corr);
+    const int pmode = matern ? kPowOne : pow_mode(g.p);
+    const dfl third = df_from_double(1.0 / 3.0);
     __syncthreads();
 
     dfl mean_p[PT], vv_p[PT], av_p[PT];
@@ -87,12 +92,15 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
             const int m = hh * PT + u;
             dfl v = {0.f, 0.f};
             if (gi < n && mbase + m < g.N) {
-                dfl s = {0.f, 0.f};
+                dfl s = {0.f, 0.f}, qp = {1.f, 0.f};
                 for (int k = 0; k < d; ++k) {
                     const dfl dx = df_sub(xsm[m * d + k], df_load(g.x + (size_t)gi * d + k));
-                    s = df_fma(th[k], df_powabs(dx, pmode, g.p, pd, tab), s);
+                    const dfl h = df_mul(th[k], df_powabs(dx, pmode, g.p, pd, tab));
+                    s = df_add(s, h);
+                    if (matern) qp = df_mul(qp, matern_q_df(h, g.corr, third));
                 }
                 v = df_exp_neg(s, tab);
+                if (matern) v = df_mul(v, qp);
             }
             mean_p[u] = df_fma(v, wi, mean_p[u]);
             rhs[m * GP_NB + r] = v;
@@ -213,7 +221,7 @@ size_t predict_work_per_cta(int nt) { return (size_t)nt * GP_NB * NR * sizeof(fl
 
 int predict_points_per_cta() { return NR; }
 
-cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, double c0,
+cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
                            const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s) {
     const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + 64) * sizeof(dfl);
@@ -222,7 +230,7 @@ cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* 
     if (e != cudaSuccess) return e;
     PredArgs g;
     g.n = n; g.d = d; g.nt = nt; g.N = N;
-    g.x = x; g.theta = theta; g.p = p; g.c0 = c0;
+    g.x = x; g.theta = theta; g.p = p; g.corr = corr; g.c0 = c0;
     g.L = L; g.w = w; g.a = a; g.sc = scalars; g.xs = xs; g.yhat = yhat; g.s2 = s2; g.work = work;
     const int blocks_total = (N + NR - 1) / NR;
     for (int b0 = 0; b0 < blocks_total; b0 += chunk) {

@@ -20,6 +20,8 @@ from . import build as _build
 GP_FP64, GP_MIXED, GP_FP32, GP_AUTO = 0, 1, 2, 3
 PRECISIONS = {"fp64": GP_FP64, "mixed": GP_MIXED, "fp32": GP_FP32, "auto": GP_AUTO}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
+# gp_correlation: eq. (2)'s power-exponential family and the Matern family
+CORRELATIONS = {"powexp": 0, "matern12": 1, "matern32": 2, "matern52": 3}
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ENOTPD", -4: "ECUDA", -5: "ETIMEOUT",
           -6: "EDEGENERATE", -7: "ENOTSUP"}
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_EDEGENERATE, GP_ENOTSUP = \
@@ -38,7 +40,8 @@ class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
                 ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int),
                 ("inject_timeout", _c_int), ("fuse_panels", _c_int), ("auto_tol", _c_double),
-                ("update_tile", _c_int), ("assemble_cols", _c_int), ("pair_update", _c_int)]
+                ("update_tile", _c_int), ("assemble_cols", _c_int), ("correlation", _c_int),
+                ("pair_update", _c_int)]
 
 
 class TuneTrial(ctypes.Structure):
@@ -232,6 +235,8 @@ class Context:
         return {f: getattr(self._opt, f) for f, _ in Options._fields_}
 
     def set_options(self, **kw):
+        if isinstance(kw.get("correlation"), str):
+            kw["correlation"] = CORRELATIONS[kw["correlation"]]
         opt = Options(**{**self.options(), **kw})
         self._check(self._lib.gp_set_options(self._h, ctypes.byref(opt)))
         self._opt = opt
