@@ -72,6 +72,8 @@ class Oracle:
         lib.gpo_fit_parts.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, c_double,
                                       _dp, _dp, _dp, _dp, _dp]
         lib.gpo_fit_parts.restype = c_int
+        lib.gpo_nll_grad.argtypes = [c_int, c_int, _dp, _dp, _dp, c_double, c_int, c_double, _dp, _dp]
+        lib.gpo_nll_grad.restype = c_int
         lib.gpo_num_threads.restype = c_int
         self.lib = lib
 
@@ -149,6 +151,18 @@ class Oracle:
         self.lib.gpo_nll_batch(n, d, _p(x), _p(y), T, _p(th), float(p), _fam(corr), float(delta),
                                int(bool(want_cond)), _p(out), st.ctypes.data_as(_ip))
         return out, st
+
+    def nll_grad(self, x, y, theta, p, delta=0.0, corr="powexp"):
+        """d(-2logL)/dtheta at one theta.  Returns (grad (d,), dict of NLL_FIELDS, status)."""
+        x = _f64(x)
+        n, d = x.shape
+        y = _f64(y).reshape(n)
+        th = _f64(theta).reshape(d)
+        g = np.empty(d)
+        out = np.empty(7)
+        st = self.lib.gpo_nll_grad(n, d, _p(x), _p(y), _p(th), float(p), _fam(corr), float(delta),
+                                   _p(g), _p(out))
+        return g, dict(zip(NLL_FIELDS, out.tolist())), int(st)
 
     def predict(self, x, y, theta, p, delta, xs, nugget_in_var=True, want_var=True, corr="powexp"):
         """Kriging mean and variance at the rows of xs.  Returns (yhat, s2|None, status)."""
@@ -230,3 +244,7 @@ def predict(*a, **k):
 
 def fit_parts(*a, **k):
     return default().fit_parts(*a, **k)
+
+
+def nll_grad(*a, **k):
+    return default().nll_grad(*a, **k)

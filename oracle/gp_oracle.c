@@ -352,6 +352,81 @@ int gpo_fit_parts(int n, int d, const double* x, const double* y, const double* 
     return GPO_OK;
 }
 
+/* d/dtheta_k of one dimension's factor, divided by the factor itself:
+ * dlog rho / dtheta for the family (h = c theta |dx| for the Matern forms):
+ *   power-exponential: -|dx|^p
+ *   nu = 1/2:  -|dx|
+ *   nu = 3/2:  rho' / rho = -h / (1 + h) * sqrt(3) |dx|
+ *   nu = 5/2:  rho' / rho = -h (1 + h) / (3 (1 + h + h^2/3)) * sqrt(5) |dx| */
+static double gpo_dlog_corr_1d(double diff, double theta, double p, int fam) {
+    double a = fabs(diff);
+    if (fam == GPO_MATERN12) return -a;
+    if (fam == GPO_MATERN32) {
+        double h = sqrt(3.0) * theta * a;
+        return -h / (1.0 + h) * sqrt(3.0) * a;
+    }
+    if (fam == GPO_MATERN52) {
+        double h = sqrt(5.0) * theta * a;
+        return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(5.0) * a;
+    }
+    return -pow(a, p);
+}
+
+/* Gradient of -2 log L (eq. 4) with respect to theta at one theta:
+ *   d(-2logL)/dtheta_k = tr(R^-1 dR_k) - (n / Q) w' dR_k w,
+ * from d log|R| = tr(R^-1 dR) and, mu_hat being the minimiser of Q over mu,
+ * dQ = -w' dR w with w = R^-1 (Y - 1 mu_hat).  dR_k = dR/dtheta_k is
+ * R_ij dlog rho(x_ik - x_jk)/dtheta_k off the diagonal and 0 on it (the
+ * nugget and the unit diagonal do not depend on theta).  R^-1 is formed
+ * column by column by two triangular solves of e_j.  grad has d entries;
+ * out is filled as by gpo_nll.  Returns the status (grad NaN if not OK). */
+int gpo_nll_grad(int n, int d, const double* x, const double* y, const double* theta,
+                 double p, int fam, double delta, double* grad, double* out) {
+    int status = gpo_nll(n, d, x, y, theta, p, fam, delta, 0, out);
+    for (int k = 0; k < d; ++k) grad[k] = NAN;
+    if (status != GPO_OK) return status;
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* Ri = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* a = (double*)malloc(sizeof(double) * (size_t)n);
+    double* b = (double*)malloc(sizeof(double) * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    double* col = (double*)malloc(sizeof(double) * (size_t)n);
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!R || !L || !Ri || !a || !b || !w || !col || !tmp) {
+        status = GPO_ENOMEM;
+        goto done;
+    }
+    status = gpo_fit_parts(n, d, x, y, theta, p, fam, delta, R, L, a, b, w);
+    if (status != GPO_OK) goto done;
+    for (int j = 0; j < n; ++j) {          /* column j of R^-1 = L^-T L^-1 e_j */
+        for (int i = 0; i < n; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+        gpo_forward(n, L, col, tmp);
+        gpo_backward(n, L, tmp, col);
+        for (int i = 0; i < n; ++i) Ri[(size_t)i * n + j] = col[i];
+    }
+    {
+        const double Q = out[4];
+        for (int k = 0; k < d; ++k) {
+            double tr = 0.0, quad = 0.0;
+            for (int i = 0; i < n; ++i) {
+                for (int j = 0; j < n; ++j) {
+                    if (i == j) continue;
+                    const double* xi = x + (size_t)i * d;
+                    const double* xj = x + (size_t)j * d;
+                    const double dR = R[(size_t)i * n + j] * gpo_dlog_corr_1d(xi[k] - xj[k], theta[k], p, fam);
+                    tr += Ri[(size_t)j * n + i] * dR;
+                    quad += w[i] * dR * w[j];
+                }
+            }
+            grad[k] = tr - n / Q * quad;
+        }
+    }
+done:
+    free(R); free(L); free(Ri); free(a); free(b); free(w); free(col); free(tmp);
+    return status;
+}
+
 int gpo_num_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);

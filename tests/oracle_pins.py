@@ -481,10 +481,52 @@ def check_matern_predict(orc, seed=43):
         assert np.max(np.abs(r - rb)) < 1e-12
 
 
+# --------------------------------------------------------------- gradient --
+
+def check_grad_finite_differences(orc, seed=47):
+    """d(-2logL)/dtheta against central differences of the oracle's own
+    -2logL (which the other pins fix), for eq. (2) and the Matern forms."""
+    g = np.random.default_rng(seed)
+    n, d = 25, 3
+    x = g.random((n, d))
+    y = np.sin(3 * x[:, 0]) + x[:, 1] * x[:, 2]
+    th = np.array([2.0, 0.7, 4.0])
+    for corr, p in (("powexp", 1.95), ("powexp", 1.0), ("matern32", 2.0), ("matern52", 2.0)):
+        grad, out, st = orc.nll_grad(x, y, th, p, 1e-3, corr=corr)
+        assert st == 0
+        _, st2 = orc.nll(x, y, th, p, 1e-3, corr=corr)
+        for k in range(d):
+            h = 1e-5 * th[k]
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            fp = orc.nll(x, y, tp, p, 1e-3, corr=corr)[0]["nll"]
+            fm = orc.nll(x, y, tm, p, 1e-3, corr=corr)[0]["nll"]
+            fd = (fp - fm) / (2 * h)
+            assert abs(grad[k] - fd) <= 1e-6 * max(abs(fd), 1.0), (corr, k, grad[k], fd)
+
+
+def check_grad_n2(orc):
+    """n = 2: -2logL = log((1+delta)^2 - rho^2) + 2 log Q with
+    Q = (y1-y2)^2 / (2 (1 + delta - rho)), so with drho = rho dlog rho,
+    d(-2logL) = drho [-2 rho / ((1+delta)^2 - rho^2) + 2 / (1 + delta - rho)]."""
+    x = np.array([[0.1, 0.2], [0.4, 0.6]])
+    th = np.array([1.5, 0.7])
+    y = np.array([1.25, -0.5])
+    p, delta = 1.95, 1e-2
+    rho = math.exp(-1.5 * 0.3 ** p) * math.exp(-0.7 * 0.4 ** p)
+    grad, out, st = orc.nll_grad(x, y, th, p, delta)
+    assert st == 0
+    common = -2 * rho / ((1 + delta) ** 2 - rho ** 2) + 2 / (1 + delta - rho)
+    for k, dx in enumerate((0.3, 0.4)):
+        drho = rho * -(dx ** p)
+        assert _rel(grad[k], drho * common) < 1e-12
+
+
 ALL_CHECKS = [
     check_corr_hand_values, check_corr_invariants, check_kms, check_n1, check_n2,
     check_n3, check_eig_logdet, check_solve_estimates, check_cholesky_reconstructs,
     check_notpd, check_cond_estimate, check_invariants, check_table_form, check_predict,
     check_fit_parts, check_matern_half_is_exponential, check_matern_bessel, check_matern_n2,
-    check_matern_predict,
+    check_matern_predict, check_grad_finite_differences, check_grad_n2,
 ]

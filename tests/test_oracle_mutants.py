@@ -47,6 +47,10 @@ MUTANTS = {
     "predict_nugget_in_r": ("gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam);",
                             "gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam) + 1e-6;"),
     "cond_no_anorm": ("return anorm * est;", "return est;"),
+    "grad_trace_sign": ("tr += Ri[(size_t)j * n + i] * dR;", "tr -= Ri[(size_t)j * n + i] * dR;"),
+    "grad_drops_n_over_q": ("grad[k] = tr - n / Q * quad;", "grad[k] = tr - quad;"),
+    "grad_power_wrong": ("    return -pow(a, p);", "    return -pow(a, p - 1.0);"),
+    "grad_matern32_dlog": ("return -h / (1.0 + h) * sqrt(3.0) * a;", "return -h * sqrt(3.0) * a;"),
 }
 
 
