@@ -771,6 +771,70 @@ int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y,
     return rc;
 }
 
+int gp_nll_grad_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                      const double* theta, double p, double delta, double* nll, double* grad, int* status) {
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (d > 16) return fail(ctx, GP_ENOTSUP, "the gradient is built for d <= 16 (d = %d)", d);
+    if (!x || !y || !theta || !nll || !grad || !status) return fail(ctx, GP_EINVAL, "null pointer argument");
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int nt = gp::num_tiles(n);
+    const long long ntiles = gp::packed_tiles(nt);
+    const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
+    const size_t z_bytes = align256((size_t)2 * nt * GP_NB * sizeof(double));
+    const size_t st_bytes = align256(sizeof(gp::InstState));
+    const size_t part_bytes = align256((size_t)ntiles * d * sizeof(double));
+    const size_t sc_bytes = align256(3 * sizeof(double));
+    // per instance: the factor, L^-1, R^-1, [a | w], its record, tile partial
+    // sums and mu / sigma2 / log|R| (which the caller does not ask for)
+    const size_t per = 3 * a_bytes + z_bytes + st_bytes + part_bytes + sc_bytes;
+    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    long long cap = (long long)(avail / per);
+    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
+    if (cap > 65535) cap = 65535;
+    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
+    const int Tc = (int)(cap < T ? cap : T);
+    rc = ensure_ws(ctx, per * (size_t)Tc);
+    if (rc) return rc;
+    char* c = (char*)ctx->ws;
+    double* A = (double*)c; c += a_bytes * Tc;
+    double* X = (double*)c; c += a_bytes * Tc;
+    double* Ri = (double*)c; c += a_bytes * Tc;
+    double* Z = (double*)c; c += z_bytes * Tc;
+    gp::InstState* st = (gp::InstState*)c; c += st_bytes * Tc;
+    double* partial = (double*)c; c += part_bytes * Tc;
+    double* sc = (double*)c;
+    for (int c0 = 0; c0 < T; c0 += Tc) {
+        const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
+        gp::Batch b{};
+        b.n = n; b.d = d; b.nt = nt; b.count = cnt; b.corr = ctx->opt.correlation;
+        b.p = p; b.delta = delta; b.x = x; b.y = y; b.theta = theta + (size_t)c0 * d;
+        b.A = A; b.inst_stride = a_bytes / sizeof(double); b.st = st;
+        {
+            PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+            GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
+            GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+        }
+        rc = run_factor_f64(ctx, b);
+        if (rc) return rc;
+        const size_t zs = z_bytes / sizeof(double);
+        {
+            PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+            GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
+            GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, sc, sc + Tc, sc + 2 * Tc, status + c0,
+                                             ctx->stream));
+        }
+        int kernels = 0;
+        cudaError_t e = gp::launch_grad(b, Z, zs, X, Ri, partial, status + c0, grad + (size_t)c0 * d,
+                                        ctx->stream, &kernels);
+        ctx->launches += kernels;
+        ctx->phase_launches[GP_PHASE_SOLVE] += kernels;
+        if (e != cudaSuccess) return fail(ctx, GP_ECUDA, "gradient launch: %s", cudaGetErrorString(e));
+    }
+    return GP_OK;
+}
+
 int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                  const double* theta, double p, double delta, int prec, double* nll,
                  double* mu_hat, double* sigma2_hat, double* logdet, int* status) {

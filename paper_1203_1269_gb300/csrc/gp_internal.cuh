@@ -181,6 +181,8 @@ cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s);
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s);
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s);
+cudaError_t launch_grad(const Batch& b, double* Z, size_t zs, double* X, double* Ri, double* partial,
+                        const int* status, double* grad, cudaStream_t s, int* kernels);
 cudaError_t launch_norm1(const MixedBatch& b, cudaStream_t s);
 cudaError_t launch_hager(const MixedBatch& b, int phase, double* cond, cudaStream_t s);
 cudaError_t launch_fill_int(int* dst, int count, int value, cudaStream_t s);

@@ -89,6 +89,7 @@ def load(path=None):
     lib.gp_nll_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
                                  P, P, P, P, P]
     lib.gp_nll_batch_ex.argtypes = lib.gp_nll_batch.argtypes + [P, P]
+    lib.gp_nll_grad_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, P, P, P]
     lib.gp_nll_batch_host.argtypes = lib.gp_nll_batch.argtypes
     lib.gp_plan_nll_batch.argtypes = lib.gp_nll_batch.argtypes + [P, ctypes.POINTER(P)]
     lib.gp_autotune.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int, _c_int,
@@ -355,6 +356,25 @@ class Context:
         self._check(self._lib.gp_get_options(self._h, ctypes.byref(opt)))
         self._opt = opt
         return trials, self.options()
+
+    def nll_grad_batch(self, x, y, thetas, p, delta, out=None):
+        """gp_nll_grad_batch: -2logL and its gradient with respect to theta
+        (T x d) at each row of thetas, in double precision."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        if out is None:
+            kw = dict(dtype=torch.float64, device=self.device)
+            out = dict(nll=torch.empty(T, **kw), grad=torch.empty((T, d), **kw),
+                       status=torch.empty(T, dtype=torch.int32, device=self.device))
+        self._check(self._lib.gp_nll_grad_batch(
+            self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta),
+            _ptr(out["nll"]), _ptr(out["grad"]), _ptr(out["status"])))
+        return out
 
     def plan_nll_batch(self, x, y, thetas, p, delta, prec="mixed", cond=False):
         """Record nll_batch(x, y, thetas, ...) as a CUDA graph; returns a Plan
