@@ -48,6 +48,15 @@ constexpr int kEpiWarps = 8;                  // epilogue warps: kEpiWarps / 4 p
 constexpr int kEpiParts = kEpiWarps / 4;       // column parts of a tile
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 MMA, then the epilogue
 constexpr int kEpiThreads = 32 * kEpiWarps;
+// Early-release update (k_split_gemm<1, 128, 4, true>): warpgroup 0 holds the
+// copy and MMA warps (and two idle ones) and gives registers up to the two
+// epilogue warpgroups, which keep a whole 64-column part of a tile's combined
+// result in registers.  The split must fit the launch's registers:
+// 128 * kRegsLow + 256 * kRegsHigh <= 384 * (registers at launch).
+constexpr int kGemmThreadsER = 128 + 32 * kEpiWarps;
+constexpr int kRegsLow = 64;
+constexpr int kRegsHigh = 216;
+static_assert(kEpiWarps == 8, "the early-release split assumes two epilogue warpgroups");
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
 
 // ---------------------------------------------------------------- PTX ------
@@ -204,6 +213,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void regs_dec() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N)); }
+template <int N>
+__device__ __forceinline__ void regs_inc() { asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N)); }
 
 // ----------------------------------------------------------- layouts -------
 
@@ -673,9 +687,19 @@ __device__ __forceinline__ void issue_stage_ns(int ns, bool first, uint32_t tacc
 // quarter, each taking one column part, with the loads of a column block
 // issued together).  Every wait is bounded; a timeout marks the instance
 // GP_ETIMEOUT and stops the CTA after its copies and MMAs have landed.
-template <int MODE, int NT, int NG>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
+//
+// ER (early release; MODE 1, NT = 128 only): the epilogue first reads and
+// combines every accumulator group of its columns into registers, releases
+// tensor memory to the MMA warp, and only then reads, updates and writes C,
+// so that C's round trip overlaps the next tile's MMAs.  Warps 2, 3 idle;
+// the epilogue warps are 4 .. 11 and hold kRegsHigh registers each.
+template <int MODE, int NT, int NG, bool ER = false>
+__global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
+    k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
     static_assert(NG * NT <= 512, "accumulators exceed tensor memory");
+    static_assert(!ER || (MODE == 1 && NT == 128 && NG == 4) || (MODE == 0 && NT == 64),
+                  "early release is built for the 128-column update and the panel solve");
+    constexpr int kEpiBase = ER ? 4 : 2;          // first epilogue warp
     // two accumulator sets when they fit (64-column update tiles): the MMAs of
     // tile i + 1 then run while the epilogue drains tile i
     constexpr int NBUF = (2 * NG * NT <= 512) ? 2 : 1;
@@ -747,6 +771,119 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
     tc_fence_after();
     const uint32_t tbase = tmem_base;
 
+    auto epilogue_er = [&]() {
+        // early-release epilogue: warp w reads TMEM lane quarter w % 4 and
+        // the column part (w - 4) / 4 of the tile
+        const int q = warp & 3;
+        const int part = (warp - kEpiBase) >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+        constexpr int kPartCols = NT / kEpiParts;
+        constexpr int CB1 = (NG > 4) ? 8 : 16;  // columns per TMEM load (phase 1)
+        constexpr int CB2 = 16;                 // columns per C block (phase 2)
+        static_assert(kPartCols % CB1 == 0 && kPartCols % CB2 == 0, "column part vs block widths");
+        const int ng_used = ns < NG ? ns : NG;
+        const int cbase = part * kPartCols;
+        int i = 0;
+        for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
+            int t, I, K, col0;
+            decode(w, t, I, K, col0);
+            if (b.st[t].status != GP_OK) continue;
+            float2* C = df_tile(b, b.A, t, I, K) + (size_t)col0 * GP_NB;
+            if (MODE == 1 && threadIdx.x == 32 * kEpiBase) prefetch_l2(C, (uint32_t)(NT * GP_NB * sizeof(float2)));
+            if (!mbar_wait(&tfull_bar[0], i & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            // phase 1: sum of the groups, as in the epilogue below, for all
+            // kPartCols columns of this thread's row
+            float hv[kPartCols], lv[kPartCols];
+#pragma unroll
+            for (int cb = 0; cb < kPartCols; cb += CB1) {
+                float d[NG][CB1];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    if (g < ng_used) {
+                        if (CB1 == 8) tmem_ld8(lane_addr + g * NT + cbase + cb, d[g]);
+                        else          tmem_ld16(lane_addr + g * NT + cbase + cb, d[g]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CB1; ++j) d[g][j] = 0.f;
+                    }
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < CB1; ++j) {
+                    float h, l;
+                    two_sum(d[0][j], d[1][j], h, l);
+                    if (MODE == 1) {
+#pragma unroll
+                        for (int g = 2; g < NG - 1; ++g) {
+                            float s2, e2;
+                            two_sum(h, d[g][j], s2, e2);
+                            h = s2;
+                            l = __fadd_rn(l, e2);
+                        }
+                        l = __fadd_rn(l, d[NG - 1][j]);
+                        two_sum(h, l, h, l);
+                    } else {
+#pragma unroll
+                        for (int g = 2; g < NG; ++g) {
+                            float s2, e2;
+                            two_sum(h, d[g][j], s2, e2);
+                            l = __fadd_rn(l, e2);
+                            fast_two_sum(s2, l, h, l);
+                        }
+                    }
+                    hv[cb + j] = h;
+                    lv[cb + j] = l;
+                }
+            }
+            // tensor memory is free for the next tile's MMAs
+            tc_fence_before();
+            mbar_arrive(&tempty_bar[0]);
+            // phase 2: C - 2^e (h + l) (update), or 2^e (h + l) (panel)
+            const int eA = ((MODE == 0 || !fused) ? pe_block(b, t, I) : fe_block(b, t, I))[r];
+            const int* eBp = ((MODE == 0) ? (b.WE + (size_t)t * b.we_stride)
+                                          : (fused ? fe_block(b, t, K) : pe_block(b, t, K))) + col0 + cbase;
+#pragma unroll
+            for (int cb = 0; cb < kPartCols; cb += CB2) {
+                float2 cv[CB2];
+                if (MODE == 1) {
+#pragma unroll
+                    for (int j = 0; j < CB2; ++j) cv[j] = C[(size_t)(cbase + cb + j) * GP_NB + r];
+                }
+#pragma unroll
+                for (int j = 0; j < CB2; ++j) {
+                    const int e = eA + __ldg(eBp + cb + j) - 14;
+                    const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
+                    const float h = __fmul_rn(hv[cb + j], sc);
+                    const float l = __fmul_rn(lv[cb + j], sc);
+                    if (MODE == 0) {
+                        float hh, ll;
+                        fast_two_sum(h, l, hh, ll);
+                        C[(size_t)(cbase + cb + j) * GP_NB + r] = make_float2(hh, ll);
+                        continue;
+                    }
+                    float sh, se;
+                    two_sum(cv[j].x, -h, sh, se);
+                    se = __fadd_rn(se, __fsub_rn(cv[j].y, l));
+                    two_sum(sh, se, sh, se);
+                    C[(size_t)(cbase + cb + j) * GP_NB + r] = make_float2(sh, se);
+                }
+            }
+            ++i;
+        }
+    };
+
+    // setmaxnreg is warpgroup-wide: one instruction per warpgroup, every
+    // thread of it executing that same instruction
+    if (ER && warp >= kEpiBase) {
+        regs_inc<kRegsHigh>();
+        epilogue_er();
+    } else {
+    if (ER) regs_dec<kRegsLow>();               // warpgroup 0: copies, MMAs, two idle warps
     if (warp == 0) {
         if (lane == 0) {
             int g = 0;   // stages issued so far
@@ -820,7 +957,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0);
         }
-    } else {
+    } else if (!ER) {
         // epilogue: warps 2 .. 1 + kEpiWarps; warp w reads TMEM lane quarter
         // w % 4 and the column part (w - 2) / 4 of the tile
         const int q = warp & 3;
@@ -924,6 +1061,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm(MixedBatch b, in
             mbar_arrive(&tempty_bar[buf]);
             ++i;
         }
+    }
     }
     tc_fence_before();
     __syncthreads();
@@ -1589,21 +1727,53 @@ static int sm_count() {
     return n;
 }
 
-template <int MODE, int NT, int NG>
+template <int MODE, int NT, int NG, bool ER = false>
 static cudaError_t launch_gemm(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s, int kind = 0) {
     const size_t smem = (size_t)2 * ns * (kChunkBytes + kChunkBytes / (GP_NB / NT)) + 1024;
     static std::atomic<size_t> attr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_split_gemm<MODE, NT, NG>, smem, attr);
+    cudaError_t e = raise_smem_limit(k_split_gemm<MODE, NT, NG, ER>, smem, attr);
     if (e != cudaSuccess) return e;
     const long long total = (long long)per_inst * b.count;
     const int grid = (int)(total < sm_count() ? total : sm_count());
-    k_split_gemm<MODE, NT, NG><<<grid, kGemmThreads, smem, s>>>(b, J, per_inst, kind);
+    k_split_gemm<MODE, NT, NG, ER><<<grid, ER ? kGemmThreadsER : kGemmThreads, smem, s>>>(b, J, per_inst, kind);
     return cudaGetLastError();
+}
+
+// The early-release kernels raise their epilogue warps to kRegsHigh
+// registers; that only completes if the block was launched with enough
+// registers for the whole split, so they run only where the built kernel's
+// register count covers it (checked once per device and kernel), else the
+// plain kernel runs.
+template <int MODE, int NT, int NG>
+static bool early_release_fits() {
+    static std::atomic<int> ok[kMaxDevices];   // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    int v = cached ? ok[dev].load(std::memory_order_relaxed) : 0;
+    if (v == 0) {
+        cudaFuncAttributes fa{};
+        v = 2;
+        if (cudaFuncGetAttributes(&fa, k_split_gemm<MODE, NT, NG, true>) == cudaSuccess &&
+            128 * kRegsLow + 32 * kEpiWarps * kRegsHigh <= kGemmThreadsER * fa.numRegs &&
+            fa.maxThreadsPerBlock >= kGemmThreadsER)
+            v = 1;
+        cudaGetLastError();
+        if (cached) ok[dev].store(v, std::memory_order_relaxed);
+    }
+    return v == 1;
+}
+
+static cudaError_t launch_update128(const MixedBatch& b, int J, int per_inst, int ns, cudaStream_t s, int kind) {
+    if (early_release_fits<1, 128, 4>()) return launch_gemm<1, 128, 4, true>(b, J, per_inst, ns, s, kind);
+    return launch_gemm<1, 128, 4>(b, J, per_inst, ns, s, kind);
 }
 
 cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
+    if (early_release_fits<0, 64, GP_PANEL_SLICES>())
+        return launch_gemm<0, 64, GP_PANEL_SLICES, true>(b, J, 2 * m, b.ps, s);
     return launch_gemm<0, 64, GP_PANEL_SLICES>(b, J, 2 * m, b.ps, s);
 }
 
@@ -1614,7 +1784,7 @@ cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
     if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, 2 * m, b.s, s, 1);
-    return launch_gemm<1, 128, 4>(b, J, m, b.s, s, 1);
+    return launch_update128(b, J, m, b.s, s, 1);
 }
 
 // The fused update by CTA pairs (k_split_gemm_pair): a cluster launch whose
@@ -1658,7 +1828,7 @@ cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s)
     if (m <= 0) return cudaSuccess;
     if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, m * (m + 1), b.s, s, 2);
     if (b.pair_update) return launch_gemm_pair(b, J, m, s);
-    return launch_gemm<1, 128, 4>(b, J, m * (m + 1) / 2, b.s, s, 2);
+    return launch_update128(b, J, m * (m + 1) / 2, b.s, s, 2);
 }
 
 cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s) {
@@ -1677,7 +1847,7 @@ cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {
         case 3: return launch_gemm<1, 128, 3>(b, J, tiles, b.s, s);
         default:
             if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, 2 * tiles, b.s, s);
-            return launch_gemm<1, 128, 4>(b, J, tiles, b.s, s);
+            return launch_update128(b, J, tiles, b.s, s, 0);
     }
 }
 
