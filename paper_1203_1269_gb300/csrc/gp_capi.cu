@@ -233,6 +233,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.fe_stride = z.FE / sizeof(int);
     mb.wt_stride = z.WT / sizeof(float2);
     mb.fuse = ctx->opt.fuse_panels;
+    mb.fwd = y != nullptr;
     mb.z_stride = z.Z / sizeof(float2);
     mb.y = y;
     return mb;
@@ -250,9 +251,10 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
     mb.d = d;
     GP_CUDA(ctx, cudaMemsetAsync(mb.err, 0, sizeof(int), ctx->stream));
     {
-        PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
+        PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, mb.fwd ? 3 : 2);
         GP_CUDA(ctx, gp::launch_validate_theta(b, ctx->stream));
         GP_CUDA(ctx, gp::launch_assemble_tiles(b, ctx->stream));
+        if (mb.fwd) GP_CUDA(ctx, gp::launch_rhs_init(mb, ctx->stream));
     }
     const int nt = mb.nt;
     auto diag = [&](int J) -> int {
@@ -263,7 +265,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
     auto panel = [&](int J) -> int {
         {
             PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
-            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, ctx->stream));
+            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, 0, ctx->stream));
         }
         PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
         GP_CUDA(ctx, gp::launch_gemm_panel(mb, J, ctx->stream));
@@ -278,7 +280,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
         if (rc) return rc;
         {
             PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
-            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.s, ctx->stream));
+            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.s, 1, ctx->stream));
         }
         if (mb.fuse && J + 2 < nt) {
             // panel pair (J, J + 1): update column J + 1 from panel J, factor and
@@ -313,8 +315,9 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
 // Solves with refinement and the likelihood for the factored instances.
 int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* mu, double* sigma2,
                     double* logdet, int* status) {
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, 3 + 3 * ctx->opt.refine_iters);
-    GP_CUDA(ctx, gp::launch_df_forward(mb, 0, 1, ctx->stream));
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, (mb.fwd ? 2 : 3) + 3 * ctx->opt.refine_iters);
+    // with mb.fwd the factorisation has already done the first forward solve
+    if (!mb.fwd) GP_CUDA(ctx, gp::launch_df_forward(mb, 0, 1, ctx->stream));
     GP_CUDA(ctx, gp::launch_df_backward(mb, 0, -1, ctx->stream));
     for (int it = 0; it < ctx->opt.refine_iters; ++it) {
         GP_CUDA(ctx, gp::launch_df_residual(mb, ctx->stream));

@@ -109,6 +109,8 @@ struct MixedBatch {
     int* FE;                      // their row exponents: [row block][128]
     size_t pf_stride, fe_stride;
     int fuse;                     // 1: trailing updates of panel pairs fused (K = 256)
+    int fwd;                      // 1: the forward solve L [x_1 x_y] = [1 Y] runs inside the
+                                  // factorisation (diagonal blocks and panel slicing)
     float2* WT;                   // L_JJ^-1 per diagonal block, double-float tiles: [J][128 x 128]
     size_t wt_stride;
     size_t ps_stride, pe_stride, ws_stride, we_stride;
@@ -172,13 +174,14 @@ size_t predict_work_per_cta(int nt);
 int predict_points_per_cta();
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s);
-cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s);
+cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, int gemv, cudaStream_t s);
 cudaError_t launch_gemm_panel(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s);
+cudaError_t launch_rhs_init(const MixedBatch& b, cudaStream_t s);
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s);
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s);
 cudaError_t launch_grad(const Batch& b, double* Z, size_t zs, double* X, double* Ri, double* partial,

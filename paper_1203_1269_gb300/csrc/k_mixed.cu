@@ -461,6 +461,23 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             *reinterpret_cast<uint2*>(dst + off) = v;
         }
     }
+    if (b.fwd) {
+        // forward solve, block J: x_J = W (b_J - sum_{K<J} L_JK x_K), the sum
+        // already subtracted by the slicing of panels K < J; b_J in, x_J out
+        // (Z columns 0, 1)
+        float2* zJ = b.Z + (size_t)t * b.z_stride + (size_t)J * GP_NB;
+        const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
+        float2* zk = zJ + (size_t)k * b.nt * GP_NB;
+        double* bj = k ? rowtmp : col;
+        if (threadIdx.x < 2 * GP_NB) bj[r] = df_to_double(df_load(zk + r));
+        __syncthreads();
+        if (threadIdx.x < 2 * GP_NB) {
+            const double* w = P + prow(r);
+            double sum = 0.0;
+            for (int c = 0; c <= r; ++c) sum = fma(w[c], bj[c], sum);
+            df_store(zk + r, df_from_double(sum));
+        }
+    }
 }
 
 // Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x / 2, into row
@@ -484,14 +501,50 @@ __device__ __forceinline__ int exponent_of(float mx) {
     return E;
 }
 
-__global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns) {
+//
+// gemv (with b.fwd; the slicing of the solved panel for the update): the
+// forward solve's panel step b_I -= L_IJ x_J for this CTA's rows, two
+// right-hand sides, from the values already in registers.
+__device__ __forceinline__ void fwd_partials(const float2 (&v)[32], const dfl (*xs)[GP_NB], int q, int rl,
+                                             dfl (*red)[2][kSplitRows]) {
+    dfl p0 = {0.f, 0.f}, p1 = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const dfl l = {v[j].x, v[j].y};
+        p0 = df_fma(l, xs[0][32 * q + j], p0);
+        p1 = df_fma(l, xs[1][32 * q + j], p1);
+    }
+    red[q][0][rl] = p0;
+    red[q][1][rl] = p1;
+}
+
+// b_I[r] -= the four column parts' partial sums, in a fixed order (q < 2 take
+// one right-hand side each); after a barrier that follows fwd_partials
+__device__ __forceinline__ void fwd_apply(const MixedBatch& b, int t, int I, int r, int q, int rl,
+                                          const dfl (*red)[2][kSplitRows]) {
+    if (q < 2) {
+        float2* z = b.Z + (size_t)t * b.z_stride + (size_t)q * b.nt * GP_NB + (size_t)I * GP_NB + r;
+        const dfl sum = df_add(df_add(red[0][q][rl], red[1][q][rl]), df_add(red[2][q][rl], red[3][q][rl]));
+        df_store(z, df_sub(df_load(z), sum));
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns, int gemv) {
     __shared__ float pmax[4][kSplitRows];
+    __shared__ dfl xs[2][GP_NB];
+    __shared__ dfl red[4][2][kSplitRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     const int I = J + 1 + blockIdx.x / 2;
     const float2* src = df_tile(b, b.A, t, I, J);
     const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
     const int r = (blockIdx.x & 1) * kSplitRows + rl;
+    gemv = gemv && b.fwd;
+    if (gemv) {
+        // x_J of both right-hand sides (256 threads, 2 x 128 values)
+        const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
+        xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)J * GP_NB + c);
+    }
     float2 v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
@@ -500,6 +553,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
     for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fabsf(v[j].x));
     pmax[q][rl] = mx;
     __syncthreads();
+    if (gemv) fwd_partials(v, xs, q, rl, red);
     mx = fmaxf(fmaxf(pmax[0][rl], pmax[1][rl]), fmaxf(pmax[2][rl], pmax[3][rl]));
     const int E = exponent_of(mx);
     if (q == 0) pe_block(b, t, I)[r] = E;
@@ -541,6 +595,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
             *reinterpret_cast<uint4*>(chunk0 + (size_t)a * kChunks * kChunkBytes + off) = u;
         }
     }
+    if (gemv) {
+        __syncthreads();
+        fwd_apply(b, t, I, r, q, rl, red);
+    }
 }
 
 // Slices of two adjacent panels at once, for the fused (K = 256) trailing
@@ -552,11 +610,18 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
 // and the values are read again for slicing.
 __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int J) {
     __shared__ float pmax[4][kSplitRows];
+    __shared__ dfl xs[2][GP_NB];
+    __shared__ dfl red[4][2][kSplitRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     const int I = J + 2 + blockIdx.x / 2;
     const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
     const int r = (blockIdx.x & 1) * kSplitRows + rl;
+    if (b.fwd) {
+        // x_{J+1}: the panel J term was applied by k_split_panel
+        const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
+        xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)(J + 1) * GP_NB + c);
+    }
     const float2* src0 = df_tile(b, b.A, t, I, J);
     const float2* src1 = df_tile(b, b.A, t, I, J + 1);
     float mx = 0.f;
@@ -580,6 +645,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
         float2 v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
+        if (half == 1 && b.fwd) fwd_partials(v, xs, q, rl, red);
         uint8_t* chunk0 = reinterpret_cast<uint8_t*>(pf_block(b, t, I) + (size_t)(4 * half + q) * kChunkElems);
 #pragma unroll
         for (int pc = 0; pc < 4; ++pc) {
@@ -612,6 +678,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
                 *reinterpret_cast<uint4*>(chunk0 + (size_t)a * 2 * kChunks * kChunkBytes + off) = u;
             }
         }
+    }
+    if (b.fwd) {
+        __syncthreads();
+        fwd_apply(b, t, I, r, q, rl, red);
     }
 }
 
@@ -1367,6 +1437,17 @@ __device__ __forceinline__ void stage_tile(const float2* __restrict__ src, dfl* 
 
 // Forward substitution L z = rhs for two columns (c0, c0 + 1) in place.
 // init != 0: the right-hand sides are [1 Y] (zero on padded rows).
+// [1 Y] (zero on padded rows) into Z columns 0, 1: the right-hand sides of
+// the forward solve that the factorisation carries out block by block
+__global__ void k_rhs_init(MixedBatch b) {
+    const int t = blockIdx.y;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= b.nt * GP_NB) return;
+    const bool in = gi < b.n;
+    df_store(zcol(b, t, 0) + gi, dfl{in ? 1.f : 0.f, 0.f});
+    df_store(zcol(b, t, 1) + gi, in ? df_from_double(b.y[gi]) : dfl{0.f, 0.f});
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int c0, int init) {
     __shared__ dfl xj[2][GP_NB];
     __shared__ dfl part[4][2][GP_NB];
@@ -1706,10 +1787,10 @@ cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, cudaStream_t s) {
+cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, int gemv, cudaStream_t s) {
     const int m = b.nt - J - 1;
     if (m <= 0) return cudaSuccess;
-    k_split_panel<<<dim3(2 * m, b.count), kSplitThreads, 0, s>>>(b, J, ns);
+    k_split_panel<<<dim3(2 * m, b.count), kSplitThreads, 0, s>>>(b, J, ns, gemv);
     return cudaGetLastError();
 }
 
@@ -1849,6 +1930,12 @@ cudaError_t launch_gemm_update(const MixedBatch& b, int J, cudaStream_t s) {
             if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, 2 * tiles, b.s, s);
             return launch_update128(b, J, tiles, b.s, s, 0);
     }
+}
+
+cudaError_t launch_rhs_init(const MixedBatch& b, cudaStream_t s) {
+    const int npad = b.nt * GP_NB;
+    k_rhs_init<<<dim3((npad + 255) / 256, b.count), 256, 0, s>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s) {
