@@ -278,25 +278,37 @@ __device__ __forceinline__ void cut_slices(float xh, float xl, int s, float* m) 
 
 // ----------------------------------------------------------- kernels -------
 
-// Diagonal block of column J in IEEE double: L_JJ = chol(A_JJ), log-det,
+// Diagonal block of column J in double-float on the FP32 pipes (an FP64
+// instruction costs about 64 FP32 ones here): L_JJ = chol(A_JJ), log-det,
 // the reciprocal diagonal, and W = L_JJ^-1 with the slices of W's rows.
 // The block lives in shared memory as a packed lower triangle (row-major,
 // P[r(r+1)/2 + c]), 66 KB, so that three CTAs share an SM.
-//   factor:  right-looking by columns; column c is copied to a contiguous
-//            buffer after scaling so the rank-1 update reads it conflict-free;
-//   inverse: in place, row by row: row i of W needs row i of L and rows < i
-//            of W (already inverted), W_ij = -(1/L_ii) sum_{k=j}^{i-1} L_ik W_kj;
-//            four threads share each entry's sum.
+//
+// Factor and inverse run in one right-looking sweep over c = 0 .. 127.  At
+// step c, position (i, p) of the triangle holds, for rows i > c,
+//   p <  c:  acc_ip = sum_{k<c} L_ik W_kp   (the inverse's partial sums)
+//   p >= c:  a_ip, the Cholesky trailing matrix,
+// and row c holds acc_c. below the diagonal and a_cc on it.  Phase 1 (one
+// thread per row p) finishes column c of L (L_pc = a_pc / L_cc, written out)
+// and row c of W (W_cp = -acc_cp / L_cc, W_cc = 1 / L_cc), and builds
+//   V_p = W_cp (p <= c),   V_p = -L_pc (p > c).
+// Phase 2 applies one rank-1 step to every row i > c, a warp per row:
+//   X_ip += L_ic V_p for p <= i   (X_ic = L_ic V_c: the first term of acc_ic),
+// which is the Cholesky update a_ip -= L_ic L_pc for p > c and the inverse's
+// acc_ip += L_ic W_cp for p <= c.  The lane that finishes a_{c+1,c+1} takes
+// the next pivot: 1 / sqrt by a float seed and three Newton steps in double.
+// After step 127 the triangle holds W.
 constexpr int kDiagThreads = 512;
 constexpr int kPacked = GP_NB * (GP_NB + 1) / 2;
 
 __device__ __forceinline__ int prow(int r) { return r * (r + 1) / 2; }
 
 __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J) {
-    extern __shared__ double P[];          // kPacked doubles
-    __shared__ double col[GP_NB];
-    __shared__ double rowtmp[GP_NB];
-    __shared__ double dinv[GP_NB];         // 1 / L_cc, reused by the inverse and the solves
+    extern __shared__ dfl P[];             // kPacked double-float values
+    __shared__ dfl V[GP_NB];
+    __shared__ dfl dinv[GP_NB];            // 1 / L_cc
+    __shared__ double lcc[GP_NB];          // L_cc
+    __shared__ double bj[2][GP_NB];
     __shared__ double lsum[GP_NB / 32];
     __shared__ int failed;
     const int t = blockIdx.x;
@@ -304,66 +316,75 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     float2* T = df_tile(b, b.A, t, J, J);
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
         const int rr = q & 127, cc = q >> 7;
-        if (rr >= cc) {
-            const float2 v = T[q];
-            P[prow(rr) + cc] = (double)v.x + (double)v.y;
-        }
+        if (rr >= cc) P[prow(rr) + cc] = df_load(T + q);
     }
     if (threadIdx.x == 0) failed = -1;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kDiagThreads / 32;
-    // FP64 instructions are scarce on this GPU (2 DFMA per clock per SM, a
-    // warp instruction takes 16 clocks whatever its active lanes), so the
-    // trailing-triangle elements of each column are dealt to all threads
-    // evenly, and the square root and reciprocal of the next pivot are taken
-    // by the thread that finishes that pivot's update, while the others work
-    // on; the logarithms of the pivots wait for the reduction below.
-    // The pivot chain is the critical path: 1 / sqrt(piv) by a float seed and
-    // three Newton-Raphson steps y <- y (3/2 - piv y^2 / 2) in double (22, 44,
-    // then rounding-limited correct bits), sqrt(piv) = piv y: ten dependent
-    // FP64 instructions, within a few ulps; pivots outside the float range
-    // take the library square root and division.
-    auto take_pivot = [&](int c, double piv) {
+    auto take_pivot = [&](int c, dfl a) {
+        const double piv = df_to_double(a);
+        double y, l;
         if (!(piv > 0.0) || !isfinite(piv)) {
             failed = c;
+            y = 1.0;
+            l = 1.0;
         } else if (piv > 1e-30 && piv < 1e30) {
-            double y = (double)rsqrtf((float)piv);
+            y = (double)rsqrtf((float)piv);
             const double h = -0.5 * piv;
 #pragma unroll
             for (int it = 0; it < 3; ++it) y = y * fma(h, y * y, 1.5);
-            P[prow(c) + c] = piv * y;
-            dinv[c] = y;
+            l = piv * y;
         } else {
-            const double l = sqrt(piv);
-            P[prow(c) + c] = l;
-            dinv[c] = 1.0 / l;
+            l = sqrt(piv);
+            y = 1.0 / l;
         }
+        lcc[c] = l;
+        dinv[c] = df_from_double(y);
     };
     if (threadIdx.x == 0) take_pivot(0, P[0]);
     __syncthreads();
-    for (int c = 0; c < GP_NB && failed < 0; ++c) {
-        const double ip = dinv[c];
-        if (threadIdx.x > c && threadIdx.x < GP_NB) {
-            const double v = P[prow(threadIdx.x) + c] * ip;
-            P[prow(threadIdx.x) + c] = v;
-            col[threadIdx.x] = v;
+    for (int c = 0; c < GP_NB; ++c) {
+        if (failed >= 0) break;            // read after a barrier: uniform
+        // phase 1: column c of L (out), row c of W, V
+        if (threadIdx.x < GP_NB) {
+            const int p = threadIdx.x;
+            const dfl di = dinv[c];
+            if (p < c) {
+                const dfl w = df_neg(df_mul(di, P[prow(c) + p]));
+                P[prow(c) + p] = w;
+                V[p] = w;
+            } else if (p == c) {
+                df_store(T + (size_t)c * GP_NB + c, df_from_double(lcc[c]));
+                P[prow(c) + c] = di;
+                V[c] = di;
+            } else {
+                const dfl l = df_mul(P[prow(p) + c], di);
+                df_store(T + (size_t)c * GP_NB + p, l);
+                V[p] = df_neg(l);
+            }
         }
         __syncthreads();
-        // A(r, k) -= L(r, c) L(k, c) for c < k <= r, element e of the trailing
-        // triangle at (r, k) = (c + 1 + u, c + 1 + v); e = 0 is the next pivot
-        const int m = GP_NB - 1 - c;
-        const int nel = m * (m + 1) / 2;
-        for (int e = threadIdx.x; e < nel; e += kDiagThreads) {
-            int u, v;
-            tri_decode(e, u, v);
-            const int r = c + 1 + u, k = c + 1 + v;
-            double* a = P + prow(r) + k;
-            const double nv = fma(-col[r], col[k], *a);
-            if (e == 0)
-                take_pivot(c + 1, nv);
-            else
-                *a = nv;
+        if (c + 1 == GP_NB) break;
+        // phase 2: rows i > c, X_ip += L_ic V_p (p <= i), a warp per row
+        dfl vl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vl[j] = V[lane + 32 * j];
+        for (int i = c + 1 + warp; i < GP_NB; i += kWarps) {
+            const dfl m = df_neg(V[i]);    // L_ic
+            dfl* row = P + prow(i);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = lane + 32 * j;
+                if (p <= i) {
+                    const dfl x0 = (p == c) ? dfl{0.f, 0.f} : row[p];
+                    const dfl x = df_fma(m, vl[j], x0);
+                    if (p == c + 1 && i == c + 1)
+                        take_pivot(c + 1, x);
+                    else
+                        row[p] = x;
+                }
+            }
         }
         __syncthreads();
     }
@@ -374,23 +395,14 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         }
         return;
     }
-    // L out (double-float, lower triangle), log-det, reciprocal diagonal
-    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
-        const int rr = q & 127, cc = q >> 7;
-        if (rr >= cc) {
-            const dfl d = df_from_double(P[prow(rr) + cc]);
-            T[q] = make_float2(d.hi, d.lo);
-        }
-    }
     // log-det: sum of log L_cc over the block in a fixed order (warp trees,
-    // then the four warp sums in turn)
+    // then the four warp sums in turn); reciprocal diagonal out
     if (threadIdx.x < GP_NB) {
-        double v = log(P[prow(threadIdx.x) + threadIdx.x]);
+        double v = log(lcc[threadIdx.x]);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) lsum[warp] = v;
         float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
-        const dfl d = df_from_double(dinv[threadIdx.x]);
-        rinv[threadIdx.x] = make_float2(d.hi, d.lo);
+        df_store(rinv + threadIdx.x, dinv[threadIdx.x]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -398,45 +410,22 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         for (int w = 0; w < GP_NB / 32; ++w) ld += lsum[w];
         b.st[t].logdet += 2.0 * ld;
     }
-    // W = L^-1 in place, row by row; thread (j, part) sums k = j + part, j + part + 4, ...
-    const int j = threadIdx.x >> 2, part = threadIdx.x & 3;
-    for (int i = 0; i < GP_NB; ++i) {
-        const double* Li = P + prow(i);
-        double sum = 0.0;
-        if (j < i)
-            for (int k = j + part; k < i; k += 4) sum = fma(Li[k], P[prow(k) + j], sum);
-        // warps whose rows j are all past i have nothing to add (warp-uniform)
-        if (8 * warp <= i) {
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            const double rinv_i = dinv[i];
-            if (part == 0 && j <= i) rowtmp[j] = (j == i) ? rinv_i : -rinv_i * sum;
-        }
-        __syncthreads();
-        if (threadIdx.x <= i) P[prow(i) + threadIdx.x] = rowtmp[threadIdx.x];
-        __syncthreads();
-    }
     // W as a double-float tile (column-major, zeros above the diagonal) for
     // the diagonal-block products of the solves
     {
         float2* Wt = b.WT + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
         for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
             const int rr = q & 127, cc = q >> 7;
-            float2 v = make_float2(0.f, 0.f);
-            if (rr >= cc) {
-                const dfl d = df_from_double(P[prow(rr) + cc]);
-                v = make_float2(d.hi, d.lo);
-            }
-            Wt[q] = v;
+            Wt[q] = (rr >= cc) ? make_float2(P[prow(rr) + cc].hi, P[prow(rr) + cc].lo) : make_float2(0.f, 0.f);
         }
     }
     // row c of W: exponent and slices; one warp per row
     __nv_bfloat16* WS = b.WS + (size_t)t * b.ws_stride;
     int* WE = b.WE + (size_t)t * b.we_stride;
     for (int c = warp; c < GP_NB; c += kWarps) {
-        const double* w = P + prow(c);
+        const dfl* w = P + prow(c);
         double mx = 0.0;
-        for (int k = lane; k <= c; k += 32) mx = fmax(mx, fabs(w[k]));
+        for (int k = lane; k <= c; k += 32) mx = fmax(mx, fabs(df_to_double(w[k])));
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         int E = 0;
         if (mx > 0.0) frexp(mx, &E);
@@ -446,7 +435,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         float m[4][GP_MAX_SLICES];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const double x = (k0 + e <= c) ? ldexp(w[k0 + e], 7 - E) : 0.0;
+            const double x = (k0 + e <= c) ? ldexp(df_to_double(w[k0 + e]), 7 - E) : 0.0;
             const dfl xd = df_from_double(x);
             cut_slices(xd.hi, xd.lo, b.ps, m[e]);
         }
@@ -468,13 +457,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         float2* zJ = b.Z + (size_t)t * b.z_stride + (size_t)J * GP_NB;
         const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
         float2* zk = zJ + (size_t)k * b.nt * GP_NB;
-        double* bj = k ? rowtmp : col;
-        if (threadIdx.x < 2 * GP_NB) bj[r] = df_to_double(df_load(zk + r));
+        if (threadIdx.x < 2 * GP_NB) bj[k][r] = df_to_double(df_load(zk + r));
         __syncthreads();
         if (threadIdx.x < 2 * GP_NB) {
-            const double* w = P + prow(r);
+            const dfl* w = P + prow(r);
             double sum = 0.0;
-            for (int c = 0; c <= r; ++c) sum = fma(w[c], bj[c], sum);
+            for (int c = 0; c <= r; ++c) sum = fma(df_to_double(w[c]), bj[k][c], sum);
             df_store(zk + r, df_from_double(sum));
         }
     }
@@ -1779,7 +1767,7 @@ __global__ void k_df_to_double(const float2* src, double* dst, size_t count) {
 }  // namespace
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s) {
-    const size_t smem = (size_t)kPacked * sizeof(double);
+    const size_t smem = (size_t)kPacked * sizeof(dfl);
     static std::atomic<size_t> attr[kMaxDevices];
     cudaError_t e = raise_smem_limit(k_diag_mixed, smem, attr);
     if (e != cudaSuccess) return e;
