@@ -278,6 +278,17 @@ __device__ __forceinline__ void cut_slices(float xh, float xl, int s, float* m) 
 
 // ----------------------------------------------------------- kernels -------
 
+__device__ __forceinline__ int exponent_of(float mx) {
+    // mx = f 2^E with f in [0.5, 1); 0 for mx == 0
+    if (mx == 0.f) return 0;
+    const int bits = __float_as_int(mx);
+    const int be = (bits >> 23) & 0xff;
+    if (be != 0) return be - 126;
+    int E;
+    frexpf(mx, &E);
+    return E;
+}
+
 // Diagonal block of column J in double-float on the FP32 pipes (an FP64
 // instruction costs about 64 FP32 ones here): L_JJ = chol(A_JJ), log-det,
 // the reciprocal diagonal, and W = L_JJ^-1 with the slices of W's rows.
@@ -308,7 +319,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     __shared__ dfl V[GP_NB];
     __shared__ dfl dinv[GP_NB];            // 1 / L_cc
     __shared__ double lcc[GP_NB];          // L_cc
-    __shared__ double bj[2][GP_NB];
+    __shared__ dfl bj[2][GP_NB];
+    __shared__ dfl xpart[2][GP_NB];
     __shared__ double lsum[GP_NB / 32];
     __shared__ int failed;
     const int t = blockIdx.x;
@@ -419,25 +431,30 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             Wt[q] = (rr >= cc) ? make_float2(P[prow(rr) + cc].hi, P[prow(rr) + cc].lo) : make_float2(0.f, 0.f);
         }
     }
-    // row c of W: exponent and slices; one warp per row
+    // row c of W: exponent (of the largest high word, as the panel slicing
+    // takes it) and slices; one warp per row, all on the FP32 pipes
     __nv_bfloat16* WS = b.WS + (size_t)t * b.ws_stride;
     int* WE = b.WE + (size_t)t * b.we_stride;
     for (int c = warp; c < GP_NB; c += kWarps) {
         const dfl* w = P + prow(c);
-        double mx = 0.0;
-        for (int k = lane; k <= c; k += 32) mx = fmax(mx, fabs(df_to_double(w[k])));
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        int E = 0;
-        if (mx > 0.0) frexp(mx, &E);
+        float mx = 0.f;
+        for (int k = lane; k <= c; k += 32) mx = fmaxf(mx, fabsf(w[k].hi));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int E = exponent_of(mx);
         if (lane == 0) WE[c] = E;
+        // x 2^(7 - E) exactly (two factors when 7 - E leaves the float range)
+        const int e2 = 7 - E;
+        const int ea = e2 > 127 ? 127 : (e2 < -126 ? -126 : e2);
+        const int eb = e2 - ea;
+        const float sa = __int_as_float((ea + 127) << 23);
+        const float sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
         // lane handles columns 4*lane .. 4*lane+3 (half of one 16-byte piece)
         const int k0 = 4 * lane;
         float m[4][GP_MAX_SLICES];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const double x = (k0 + e <= c) ? ldexp(df_to_double(w[k0 + e]), 7 - E) : 0.0;
-            const dfl xd = df_from_double(x);
-            cut_slices(xd.hi, xd.lo, b.ps, m[e]);
+            const dfl x = (k0 + e <= c) ? w[k0 + e] : dfl{0.f, 0.f};
+            cut_slices(__fmul_rn(__fmul_rn(x.hi, sa), sb), __fmul_rn(__fmul_rn(x.lo, sa), sb), b.ps, m[e]);
         }
         const uint32_t off = image_piece(c, k0 & ~7) + ((k0 & 4) ? 8u : 0u);
 #pragma unroll
@@ -453,114 +470,64 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     if (b.fwd) {
         // forward solve, block J: x_J = W (b_J - sum_{K<J} L_JK x_K), the sum
         // already subtracted by the slicing of panels K < J; b_J in, x_J out
-        // (Z columns 0, 1)
+        // (Z columns 0, 1), in double-float: thread (k, r, h) sums the
+        // columns c = h, h + 2, ... of row r, then the two halves add in a
+        // fixed order
         float2* zJ = b.Z + (size_t)t * b.z_stride + (size_t)J * GP_NB;
-        const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
+        const int k = (threadIdx.x >> 7) & 1, r = threadIdx.x & 127, h = threadIdx.x >> 8;
         float2* zk = zJ + (size_t)k * b.nt * GP_NB;
-        if (threadIdx.x < 2 * GP_NB) bj[k][r] = df_to_double(df_load(zk + r));
+        if (threadIdx.x < 2 * GP_NB) bj[k][r] = df_load(zk + r);
         __syncthreads();
-        if (threadIdx.x < 2 * GP_NB) {
-            const dfl* w = P + prow(r);
-            double sum = 0.0;
-            for (int c = 0; c <= r; ++c) sum = fma(df_to_double(w[c]), bj[k][c], sum);
-            df_store(zk + r, df_from_double(sum));
-        }
+        const dfl* w = P + prow(r);
+        dfl sum = {0.f, 0.f};
+        for (int c = h; c <= r; c += 2) sum = df_fma(w[c], bj[k][c], sum);
+        if (h == 1) xpart[k][r] = sum;
+        __syncthreads();
+        if (h == 0) df_store(zk + r, df_add(sum, xpart[k][r]));
     }
 }
 
 // Slices of the panel tiles (I, J), I = J + 1 + blockIdx.x / 2, into row
-// block I of PS.  A CTA of 256 threads takes one half (64 rows) of a tile,
-// so that two CTAs share an SM and one's loads overlap the other's slicing:
-// thread (r, q) owns row r's columns 32q .. 32q + 31, which form exactly
-// image chunk q, so it loads its values once (coalesced along r) and writes
-// only its own 16-byte pieces.  The four owners of a row agree on the row's
-// exponent through shared memory.
-constexpr int kSplitThreads = 256;
-constexpr int kSplitRows = kSplitThreads / 4;   // rows of a tile per CTA
+// block I of PS.  A CTA of 512 threads takes one half (64 rows) of a tile:
+// thread (r, q, u) owns row r's columns 32q + 16u .. 32q + 16u + 15, two of
+// the 16-byte pieces of image chunk q, so it loads its values once
+// (coalesced along r) and writes only its own pieces; 16 values per thread
+// leave registers for four CTAs per SM, whose loads overlap each other's
+// slicing.  The eight owners of a row agree on the row's exponent through
+// shared memory.
+constexpr int kSplitThreads = 512;
+constexpr int kSplitParts = 8;                          // column parts of a row
+constexpr int kSplitRows = kSplitThreads / kSplitParts; // rows of a tile per CTA
+constexpr int kSplitCols = GP_NB / kSplitParts;         // 16 columns per thread
+// k_split_fused: 8 columns of each of two panels per thread, a quarter tile
+constexpr int kFusedParts = 16;
+constexpr int kFusedRows = kSplitThreads / kFusedParts;
+constexpr int kFusedCols = GP_NB / kFusedParts;
 
-__device__ __forceinline__ int exponent_of(float mx) {
-    // mx = f 2^E with f in [0.5, 1); 0 for mx == 0
-    if (mx == 0.f) return 0;
-    const int bits = __float_as_int(mx);
-    const int be = (bits >> 23) & 0xff;
-    if (be != 0) return be - 126;
-    int E;
-    frexpf(mx, &E);
-    return E;
-}
-
-//
-// gemv (with b.fwd; the slicing of the solved panel for the update): the
-// forward solve's panel step b_I -= L_IJ x_J for this CTA's rows, two
-// right-hand sides, from the values already in registers.
-__device__ __forceinline__ void fwd_partials(const float2 (&v)[32], const dfl (*xs)[GP_NB], int q, int rl,
-                                             dfl (*red)[2][kSplitRows]) {
-    dfl p0 = {0.f, 0.f}, p1 = {0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const dfl l = {v[j].x, v[j].y};
-        p0 = df_fma(l, xs[0][32 * q + j], p0);
-        p1 = df_fma(l, xs[1][32 * q + j], p1);
-    }
-    red[q][0][rl] = p0;
-    red[q][1][rl] = p1;
-}
-
-// b_I[r] -= the four column parts' partial sums, in a fixed order (q < 2 take
-// one right-hand side each); after a barrier that follows fwd_partials
-__device__ __forceinline__ void fwd_apply(const MixedBatch& b, int t, int I, int r, int q, int rl,
-                                          const dfl (*red)[2][kSplitRows]) {
-    if (q < 2) {
-        float2* z = b.Z + (size_t)t * b.z_stride + (size_t)q * b.nt * GP_NB + (size_t)I * GP_NB + r;
-        const dfl sum = df_add(df_add(red[0][q][rl], red[1][q][rl]), df_add(red[2][q][rl], red[3][q][rl]));
-        df_store(z, df_sub(df_load(z), sum));
-    }
-}
-
-__global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns, int gemv) {
-    __shared__ float pmax[4][kSplitRows];
-    __shared__ dfl xs[2][GP_NB];
-    __shared__ dfl red[4][2][kSplitRows];
-    const int t = blockIdx.y;
-    if (b.st[t].status != GP_OK) return;
-    const int I = J + 1 + blockIdx.x / 2;
-    const float2* src = df_tile(b, b.A, t, I, J);
-    const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
-    const int r = (blockIdx.x & 1) * kSplitRows + rl;
-    gemv = gemv && b.fwd;
-    if (gemv) {
-        // x_J of both right-hand sides (256 threads, 2 x 128 values)
-        const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
-        xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)J * GP_NB + c);
-    }
-    float2 v[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
-    float mx = 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fabsf(v[j].x));
-    pmax[q][rl] = mx;
-    __syncthreads();
-    if (gemv) fwd_partials(v, xs, q, rl, red);
-    mx = fmaxf(fmaxf(pmax[0][rl], pmax[1][rl]), fmaxf(pmax[2][rl], pmax[3][rl]));
-    const int E = exponent_of(mx);
-    if (q == 0) pe_block(b, t, I)[r] = E;
-    // scale by 2^(7 - E) exactly (two factors when 7 - E leaves the float range)
+// 2^(7 - E) as two exact float factors (7 - E may leave the float range)
+__device__ __forceinline__ void slice_scale(int E, float& sa, float& sb) {
     const int e2 = 7 - E;
     const int ea = e2 > 127 ? 127 : (e2 < -126 ? -126 : e2);
     const int eb = e2 - ea;
-    const float sa = __int_as_float((ea + 127) << 23);
-    const float sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
-    uint8_t* chunk0 = reinterpret_cast<uint8_t*>(ps_block(b, t, I) + (size_t)q * kChunkElems);
+    sa = __int_as_float((ea + 127) << 23);
+    sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
+}
+
+// Slices of one thread's NC values of row r (columns k0 .. k0 + NC - 1 of
+// image chunk `chunk0`, k0 = 0, 8, 16 or 24; slice a at chunk0 + a *
+// slice_bytes): NC / 8 pieces of 8.
+template <int NC>
+__device__ __forceinline__ void slice_pieces(const float2 (&v)[NC], float sa, float sb, int r, int k0,
+                                             int ns, uint8_t* chunk0, size_t slice_bytes) {
 #pragma unroll
-    for (int pc = 0; pc < 4; ++pc) {
+    for (int h = 0; h < NC / 8; ++h) {
         float xh[8], xl[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            xh[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].x, sa), sb);
-            xl[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].y, sa), sb);
+            xh[e] = __fmul_rn(__fmul_rn(v[8 * h + e].x, sa), sb);
+            xl[e] = __fmul_rn(__fmul_rn(v[8 * h + e].y, sa), sb);
         }
-        const uint32_t off = image_piece(r, 8 * pc);
+        const uint32_t off = image_piece(r, k0 + 8 * h);
         float w = 1.f;
 #pragma unroll
         for (int a = 0; a < GP_MAX_SLICES; ++a) {
@@ -575,101 +542,144 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
                 xl[e] = __fmul_rn(xl[e], 256.f);
             }
             w = __fmul_rn(w, 0.00390625f);
-            uint4 u;
-            u.x = pack_bf16x2(m[0], m[1]);
-            u.y = pack_bf16x2(m[2], m[3]);
-            u.z = pack_bf16x2(m[4], m[5]);
-            u.w = pack_bf16x2(m[6], m[7]);
-            *reinterpret_cast<uint4*>(chunk0 + (size_t)a * kChunks * kChunkBytes + off) = u;
+            uint4 pk;
+            pk.x = pack_bf16x2(m[0], m[1]);
+            pk.y = pack_bf16x2(m[2], m[3]);
+            pk.z = pack_bf16x2(m[4], m[5]);
+            pk.w = pack_bf16x2(m[6], m[7]);
+            *reinterpret_cast<uint4*>(chunk0 + (size_t)a * slice_bytes + off) = pk;
         }
     }
+}
+
+// gemv (with b.fwd; the slicing of the solved panel for the update): the
+// forward solve's panel step b_I -= L_IJ x_J for this CTA's rows, two
+// right-hand sides, from the values already in registers.  c0: the first of
+// the thread's 16 columns.
+template <int NC, int ROWS>
+__device__ __forceinline__ void fwd_partials(const float2 (&v)[NC], const dfl (*xs)[GP_NB], int c0,
+                                             int part, int rl, dfl (*red)[2][ROWS]) {
+    dfl p0 = {0.f, 0.f}, p1 = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const dfl l = {v[j].x, v[j].y};
+        p0 = df_fma(l, xs[0][c0 + j], p0);
+        p1 = df_fma(l, xs[1][c0 + j], p1);
+    }
+    red[part][0][rl] = p0;
+    red[part][1][rl] = p1;
+}
+
+// b_I[r] -= the PARTS column parts' partial sums, pairwise in a fixed order
+// (parts 0 and 1 take one right-hand side each); after a barrier that
+// follows fwd_partials
+template <int PARTS, int ROWS>
+__device__ __forceinline__ void fwd_apply(const MixedBatch& b, int t, int I, int r, int part, int rl,
+                                          const dfl (*red)[2][ROWS]) {
+    if (part < 2) {
+        const int k = part;
+        dfl acc[PARTS];
+#pragma unroll
+        for (int i = 0; i < PARTS; ++i) acc[i] = red[i][k][rl];
+#pragma unroll
+        for (int w = 1; w < PARTS; w *= 2)
+#pragma unroll
+            for (int i = 0; i + w < PARTS; i += 2 * w) acc[i] = df_add(acc[i], acc[i + w]);
+        float2* z = b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)I * GP_NB + r;
+        df_store(z, df_sub(df_load(z), acc[0]));
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int J, int ns, int gemv) {
+    __shared__ float pmax[kSplitParts][kSplitRows];
+    __shared__ dfl xs[2][GP_NB];
+    __shared__ dfl red[kSplitParts][2][kSplitRows];
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int I = J + 1 + blockIdx.x / 2;
+    const float2* src = df_tile(b, b.A, t, I, J);
+    const int rl = threadIdx.x % kSplitRows, part = threadIdx.x / kSplitRows;
+    const int q = part >> 1, u = part & 1, c0 = kSplitCols * part;
+    const int r = (blockIdx.x & 1) * kSplitRows + rl;
+    gemv = gemv && b.fwd;
+    if (gemv && threadIdx.x < 2 * GP_NB) {
+        // x_J of both right-hand sides
+        const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
+        xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)J * GP_NB + c);
+    }
+    float2 v[kSplitCols];
+#pragma unroll
+    for (int j = 0; j < kSplitCols; ++j) v[j] = src[(size_t)(c0 + j) * GP_NB + r];
+    float mx = 0.f;
+#pragma unroll
+    for (int j = 0; j < kSplitCols; ++j) mx = fmaxf(mx, fabsf(v[j].x));
+    pmax[part][rl] = mx;
+    __syncthreads();
+    if (gemv) fwd_partials(v, xs, c0, part, rl, red);
+#pragma unroll
+    for (int k = 0; k < kSplitParts; ++k) mx = fmaxf(mx, pmax[k][rl]);
+    const int E = exponent_of(mx);
+    if (part == 0) pe_block(b, t, I)[r] = E;
+    float sa, sb;
+    slice_scale(E, sa, sb);
+    uint8_t* chunk0 = reinterpret_cast<uint8_t*>(ps_block(b, t, I) + (size_t)q * kChunkElems);
+    slice_pieces(v, sa, sb, r, 16 * u, ns, chunk0, (size_t)kChunks * kChunkBytes);
     if (gemv) {
         __syncthreads();
-        fwd_apply(b, t, I, r, q, rl, red);
+        fwd_apply<kSplitParts>(b, t, I, r, part, rl, red);
     }
 }
 
 // Slices of two adjacent panels at once, for the fused (K = 256) trailing
-// update: row r of row block I = J + 2 + blockIdx.x / 2 (one half of its rows
-// per CTA, as in k_split_panel) spans tiles (I, J) and
+// update: row r of row block I = J + 2 + blockIdx.x / 4 spans tiles (I, J) and
 // (I, J + 1) and gets one exponent for all 256 columns, so the products of
-// both panels accumulate in the same tensor-memory groups.  Thread (r, q)
-// owns image chunk q of each panel; the row maximum is taken in a first pass
-// and the values are read again for slicing.
+// both panels accumulate in the same tensor-memory groups.  A CTA takes a
+// quarter tile (32 rows); thread (r, part) owns the same 16-byte piece (8
+// columns) of each panel and keeps both panels' values in registers for the
+// row maximum and the slicing.
 __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int J) {
-    __shared__ float pmax[4][kSplitRows];
+    __shared__ float pmax[kFusedParts][kFusedRows];
     __shared__ dfl xs[2][GP_NB];
-    __shared__ dfl red[4][2][kSplitRows];
+    __shared__ dfl red[kFusedParts][2][kFusedRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
-    const int I = J + 2 + blockIdx.x / 2;
-    const int rl = threadIdx.x % kSplitRows, q = threadIdx.x / kSplitRows;
-    const int r = (blockIdx.x & 1) * kSplitRows + rl;
-    if (b.fwd) {
+    const int I = J + 2 + blockIdx.x / 4;
+    const int rl = threadIdx.x % kFusedRows, part = threadIdx.x / kFusedRows;
+    const int q = part >> 2, c0 = kFusedCols * part;
+    const int r = (blockIdx.x & 3) * kFusedRows + rl;
+    if (b.fwd && threadIdx.x < 2 * GP_NB) {
         // x_{J+1}: the panel J term was applied by k_split_panel
         const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
         xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)(J + 1) * GP_NB + c);
     }
     const float2* src0 = df_tile(b, b.A, t, I, J);
     const float2* src1 = df_tile(b, b.A, t, I, J + 1);
+    // both panels' values stay in registers: each tile is read once
+    float2 v0[kFusedCols], v1[kFusedCols];
+#pragma unroll
+    for (int j = 0; j < kFusedCols; ++j) {
+        v0[j] = src0[(size_t)(c0 + j) * GP_NB + r];
+        v1[j] = src1[(size_t)(c0 + j) * GP_NB + r];
+    }
     float mx = 0.f;
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) {
-        mx = fmaxf(mx, fabsf(src0[(32 * q + j) * GP_NB + r].x));
-        mx = fmaxf(mx, fabsf(src1[(32 * q + j) * GP_NB + r].x));
-    }
-    pmax[q][rl] = mx;
+#pragma unroll
+    for (int j = 0; j < kFusedCols; ++j) mx = fmaxf(mx, fmaxf(fabsf(v0[j].x), fabsf(v1[j].x)));
+    pmax[part][rl] = mx;
     __syncthreads();
-    mx = fmaxf(fmaxf(pmax[0][rl], pmax[1][rl]), fmaxf(pmax[2][rl], pmax[3][rl]));
+    if (b.fwd) fwd_partials(v1, xs, c0, part, rl, red);
+#pragma unroll
+    for (int k = 0; k < kFusedParts; ++k) mx = fmaxf(mx, pmax[k][rl]);
     const int E = exponent_of(mx);
-    if (q == 0) fe_block(b, t, I)[r] = E;
-    const int e2 = 7 - E;
-    const int ea = e2 > 127 ? 127 : (e2 < -126 ? -126 : e2);
-    const int eb = e2 - ea;
-    const float sa = __int_as_float((ea + 127) << 23);
-    const float sb = (eb == 0) ? 1.f : __int_as_float(((eb > 127 ? 127 : (eb < -126 ? -126 : eb)) + 127) << 23);
-    for (int half = 0; half < 2; ++half) {
-        const float2* src = half ? src1 : src0;
-        float2 v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = src[(32 * q + j) * GP_NB + r];
-        if (half == 1 && b.fwd) fwd_partials(v, xs, q, rl, red);
-        uint8_t* chunk0 = reinterpret_cast<uint8_t*>(pf_block(b, t, I) + (size_t)(4 * half + q) * kChunkElems);
-#pragma unroll
-        for (int pc = 0; pc < 4; ++pc) {
-            float xh[8], xl[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                xh[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].x, sa), sb);
-                xl[e] = __fmul_rn(__fmul_rn(v[8 * pc + e].y, sa), sb);
-            }
-            const uint32_t off = image_piece(r, 8 * pc);
-            float w = 1.f;
-#pragma unroll
-            for (int a = 0; a < GP_MAX_SLICES; ++a) {
-                if (a >= b.s) break;
-                float m[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float qv = rintf(xh[e]);
-                    m[e] = __fmul_rn(qv, w);
-                    two_sum(__fsub_rn(xh[e], qv), xl[e], xh[e], xl[e]);
-                    xh[e] = __fmul_rn(xh[e], 256.f);
-                    xl[e] = __fmul_rn(xl[e], 256.f);
-                }
-                w = __fmul_rn(w, 0.00390625f);
-                uint4 u;
-                u.x = pack_bf16x2(m[0], m[1]);
-                u.y = pack_bf16x2(m[2], m[3]);
-                u.z = pack_bf16x2(m[4], m[5]);
-                u.w = pack_bf16x2(m[6], m[7]);
-                *reinterpret_cast<uint4*>(chunk0 + (size_t)a * 2 * kChunks * kChunkBytes + off) = u;
-            }
-        }
-    }
+    if (part == 0) fe_block(b, t, I)[r] = E;
+    float sa, sb;
+    slice_scale(E, sa, sb);
+    const size_t slice_bytes = (size_t)2 * kChunks * kChunkBytes;
+    uint8_t* base = reinterpret_cast<uint8_t*>(pf_block(b, t, I));
+    slice_pieces(v0, sa, sb, r, c0 & 31, b.s, base + (size_t)q * kChunkElems * 2, slice_bytes);
+    slice_pieces(v1, sa, sb, r, c0 & 31, b.s, base + (size_t)(4 + q) * kChunkElems * 2, slice_bytes);
     if (b.fwd) {
         __syncthreads();
-        fwd_apply(b, t, I, r, q, rl, red);
+        fwd_apply<kFusedParts>(b, t, I, r, part, rl, red);
     }
 }
 
@@ -1903,7 +1913,7 @@ cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s)
 cudaError_t launch_split_fused(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 2;
     if (m <= 0) return cudaSuccess;
-    k_split_fused<<<dim3(2 * m, b.count), kSplitThreads, 0, s>>>(b, J);
+    k_split_fused<<<dim3(4 * m, b.count), kSplitThreads, 0, s>>>(b, J);
     return cudaGetLastError();
 }
 
