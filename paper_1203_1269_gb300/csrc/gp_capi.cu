@@ -178,7 +178,7 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
 
 // Bytes of workspace per instance of the split-precision path.
 struct MixedSizes {
-    size_t A, PS, PE, WS, WE, PF, FE, WT, Z, st, per;
+    size_t A, PS, PE, WS, WE, PF, FE, WT, Z, RP, st, per;   // WT also sizes WR
 };
 
 MixedSizes mixed_sizes(int n, int s) {
@@ -195,8 +195,9 @@ MixedSizes mixed_sizes(int n, int s) {
     z.FE = align256((size_t)nt * GP_NB * sizeof(int));
     z.WT = align256((size_t)nt * GP_TILE_ELEMS * sizeof(float2));
     z.Z = align256((size_t)gp::kZCols * nt * GP_NB * sizeof(float2));
+    z.RP = align256((size_t)gp::packed_tiles(nt) * gp::kRpTile * sizeof(float2));
     z.st = align256(sizeof(gp::InstState));
-    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + z.WT + z.Z + z.st;
+    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + 2 * z.WT + z.Z + z.RP + z.st;
     return z;
 }
 
@@ -214,7 +215,9 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.PF = (__nv_bfloat16*)c; c += z.PF * Tc;
     mb.FE = (int*)c; c += z.FE * Tc;
     mb.WT = (float2*)c; c += z.WT * Tc;
+    mb.WR = (float2*)c; c += z.WT * Tc;
     mb.Z = (float2*)c; c += z.Z * Tc;
+    mb.RP = (float2*)c; c += z.RP * Tc;
     mb.st = (gp::InstState*)c; c += z.st * Tc;
     mb.err = (int*)c;
     mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = slices;
@@ -235,6 +238,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.fuse = ctx->opt.fuse_panels;
     mb.fwd = y != nullptr;
     mb.z_stride = z.Z / sizeof(float2);
+    mb.rp_stride = z.RP / sizeof(float2);
     mb.y = y;
     return mb;
 }
@@ -315,7 +319,8 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
 // Solves with refinement and the likelihood for the factored instances.
 int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* mu, double* sigma2,
                     double* logdet, int* status) {
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, (mb.fwd ? 2 : 3) + 3 * ctx->opt.refine_iters);
+    const int sp = gp::subst_launches(mb.nt);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, (mb.fwd ? 0 : 1 + sp) + sp + ctx->opt.refine_iters * (2 + 2 * sp) + 1);
     // with mb.fwd the factorisation has already done the first forward solve
     if (!mb.fwd) GP_CUDA(ctx, gp::launch_df_forward(mb, 0, 1, ctx->stream));
     GP_CUDA(ctx, gp::launch_df_backward(mb, 0, -1, ctx->stream));
@@ -332,7 +337,8 @@ int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* 
 // then Hager's iteration, all instances in step, at most five rounds.
 int run_mixed_cond(gp_ctx* ctx, const gp::MixedBatch& mb, double* cond) {
     constexpr int kRounds = 5;
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, 3 + kRounds * 3 + (kRounds - 1) * 3);
+    const int sp = gp::subst_launches(mb.nt);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 3 + kRounds * (1 + 2 * sp) + (kRounds - 1) * (1 + 2 * sp));
     GP_CUDA(ctx, gp::launch_norm1(mb, ctx->stream));
     GP_CUDA(ctx, gp::launch_hager(mb, 0, nullptr, ctx->stream));
     for (int it = 0; it < kRounds; ++it) {

@@ -112,18 +112,27 @@ struct MixedBatch {
     int fwd;                      // 1: the forward solve L [x_1 x_y] = [1 Y] runs inside the
                                   // factorisation (diagonal blocks and panel slicing)
     float2* WT;                   // L_JJ^-1 per diagonal block, double-float tiles: [J][128 x 128]
+    float2* WR;                   // the same, row-major (its transpose column-major), stride wt_stride
     size_t wt_stride;
     size_t ps_stride, pe_stride, ws_stride, we_stride;
     float2* Z;                    // 8 columns of npad double-float values: x_1, x_y, two
                                   // residual columns, 1 / L_ii, two condition-estimate
                                   // columns, |R| row sums
     size_t z_stride;
+    float2* RP;                   // per-tile partial sums of the tile-parallel residual (or null)
+    size_t rp_stride;
     const double* y;
     InstState* st;
     int* err;                     // set when a bounded device wait gave up
 };
 
 constexpr int kZCols = 8;
+// kernel launches of one forward or backward substitution pass (a diagonal
+// step per block column, a tile step between consecutive ones)
+inline int subst_launches(int nt) { return 2 * nt - 1; }
+// partial sums of the tile-parallel residual per lower tile: row products
+// [2 column halves][2 right-hand sides][128], then column products [2][2][64]
+constexpr int kRpTile = 2 * 2 * GP_NB + 2 * 2 * (GP_NB / 2);
 
 // A kernel's dynamic shared-memory limit is a per-device attribute: each
 // launcher keeps the largest size it has set on every device ordinal and

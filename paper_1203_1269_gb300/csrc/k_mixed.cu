@@ -173,21 +173,6 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -424,11 +409,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     }
     // W as a double-float tile (column-major, zeros above the diagonal) for
     // the diagonal-block products of the solves
+    // and row-major (W^T column-major) for the backward substitution
     {
         float2* Wt = b.WT + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
+        float2* Wr = b.WR + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
         for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
             const int rr = q & 127, cc = q >> 7;
             Wt[q] = (rr >= cc) ? make_float2(P[prow(rr) + cc].hi, P[prow(rr) + cc].lo) : make_float2(0.f, 0.f);
+            // row cc, column rr of W
+            Wr[q] = (cc >= rr) ? make_float2(P[prow(cc) + rr].hi, P[prow(cc) + rr].lo) : make_float2(0.f, 0.f);
         }
     }
     // row c of W: exponent (of the largest high word, as the panel slicing
@@ -686,6 +675,13 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+
+// 8-byte asynchronous global -> shared copies (every one of a thread's
+// copies in flight at once), then a wait for all of them
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
@@ -1388,14 +1384,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch 
 // ------------------------------------------------------------ solves -------
 // Z (per instance, float2): column k of length npad at Z + k * npad.
 //   0: x_1   1: x_y   2, 3: residual / correction   4: 1 / L_ii
-// One CTA of 512 threads per instance.  Tiles whose transpose is needed are
-// staged in shared memory as T[c][k] with a row stride of 129 entries, so
-// that thread c walking row c and thread k walking column k both read
-// conflict-free (2-way for the 8-byte entries).
+// The substitutions and the residual are tile-parallel (kernels below);
+// tiles whose transpose is needed are staged in shared memory column by
+// column with one entry of padding, so that a thread walking a column and
+// one walking a row both read conflict-free (2-way for the 8-byte entries).
 
-constexpr int kSolveThreads = 512;
-constexpr uint32_t kTileDfBytes = GP_TILE_ELEMS * sizeof(float2);   // one double-float tile, 128 KB
-constexpr int kTs = GP_NB + 1;   // staged tile row stride
+constexpr int kSolveThreads = 512;   // the finalising reduction
+constexpr int kTs = GP_NB + 1;       // staged column stride of a 128-row tile part
 
 __device__ __forceinline__ float2* zcol(const MixedBatch& b, int t, int k) {
     return b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB;
@@ -1424,17 +1419,7 @@ __device__ dfl block_sum_df(dfl v, dfl* red) {
     return s;
 }
 
-// Stage tile `src` (column-major 128 x 128) as T[c * kTs + k] = src(k, c).
-__device__ __forceinline__ void stage_tile(const float2* __restrict__ src, dfl* T) {
-#pragma unroll 8
-    for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kSolveThreads) {
-        const float2 v = __ldg(src + q);
-        T[(q >> 7) * kTs + (q & 127)] = dfl{v.x, v.y};
-    }
-}
 
-// Forward substitution L z = rhs for two columns (c0, c0 + 1) in place.
-// init != 0: the right-hand sides are [1 Y] (zero on padded rows).
 // [1 Y] (zero on padded rows) into Z columns 0, 1: the right-hand sides of
 // the forward solve that the factorisation carries out block by block
 __global__ void k_rhs_init(MixedBatch b) {
@@ -1446,258 +1431,248 @@ __global__ void k_rhs_init(MixedBatch b) {
     df_store(zcol(b, t, 1) + gi, in ? df_from_double(b.y[gi]) : dfl{0.f, 0.f});
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_df_forward(MixedBatch b, int c0, int init) {
-    __shared__ dfl xj[2][GP_NB];
-    __shared__ dfl part[4][2][GP_NB];
-    __shared__ dfl rhs[2][GP_NB];
-    const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK || b.st[t].hager_done) return;
-    const int nt = b.nt, n = b.n;
-    float2* z0 = zcol(b, t, c0);
-    float2* z1 = zcol(b, t, c0 + 1);
-    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
-    for (int I = 0; I < nt; ++I) {
-        const int gi = I * GP_NB + r;
-        dfl a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
-        for (int Jt = 0; Jt < I; ++Jt) {
-            __syncthreads();
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x >> 7;
-                xj[k][r] = df_load((k ? z1 : z0) + Jt * GP_NB + r);
-            }
-            // the next tile of the walk heads for L2 while this one is used
-            if (threadIdx.x == 0)
-                prefetch_l2(Jt + 1 < I ? df_tile(b, b.A, t, I, Jt + 1)
-                                       : b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS,
-                            kTileDfBytes);
-            __syncthreads();
-            const float2* L = df_tile(b, b.A, t, I, Jt);
-            // thread (r, h) takes columns h, h + 8, ... and h + 4, h + 12, ...: 4 chains
-#pragma unroll 4
-            for (int c = h; c < GP_NB; c += 8) {
-                const float2 u = __ldg(L + c * GP_NB + r);
-                const float2 v = __ldg(L + (c + 4) * GP_NB + r);
-                const dfl l0 = {u.x, u.y}, l1 = {v.x, v.y};
-                a00 = df_fma(l0, xj[0][c], a00);
-                a01 = df_fma(l1, xj[0][c + 4], a01);
-                a10 = df_fma(l0, xj[1][c], a10);
-                a11 = df_fma(l1, xj[1][c + 4], a11);
-            }
-        }
-        part[h][0][r] = df_add(a00, a01);
-        part[h][1][r] = df_add(a10, a11);
-        __syncthreads();
-        if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x >> 7;
-            dfl bk;
-            if (init) {
-                if (k == 0) bk = {(gi < n) ? 1.f : 0.f, 0.f};
-                else        bk = (gi < n) ? df_from_double(b.y[gi]) : dfl{0.f, 0.f};
-            } else {
-                bk = df_load((k ? z1 : z0) + gi);
-            }
-            const dfl sm = df_add(df_add(part[0][k][r], part[1][k][r]), df_add(part[2][k][r], part[3][k][r]));
-            rhs[k][r] = df_sub(bk, sm);
-        }
-        __syncthreads();
-        // x_I = W_I rhs_I with W_I = L_II^-1 (lower): thread (r, h) sums columns
-        // c <= r of its parity classes, four chains
-        if (threadIdx.x == 0 && I + 1 < nt) prefetch_l2(df_tile(b, b.A, t, I + 1, 0), kTileDfBytes);
-        {
-            const float2* W = b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS;
-            dfl s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
-#pragma unroll 4
-            for (int c = h; c < GP_NB; c += 8) {
-                const float2 u = __ldg(W + c * GP_NB + r);
-                const float2 v = __ldg(W + (c + 4) * GP_NB + r);
-                const dfl w0 = {u.x, u.y}, w1 = {v.x, v.y};
-                s00 = df_fma(w0, rhs[0][c], s00);
-                s01 = df_fma(w1, rhs[0][c + 4], s01);
-                s10 = df_fma(w0, rhs[1][c], s10);
-                s11 = df_fma(w1, rhs[1][c + 4], s11);
-            }
-            part[h][0][r] = df_add(s00, s01);
-            part[h][1][r] = df_add(s10, s11);
-        }
-        __syncthreads();
-        if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x >> 7;
-            const dfl x = df_add(df_add(part[0][k][r], part[1][k][r]), df_add(part[2][k][r], part[3][k][r]));
-            df_store((k ? z1 : z0) + gi, x);
-        }
-        __syncthreads();
-    }
+
+
+
+// Forward and backward substitution with the double-float factor for two
+// columns (c0, c0 + 1) of Z in place, tile-parallel: block column by block
+// column, a small kernel finishes the diagonal block from the partial
+// products of the tiles already applied (fixed order), and a tile kernel
+// forms the next partial products of every tile of that block column (or
+// row) at once, one CTA per tile half.  Partial products live in RP:
+// per lower tile q, [2 halves][2 columns][128] double-float values.
+constexpr int kSubThreads = 256;
+
+__device__ __forceinline__ bool sub_active(const MixedBatch& b, int t) {
+    return b.st[t].status == GP_OK && !b.st[t].hager_done;
 }
 
-// Backward substitution L^T w = z for columns (c0, c0 + 1) in place; when
-// add_to >= 0 the result is also added into columns (add_to, add_to + 1).
-// Dynamic smem: the staged tile (128 x kTs double-float).
-__global__ void __launch_bounds__(kSolveThreads) k_df_backward(MixedBatch b, int c0, int add_to) {
-    extern __shared__ dfl T[];
-    __shared__ dfl wk[2][GP_NB];
-    __shared__ dfl part[4][2][GP_NB];
+__device__ __forceinline__ float2* rp_part(const MixedBatch& b, int t, int I, int J) {
+    return b.RP + (size_t)t * b.rp_stride + (size_t)tile_index(I, J, b.nt) * kRpTile;
+}
+
+// forward, block J: z_J <- W_J (z_J - sum_{K<J} L_JK z_K), W_J = L_JJ^-1
+// (column-major WT: thread (k, r) reads row r of W along its columns)
+__global__ void __launch_bounds__(kSubThreads) k_fwd_diag(MixedBatch b, int c0, int J) {
     __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK || b.st[t].hager_done) return;
+    if (!sub_active(b, t)) return;
+    const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
+    float2* z = zcol(b, t, c0 + k) + (size_t)J * GP_NB;
+    dfl v = df_load(z + r);
+#pragma unroll 4
+    for (int K = 0; K < J; ++K) {
+        const float2* pp = rp_part(b, t, J, K) + k * GP_NB + r;
+        v = df_sub(v, df_add(df_load(pp), df_load(pp + 2 * GP_NB)));
+    }
+    rhs[k][r] = v;
+    __syncthreads();
+    // all 128 columns (W is zero above its diagonal): a fixed trip count
+    // lets the loads run ahead of the four accumulation chains
+    const float2* W = b.WT + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
+    dfl x[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 16
+    for (int c = 0; c < GP_NB; ++c) x[c & 3] = df_fma(df_load(W + (size_t)c * GP_NB + r), rhs[k][c], x[c & 3]);
+    df_store(z + r, df_add(df_add(x[0], x[1]), df_add(x[2], x[3])));
+}
+
+// forward, tiles (I, J), I > J, half h of the columns: L_IJ(:, h) z_J(h)
+__global__ void __launch_bounds__(kSubThreads) k_fwd_tiles(MixedBatch b, int c0, int J) {
+    __shared__ dfl xs[2][GP_NB / 2];
+    __shared__ dfl part[2][2][GP_NB];
+    const int t = blockIdx.y;
+    if (!sub_active(b, t)) return;
+    const int I = J + 1 + (blockIdx.x >> 1), h = blockIdx.x & 1;
+    const int tid = threadIdx.x;
+    if (tid < GP_NB) xs[tid >> 6][tid & 63] = df_load(zcol(b, t, c0 + (tid >> 6)) + (size_t)J * GP_NB + 64 * h + (tid & 63));
+    __syncthreads();
+    const float2* L = df_tile(b, b.A, t, I, J) + (size_t)h * 64 * GP_NB;
+    const int r = tid & 127, g = tid >> 7;
+    dfl u0 = {0.f, 0.f}, u1 = {0.f, 0.f};
+#pragma unroll 8
+    for (int c = 32 * g; c < 32 * g + 32; ++c) {
+        const float2 l = __ldg(L + (size_t)c * GP_NB + r);
+        const dfl ld = {l.x, l.y};
+        u0 = df_fma(ld, xs[0][c], u0);
+        u1 = df_fma(ld, xs[1][c], u1);
+    }
+    part[g][0][r] = u0;
+    part[g][1][r] = u1;
+    __syncthreads();
+    const int k = tid >> 7;
+    df_store(rp_part(b, t, I, J) + (h * 2 + k) * GP_NB + r, df_add(part[0][k][r], part[1][k][r]));
+}
+
+// backward, block K: z_K <- W_K^T (z_K - sum_{K' > K} L_K'K^T z_K'); W^T
+// from the row-major copy WR (thread (k, c) reads column c of W along its
+// rows); with add_to >= 0 the result is also added into (add_to, add_to + 1)
+__global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, int K, int add_to) {
+    __shared__ dfl rhs[2][GP_NB];
+    const int t = blockIdx.x;
+    if (!sub_active(b, t)) return;
     const int nt = b.nt;
-    float2* z0 = zcol(b, t, c0);
-    float2* z1 = zcol(b, t, c0 + 1);
-    const int c = threadIdx.x & 127, h = threadIdx.x >> 7;
-    for (int I = nt - 1; I >= 0; --I) {
-        if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x >> 7;
-            rhs[k][c] = df_load((k ? z1 : z0) + I * GP_NB + c);
-        }
-        dfl a00 = {0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = {0.f, 0.f};
-        for (int K = I + 1; K < nt; ++K) {
-            __syncthreads();
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x >> 7;
-                wk[k][c] = df_load((k ? z1 : z0) + K * GP_NB + c);
-            }
-            if (threadIdx.x == 0)
-                prefetch_l2(K + 1 < nt ? df_tile(b, b.A, t, K + 1, I)
-                                       : b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS,
-                            kTileDfBytes);
-            stage_tile(df_tile(b, b.A, t, K, I), T);
-            __syncthreads();
-            // (L_KI^T w_K)[c] = sum_k L_KI(k, c) w_K[k] = sum_k T[c][k] w_K[k]; k in [32h, 32h + 32)
-            const dfl* row = T + c * kTs + 32 * h;
+    const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
+    float2* z = zcol(b, t, c0 + k) + (size_t)K * GP_NB;
+    dfl v = df_load(z + c);
 #pragma unroll 4
-            for (int k = 0; k < 32; k += 2) {
-                a00 = df_fma(row[k], wk[0][32 * h + k], a00);
-                a01 = df_fma(row[k + 1], wk[0][32 * h + k + 1], a01);
-                a10 = df_fma(row[k], wk[1][32 * h + k], a10);
-                a11 = df_fma(row[k + 1], wk[1][32 * h + k + 1], a11);
-            }
-        }
-        part[h][0][c] = df_add(a00, a01);
-        part[h][1][c] = df_add(a10, a11);
-        __syncthreads();
-        // W_I = L_II^-1 staged; w_I = W_I^T rhs: w[c] = sum_k W(k, c) rhs[k] = sum_k T[c][k] rhs[k]
-        if (threadIdx.x == 0 && I > 0)
-            prefetch_l2(df_tile(b, b.A, t, I, I - 1), kTileDfBytes);
-        stage_tile(b.WT + (size_t)t * b.wt_stride + (size_t)I * GP_TILE_ELEMS, T);
-        if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x >> 7;
-            const dfl sm = df_add(df_add(part[0][k][c], part[1][k][c]), df_add(part[2][k][c], part[3][k][c]));
-            rhs[k][c] = df_sub(rhs[k][c], sm);
-        }
-        __syncthreads();
-        {
-            const dfl* row = T + c * kTs + 32 * h;
-            dfl s00 = {0.f, 0.f}, s01 = {0.f, 0.f}, s10 = {0.f, 0.f}, s11 = {0.f, 0.f};
-#pragma unroll 4
-            for (int k = 0; k < 32; k += 2) {
-                s00 = df_fma(row[k], rhs[0][32 * h + k], s00);
-                s01 = df_fma(row[k + 1], rhs[0][32 * h + k + 1], s01);
-                s10 = df_fma(row[k], rhs[1][32 * h + k], s10);
-                s11 = df_fma(row[k + 1], rhs[1][32 * h + k + 1], s11);
-            }
-            part[h][0][c] = df_add(s00, s01);
-            part[h][1][c] = df_add(s10, s11);
-        }
-        __syncthreads();
-        if (threadIdx.x < 2 * GP_NB) {
-            const int k = threadIdx.x >> 7;
-            const dfl x = df_add(df_add(part[0][k][c], part[1][k][c]), df_add(part[2][k][c], part[3][k][c]));
-            df_store((k ? z1 : z0) + I * GP_NB + c, x);
-            if (add_to >= 0) {
-                float2* acc = zcol(b, t, add_to + k) + I * GP_NB + c;
-                df_store(acc, df_add(df_load(acc), x));
-            }
-        }
-        __syncthreads();
+    for (int K2 = K + 1; K2 < nt; ++K2) {
+        const float2* pp = rp_part(b, t, K2, K) + k * GP_NB + c;
+        v = df_sub(v, df_add(df_load(pp), df_load(pp + 2 * GP_NB)));
+    }
+    rhs[k][c] = v;
+    __syncthreads();
+    // all 128 rows (W is zero above its diagonal): a fixed trip count lets
+    // the loads run ahead of the four accumulation chains
+    const float2* Wr = b.WR + (size_t)t * b.wt_stride + (size_t)K * GP_TILE_ELEMS;
+    dfl xa[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 16
+    for (int r = 0; r < GP_NB; ++r) xa[r & 3] = df_fma(df_load(Wr + (size_t)r * GP_NB + c), rhs[k][r], xa[r & 3]);
+    const dfl x = df_add(df_add(xa[0], xa[1]), df_add(xa[2], xa[3]));
+    df_store(z + c, x);
+    if (add_to >= 0) {
+        float2* acc = zcol(b, t, add_to + k) + (size_t)K * GP_NB + c;
+        df_store(acc, df_add(df_load(acc), x));
     }
 }
 
-// Residuals [r_1 r_y] = [1 Y] - R [x_1 x_y] into columns 2, 3, with the
-// double-float copy of R.  Every stored tile (I, J) is read once and applied
-// both ways: y_I += R_IJ x_J and, off the diagonal, y_J += R_IJ^T x_I.
-// y accumulates in columns 2, 3 (each entry always by the same thread).
-// Dynamic smem: the staged tile.
-__global__ void __launch_bounds__(kSolveThreads) k_df_residual(MixedBatch b) {
-    extern __shared__ dfl T[];
-    __shared__ dfl xa[2][GP_NB];
-    __shared__ dfl xb[2][GP_NB];
-    __shared__ dfl part[4][2][GP_NB];
-    const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK) return;
-    const int nt = b.nt, n = b.n;
-    const float2* x0 = zcol(b, t, 0);
-    const float2* x1 = zcol(b, t, 1);
-    const int i = threadIdx.x & 127, h = threadIdx.x >> 7;
-    float2* y0 = zcol(b, t, 2);
-    float2* y1 = zcol(b, t, 3);
-    if (threadIdx.x < 2 * GP_NB) {
-        float2* y = (threadIdx.x >> 7) ? y1 : y0;
-        for (int I = 0; I < nt; ++I) y[I * GP_NB + i] = make_float2(0.f, 0.f);
+// backward, tiles (K, I), I < K, half h of the rows: L_KI(h, :)^T z_K(h);
+// the half tile is staged column by column (64 rows + 1 of padding) so that
+// thread c walks column c conflict-free
+constexpr int kBwdTs = GP_NB / 2 + 1;
+__global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0, int K) {
+    extern __shared__ dfl T[];                  // GP_NB x kBwdTs
+    __shared__ dfl xs[2][GP_NB / 2];
+    __shared__ dfl part[2][2][GP_NB];
+    const int t = blockIdx.y;
+    if (!sub_active(b, t)) return;
+    const int I = blockIdx.x >> 1, h = blockIdx.x & 1;
+    const int tid = threadIdx.x;
+    if (tid < GP_NB) xs[tid >> 6][tid & 63] = df_load(zcol(b, t, c0 + (tid >> 6)) + (size_t)K * GP_NB + 64 * h + (tid & 63));
+    const float2* L = df_tile(b, b.A, t, K, I) + 64 * h;
+#pragma unroll
+    for (int e = tid; e < 64 * GP_NB; e += kSubThreads) {
+        const int c = e >> 6, rr = e & 63;
+        cp_async8(T + c * kBwdTs + rr, L + (size_t)c * GP_NB + rr);
     }
-    for (int J = 0; J < nt; ++J) {
-        for (int I = J; I < nt; ++I) {
-            __syncthreads();
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x >> 7;
-                xa[k][i] = df_load((k ? x1 : x0) + J * GP_NB + i);   // x_J
-                xb[k][i] = df_load((k ? x1 : x0) + I * GP_NB + i);   // x_I
-            }
-            // stored tiles are walked in packed order: the next one is adjacent
-            if (threadIdx.x == 0 && !(I + 1 == nt && J + 1 == nt))
-                prefetch_l2(df_tile(b, b.Rc, t, I, J) + GP_TILE_ELEMS, kTileDfBytes);
-            stage_tile(df_tile(b, b.Rc, t, I, J), T);
-            __syncthreads();
-            // rows: (R_IJ x_J)[i] = sum_c T[c][i] x_J[c], c in [32h, 32h + 32)
-            dfl r0 = {0.f, 0.f}, r1 = {0.f, 0.f};
+    cp_async_wait_all();
+    __syncthreads();
+    const int c = tid & 127, g = tid >> 7;
+    const dfl* col = T + c * kBwdTs;
+    dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+#pragma unroll 8
+    for (int rr = 32 * g; rr < 32 * g + 32; ++rr) {
+        s0 = df_fma(col[rr], xs[0][rr], s0);
+        s1 = df_fma(col[rr], xs[1][rr], s1);
+    }
+    part[g][0][c] = s0;
+    part[g][1][c] = s1;
+    __syncthreads();
+    const int k = tid >> 7;
+    df_store(rp_part(b, t, K, I) + (h * 2 + k) * GP_NB + c, df_add(part[0][k][c], part[1][k][c]));
+}
+
+// Residual r = b - R x of the solution columns (0, 1) into columns (2, 3),
+// against the double-float copy of R, tile-parallel: one CTA per (lower tile
+// (I, J) of the R copy, column half hc) stages its 128 x 64 part and writes
+// the partial sums
+//   U = R_IJ(:, half) x_J(half)        two columns of 128 (row products)
+//   V = R_IJ(:, half)^T x_I            two columns of 64 (column products, I != J)
+// into RP; k_resid_reduce adds them per row block in a fixed order.  The
+// diagonal tiles of the R copy hold both triangles, so they give U only.
+// RP per tile q: U[hc][k][128] then V[hc][k][64] (kRpTile values).
+constexpr int kResThreads = 256;
+constexpr int kResCols = GP_NB / 2;
+static_assert(kRpTile == 2 * 2 * GP_NB + 2 * 2 * kResCols, "residual partial layout");
+
+__global__ void __launch_bounds__(kResThreads) k_resid_tiles(MixedBatch b) {
+    extern __shared__ dfl T[];                  // kResCols x kTs
+    __shared__ dfl xa[2][kResCols];             // x_J on this half's columns
+    __shared__ dfl xb[2][GP_NB];                // x_I
+    __shared__ dfl part[2 * 2 * GP_NB];           // U: [2][2][128], then V: [4][2][64]
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int nt = b.nt;
+    const int q = blockIdx.x >> 1, hc = blockIdx.x & 1;
+    int J = 0, rem = q;
+    while (rem >= nt - J) {
+        rem -= nt - J;
+        ++J;
+    }
+    const int I = J + rem;
+    const int tid = threadIdx.x;
+    if (tid < 2 * kResCols) xa[tid >> 6][tid & 63] = df_load(zcol(b, t, tid >> 6) + J * GP_NB + hc * kResCols + (tid & 63));
+    xb[tid >> 7][tid & 127] = df_load(zcol(b, t, tid >> 7) + I * GP_NB + (tid & 127));
+    const float2* src = df_tile(b, b.Rc, t, I, J) + (size_t)hc * kResCols * GP_NB;
+#pragma unroll
+    for (int e = tid; e < kResCols * GP_NB; e += kResThreads) cp_async8(T + (e >> 7) * kTs + (e & 127), src + e);
+    cp_async_wait_all();
+    __syncthreads();
+    float2* rp = b.RP + (size_t)t * b.rp_stride + (size_t)q * kRpTile;
+    {
+        // U: thread (r, h) takes the columns 32h .. 32h + 31 of the half
+        const int r = tid & 127, h = tid >> 7;
+        dfl u0 = {0.f, 0.f}, u1 = {0.f, 0.f};
 #pragma unroll 4
-            for (int c = 32 * h; c < 32 * h + 32; ++c) {
-                const dfl v = T[c * kTs + i];
-                r0 = df_fma(v, xa[0][c], r0);
-                r1 = df_fma(v, xa[1][c], r1);
-            }
-            part[h][0][i] = r0;
-            part[h][1][i] = r1;
-            __syncthreads();
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x >> 7;
-                float2* y = (k ? y1 : y0) + I * GP_NB + i;
-                df_store(y, df_add(df_load(y), df_add(df_add(part[0][k][i], part[1][k][i]),
-                                                      df_add(part[2][k][i], part[3][k][i]))));
-            }
-            if (I == J) continue;
-            __syncthreads();
-            // columns: (R_IJ^T x_I)[c] = sum_k T[c][k] x_I[k], k in [32h, 32h + 32)
-            const int c = i;
-            dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-            const dfl* row = T + c * kTs;
-#pragma unroll 4
-            for (int k = 32 * h; k < 32 * h + 32; ++k) {
-                s0 = df_fma(row[k], xb[0][k], s0);
-                s1 = df_fma(row[k], xb[1][k], s1);
-            }
-            part[h][0][c] = s0;
-            part[h][1][c] = s1;
-            __syncthreads();
-            if (threadIdx.x < 2 * GP_NB) {
-                const int k = threadIdx.x >> 7;
-                float2* y = (k ? y1 : y0) + J * GP_NB + c;
-                df_store(y, df_add(df_load(y), df_add(df_add(part[0][k][c], part[1][k][c]),
-                                                      df_add(part[2][k][c], part[3][k][c]))));
-            }
+        for (int c = 32 * h; c < 32 * h + 32; ++c) {
+            const dfl v = T[c * kTs + r];
+            u0 = df_fma(v, xa[0][c], u0);
+            u1 = df_fma(v, xa[1][c], u1);
         }
+        part[(h * 2 + 0) * GP_NB + r] = u0;
+        part[(h * 2 + 1) * GP_NB + r] = u1;
     }
     __syncthreads();
-    if (threadIdx.x < 2 * GP_NB) {
-        // r = b - y by the owning threads; padded rows: R is the identity there
-        // and x is zero, so r = 0
-        const int k = threadIdx.x >> 7;
-        float2* y = k ? y1 : y0;
-        for (int I = 0; I < nt; ++I) {
-            const int q = I * GP_NB + i;
-            dfl bq = {0.f, 0.f};
-            if (q < n) bq = k ? df_from_double(b.y[q]) : dfl{1.f, 0.f};
-            df_store(y + q, (q < n) ? df_sub(bq, df_load(y + q)) : dfl{0.f, 0.f});
-        }
+    {
+        const int k = tid >> 7, r = tid & 127;
+        df_store(rp + (hc * 2 + k) * GP_NB + r, df_add(part[k * GP_NB + r], part[(2 + k) * GP_NB + r]));
     }
+    if (I == J) return;                         // uniform
+    __syncthreads();
+    {
+        // V: thread (c, h) takes the rows 32h .. 32h + 31 of column c
+        const int c = tid & 63, h = tid >> 6;
+        const dfl* col = T + c * kTs;
+        dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+#pragma unroll 4
+        for (int r = 32 * h; r < 32 * h + 32; ++r) {
+            s0 = df_fma(col[r], xb[0][r], s0);
+            s1 = df_fma(col[r], xb[1][r], s1);
+        }
+        part[(h * 2 + 0) * kResCols + c] = s0;
+        part[(h * 2 + 1) * kResCols + c] = s1;
+    }
+    __syncthreads();
+    if (tid < 2 * kResCols) {
+        const int k = tid >> 6, c = tid & 63;
+        const dfl v = df_add(df_add(part[(0 + k) * kResCols + c], part[(2 + k) * kResCols + c]),
+                             df_add(part[(4 + k) * kResCols + c], part[(6 + k) * kResCols + c]));
+        df_store(rp + 4 * GP_NB + (hc * 2 + k) * kResCols + c, v);
+    }
+}
+
+// r_I = b_I - (sum_{J <= I} U(I, J) + sum_{J > I} V(J, I)) for both columns,
+// into Z columns 2, 3; padded rows: R is the identity there and x is zero,
+// so r = 0.  One CTA per (row block I, instance).
+__global__ void __launch_bounds__(kResThreads) k_resid_reduce(MixedBatch b) {
+    const int t = blockIdx.y, I = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    const int nt = b.nt, n = b.n;
+    const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
+    const float2* rp = b.RP + (size_t)t * b.rp_stride;
+    dfl y = {0.f, 0.f};
+    for (int J = 0; J <= I; ++J) {
+        const float2* u = rp + (size_t)tile_index(I, J, nt) * kRpTile;
+        y = df_add(y, df_load(u + k * GP_NB + r));
+        y = df_add(y, df_load(u + (2 + k) * GP_NB + r));
+    }
+    for (int K = I + 1; K < nt; ++K) {
+        const float2* v = rp + (size_t)tile_index(K, I, nt) * kRpTile + 4 * GP_NB;
+        y = df_add(y, df_load(v + ((r >> 6) * 2 + k) * kResCols + (r & 63)));
+    }
+    const int gi = I * GP_NB + r;
+    dfl bq = {0.f, 0.f};
+    if (gi < n) bq = k ? df_from_double(b.y[gi]) : dfl{1.f, 0.f};
+    df_store(zcol(b, t, 2 + k) + gi, (gi < n) ? df_sub(bq, y) : dfl{0.f, 0.f});
 }
 
 // mu_hat = 1'x_y / 1'x_1, w = x_y - mu x_1 = R^-1 (Y - 1 mu), Q = (Y - 1 mu)'w,
@@ -1937,25 +1912,37 @@ cudaError_t launch_rhs_init(const MixedBatch& b, cudaStream_t s) {
 }
 
 cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_t s) {
-    k_df_forward<<<b.count, kSolveThreads, 0, s>>>(b, c0, init);
+    if (init) {
+        if (c0 != 0) return cudaErrorInvalidValue;
+        cudaError_t e = launch_rhs_init(b, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int J = 0; J < b.nt; ++J) {
+        k_fwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, J);
+        if (J + 1 < b.nt) k_fwd_tiles<<<dim3(2 * (b.nt - 1 - J), b.count), kSubThreads, 0, s>>>(b, c0, J);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStream_t s) {
-    const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
+    const size_t smem = (size_t)GP_NB * kBwdTs * sizeof(dfl);
     static std::atomic<size_t> attr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_df_backward, smem, attr);
+    cudaError_t e = raise_smem_limit(k_bwd_tiles, smem, attr);
     if (e != cudaSuccess) return e;
-    k_df_backward<<<b.count, kSolveThreads, smem, s>>>(b, c0, add_to);
+    for (int K = b.nt - 1; K >= 0; --K) {
+        k_bwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, K, add_to);
+        if (K > 0) k_bwd_tiles<<<dim3(2 * K, b.count), kSubThreads, smem, s>>>(b, c0, K);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
-    const size_t smem = (size_t)GP_NB * kTs * sizeof(dfl);
+    const size_t smem = (size_t)kResCols * kTs * sizeof(dfl);
     static std::atomic<size_t> attr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_df_residual, smem, attr);
+    cudaError_t e = raise_smem_limit(k_resid_tiles, smem, attr);
     if (e != cudaSuccess) return e;
-    k_df_residual<<<b.count, kSolveThreads, smem, s>>>(b);
+    k_resid_tiles<<<dim3(2 * (unsigned)packed_tiles(b.nt), b.count), kResThreads, smem, s>>>(b);
+    k_resid_reduce<<<dim3(b.nt, b.count), kResThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
