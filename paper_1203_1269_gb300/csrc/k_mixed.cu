@@ -199,6 +199,13 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// 8-byte asynchronous global -> shared copies (every one of a thread's
+// copies in flight at once), then a wait for all of them
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int N>
 __device__ __forceinline__ void regs_dec() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N)); }
 template <int N>
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     extern __shared__ dfl P[];             // kPacked double-float values
     __shared__ dfl V[GP_NB];
     __shared__ dfl dinv[GP_NB];            // 1 / L_cc
-    __shared__ double lcc[GP_NB];          // L_cc
+    __shared__ dfl lcc[GP_NB];             // L_cc
     __shared__ dfl bj[2][GP_NB];
     __shared__ dfl xpart[2][GP_NB];
     __shared__ double lsum[GP_NB / 32];
@@ -313,31 +320,41 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     float2* T = df_tile(b, b.A, t, J, J);
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kDiagThreads) {
         const int rr = q & 127, cc = q >> 7;
-        if (rr >= cc) P[prow(rr) + cc] = df_load(T + q);
+        if (rr >= cc) cp_async8(P + prow(rr) + cc, T + q);
     }
     if (threadIdx.x == 0) failed = -1;
+    cp_async_wait_all();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kDiagThreads / 32;
+    // pivot c: 1 / sqrt(a) from a float seed (about 22 correct bits) and two
+    // Newton steps in double-float, y <- y + y (1 - a y^2) / 2 (44, then
+    // about 48 bits), L_cc = a y; all on the FP32 pipes, since this chain is
+    // the sweep's critical path.  Pivots outside [2^-100, 2^100] (the float
+    // seed's comfortable range) take the double route.
     auto take_pivot = [&](int c, dfl a) {
-        const double piv = df_to_double(a);
-        double y, l;
-        if (!(piv > 0.0) || !isfinite(piv)) {
+        dfl y, l;
+        if (!(a.hi > 0.f) || !isfinite(a.hi)) {
             failed = c;
-            y = 1.0;
-            l = 1.0;
-        } else if (piv > 1e-30 && piv < 1e30) {
-            y = (double)rsqrtf((float)piv);
-            const double h = -0.5 * piv;
+            y = dfl{1.f, 0.f};
+            l = y;
+        } else if (a.hi > 7.9e-31f && a.hi < 1.26e30f) {
+            const float y0 = rsqrtf(a.hi);
+            y = dfl{y0, 0.f};
 #pragma unroll
-            for (int it = 0; it < 3; ++it) y = y * fma(h, y * y, 1.5);
-            l = piv * y;
+            for (int it = 0; it < 2; ++it) {
+                const dfl e = df_sub(dfl{1.f, 0.f}, df_mul(df_mul(a, y), y));
+                y = df_fma(df_mul(dfl{0.5f, 0.f}, y), e, y);
+            }
+            l = df_mul(a, y);
         } else {
-            l = sqrt(piv);
-            y = 1.0 / l;
+            const double piv = df_to_double(a);
+            const double ld = sqrt(piv);
+            y = df_from_double(1.0 / ld);
+            l = df_from_double(ld);
         }
         lcc[c] = l;
-        dinv[c] = df_from_double(y);
+        dinv[c] = y;
     };
     if (threadIdx.x == 0) take_pivot(0, P[0]);
     __syncthreads();
@@ -352,7 +369,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
                 P[prow(c) + p] = w;
                 V[p] = w;
             } else if (p == c) {
-                df_store(T + (size_t)c * GP_NB + c, df_from_double(lcc[c]));
+                df_store(T + (size_t)c * GP_NB + c, lcc[c]);
                 P[prow(c) + c] = di;
                 V[c] = di;
             } else {
@@ -363,11 +380,14 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         }
         __syncthreads();
         if (c + 1 == GP_NB) break;
-        // phase 2: rows i > c, X_ip += L_ic V_p (p <= i), a warp per row
+        // phase 2: rows i > c, X_ip += L_ic V_p (p <= i), a warp per row; warp
+        // 0 takes only row c + 1 and its pivot, the others deal the rest
         dfl vl[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) vl[j] = V[lane + 32 * j];
-        for (int i = c + 1 + warp; i < GP_NB; i += kWarps) {
+        const int i0 = (warp == 0) ? c + 1 : c + 1 + warp;
+        const int di = (warp == 0) ? GP_NB : kWarps - 1;
+        for (int i = i0; i < GP_NB; i += di) {
             const dfl m = df_neg(V[i]);    // L_ic
             dfl* row = P + prow(i);
 #pragma unroll
@@ -395,7 +415,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     // log-det: sum of log L_cc over the block in a fixed order (warp trees,
     // then the four warp sums in turn); reciprocal diagonal out
     if (threadIdx.x < GP_NB) {
-        double v = log(lcc[threadIdx.x]);
+        double v = log(df_to_double(lcc[threadIdx.x]));
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) lsum[warp] = v;
         float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
@@ -675,13 +695,6 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-
-// 8-byte asynchronous global -> shared copies (every one of a thread's
-// copies in flight at once), then a wait for all of them
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
@@ -1484,6 +1497,9 @@ __global__ void __launch_bounds__(kSubThreads) k_fwd_tiles(MixedBatch b, int c0,
     if (!sub_active(b, t)) return;
     const int I = J + 1 + (blockIdx.x >> 1), h = blockIdx.x & 1;
     const int tid = threadIdx.x;
+    // W_{J+1} heads for L2 for the next diagonal step
+    if (tid == 0 && I == J + 1 && h == 0)
+        prefetch_l2(b.WT + (size_t)t * b.wt_stride + (size_t)(J + 1) * GP_TILE_ELEMS, GP_TILE_ELEMS * sizeof(float2));
     if (tid < GP_NB) xs[tid >> 6][tid & 63] = df_load(zcol(b, t, c0 + (tid >> 6)) + (size_t)J * GP_NB + 64 * h + (tid & 63));
     __syncthreads();
     const float2* L = df_tile(b, b.A, t, I, J) + (size_t)h * 64 * GP_NB;
@@ -1547,6 +1563,9 @@ __global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0,
     if (!sub_active(b, t)) return;
     const int I = blockIdx.x >> 1, h = blockIdx.x & 1;
     const int tid = threadIdx.x;
+    // W_{K-1} (row-major) heads for L2 for the next diagonal step
+    if (tid == 0 && I == K - 1 && h == 0)
+        prefetch_l2(b.WR + (size_t)t * b.wt_stride + (size_t)(K - 1) * GP_TILE_ELEMS, GP_TILE_ELEMS * sizeof(float2));
     if (tid < GP_NB) xs[tid >> 6][tid & 63] = df_load(zcol(b, t, c0 + (tid >> 6)) + (size_t)K * GP_NB + 64 * h + (tid & 63));
     const float2* L = df_tile(b, b.A, t, K, I) + 64 * h;
 #pragma unroll
