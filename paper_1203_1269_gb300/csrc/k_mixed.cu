@@ -48,15 +48,20 @@ constexpr int kEpiWarps = 8;                  // epilogue warps: kEpiWarps / 4 p
 constexpr int kEpiParts = kEpiWarps / 4;       // column parts of a tile
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 MMA, then the epilogue
 constexpr int kEpiThreads = 32 * kEpiWarps;
-// Early-release update (k_split_gemm<1, 128, 4, true>): warpgroup 0 holds the
-// copy and MMA warps (and two idle ones) and gives registers up to the two
-// epilogue warpgroups, which keep a whole 64-column part of a tile's combined
-// result in registers.  The split must fit the launch's registers:
-// 128 * kRegsLow + 256 * kRegsHigh <= 384 * (registers at launch).
-constexpr int kGemmThreadsER = 128 + 32 * kEpiWarps;
-constexpr int kRegsLow = 64;
-constexpr int kRegsHigh = 216;
-static_assert(kEpiWarps == 8, "the early-release split assumes two epilogue warpgroups");
+// Early-release kernels (k_split_gemm<..., true>): warpgroup 0 holds the copy
+// and MMA warps (and two idle ones) and gives registers up to the
+// kEpiWarpsER epilogue warps, which keep a whole column part of a tile's
+// combined result in registers.  The split must fit the launch's registers:
+// 128 * kRegsLow + 32 * kEpiWarpsER * kRegsHigh <= kGemmThreadsER * (registers
+// at launch, 96 for 640 threads).
+constexpr int kEpiWarpsER = 16;
+constexpr int kEpiPartsER = kEpiWarpsER / 4;
+constexpr int kGemmThreadsER = 128 + 32 * kEpiWarpsER;
+constexpr int kEpiThreadsER = 32 * kEpiWarpsER;
+constexpr int kRegsLow = 32;
+constexpr int kRegsHigh = 112;
+static_assert(128 * kRegsLow + 32 * kEpiWarpsER * kRegsHigh <= kGemmThreadsER * (65536 / kGemmThreadsER / 8 * 8),
+              "register split exceeds the launch's registers");
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
 
 // ---------------------------------------------------------------- PTX ------
@@ -769,7 +774,7 @@ __device__ __forceinline__ void issue_stage_ns(int ns, bool first, uint32_t tacc
 // combines every accumulator group of its columns into registers, releases
 // tensor memory to the MMA warp, and only then reads, updates and writes C,
 // so that C's round trip overlaps the next tile's MMAs.  Warps 2, 3 idle;
-// the epilogue warps are 4 .. 11 and hold kRegsHigh registers each.
+// the epilogue warps are 4 .. 3 + kEpiWarpsER and hold kRegsHigh registers each.
 template <int MODE, int NT, int NG, bool ER = false>
 __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
     k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
@@ -832,7 +837,7 @@ __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
         mbar_init(&empty_bar[1], 1);
         for (int u = 0; u < NBUF; ++u) {
             mbar_init(&tfull_bar[u], 1);
-            mbar_init(&tempty_bar[u], kEpiThreads);
+            mbar_init(&tempty_bar[u], ER ? kEpiThreadsER : kEpiThreads);
         }
         mbar_init(&drain_bar, 1);
         mbar_init(&never_bar, 1);
@@ -850,14 +855,14 @@ __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
 
     auto epilogue_er = [&]() {
         // early-release epilogue: warp w reads TMEM lane quarter w % 4 and
-        // the column part (w - 4) / 4 of the tile
+        // the column part (w - 4) / 4 of the tile (NT / kEpiPartsER columns)
         const int q = warp & 3;
         const int part = (warp - kEpiBase) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-        constexpr int kPartCols = NT / kEpiParts;
-        constexpr int CB1 = (NG > 4) ? 8 : 16;  // columns per TMEM load (phase 1)
-        constexpr int CB2 = 16;                 // columns per C block (phase 2)
+        constexpr int kPartCols = NT / kEpiPartsER;
+        constexpr int CB1 = 8;                  // columns per TMEM load (phase 1)
+        constexpr int CB2 = (kPartCols < 16) ? kPartCols : 16;   // columns per C block (phase 2)
         static_assert(kPartCols % CB1 == 0 && kPartCols % CB2 == 0, "column part vs block widths");
         const int ng_used = ns < NG ? ns : NG;
         const int cbase = part * kPartCols;
@@ -1828,7 +1833,7 @@ static bool early_release_fits() {
         cudaFuncAttributes fa{};
         v = 2;
         if (cudaFuncGetAttributes(&fa, k_split_gemm<MODE, NT, NG, true>) == cudaSuccess &&
-            128 * kRegsLow + 32 * kEpiWarps * kRegsHigh <= kGemmThreadsER * fa.numRegs &&
+            128 * kRegsLow + 32 * kEpiWarpsER * kRegsHigh <= kGemmThreadsER * fa.numRegs &&
             fa.maxThreadsPerBlock >= kGemmThreadsER)
             v = 1;
         cudaGetLastError();
