@@ -299,7 +299,7 @@ def run_gp(args):
         units = tiles * w.T * args.steps / max(upd_n, 1)
         roof = {"kernel": "k_split_gemm<update>", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": stored_traffic("k_split_gemm<update>", ["k_mixed.cu"], units),
+                "traffic": stored_traffic("k_split_gemm<update>", ["k_gemm.cu", "mixed_common.cuh"], units),
                 "units_per_launch": units,
                 "algorithmic_bytes_per_launch": units * NB * NB * 8,
                 "peak_source": f"bf16 dense sustained, {pk_src} (MEASURED_PEAKS.json)",
