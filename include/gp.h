@@ -231,16 +231,19 @@ int gp_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, in
                  int* status);
 
 /* Gradient of -2 log L (eq. 4) with respect to theta, with -2logL itself,
- * at T candidates (T x d), in IEEE double:
+ * at T candidates (T x d):
  *   grad[t*d + k] = d(-2logL)/dtheta_k = tr(R^-1 dR_k) - (n/Q) w' dR_k w,
  * w = R^-1 (Y - 1 mu_hat) (mu_hat minimises Q, so it does not move the
  * gradient), dR_k = dR/dtheta_k (zero on the diagonal: the nugget does not
  * depend on theta); for every gp_correlation.  Section 2 names a multi-start
  * gradient-based search as a possibly faster alternative to its GA; this is
- * the gradient such a search needs.  R^-1 is formed from the double-precision
- * factor (L^-1 by tile diagonals, then L^-T L^-1), twice the factorisation's
- * n^3/6 multiply-adds.  nll, status as gp_nll_batch; grad rows are NaN
- * where the status is not GP_OK.  d <= 16 (GP_ENOTSUP above).
+ * the gradient such a search needs.  -2logL, mu_hat and w come from the
+ * IEEE-double factor (nll equals gp_nll_batch's GP_FP64 result); R^-1 is
+ * formed from that factor in double-float, about 48 bits (L^-1 by tile
+ * diagonals, then L^-T L^-1: twice the factorisation's n^3/6 multiply-adds),
+ * so the gradient's relative error is about cond(R) 2^-47 at worst.  nll,
+ * status as gp_nll_batch; grad rows are NaN where the status is not GP_OK.
+ * d <= 16 (GP_ENOTSUP above).
  * Asynchronous. */
 int gp_nll_grad_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                       const double* theta, double p, double delta, double* nll, double* grad,

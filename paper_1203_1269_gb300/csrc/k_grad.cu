@@ -1,5 +1,5 @@
-// k_grad.cu -- gradient of -2 log L (eq. 4) with respect to theta, in IEEE
-// double, for a batch of candidates factored by the FP64 path.
+// k_grad.cu -- gradient of -2 log L (eq. 4) with respect to theta for a
+// batch of candidates factored by the FP64 path.
 //
 //   d(-2logL)/dtheta_k = tr(R^-1 dR_k) - (n / Q) w' dR_k w
 //                      = sum_{i != j} M_ij R_ij dlog rho_k(x_i, x_j),
@@ -7,13 +7,18 @@
 //
 // from d log|R| = tr(R^-1 dR) and dQ = -w' dR w (mu_hat minimises Q); dR_k
 // is zero on the diagonal (the nugget and the unit diagonal do not depend on
-// theta).  R^-1 comes from the factor in the tile layout:
-//   X = L^-1:   X_JJ = L_JJ^-1, then along tile diagonals s = I - J = 1, 2, ...
+// theta).  -2logL and w come from the IEEE-double factor; R^-1 is formed
+// from it in double-float on the FP32 pipes (n^3/3 multiply-adds, which on
+// the FP64 pipes would cost more than the factorisation itself):
+//   X = L^-1:   X_JJ = L_JJ^-1 (double, in shared memory), then along tile
+//               diagonals s = I - J = 1, 2, ...
 //               X_IJ = -X_II sum_{K=J}^{I-1} L_IK X_KJ  (all J of a diagonal at once)
 //   R^-1 = X' X:  (R^-1)_IJ = sum_{K >= I} X_KI' X_KJ  (I >= J)
-// (n^3/3 more FMAs on the FP64 pipes, like a second factorisation), and one
-// pass over the lower tiles recomputes R_ij and dlog rho, reducing d partial
-// sums per tile that a last kernel adds in a fixed order.
+// The factor is rewritten in place as double-float once the likelihood is
+// done (8 bytes either way), so every tile operand is a float pair.  One pass
+// over the lower tiles then recomputes R_ij (powers in double-float, as the
+// assembly takes them) and dlog rho, reducing d partial sums per tile that a
+// last kernel adds in a fixed order.
 #include "corr.cuh"
 #include "gp_internal.cuh"
 
@@ -23,42 +28,48 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double* tile_at(double* base, size_t stride, int t, int I, int J, int nt) {
+template <typename T>
+__device__ __forceinline__ T* tile_at(T* base, size_t stride, int t, int I, int J, int nt) {
     return base + (size_t)t * stride + (size_t)tile_index(I, J, nt) * GP_TILE_ELEMS;
 }
 
 // acc(r, c) += sum_k opA(A)(r, k) opB(B)(k, c) for one pair of column-major
-// 128 x 128 tiles; thread (tx, ty) of a 16 x 16 layout owns rows tx + 16i and
-// columns ty + 16j.  TA / TB: use the transpose of A / B.  The operands are
-// plain (coherent) loads: k_trtri_step reads a tile it wrote itself.
+// 128 x 128 double-float tiles; thread (tx, ty) of a 16 x 16 layout owns
+// rows tx + 16i and columns ty + 16j.  TA / TB: use the transpose of A / B.
+// The operands are plain (coherent) loads: k_trtri_step reads a tile it
+// wrote itself.
 template <bool TA, bool TB>
-__device__ __forceinline__ void tile_mma(double (&acc)[8][8], const double* A, const double* B,
-                                         double (*As)[GP_NB], double (*Bs)[GP_NB]) {
+__device__ __forceinline__ void tile_mma(dfl (&acc)[8][8], const float2* A, const float2* B,
+                                         dfl (*As)[GP_NB], dfl (*Bs)[GP_NB]) {
     constexpr int KC = 16;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     for (int k0 = 0; k0 < GP_NB; k0 += KC) {
         __syncthreads();
         for (int q = threadIdx.x; q < KC * GP_NB; q += kThreads) {
             // element (row or column index u, k0 + kq), read along the contiguous index
+            float2 a, bv;
+            int ka, ua, kb, ub;
             if (!TA) {
-                const int kq = q / GP_NB, u = q % GP_NB;
-                As[kq][u] = A[(size_t)(k0 + kq) * GP_NB + u];           // A(u, k)
+                ka = q / GP_NB; ua = q % GP_NB;
+                a = A[(size_t)(k0 + ka) * GP_NB + ua];          // A(u, k)
             } else {
-                const int u = q / KC, kq = q % KC;
-                As[kq][u] = A[(size_t)u * GP_NB + k0 + kq];             // A(k, u)
+                ua = q / KC; ka = q % KC;
+                a = A[(size_t)ua * GP_NB + k0 + ka];            // A(k, u)
             }
             if (!TB) {
-                const int u = q / KC, kq = q % KC;
-                Bs[kq][u] = B[(size_t)u * GP_NB + k0 + kq];             // B(k, u)
+                ub = q / KC; kb = q % KC;
+                bv = B[(size_t)ub * GP_NB + k0 + kb];           // B(k, u)
             } else {
-                const int kq = q / GP_NB, u = q % GP_NB;
-                Bs[kq][u] = B[(size_t)(k0 + kq) * GP_NB + u];           // B(u, k)
+                kb = q / GP_NB; ub = q % GP_NB;
+                bv = B[(size_t)(k0 + kb) * GP_NB + ub];         // B(u, k)
             }
+            As[ka][ua] = dfl{a.x, a.y};
+            Bs[kb][ub] = dfl{bv.x, bv.y};
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int k = 0; k < KC; ++k) {
-            double a[8], bb[8];
+            dfl a[8], bb[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
@@ -66,47 +77,64 @@ __device__ __forceinline__ void tile_mma(double (&acc)[8][8], const double* A, c
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = df_fma(a[i], bb[j], acc[i][j]);
         }
     }
 }
 
-__device__ __forceinline__ void acc_zero(double (&acc)[8][8]) {
+__device__ __forceinline__ void acc_zero(dfl (&acc)[8][8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 8; ++j) acc[i][j] = dfl{0.f, 0.f};
 }
 
-__device__ __forceinline__ void acc_store(const double (&acc)[8][8], double* C, double scale) {
+__device__ __forceinline__ void acc_store(const dfl (&acc)[8][8], float2* C, bool negate) {
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
     for (int j = 0; j < 8; ++j)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) C[(size_t)(ty + 16 * j) * GP_NB + tx + 16 * i] = scale * acc[i][j];
+        for (int i = 0; i < 8; ++i) {
+            const dfl v = negate ? df_neg(acc[i][j]) : acc[i][j];
+            C[(size_t)(ty + 16 * j) * GP_NB + tx + 16 * i] = make_float2(v.hi, v.lo);
+        }
 }
 
-// X_JJ = L_JJ^-1 (lower; zeros above the diagonal), one CTA per (J, instance):
-// row i of W from rows j < i, W_ij = -(1/L_ii) sum_{k=j}^{i-1} L_ik W_kj.
+// The factor, rewritten in place as double-float (hi, lo) pairs.
+__global__ void k_factor_to_df(Batch b, size_t elems) {
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    double* A = b.A + (size_t)t * b.inst_stride;
+    float2* F = reinterpret_cast<float2*>(A);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < elems; q += (size_t)gridDim.x * blockDim.x) {
+        const dfl v = df_from_double(A[q]);
+        F[q] = make_float2(v.hi, v.lo);
+    }
+}
+
+// X_JJ = L_JJ^-1 (lower; zeros above the diagonal), one CTA per (J, instance),
+// in double: row i of W from rows j < i, W_ij = -(1/L_ii) sum_{k=j}^{i-1} L_ik W_kj.
 // Dynamic smem: L and W as packed lower triangles (row r at r (r + 1) / 2).
 constexpr int kPackedTri = GP_NB * (GP_NB + 1) / 2;
 __device__ __forceinline__ int prow(int r) { return r * (r + 1) / 2; }
 
-__global__ void __launch_bounds__(kThreads) k_inv_diag(Batch b, double* X) {
+__global__ void __launch_bounds__(kThreads) k_inv_diag(Batch b, const float2* L2, float2* X) {
     extern __shared__ double sm[];
     double* Lp = sm;
     double* Wp = sm + kPackedTri;
     __shared__ double dinv[GP_NB];
     const int J = blockIdx.x, t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
-    const double* L = tile_at(b.A, b.inst_stride, t, J, J, b.nt);
+    const float2* L = tile_at(L2, b.inst_stride, t, J, J, b.nt);
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) {
         const int r = q % GP_NB, c = q / GP_NB;
         if (r >= c) {
-            Lp[prow(r) + c] = L[q];
+            const float2 v = L[q];
+            const double l = (double)v.x + (double)v.y;
+            Lp[prow(r) + c] = l;
             Wp[prow(r) + c] = 0.0;
+            if (r == c) dinv[r] = 1.0 / l;    // one division per pivot
         }
-        if (r == c) dinv[r] = 1.0 / L[q];    // one division per pivot
     }
     __syncthreads();
     for (int i = 0; i < GP_NB; ++i) {
@@ -119,38 +147,39 @@ __global__ void __launch_bounds__(kThreads) k_inv_diag(Batch b, double* X) {
         if (threadIdx.x == 0) Wp[prow(i) + i] = inv;
         __syncthreads();
     }
-    double* Xt = tile_at(X, b.inst_stride, t, J, J, b.nt);
+    float2* Xt = tile_at(X, b.inst_stride, t, J, J, b.nt);
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) {
         const int r = q % GP_NB, c = q / GP_NB;
-        Xt[q] = (r >= c) ? Wp[prow(r) + c] : 0.0;
+        const dfl v = (r >= c) ? df_from_double(Wp[prow(r) + c]) : dfl{0.f, 0.f};
+        Xt[q] = make_float2(v.hi, v.lo);
     }
 }
 
 // Tile diagonal s of X = L^-1: X_IJ, I = J + s, for J = blockIdx.x.
-__global__ void __launch_bounds__(kThreads) k_trtri_step(Batch b, double* X, int s) {
-    __shared__ double As[16][GP_NB];
-    __shared__ double Bs[16][GP_NB];
+__global__ void __launch_bounds__(kThreads, 1) k_trtri_step(Batch b, const float2* L2, float2* X, int s) {
+    __shared__ dfl As[16][GP_NB];
+    __shared__ dfl Bs[16][GP_NB];
     const int J = blockIdx.x, t = blockIdx.y, I = J + s, nt = b.nt;
     if (b.st[t].status != GP_OK) return;
-    double acc[8][8];
+    dfl acc[8][8];
     acc_zero(acc);
     for (int K = J; K < I; ++K)
-        tile_mma<false, false>(acc, tile_at(b.A, b.inst_stride, t, I, K, nt),
-                               tile_at(X, b.inst_stride, t, K, J, nt), As, Bs);
-    double* Xij = tile_at(X, b.inst_stride, t, I, J, nt);
+        tile_mma<false, false>(acc, tile_at(L2, b.inst_stride, t, I, K, nt), tile_at(X, b.inst_stride, t, K, J, nt),
+                               As, Bs);
+    float2* Xij = tile_at(X, b.inst_stride, t, I, J, nt);
     __syncthreads();
-    acc_store(acc, Xij, 1.0);                 // S = sum_K L_IK X_KJ, for the product below
+    acc_store(acc, Xij, false);               // S = sum_K L_IK X_KJ, for the product below
     __syncthreads();
     acc_zero(acc);
     tile_mma<false, false>(acc, tile_at(X, b.inst_stride, t, I, I, nt), Xij, As, Bs);
     __syncthreads();                          // every read of S is done
-    acc_store(acc, Xij, -1.0);
+    acc_store(acc, Xij, true);
 }
 
 // (R^-1)_IJ = sum_{K >= I} X_KI' X_KJ for the lower tile q = blockIdx.x.
-__global__ void __launch_bounds__(kThreads) k_lauum(Batch b, const double* X, double* Ri) {
-    __shared__ double As[16][GP_NB];
-    __shared__ double Bs[16][GP_NB];
+__global__ void __launch_bounds__(kThreads, 1) k_lauum(Batch b, const float2* X, float2* Ri) {
+    __shared__ dfl As[16][GP_NB];
+    __shared__ dfl Bs[16][GP_NB];
     const int t = blockIdx.y, nt = b.nt;
     if (b.st[t].status != GP_OK) return;
     int J = 0;
@@ -159,12 +188,12 @@ __global__ void __launch_bounds__(kThreads) k_lauum(Batch b, const double* X, do
         while (rem >= nt - J) { rem -= nt - J; ++J; }
     }
     const int I = J + (int)(blockIdx.x - tile_index(J, J, nt));
-    double acc[8][8];
+    dfl acc[8][8];
     acc_zero(acc);
     for (int K = I; K < nt; ++K)
-        tile_mma<true, false>(acc, tile_at(const_cast<double*>(X), b.inst_stride, t, K, I, nt),
-                              tile_at(const_cast<double*>(X), b.inst_stride, t, K, J, nt), As, Bs);
-    acc_store(acc, tile_at(Ri, b.inst_stride, t, I, J, nt), 1.0);
+        tile_mma<true, false>(acc, tile_at(X, b.inst_stride, t, K, I, nt), tile_at(X, b.inst_stride, t, K, J, nt),
+                              As, Bs);
+    acc_store(acc, tile_at(Ri, b.inst_stride, t, I, J, nt), false);
 }
 
 // e = b - mu_hat a in column 1 of Z (w = L^-T e follows by the backward solve)
@@ -186,9 +215,12 @@ __global__ void k_residual_vec(Batch b, double* Z, size_t zs) {
 //                         = -h / (1 + h) c D_k          (3/2, h = c theta_k D_k)
 //                         = -h (1 + h) / (3 + 3h + h^2) c D_k   (5/2)
 template <int DB>
-__global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const double* Ri, const double* Z, size_t zs,
+__global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const float2* Ri, const double* Z, size_t zs,
                                                          double* partial, int ntiles) {
     __shared__ double red[kThreads / 32][DB];
+    __shared__ dfl tab[64];
+    fill_exp2_table(tab);
+    __syncthreads();
     const int t = blockIdx.y, nt = b.nt, n = b.n, d = b.d;
     const InstState st = b.st[t];
     if (st.status != GP_OK) return;
@@ -198,7 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const double* 
         while (rem >= nt - J) { rem -= nt - J; ++J; }
     }
     const int I = J + (int)(blockIdx.x - tile_index(J, J, nt));
-    const double* R1 = tile_at(const_cast<double*>(Ri), b.inst_stride, t, I, J, nt);
+    const float2* R1 = tile_at(Ri, b.inst_stride, t, I, J, nt);
+    const int pmode = pow_mode(b.p);
+    const dfl pd = df_from_double(b.p);
     const double* w = Z + (size_t)t * zs + (size_t)nt * GP_NB;
     const double* th = b.theta + (size_t)t * d;
     const double nq = n / st.Q;
@@ -212,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const double* 
         const int r = q % GP_NB, c = q / GP_NB;
         const int gi = I * GP_NB + r, gj = J * GP_NB + c;
         if (gi >= n || gj >= n || gi <= gj) continue;
-        const double m = R1[q] - nq * w[gi] * w[gj];
+        const double m = ((double)R1[q].x + (double)R1[q].y) - nq * w[gi] * w[gj];
         double D[DB], h[DB];
         double s = 0.0, qp = 1.0;
 #pragma unroll
@@ -221,7 +255,10 @@ __global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const double* 
             h[k] = 0.0;
             if (k < d) {
                 const double a = fabs(b.x[(size_t)gi * d + k] - b.x[(size_t)gj * d + k]);
-                D[k] = matern ? a : ((b.p == 2.0) ? a * a : (b.p == 1.0 ? a : (a == 0.0 ? 0.0 : pow(a, b.p))));
+                // |dx|^p for general p in double-float (FP64 pow is scarce here)
+                D[k] = (matern || pmode == kPowOne) ? a
+                                                    : (pmode == kPowTwo ? a * a
+                                                                        : df_to_double(df_powabs(df_from_double(a), pmode, b.p, pd, tab)));
                 h[k] = cm * th[k] * D[k];
                 s += h[k];
                 if (matern) qp *= matern_q(h[k], corr);
@@ -278,29 +315,36 @@ cudaError_t launch_grad(const Batch& b, double* Z, size_t zs, double* X, double*
     int k = 0;
     k_residual_vec<<<b.count, kThreads, 0, s>>>(b, Z, zs);
     ++k;
-    cudaError_t e = launch_backward_solve(b, Z, zs, 1, s);   // w = L^-T (b - mu a)
+    cudaError_t e = launch_backward_solve(b, Z, zs, 1, s);   // w = L^-T (b - mu a), double factor
     if (e != cudaSuccess) return e;
     ++k;
+    // from here on the factor, X and R^-1 are double-float tiles
+    const size_t elems = (size_t)ntiles * GP_TILE_ELEMS;
+    k_factor_to_df<<<dim3(64, b.count), kThreads, 0, s>>>(b, elems);
+    ++k;
+    const float2* L2 = reinterpret_cast<const float2*>(b.A);
+    float2* X2 = reinterpret_cast<float2*>(X);
+    float2* R2 = reinterpret_cast<float2*>(Ri);
     {
         const size_t smem = (size_t)2 * kPackedTri * sizeof(double);
         static std::atomic<size_t> attr[kMaxDevices];
         e = raise_smem_limit(k_inv_diag, smem, attr);
         if (e != cudaSuccess) return e;
-        k_inv_diag<<<dim3(nt, b.count), kThreads, smem, s>>>(b, X);
+        k_inv_diag<<<dim3(nt, b.count), kThreads, smem, s>>>(b, L2, X2);
         ++k;
     }
     for (int st = 1; st < nt; ++st) {
-        k_trtri_step<<<dim3(nt - st, b.count), kThreads, 0, s>>>(b, X, st);
+        k_trtri_step<<<dim3(nt - st, b.count), kThreads, 0, s>>>(b, L2, X2, st);
         ++k;
     }
-    k_lauum<<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, X, Ri);
+    k_lauum<<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, X2, R2);
     ++k;
     if (b.d <= 4)
-        k_grad_tiles<4><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, Ri, Z, zs, partial, ntiles);
+        k_grad_tiles<4><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, R2, Z, zs, partial, ntiles);
     else if (b.d <= 8)
-        k_grad_tiles<8><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, Ri, Z, zs, partial, ntiles);
+        k_grad_tiles<8><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, R2, Z, zs, partial, ntiles);
     else
-        k_grad_tiles<16><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, Ri, Z, zs, partial, ntiles);
+        k_grad_tiles<16><<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, R2, Z, zs, partial, ntiles);
     ++k;
     k_grad_reduce<<<b.count, 64, 0, s>>>(b, partial, ntiles, status, grad);
     ++k;
