@@ -19,6 +19,41 @@ class _Bowl:
         return {"nll": torch.as_tensor(f), "status": torch.zeros(len(f), dtype=torch.int32)}
 
 
+class _BowlGrad(_Bowl):
+    """The same bowl with its gradient in theta, as gp.Context.nll_grad_batch
+    returns it: d/dtheta_k sum (log10 theta - t)^2 = 2 (z_k - t_k) / (theta_k ln 10)."""
+
+    def nll_grad_batch(self, x, y, th, p, delta):
+        t = th.cpu().numpy()
+        z = np.log10(t)
+        f = np.sum((z - self.target) ** 2, axis=1)
+        g = 2.0 * (z - self.target) / (t * np.log(10.0))
+        return {"nll": torch.as_tensor(f), "grad": torch.as_tensor(g),
+                "status": torch.zeros(len(f), dtype=torch.int32)}
+
+
+class _Ridge(_BowlGrad):
+    """A minimum outside the box in one coordinate: the search must stop on
+    the boundary there (projected gradient)."""
+    target = np.array([-0.7, 1.6])
+
+
+def test_gradient_search_on_a_bowl():
+    x = torch.zeros((5, 2), dtype=torch.float64)
+    y = torch.zeros(5, dtype=torch.float64)
+    z, f, evals, hist = fit.gradient_search(_BowlGrad(), x, y, 2.0, 0.0, starts=8, iterations=40, seed=5)
+    assert all(a >= b for a, b in zip(hist, hist[1:]))
+    assert f < 1e-10 and np.max(np.abs(z - _BowlGrad.target)) < 1e-5
+    assert evals <= 8 * 41
+    z2, f2, _, _ = fit.gradient_search(_BowlGrad(), x, y, 2.0, 0.0, starts=8, iterations=40, seed=5)
+    assert np.array_equal(z2, z) and f2 == f                     # seeded: reproducible
+    z4, f4, e4, _ = fit.gradient_search(_BowlGrad(), x, y, 2.0, 0.0, iterations=30, z0=np.array([[0.5, -1.5]]))
+    assert e4 <= 31 and f4 < 1e-10                               # one given start
+    zr, fr, _, _ = fit.gradient_search(_Ridge(), x, y, 2.0, 0.0, starts=8, iterations=60, seed=6)
+    assert abs(zr[0] + 0.7) < 1e-4 and zr[1] == fit.HI            # on the box's edge
+    assert abs(fr - 0.6 ** 2) < 1e-8
+
+
 def test_genetic_search_and_refinement_on_a_bowl():
     ctx = _Bowl()
     x = torch.zeros((5, 2), dtype=torch.float64)
@@ -46,8 +81,10 @@ def test_fit_driver_matches_oracle_at_chosen_theta():
     xs = inputs.uniform_design(g, 300, 2)
     ys = inputs.y_trig2(xs)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
-    res = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50)
-    res2 = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50)
+    res = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50,
+                              refine_method="compass")
+    res2 = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=6, population=50,
+                               refine_method="compass")
     assert res["log10_theta"] == res2["log10_theta"] and res["nll"] == res2["nll"]
     th = 10.0 ** np.array(res["log10_theta"])
     o, st = oracle.nll(x, y, th, 2.0, 1e-8)
@@ -57,4 +94,36 @@ def test_fit_driver_matches_oracle_at_chosen_theta():
     yo, _, _ = oracle.predict(x, y, th, 2.0, 1e-8, xs, want_var=False)
     sspe_o = float(np.sum((ys - yo) ** 2))
     assert abs(res["sspe"] - sspe_o) <= 1e-8 * max(1.0, sspe_o)
+    ctx.close()
+
+
+@pytest.mark.gpu
+def test_gradient_search_reaches_the_genetic_optimum():
+    """Multi-start gradient search on gp_nll_grad_batch: its optimum is no
+    worse than the GA's (double-refined) one, and -2logL there is the
+    oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1203_1269_gb300 import gp, inputs
+    ctx = gp.Context(0)
+    g = inputs.rng(78)
+    x = inputs.random_lhd(g, 200, 2)
+    y = inputs.y_trig2(x)
+    xs = inputs.uniform_design(g, 300, 2)
+    ys = inputs.y_trig2(xs)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    ga = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=10, population=60,
+                             refine_method="compass")
+    gr = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, search="grad", starts=12, iterations=40)
+    print(f"\nGA + refine: {ga['nll']:.6f} at {ga['log10_theta']} ({ga['evaluations']} evaluations); "
+          f"gradient: {gr['nll']:.6f} at {gr['log10_theta']} ({gr['evaluations']} evaluations)")
+    assert gr["nll"] <= ga["nll"] + 1e-6 * abs(ga["nll"])
+    # the GA's best point refined by gradient steps instead of the compass search
+    gg = fit.fit_and_predict(ctx, dev(x), dev(y), 2.0, 1e-8, dev(xs), ys, generations=10, population=60,
+                             refine_method="grad")
+    assert gg["nll"] <= ga["nll"] + 1e-9 * abs(ga["nll"])
+    th = 10.0 ** np.array(gr["log10_theta"])
+    o, st = oracle.nll(x, y, th, 2.0, 1e-8)
+    assert st == 0 and abs(gr["nll"] - o["nll"]) <= 1e-9 * abs(o["nll"]) + 1e-9
     ctx.close()
