@@ -178,7 +178,7 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
 
 // Bytes of workspace per instance of the split-precision path.
 struct MixedSizes {
-    size_t A, PS, PE, WS, WE, PF, FE, WT, Z, RP, st, per;   // WT also sizes WR
+    size_t A, PS, PE, WS, WE, PF, FE, WT, Z, RP, SC, st, per;   // WT also sizes WR
 };
 
 MixedSizes mixed_sizes(int n, int s) {
@@ -196,8 +196,9 @@ MixedSizes mixed_sizes(int n, int s) {
     z.WT = align256((size_t)nt * GP_TILE_ELEMS * sizeof(float2));
     z.Z = align256((size_t)gp::kZCols * nt * GP_NB * sizeof(float2));
     z.RP = align256((size_t)gp::packed_tiles(nt) * gp::kRpTile * sizeof(float2));
+    z.SC = align256((size_t)nt * sizeof(int));
     z.st = align256(sizeof(gp::InstState));
-    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + 2 * z.WT + z.Z + z.RP + z.st;
+    z.per = 2 * z.A + z.PS + z.PE + z.WS + z.WE + z.PF + z.FE + 2 * z.WT + z.Z + z.RP + z.SC + z.st;
     return z;
 }
 
@@ -218,6 +219,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.WR = (float2*)c; c += z.WT * Tc;
     mb.Z = (float2*)c; c += z.Z * Tc;
     mb.RP = (float2*)c; c += z.RP * Tc;
+    mb.SC = (int*)c; c += z.SC * Tc;
     mb.st = (gp::InstState*)c; c += z.st * Tc;
     mb.err = (int*)c;
     mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = slices;
@@ -239,6 +241,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.fwd = y != nullptr;
     mb.z_stride = z.Z / sizeof(float2);
     mb.rp_stride = z.RP / sizeof(float2);
+    mb.sc_stride = z.SC / sizeof(int);
     mb.y = y;
     return mb;
 }

@@ -119,17 +119,20 @@ struct MixedBatch {
                                   // residual columns, 1 / L_ii, two condition-estimate
                                   // columns, |R| row sums
     size_t z_stride;
-    float2* RP;                   // per-tile partial sums of the tile-parallel residual (or null)
+    float2* RP;                   // per-tile partial sums of the tile-parallel solves and residual
     size_t rp_stride;
+    int* SC;                      // per-block counters of the tile-parallel substitutions
+    size_t sc_stride;
     const double* y;
     InstState* st;
     int* err;                     // set when a bounded device wait gave up
 };
 
 constexpr int kZCols = 8;
-// kernel launches of one forward or backward substitution pass (a diagonal
-// step per block column, a tile step between consecutive ones)
-inline int subst_launches(int nt) { return 2 * nt - 1; }
+// kernel launches of one forward or backward substitution pass (the first
+// block's diagonal step, then a tile step per further block column that
+// also finishes the next block)
+inline int subst_launches(int nt) { return nt; }
 // partial sums of the tile-parallel residual per lower tile: row products
 // [2 column halves][2 right-hand sides][128], then column products [2][2][64]
 constexpr int kRpTile = 2 * 2 * GP_NB + 2 * 2 * (GP_NB / 2);

@@ -523,19 +523,38 @@ __device__ __forceinline__ float2* rp_part(const MixedBatch& b, int t, int I, in
     return b.RP + (size_t)t * b.rp_stride + (size_t)tile_index(I, J, b.nt) * kRpTile;
 }
 
+__device__ __forceinline__ dfl df_load_cg(const float2* p) {
+    const float2 v = __ldcg(p);
+    return {v.x, v.y};
+}
+
+// The diagonal steps run either as their own launch (the first block of a
+// pass) or inside the tile launch before them, by whichever of the two CTAs
+// writing the block's last partial products finishes second: each of them
+// fences its partial products device-wide and counts itself on the block's
+// counter (zeroed per pass); the second reads all the block's partial
+// products in the same fixed order as a separate launch would.  No CTA
+// waits for another.
+__device__ __forceinline__ bool second_of_two(const MixedBatch& b, int t, int blk) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(b.SC + (size_t)t * b.sc_stride + blk, 1) == 1);
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
 // forward, block J: z_J <- W_J (z_J - sum_{K<J} L_JK z_K), W_J = L_JJ^-1
 // (column-major WT: thread (k, r) reads row r of W along its columns)
-__global__ void __launch_bounds__(kSubThreads) k_fwd_diag(MixedBatch b, int c0, int J) {
-    __shared__ dfl rhs[2][GP_NB];
-    const int t = blockIdx.x;
-    if (!sub_active(b, t)) return;
+__device__ __forceinline__ void fwd_diag_step(const MixedBatch& b, int t, int c0, int J, dfl (*rhs)[GP_NB]) {
     const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
     float2* z = zcol(b, t, c0 + k) + (size_t)J * GP_NB;
     dfl v = df_load(z + r);
 #pragma unroll 4
     for (int K = 0; K < J; ++K) {
         const float2* pp = rp_part(b, t, J, K) + k * GP_NB + r;
-        v = df_sub(v, df_add(df_load(pp), df_load(pp + 2 * GP_NB)));
+        v = df_sub(v, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
     }
     rhs[k][r] = v;
     __syncthreads();
@@ -548,15 +567,25 @@ __global__ void __launch_bounds__(kSubThreads) k_fwd_diag(MixedBatch b, int c0, 
     df_store(z + r, df_add(df_add(x[0], x[1]), df_add(x[2], x[3])));
 }
 
-// forward, tiles (I, J), I > J, half h of the columns: L_IJ(:, h) z_J(h)
+__global__ void __launch_bounds__(kSubThreads) k_fwd_diag(MixedBatch b, int c0, int J) {
+    __shared__ dfl rhs[2][GP_NB];
+    const int t = blockIdx.x;
+    if (!sub_active(b, t)) return;
+    fwd_diag_step(b, t, c0, J, rhs);
+}
+
+// forward, tiles (I, J), I > J, half h of the columns: L_IJ(:, h) z_J(h);
+// the CTA finishing tile (J + 1, J) second then takes block J + 1's
+// diagonal step
 __global__ void __launch_bounds__(kSubThreads) k_fwd_tiles(MixedBatch b, int c0, int J) {
     __shared__ dfl xs[2][GP_NB / 2];
     __shared__ dfl part[2][2][GP_NB];
+    __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.y;
     if (!sub_active(b, t)) return;
     const int I = J + 1 + (blockIdx.x >> 1), h = blockIdx.x & 1;
     const int tid = threadIdx.x;
-    // W_{J+1} heads for L2 for the next diagonal step
+    // W_{J+1} heads for L2 for the diagonal step
     if (tid == 0 && I == J + 1 && h == 0)
         prefetch_l2(b.WT + (size_t)t * b.wt_stride + (size_t)(J + 1) * GP_TILE_ELEMS, GP_TILE_ELEMS * sizeof(float2));
     if (tid < GP_NB) xs[tid >> 6][tid & 63] = df_load(zcol(b, t, c0 + (tid >> 6)) + (size_t)J * GP_NB + 64 * h + (tid & 63));
@@ -576,15 +605,14 @@ __global__ void __launch_bounds__(kSubThreads) k_fwd_tiles(MixedBatch b, int c0,
     __syncthreads();
     const int k = tid >> 7;
     df_store(rp_part(b, t, I, J) + (h * 2 + k) * GP_NB + r, df_add(part[0][k][r], part[1][k][r]));
+    if (I == J + 1 && second_of_two(b, t, I)) fwd_diag_step(b, t, c0, I, rhs);
 }
 
 // backward, block K: z_K <- W_K^T (z_K - sum_{K' > K} L_K'K^T z_K'); W^T
 // from the row-major copy WR (thread (k, c) reads column c of W along its
 // rows); with add_to >= 0 the result is also added into (add_to, add_to + 1)
-__global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, int K, int add_to) {
-    __shared__ dfl rhs[2][GP_NB];
-    const int t = blockIdx.x;
-    if (!sub_active(b, t)) return;
+__device__ __forceinline__ void bwd_diag_step(const MixedBatch& b, int t, int c0, int K, int add_to,
+                                              dfl (*rhs)[GP_NB]) {
     const int nt = b.nt;
     const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
     float2* z = zcol(b, t, c0 + k) + (size_t)K * GP_NB;
@@ -592,7 +620,7 @@ __global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, 
 #pragma unroll 4
     for (int K2 = K + 1; K2 < nt; ++K2) {
         const float2* pp = rp_part(b, t, K2, K) + k * GP_NB + c;
-        v = df_sub(v, df_add(df_load(pp), df_load(pp + 2 * GP_NB)));
+        v = df_sub(v, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
     }
     rhs[k][c] = v;
     __syncthreads();
@@ -610,14 +638,23 @@ __global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, 
     }
 }
 
+__global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, int K, int add_to) {
+    __shared__ dfl rhs[2][GP_NB];
+    const int t = blockIdx.x;
+    if (!sub_active(b, t)) return;
+    bwd_diag_step(b, t, c0, K, add_to, rhs);
+}
+
 // backward, tiles (K, I), I < K, half h of the rows: L_KI(h, :)^T z_K(h);
 // the half tile is staged column by column (64 rows + 1 of padding) so that
-// thread c walks column c conflict-free
+// thread c walks column c conflict-free; the CTA finishing tile (K, K - 1)
+// second then takes block K - 1's diagonal step
 constexpr int kBwdTs = GP_NB / 2 + 1;
-__global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0, int K) {
+__global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0, int K, int add_to) {
     extern __shared__ dfl T[];                  // GP_NB x kBwdTs
     __shared__ dfl xs[2][GP_NB / 2];
     __shared__ dfl part[2][2][GP_NB];
+    __shared__ dfl rhs[2][GP_NB];
     const int t = blockIdx.y;
     if (!sub_active(b, t)) return;
     const int I = blockIdx.x >> 1, h = blockIdx.x & 1;
@@ -647,6 +684,8 @@ __global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0,
     __syncthreads();
     const int k = tid >> 7;
     df_store(rp_part(b, t, K, I) + (h * 2 + k) * GP_NB + c, df_add(part[0][k][c], part[1][k][c]));
+    // the CTA finishing tile (K, K - 1) second takes block K - 1's diagonal step
+    if (I == K - 1 && second_of_two(b, t, I)) bwd_diag_step(b, t, c0, I, add_to, rhs);
 }
 
 // Residual r = b - R x of the solution columns (0, 1) into columns (2, 3),
@@ -864,10 +903,11 @@ cudaError_t launch_df_forward(const MixedBatch& b, int c0, int init, cudaStream_
         cudaError_t e = launch_rhs_init(b, s);
         if (e != cudaSuccess) return e;
     }
-    for (int J = 0; J < b.nt; ++J) {
-        k_fwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, J);
-        if (J + 1 < b.nt) k_fwd_tiles<<<dim3(2 * (b.nt - 1 - J), b.count), kSubThreads, 0, s>>>(b, c0, J);
-    }
+    cudaError_t e = cudaMemsetAsync(b.SC, 0, (size_t)b.count * b.sc_stride * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_fwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, 0);
+    for (int J = 0; J + 1 < b.nt; ++J)
+        k_fwd_tiles<<<dim3(2 * (b.nt - 1 - J), b.count), kSubThreads, 0, s>>>(b, c0, J);
     return cudaGetLastError();
 }
 
@@ -876,10 +916,11 @@ cudaError_t launch_df_backward(const MixedBatch& b, int c0, int add_to, cudaStre
     static std::atomic<size_t> attr[kMaxDevices];
     cudaError_t e = raise_smem_limit(k_bwd_tiles, smem, attr);
     if (e != cudaSuccess) return e;
-    for (int K = b.nt - 1; K >= 0; --K) {
-        k_bwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, K, add_to);
-        if (K > 0) k_bwd_tiles<<<dim3(2 * K, b.count), kSubThreads, smem, s>>>(b, c0, K);
-    }
+    e = cudaMemsetAsync(b.SC, 0, (size_t)b.count * b.sc_stride * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_bwd_diag<<<b.count, kSubThreads, 0, s>>>(b, c0, b.nt - 1, add_to);
+    for (int K = b.nt - 1; K > 0; --K)
+        k_bwd_tiles<<<dim3(2 * K, b.count), kSubThreads, smem, s>>>(b, c0, K, add_to);
     return cudaGetLastError();
 }
 
