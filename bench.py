@@ -20,6 +20,7 @@ region, and the CPU oracle timed on a bounded sample on the host cores.
 """
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -130,11 +131,19 @@ def workload_for_rank(rank, n=4000, T=256):
     return w
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed: what the
+    compiler sees, so that editing a comment keeps a capture valid."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(files):
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_1203_1269_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1203_1269_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -10,8 +10,8 @@ namespace gp {
 
 namespace {
 
-constexpr int kEpiWarps = 8;                  // epilogue warps: kEpiWarps / 4 per tensor-memory lane quarter
-                                               // (16 measured 2% slower on the update)
+constexpr int kEpiWarps = 8;                  // epilogue warps of the plain kernels: kEpiWarps / 4 per
+                                               // tensor-memory lane quarter
 constexpr int kEpiParts = kEpiWarps / 4;       // column parts of a tile
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 MMA, then the epilogue
 constexpr int kEpiThreads = 32 * kEpiWarps;
@@ -95,11 +95,13 @@ __device__ __forceinline__ void issue_stage_ns(int ns, bool first, uint32_t tacc
 // issued together).  Every wait is bounded; a timeout marks the instance
 // GP_ETIMEOUT and stops the CTA after its copies and MMAs have landed.
 //
-// ER (early release; MODE 1, NT = 128 only): the epilogue first reads and
+// ER (early release; the 128-column update and the panel solve, the default
+// where the built kernel's registers allow it): the epilogue first reads and
 // combines every accumulator group of its columns into registers, releases
-// tensor memory to the MMA warp, and only then reads, updates and writes C,
-// so that C's round trip overlaps the next tile's MMAs.  Warps 2, 3 idle;
-// the epilogue warps are 4 .. 3 + kEpiWarpsER and hold kRegsHigh registers each.
+// tensor memory to the MMA warp, and only then reads, updates and writes C
+// (or stores the panel), so that this overlaps the next tile's MMAs.  Warps
+// 2, 3 idle; the epilogue warps are 4 .. 3 + kEpiWarpsER and hold kRegsHigh
+// registers each.
 template <int MODE, int NT, int NG, bool ER = false>
 __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
     k_split_gemm(MixedBatch b, int J, int per_inst, int kind) {
