@@ -545,33 +545,59 @@ __device__ __forceinline__ bool second_of_two(const MixedBatch& b, int t, int bl
     return last;
 }
 
-// forward, block J: z_J <- W_J (z_J - sum_{K<J} L_JK z_K), W_J = L_JJ^-1
-// (column-major WT: thread (k, r) reads row r of W along its columns)
-__device__ __forceinline__ void fwd_diag_step(const MixedBatch& b, int t, int c0, int J, dfl (*rhs)[GP_NB]) {
-    const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
-    float2* z = zcol(b, t, c0 + k) + (size_t)J * GP_NB;
-    dfl v = df_load(z + r);
+// forward, block J: z_J <- W_J (z_J - sum_{K<J} L_JK z_K), W_J = L_JJ^-1.
+// Thread (r, h) takes both right-hand sides of row r over half h of the
+// terms (every other partial-product tile, then columns 64h .. 64h + 63 of
+// the column-major WT, one load serving both sums); the halves add in a
+// fixed order.  part: 2 x 2 x 128 scratch.
+__device__ __forceinline__ void fwd_diag_step(const MixedBatch& b, int t, int c0, int J, dfl (*rhs)[GP_NB],
+                                              dfl (*part)[2][GP_NB]) {
+    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
+    float2* z0 = zcol(b, t, c0) + (size_t)J * GP_NB;
+    float2* z1 = zcol(b, t, c0 + 1) + (size_t)J * GP_NB;
+    dfl p0 = {0.f, 0.f}, p1 = {0.f, 0.f};
 #pragma unroll 4
-    for (int K = 0; K < J; ++K) {
-        const float2* pp = rp_part(b, t, J, K) + k * GP_NB + r;
-        v = df_sub(v, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
+    for (int K = h; K < J; K += 2) {
+        const float2* pp = rp_part(b, t, J, K) + r;
+        p0 = df_add(p0, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
+        p1 = df_add(p1, df_add(df_load_cg(pp + GP_NB), df_load_cg(pp + 3 * GP_NB)));
     }
-    rhs[k][r] = v;
+    part[h][0][r] = p0;
+    part[h][1][r] = p1;
     __syncthreads();
-    // all 128 columns (W is zero above its diagonal): a fixed trip count
-    // lets the loads run ahead of the four accumulation chains
+    if (h == 0) {
+        rhs[0][r] = df_sub(df_load(z0 + r), df_add(part[0][0][r], part[1][0][r]));
+        rhs[1][r] = df_sub(df_load(z1 + r), df_add(part[0][1][r], part[1][1][r]));
+    }
+    __syncthreads();
+    // 64 columns (W is zero above its diagonal: a fixed trip count lets the
+    // loads run ahead of the accumulation chains)
     const float2* W = b.WT + (size_t)t * b.wt_stride + (size_t)J * GP_TILE_ELEMS;
-    dfl x[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
 #pragma unroll 16
-    for (int c = 0; c < GP_NB; ++c) x[c & 3] = df_fma(df_load(W + (size_t)c * GP_NB + r), rhs[k][c], x[c & 3]);
-    df_store(z + r, df_add(df_add(x[0], x[1]), df_add(x[2], x[3])));
+    for (int c = 64 * h; c < 64 * h + 64; c += 2) {
+        const dfl w0 = df_load(W + (size_t)c * GP_NB + r), w1 = df_load(W + (size_t)(c + 1) * GP_NB + r);
+        a0 = df_fma(w0, rhs[0][c], a0);
+        b0 = df_fma(w0, rhs[1][c], b0);
+        a1 = df_fma(w1, rhs[0][c + 1], a1);
+        b1 = df_fma(w1, rhs[1][c + 1], b1);
+    }
+    __syncthreads();
+    part[h][0][r] = df_add(a0, a1);
+    part[h][1][r] = df_add(b0, b1);
+    __syncthreads();
+    if (h == 0) {
+        df_store(z0 + r, df_add(part[0][0][r], part[1][0][r]));
+        df_store(z1 + r, df_add(part[0][1][r], part[1][1][r]));
+    }
 }
 
 __global__ void __launch_bounds__(kSubThreads) k_fwd_diag(MixedBatch b, int c0, int J) {
     __shared__ dfl rhs[2][GP_NB];
+    __shared__ dfl part[2][2][GP_NB];
     const int t = blockIdx.x;
     if (!sub_active(b, t)) return;
-    fwd_diag_step(b, t, c0, J, rhs);
+    fwd_diag_step(b, t, c0, J, rhs, part);
 }
 
 // forward, tiles (I, J), I > J, half h of the columns: L_IJ(:, h) z_J(h);
@@ -605,44 +631,69 @@ __global__ void __launch_bounds__(kSubThreads) k_fwd_tiles(MixedBatch b, int c0,
     __syncthreads();
     const int k = tid >> 7;
     df_store(rp_part(b, t, I, J) + (h * 2 + k) * GP_NB + r, df_add(part[0][k][r], part[1][k][r]));
-    if (I == J + 1 && second_of_two(b, t, I)) fwd_diag_step(b, t, c0, I, rhs);
+    if (I == J + 1 && second_of_two(b, t, I)) fwd_diag_step(b, t, c0, I, rhs, part);
 }
 
 // backward, block K: z_K <- W_K^T (z_K - sum_{K' > K} L_K'K^T z_K'); W^T
-// from the row-major copy WR (thread (k, c) reads column c of W along its
-// rows); with add_to >= 0 the result is also added into (add_to, add_to + 1)
+// from the row-major copy WR (thread (c, h) reads column c of W along rows
+// 64h .. 64h + 63, both right-hand sides per load; the partial-product
+// tiles alternate between the halves); the halves add in a fixed order.
+// With add_to >= 0 the result is also added into (add_to, add_to + 1).
 __device__ __forceinline__ void bwd_diag_step(const MixedBatch& b, int t, int c0, int K, int add_to,
-                                              dfl (*rhs)[GP_NB]) {
+                                              dfl (*rhs)[GP_NB], dfl (*part)[2][GP_NB]) {
     const int nt = b.nt;
-    const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
-    float2* z = zcol(b, t, c0 + k) + (size_t)K * GP_NB;
-    dfl v = df_load(z + c);
+    const int c = threadIdx.x & 127, h = threadIdx.x >> 7;
+    float2* z0 = zcol(b, t, c0) + (size_t)K * GP_NB;
+    float2* z1 = zcol(b, t, c0 + 1) + (size_t)K * GP_NB;
+    dfl p0 = {0.f, 0.f}, p1 = {0.f, 0.f};
 #pragma unroll 4
-    for (int K2 = K + 1; K2 < nt; ++K2) {
-        const float2* pp = rp_part(b, t, K2, K) + k * GP_NB + c;
-        v = df_sub(v, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
+    for (int K2 = K + 1 + h; K2 < nt; K2 += 2) {
+        const float2* pp = rp_part(b, t, K2, K) + c;
+        p0 = df_add(p0, df_add(df_load_cg(pp), df_load_cg(pp + 2 * GP_NB)));
+        p1 = df_add(p1, df_add(df_load_cg(pp + GP_NB), df_load_cg(pp + 3 * GP_NB)));
     }
-    rhs[k][c] = v;
+    part[h][0][c] = p0;
+    part[h][1][c] = p1;
     __syncthreads();
-    // all 128 rows (W is zero above its diagonal): a fixed trip count lets
-    // the loads run ahead of the four accumulation chains
+    if (h == 0) {
+        rhs[0][c] = df_sub(df_load(z0 + c), df_add(part[0][0][c], part[1][0][c]));
+        rhs[1][c] = df_sub(df_load(z1 + c), df_add(part[0][1][c], part[1][1][c]));
+    }
+    __syncthreads();
     const float2* Wr = b.WR + (size_t)t * b.wt_stride + (size_t)K * GP_TILE_ELEMS;
-    dfl xa[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    dfl a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
 #pragma unroll 16
-    for (int r = 0; r < GP_NB; ++r) xa[r & 3] = df_fma(df_load(Wr + (size_t)r * GP_NB + c), rhs[k][r], xa[r & 3]);
-    const dfl x = df_add(df_add(xa[0], xa[1]), df_add(xa[2], xa[3]));
-    df_store(z + c, x);
-    if (add_to >= 0) {
-        float2* acc = zcol(b, t, add_to + k) + (size_t)K * GP_NB + c;
-        df_store(acc, df_add(df_load(acc), x));
+    for (int r = 64 * h; r < 64 * h + 64; r += 2) {
+        const dfl w0 = df_load(Wr + (size_t)r * GP_NB + c), w1 = df_load(Wr + (size_t)(r + 1) * GP_NB + c);
+        a0 = df_fma(w0, rhs[0][r], a0);
+        b0 = df_fma(w0, rhs[1][r], b0);
+        a1 = df_fma(w1, rhs[0][r + 1], a1);
+        b1 = df_fma(w1, rhs[1][r + 1], b1);
+    }
+    __syncthreads();
+    part[h][0][c] = df_add(a0, a1);
+    part[h][1][c] = df_add(b0, b1);
+    __syncthreads();
+    if (h == 0) {
+        const dfl x0 = df_add(part[0][0][c], part[1][0][c]);
+        const dfl x1 = df_add(part[0][1][c], part[1][1][c]);
+        df_store(z0 + c, x0);
+        df_store(z1 + c, x1);
+        if (add_to >= 0) {
+            float2* acc0 = zcol(b, t, add_to) + (size_t)K * GP_NB + c;
+            float2* acc1 = zcol(b, t, add_to + 1) + (size_t)K * GP_NB + c;
+            df_store(acc0, df_add(df_load(acc0), x0));
+            df_store(acc1, df_add(df_load(acc1), x1));
+        }
     }
 }
 
 __global__ void __launch_bounds__(kSubThreads) k_bwd_diag(MixedBatch b, int c0, int K, int add_to) {
     __shared__ dfl rhs[2][GP_NB];
+    __shared__ dfl part[2][2][GP_NB];
     const int t = blockIdx.x;
     if (!sub_active(b, t)) return;
-    bwd_diag_step(b, t, c0, K, add_to, rhs);
+    bwd_diag_step(b, t, c0, K, add_to, rhs, part);
 }
 
 // backward, tiles (K, I), I < K, half h of the rows: L_KI(h, :)^T z_K(h);
@@ -685,7 +736,7 @@ __global__ void __launch_bounds__(kSubThreads) k_bwd_tiles(MixedBatch b, int c0,
     const int k = tid >> 7;
     df_store(rp_part(b, t, K, I) + (h * 2 + k) * GP_NB + c, df_add(part[0][k][c], part[1][k][c]));
     // the CTA finishing tile (K, K - 1) second takes block K - 1's diagonal step
-    if (I == K - 1 && second_of_two(b, t, I)) bwd_diag_step(b, t, c0, I, add_to, rhs);
+    if (I == K - 1 && second_of_two(b, t, I)) bwd_diag_step(b, t, c0, I, add_to, rhs, part);
 }
 
 // Residual r = b - R x of the solution columns (0, 1) into columns (2, 3),
