@@ -98,3 +98,20 @@ def test_grad_full_size_finite_differences(ctx):
     rel = np.abs(G - fd) / np.maximum(np.abs(fd), 1.0)
     print(f"\nn=4000 d=6: |grad| up to {np.abs(G).max():.3e}, max rel diff to central differences {rel.max():.2e}")
     assert rel.max() <= 1e-4
+
+
+def test_grad_chunked_matches_one_chunk(ctx):
+    g = np.random.default_rng(64)
+    x = inputs.random_lhd(g, 260, 2)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 5, 2, lo=0.0, hi=1.0)
+    base = ctx.options()
+    try:
+        ref = ctx.nll_grad_batch(dev(x), dev(y), dev(th), 1.95, 1e-5)
+        ctx.set_options(max_batch=2)
+        got = ctx.nll_grad_batch(dev(x), dev(y), dev(th), 1.95, 1e-5)
+    finally:
+        ctx.set_options(**base)
+    for k in ("nll", "grad", "status"):
+        assert np.array_equal(host(got[k]), host(ref[k]), equal_nan=True), k
+

@@ -310,3 +310,25 @@ def test_few_slices_bounded_by_condition(ctx):
             assert np.all(rel <= cond * c)
     finally:
         ctx.set_options(slices=5)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_chunked_batch_matches_one_chunk(ctx, prec):
+    """A batch cut into workspace chunks (max_batch) gives the same bits as
+    one chunk: each candidate's arithmetic is independent of the others and
+    of the chunking (the split path's per-tile buffers and counters are
+    reused chunk after chunk)."""
+    g = np.random.default_rng(808)
+    x = inputs.random_lhd(g, 389, 3)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 11, 3, lo=-0.5, hi=1.0)
+    base = ctx.options()
+    try:
+        ref = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, prec)
+        ctx.set_options(max_batch=4)
+        got = ctx.nll_batch(dev(x), dev(y), dev(th), 1.95, 1e-6, prec)
+    finally:
+        ctx.set_options(**base)
+    for k in ("nll", "mu", "sigma2", "logdet", "status"):
+        assert np.array_equal(host(got[k]), host(ref[k]), equal_nan=True), k
+
