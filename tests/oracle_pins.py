@@ -491,7 +491,7 @@ def check_grad_finite_differences(orc, seed=47):
     x = g.random((n, d))
     y = np.sin(3 * x[:, 0]) + x[:, 1] * x[:, 2]
     th = np.array([2.0, 0.7, 4.0])
-    for corr, p in (("powexp", 1.95), ("powexp", 1.0), ("matern32", 2.0), ("matern52", 2.0)):
+    for corr, p in (("powexp", 1.95), ("powexp", 1.0), ("matern12", 2.0), ("matern32", 2.0), ("matern52", 2.0)):
         grad, out, st = orc.nll_grad(x, y, th, p, 1e-3, corr=corr)
         assert st == 0
         _, st2 = orc.nll(x, y, th, p, 1e-3, corr=corr)

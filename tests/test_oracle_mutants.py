@@ -51,6 +51,10 @@ MUTANTS = {
     "grad_drops_n_over_q": ("grad[k] = tr - n / Q * quad;", "grad[k] = tr - quad;"),
     "grad_power_wrong": ("    return -pow(a, p);", "    return -pow(a, p - 1.0);"),
     "grad_matern32_dlog": ("return -h / (1.0 + h) * sqrt(3.0) * a;", "return -h * sqrt(3.0) * a;"),
+    "grad_matern52_dlog": ("return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(5.0) * a;",
+                           "return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(3.0) * a;"),
+    "grad_quad_one_sided": ("quad += w[i] * dR * w[j];", "quad += w[i] * dR * w[i];"),
+    "grad_exponential_dlog": ("if (fam == GPO_MATERN12) return -a;", "if (fam == GPO_MATERN12) return -a * a;"),
 }
 
 
