@@ -265,8 +265,12 @@ def check_notpd(orc):
 
 
 def check_cond_estimate(orc, seed=19):
+    """Hager's estimate is a lower bound within a small factor of the exact
+    cond_1 (numpy); the last case is R = I to rounding (cond_1 = 1), where
+    the iteration stops after its first round, so it also fixes the scale of
+    the starting vector."""
     g = np.random.default_rng(seed)
-    for (n, th) in [(20, 5.0), (50, 1.0), (40, 20.0)]:
+    for (n, th) in [(20, 5.0), (50, 1.0), (40, 20.0), (30, 1e4)]:
         x = g.random((n, 2))
         R = orc.corr_matrix(x, [th, th], 1.95, 1e-8)
         L, info = orc.cholesky(R)

@@ -28,7 +28,7 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.mark.parametrize("corr,p", [("powexp", 1.95), ("powexp", 1.0), ("matern32", 2.0), ("matern52", 2.0)])
+@pytest.mark.parametrize("corr,p", [("powexp", 1.95), ("powexp", 1.0), ("matern12", 2.0), ("matern32", 2.0), ("matern52", 2.0)])
 def test_grad_matches_oracle(ctx, corr, p):
     g = np.random.default_rng(61)
     n, d, T, delta = 300, 3, 5, 1e-4

@@ -47,6 +47,9 @@ MUTANTS = {
     "predict_nugget_in_r": ("gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam);",
                             "gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam) + 1e-6;"),
     "cond_no_anorm": ("return anorm * est;", "return est;"),
+    "cond_start_unscaled": ("for (int i = 0; i < n; ++i) v[i] = 1.0 / n;", "for (int i = 0; i < n; ++i) v[i] = 1.0;"),
+    "cond_est_not_abs": ("for (int i = 0; i < n; ++i) est += fabs(yv[i]);", "for (int i = 0; i < n; ++i) est += yv[i];"),
+    "cond_no_second_round": ("if (zmax <= ztv || jmax == jprev) break;", "break;"),
     "grad_trace_sign": ("tr += Ri[(size_t)j * n + i] * dR;", "tr -= Ri[(size_t)j * n + i] * dR;"),
     "grad_drops_n_over_q": ("grad[k] = tr - n / Q * quad;", "grad[k] = tr - quad;"),
     "grad_power_wrong": ("    return -pow(a, p);", "    return -pow(a, p - 1.0);"),
