@@ -22,6 +22,9 @@ MUTANTS = {
     "matern12_squares": ("if (fam == GPO_MATERN12) return exp(-theta * a);",
                          "if (fam == GPO_MATERN12) return exp(-theta * a * a);"),
     "matern32_constant": ("double h = sqrt(3.0) * theta * a;", "double h = sqrt(5.0) * theta * a;"),
+    "matern32_linear_coeff": ("return (1.0 + h) * exp(-h);", "return (1.0 + 0.5 * h) * exp(-h);"),
+    "q_zero_threshold_off": ("return Q <= 16.0 * n * u * u * bb;", "return Q <= 0.0;"),
+    "predict_nugget_ignored": ("double c0 = nugget_in_var ? 1.0 + delta : 1.0;", "double c0 = 1.0;"),
     "matern52_drops_quadratic": ("return (1.0 + h + h * h / 3.0) * exp(-h);", "return (1.0 + h) * exp(-h);"),
     "matern52_quadratic_coeff": ("return (1.0 + h + h * h / 3.0) * exp(-h);",
                                  "return (1.0 + h + h * h / 2.0) * exp(-h);"),
