@@ -16,6 +16,7 @@ With --search grad the GA is replaced by a multi-start gradient search
 (Section 2 names it as a possibly faster alternative) on gp_nll_grad_batch.
 
     python -m paper_1203_1269_gb300.fit [--n 4064] [--d 6] [--prec mixed] [--search ga|grad]
+    python -m paper_1203_1269_gb300.fit --table example1|example2
 """
 import argparse
 import json
@@ -190,6 +191,43 @@ def fit_and_predict(ctx, x, y, p, delta, xs, ys, prec="mixed", seed=0, generatio
     return res
 
 
+# The shapes of the paper's two simulation studies (Section 4, Tables 1-2):
+# design sizes and replications.  The responses are this package's seeded
+# stand-ins (inputs.y_trig2, inputs.y_sinsum), not the paper's test
+# functions, so only the times are comparable in kind.
+TABLES = {
+    "example1": {"d": 2, "sizes": [(16, 10), (32, 10), (64, 10), (128, 10), (256, 10), (512, 10)],
+                 "y": "y_trig2"},
+    "example2": {"d": 6, "sizes": [(64, 10), (256, 10), (1024, 10), (4064, 1)], "y": "y_sinsum"},
+}
+
+
+def replicate(ctx, table, p=1.95, delta=1e-8, prec="mixed", device=None):
+    """One fit per replication (a fresh seeded random LHD of size n, a fixed
+    1000-point test LHD per size) and the means over replications of the
+    time, -2logL, mu, sigma2 and SSPE, per design size."""
+    spec = TABLES[table]
+    d = spec["d"]
+    fy = getattr(inputs, spec["y"])
+    device = device or torch.device("cuda", 0)
+    rows = []
+    for n, reps in spec["sizes"]:
+        gt = inputs.rng(inputs.BASE_SEED + 500 + n)
+        xs = inputs.random_lhd(gt, 1000, d)
+        ys = fy(xs)
+        acc = []
+        for r in range(reps):
+            g = inputs.rng(inputs.BASE_SEED + 600 + 7919 * r + n)
+            x = inputs.random_lhd(g, n, d)
+            y = fy(x)
+            res = fit_and_predict(ctx, _dev(x, device), _dev(y, device), p, delta, _dev(xs, device), ys, prec, seed=r)
+            acc.append([res["seconds"], res["nll"], res["mu"], res["sigma2"], res["sspe"]])
+        m = np.mean(np.array(acc), axis=0)
+        rows.append({"n": n, "replications": reps, "seconds": float(m[0]), "nll": float(m[1]), "mu": float(m[2]),
+                     "sigma2": float(m[3]), "sspe": float(m[4])})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=4064)
@@ -199,7 +237,16 @@ def main():
     ap.add_argument("--search", default="ga", choices=["ga", "grad"])
     ap.add_argument("--refine", default="grad", choices=["grad", "compass"])
     ap.add_argument("--starts", type=int, default=16)
+    ap.add_argument("--table", choices=sorted(TABLES), help="replicate a simulation study's shape instead")
     args = ap.parse_args()
+    if args.table:
+        ctx = gp.Context(0)
+        for row in replicate(ctx, args.table, prec=args.prec):
+            row.update({"table": args.table, "d": TABLES[args.table]["d"], "p": 1.95, "delta": 1e-8,
+                        "search": "GA 20 x 100 + gradient refinement", "prec": args.prec})
+            print(json.dumps(row))
+        ctx.close()
+        return
     g = inputs.rng(inputs.BASE_SEED + 10)
     x = inputs.random_lhd(g, args.n, args.d)
     y = inputs.y_sinsum(x)

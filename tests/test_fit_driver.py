@@ -127,3 +127,25 @@ def test_gradient_search_reaches_the_genetic_optimum():
     o, st = oracle.nll(x, y, th, 2.0, 1e-8)
     assert st == 0 and abs(gr["nll"] - o["nll"]) <= 1e-9 * abs(o["nll"]) + 1e-9
     ctx.close()
+
+
+def test_replicate_table_shapes_and_means(monkeypatch):
+    """The replication harness runs one fit per replication with a fresh
+    design and averages the five reported quantities per size."""
+    calls = []
+
+    def fake_fit(ctx, x, y, p, delta, xs, ys, prec="mixed", seed=0, **kw):
+        calls.append((x.shape[0], x.shape[1], seed, float(x[0, 0])))
+        n = x.shape[0]
+        return {"seconds": 1.0 + seed, "nll": -n, "mu": 0.5, "sigma2": 2.0, "sspe": 3.0 * seed}
+
+    monkeypatch.setattr(fit, "fit_and_predict", fake_fit)
+    monkeypatch.setitem(fit.TABLES, "tiny", {"d": 2, "sizes": [(16, 3), (32, 2)], "y": "y_trig2"})
+    rows = fit.replicate(None, "tiny", device=torch.device("cpu"))
+    assert [r["n"] for r in rows] == [16, 32] and [r["replications"] for r in rows] == [3, 2]
+    assert [c[:3] for c in calls] == [(16, 2, 0), (16, 2, 1), (16, 2, 2), (32, 2, 0), (32, 2, 1)]
+    assert len({c[3] for c in calls[:3]}) == 3                     # a fresh design per replication
+    assert rows[0]["seconds"] == 2.0 and rows[0]["nll"] == -16 and rows[0]["sspe"] == 3.0
+    assert rows[1]["seconds"] == 1.5 and rows[1]["sspe"] == 1.5
+    assert fit.TABLES["example1"]["sizes"][-1] == (512, 10) and fit.TABLES["example2"]["sizes"][-1] == (4064, 1)
+
