@@ -12,7 +12,8 @@
 // the FP64 pipes would cost more than the factorisation itself):
 //   X = L^-1:   X_JJ = L_JJ^-1 (double, in shared memory), then along tile
 //               diagonals s = I - J = 1, 2, ...
-//               X_IJ = -X_II sum_{K=J}^{I-1} L_IK X_KJ  (all J of a diagonal at once)
+//               X_IJ = -X_II sum_{K=J}^{I-1} L_IK X_KJ  (all J of a diagonal at
+//               once, in 64 x 64 quadrants, the sum staged in the R^-1 buffer)
 //   R^-1 = X' X:  (R^-1)_IJ = sum_{K >= I} X_KI' X_KJ  (I >= J)
 // The factor is rewritten in place as double-float once the likelihood is
 // done (8 bytes either way), so every tile operand is a float pair.  One pass
@@ -36,8 +37,7 @@ __device__ __forceinline__ T* tile_at(T* base, size_t stride, int t, int I, int 
 // acc(r, c) += sum_k opA(A)(r, k) opB(B)(k, c) for one pair of column-major
 // 128 x 128 double-float tiles; thread (tx, ty) of a 16 x 16 layout owns
 // rows tx + 16i and columns ty + 16j.  TA / TB: use the transpose of A / B.
-// The operands are plain (coherent) loads: k_trtri_step reads a tile it
-// wrote itself.
+// The operands are plain (coherent) loads.
 template <bool TA, bool TB>
 __device__ __forceinline__ void tile_mma(dfl (&acc)[8][8], const float2* A, const float2* B,
                                          dfl (*As)[GP_NB], dfl (*Bs)[GP_NB]) {
@@ -155,25 +155,90 @@ __global__ void __launch_bounds__(kThreads) k_inv_diag(Batch b, const float2* L2
     }
 }
 
-// Tile diagonal s of X = L^-1: X_IJ, I = J + s, for J = blockIdx.x.
-__global__ void __launch_bounds__(kThreads, 1) k_trtri_step(Batch b, const float2* L2, float2* X, int s) {
-    __shared__ dfl As[16][GP_NB];
-    __shared__ dfl Bs[16][GP_NB];
+// Quadrant products for the tile diagonals of X = L^-1: a CTA forms one
+// 64 x 64 quadrant (qr, qc) of a 128 x 128 output tile, thread (tx, ty) of a
+// 16 x 16 layout rows tx + 16i and columns ty + 16j (4 x 4), so that a tile
+// diagonal spreads over four times as many CTAs as tiles: a single
+// candidate's inverse is a chain of nt - 1 such steps.
+// acc(r, c) += sum_k A(64 qr + r, k) B(k, 64 qc + c) for column-major tiles.
+__device__ __forceinline__ void quad_mma(dfl (&acc)[4][4], const float2* A, const float2* B, int qr, int qc,
+                                         dfl (*As)[64], dfl (*Bs)[64]) {
+    constexpr int KC = 16;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int k0 = 0; k0 < GP_NB; k0 += KC) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < KC * 64; q += kThreads) {
+            {
+                const int kq = q / 64, u = q % 64;                   // A(64 qr + u, k0 + kq)
+                const float2 a = A[(size_t)(k0 + kq) * GP_NB + 64 * qr + u];
+                As[kq][u] = dfl{a.x, a.y};
+            }
+            {
+                const int u = q / KC, kq = q % KC;                   // B(k0 + kq, 64 qc + u)
+                const float2 v = B[(size_t)(64 * qc + u) * GP_NB + k0 + kq];
+                Bs[kq][u] = dfl{v.x, v.y};
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            dfl a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = df_fma(a[i], bb[j], acc[i][j]);
+        }
+    }
+}
+
+__device__ __forceinline__ void quad_store(const dfl (&acc)[4][4], float2* C, int qr, int qc, bool negate) {
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const dfl v = negate ? df_neg(acc[i][j]) : acc[i][j];
+            C[(size_t)(64 * qc + ty + 16 * j) * GP_NB + 64 * qr + tx + 16 * i] = make_float2(v.hi, v.lo);
+        }
+}
+
+// Tile diagonal s of X = L^-1, first half: S_IJ = sum_{K=J}^{I-1} L_IK X_KJ
+// (I = J + s, J = blockIdx.x, quadrant blockIdx.z) into S (the R^-1 buffer,
+// free until k_lauum).
+__global__ void __launch_bounds__(kThreads) k_trtri_sum(Batch b, const float2* L2, const float2* X, float2* S, int s) {
+    __shared__ dfl As[16][64];
+    __shared__ dfl Bs[16][64];
     const int J = blockIdx.x, t = blockIdx.y, I = J + s, nt = b.nt;
+    const int qr = blockIdx.z & 1, qc = blockIdx.z >> 1;
     if (b.st[t].status != GP_OK) return;
-    dfl acc[8][8];
-    acc_zero(acc);
+    dfl acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = dfl{0.f, 0.f};
     for (int K = J; K < I; ++K)
-        tile_mma<false, false>(acc, tile_at(L2, b.inst_stride, t, I, K, nt), tile_at(X, b.inst_stride, t, K, J, nt),
-                               As, Bs);
-    float2* Xij = tile_at(X, b.inst_stride, t, I, J, nt);
-    __syncthreads();
-    acc_store(acc, Xij, false);               // S = sum_K L_IK X_KJ, for the product below
-    __syncthreads();
-    acc_zero(acc);
-    tile_mma<false, false>(acc, tile_at(X, b.inst_stride, t, I, I, nt), Xij, As, Bs);
-    __syncthreads();                          // every read of S is done
-    acc_store(acc, Xij, true);
+        quad_mma(acc, tile_at(L2, b.inst_stride, t, I, K, nt), tile_at(X, b.inst_stride, t, K, J, nt), qr, qc, As, Bs);
+    quad_store(acc, tile_at(S, b.inst_stride, t, I, J, nt), qr, qc, false);
+}
+
+// Second half: X_IJ = -X_II S_IJ.
+__global__ void __launch_bounds__(kThreads) k_trtri_apply(Batch b, float2* X, const float2* S, int s) {
+    __shared__ dfl As[16][64];
+    __shared__ dfl Bs[16][64];
+    const int J = blockIdx.x, t = blockIdx.y, I = J + s, nt = b.nt;
+    const int qr = blockIdx.z & 1, qc = blockIdx.z >> 1;
+    if (b.st[t].status != GP_OK) return;
+    dfl acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = dfl{0.f, 0.f};
+    quad_mma(acc, tile_at(X, b.inst_stride, t, I, I, nt), tile_at(S, b.inst_stride, t, I, J, nt), qr, qc, As, Bs);
+    quad_store(acc, tile_at(X, b.inst_stride, t, I, J, nt), qr, qc, true);
 }
 
 // (R^-1)_IJ = sum_{K >= I} X_KI' X_KJ for the lower tile q = blockIdx.x.
@@ -334,8 +399,9 @@ cudaError_t launch_grad(const Batch& b, double* Z, size_t zs, double* X, double*
         ++k;
     }
     for (int st = 1; st < nt; ++st) {
-        k_trtri_step<<<dim3(nt - st, b.count), kThreads, 0, s>>>(b, L2, X2, st);
-        ++k;
+        k_trtri_sum<<<dim3(nt - st, b.count, 4), kThreads, 0, s>>>(b, L2, X2, R2, st);
+        k_trtri_apply<<<dim3(nt - st, b.count, 4), kThreads, 0, s>>>(b, X2, R2, st);
+        k += 2;
     }
     k_lauum<<<dim3(ntiles, b.count), kThreads, 0, s>>>(b, X2, R2);
     ++k;
