@@ -622,7 +622,7 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
     if (opt->slices < 2 || opt->slices > 6)
         return fail(ctx, GP_EINVAL, "slices = %d outside [2, 6]", opt->slices);
     if (opt->panel_slices != GP_PANEL_SLICES)
-        return fail(ctx, GP_EINVAL, "panel_slices is fixed at %d in this build", GP_PANEL_SLICES);
+        return fail(ctx, GP_EINVAL, "panel_slices is fixed at %d (GP_PANEL_SLICES, a compile-time constant)", GP_PANEL_SLICES);
     if (opt->refine_iters < 0 || opt->refine_iters > 10)
         return fail(ctx, GP_EINVAL, "refine_iters = %d outside [0, 10]", opt->refine_iters);
     if (opt->max_batch < 0) return fail(ctx, GP_EINVAL, "max_batch must be >= 0");
