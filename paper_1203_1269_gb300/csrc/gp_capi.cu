@@ -1212,10 +1212,15 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int npad = m->nt * GP_NB;
-    const size_t per_cta = gp::predict_work_per_cta(m->nt);
-    const int ppc = gp::predict_points_per_cta();
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    const int ppc = gp::predict_points_per_cta(N, sms);
+    const size_t per_cta = gp::predict_work_per_cta(m->nt, ppc);
     const int blocks_total = (N + ppc - 1) / ppc;
-    int chunk = blocks_total < 4 * 152 ? blocks_total : 4 * 152;
+    int chunk = blocks_total < 4 * sms ? blocks_total : 4 * sms;
     size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
     while (chunk > 1 && per_cta * chunk > avail) chunk /= 2;
     int rc = ensure_ws(ctx, s2 ? per_cta * chunk : 256);
@@ -1226,7 +1231,7 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     PhaseScope ps(ctx, GP_PHASE_PREDICT, (blocks_total + chunk - 1) / chunk);
     GP_CUDA(ctx, gp::launch_predict(m->n, m->d, m->nt, reinterpret_cast<const float2*>(m->x), m->theta, m->p, m->corr,
                                     c0, Ldf, Zdf + npad, Zdf, m->scalars, N, xstar, yhat, s2,
-                                    (float2*)ctx->ws, chunk, ctx->stream));
+                                    (float2*)ctx->ws, chunk, ppc, ctx->stream));
     return GP_OK;
 }
 

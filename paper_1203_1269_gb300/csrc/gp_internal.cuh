@@ -180,10 +180,12 @@ cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t z_stride, in
                                   cudaStream_t s);
 cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
-                           const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s);
+                           const double* xs, double* yhat, double* s2, float2* work, int chunk, int nr,
+                           cudaStream_t s);
 cudaError_t launch_to_df_inplace(double* p, size_t count, cudaStream_t s);
-size_t predict_work_per_cta(int nt);
-int predict_points_per_cta();
+size_t predict_work_per_cta(int nt, int nr);
+// test points per CTA for N points on a device of `sms` SMs (8 or 16)
+int predict_points_per_cta(int N, int sms);
 
 cudaError_t launch_diag_mixed(const MixedBatch& b, int J, cudaStream_t s);
 cudaError_t launch_split_panel(const MixedBatch& b, int J, int ns, int gemv, cudaStream_t s);

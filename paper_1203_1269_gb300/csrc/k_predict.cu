@@ -12,8 +12,9 @@
 // FP32 pipes: |dx|^p = exp(p ln|dx|) and exp(-S) in double-float arithmetic,
 // and the forward solve v = L^-1 r in double-float.
 //
-// One CTA takes NR = 16 test points as right-hand sides and walks the tile
-// rows of L: it forms the r block of the tile row on the fly, removes the
+// One CTA takes NR test points (16, or 8 when there are too few points to
+// give every SM two CTAs at 16) as right-hand sides and walks the tile rows
+// of L: it forms the r block of the tile row on the fly, removes the
 // solved blocks above it (a 128 x 128 by 128 x 16 product per tile), solves
 // with the diagonal tile and folds the finished block into v'v and a'v.
 // Solved blocks are kept in a per-CTA slice of `work` (npad x NR pairs).
@@ -26,8 +27,6 @@ namespace gp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int NR = 16;          // test points per CTA
-constexpr int PT = NR / 2;      // points per thread (two threads per row)
 
 struct PredArgs {
     int n, d, nt, N, m0;   // m0: first test point of this launch
@@ -45,8 +44,11 @@ struct PredArgs {
     float2* work;          // per CTA: npad * NR
 };
 
+// NR test points per CTA, PT = NR / 2 per thread (two threads per row).
 // dynamic shared memory: rhs[NR][NB] + vs[NB][NR] (dfl) + xs[NR][d] + th[d] (dfl) + tab[64]
+template <int NR>
 __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
+    constexpr int PT = NR / 2;
     extern __shared__ dfl sm[];
     dfl* rhs = sm;                                 // [NR][NB]
     dfl* vs = rhs + NR * GP_NB;                    // [NB][NR]
@@ -217,30 +219,39 @@ cudaError_t launch_to_df_inplace(double* p, size_t count, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t predict_work_per_cta(int nt) { return (size_t)nt * GP_NB * NR * sizeof(float2); }
+size_t predict_work_per_cta(int nt, int nr) { return (size_t)nt * GP_NB * nr * sizeof(float2); }
 
-int predict_points_per_cta() { return NR; }
+int predict_points_per_cta(int N, int sms) { return (N + 15) / 16 < 2 * sms ? 8 : 16; }
 
-cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
-                           const float2* L, const float2* w, const float2* a, const double* scalars, int N,
-                           const double* xs, double* yhat, double* s2, float2* work, int chunk, cudaStream_t s) {
+template <int NR>
+static cudaError_t launch_predict_nr(const PredArgs& g0, int d, int N, int chunk, cudaStream_t s) {
     const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + 64) * sizeof(dfl);
     static std::atomic<size_t> attr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_predict, smem, attr);
+    cudaError_t e = raise_smem_limit(k_predict<NR>, smem, attr);
     if (e != cudaSuccess) return e;
-    PredArgs g;
-    g.n = n; g.d = d; g.nt = nt; g.N = N;
-    g.x = x; g.theta = theta; g.p = p; g.corr = corr; g.c0 = c0;
-    g.L = L; g.w = w; g.a = a; g.sc = scalars; g.xs = xs; g.yhat = yhat; g.s2 = s2; g.work = work;
+    PredArgs g = g0;
     const int blocks_total = (N + NR - 1) / NR;
     for (int b0 = 0; b0 < blocks_total; b0 += chunk) {
         const int nb = (blocks_total - b0 < chunk) ? (blocks_total - b0) : chunk;
         g.m0 = b0 * NR;
-        k_predict<<<nb, kThreads, smem, s>>>(g);
-        cudaError_t e = cudaGetLastError();
+        k_predict<NR><<<nb, kThreads, smem, s>>>(g);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
+                           const float2* L, const float2* w, const float2* a, const double* scalars, int N,
+                           const double* xs, double* yhat, double* s2, float2* work, int chunk, int nr,
+                           cudaStream_t s) {
+    PredArgs g;
+    g.n = n; g.d = d; g.nt = nt; g.N = N; g.m0 = 0;
+    g.x = x; g.theta = theta; g.p = p; g.corr = corr; g.c0 = c0;
+    g.L = L; g.w = w; g.a = a; g.sc = scalars; g.xs = xs; g.yhat = yhat; g.s2 = s2; g.work = work;
+    if (nr == 8) return launch_predict_nr<8>(g, d, N, chunk, s);
+    if (nr == 16) return launch_predict_nr<16>(g, d, N, chunk, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gp
