@@ -269,10 +269,9 @@ constexpr int kSplitThreads = 512;
 constexpr int kSplitParts = 8;                          // column parts of a row
 constexpr int kSplitRows = kSplitThreads / kSplitParts; // rows of a tile per CTA
 constexpr int kSplitCols = GP_NB / kSplitParts;         // 16 columns per thread
-// k_split_fused: 8 columns of each of two panels per thread, a quarter tile
+// k_split_fused: 16 columns of one of the two panels per thread, a quarter tile
 constexpr int kFusedParts = 16;
 constexpr int kFusedRows = kSplitThreads / kFusedParts;
-constexpr int kFusedCols = GP_NB / kFusedParts;
 
 // 2^(7 - E) as two exact float factors (7 - E may leave the float range)
 __device__ __forceinline__ void slice_scale(int E, float& sa, float& sb) {
@@ -286,39 +285,65 @@ __device__ __forceinline__ void slice_scale(int E, float& sa, float& sb) {
 // Slices of one thread's NC values of row r (columns k0 .. k0 + NC - 1 of
 // image chunk `chunk0`, k0 = 0, 8, 16 or 24; slice a at chunk0 + a *
 // slice_bytes): NC / 8 pieces of 8.
+// One 256-bit store (two adjacent 16-byte pieces, 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(void* p, uint4 a, uint4 b) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
+// Slices of 8 values (one 16-byte piece per slice): m = the slice's values.
+__device__ __forceinline__ uint4 next_slice8(float (&xh)[8], float (&xl)[8], float w) {
+    float m[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float qv = rintf(xh[e]);
+        m[e] = __fmul_rn(qv, w);
+        two_sum(__fsub_rn(xh[e], qv), xl[e], xh[e], xl[e]);
+        xh[e] = __fmul_rn(xh[e], 256.f);
+        xl[e] = __fmul_rn(xl[e], 256.f);
+    }
+    uint4 pk;
+    pk.x = pack_bf16x2(m[0], m[1]);
+    pk.y = pack_bf16x2(m[2], m[3]);
+    pk.z = pack_bf16x2(m[4], m[5]);
+    pk.w = pack_bf16x2(m[6], m[7]);
+    return pk;
+}
+
+// Slices of one thread's NC values of row r (columns k0 .. k0 + NC - 1 of
+// image chunk `chunk0`, k0 = 0, 8, 16 or 24; slice a at chunk0 + a *
+// slice_bytes): NC / 8 pieces of 8.  With NC = 16 (k0 = 0 or 16) the two
+// pieces of a slice occupy one aligned 32-byte sector of the row (the
+// swizzle only swaps them), written by one 256-bit store.
 template <int NC>
 __device__ __forceinline__ void slice_pieces(const float2 (&v)[NC], float sa, float sb, int r, int k0,
                                              int ns, uint8_t* chunk0, size_t slice_bytes) {
+    static_assert(NC == 8 || NC == 16, "one or two pieces per thread");
+    float xh[NC / 8][8], xl[NC / 8][8];
 #pragma unroll
-    for (int h = 0; h < NC / 8; ++h) {
-        float xh[8], xl[8];
+    for (int h = 0; h < NC / 8; ++h)
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            xh[e] = __fmul_rn(__fmul_rn(v[8 * h + e].x, sa), sb);
-            xl[e] = __fmul_rn(__fmul_rn(v[8 * h + e].y, sa), sb);
+            xh[h][e] = __fmul_rn(__fmul_rn(v[8 * h + e].x, sa), sb);
+            xl[h][e] = __fmul_rn(__fmul_rn(v[8 * h + e].y, sa), sb);
         }
-        const uint32_t off = image_piece(r, k0 + 8 * h);
-        float w = 1.f;
+    const uint32_t off0 = image_piece(r, k0);
+    const uint32_t off1 = (NC == 16) ? image_piece(r, k0 + 8) : off0;
+    float w = 1.f;
 #pragma unroll
-        for (int a = 0; a < GP_MAX_SLICES; ++a) {
-            if (a >= ns) break;
-            float m[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float qv = rintf(xh[e]);
-                m[e] = __fmul_rn(qv, w);
-                two_sum(__fsub_rn(xh[e], qv), xl[e], xh[e], xl[e]);
-                xh[e] = __fmul_rn(xh[e], 256.f);
-                xl[e] = __fmul_rn(xl[e], 256.f);
-            }
-            w = __fmul_rn(w, 0.00390625f);
-            uint4 pk;
-            pk.x = pack_bf16x2(m[0], m[1]);
-            pk.y = pack_bf16x2(m[2], m[3]);
-            pk.z = pack_bf16x2(m[4], m[5]);
-            pk.w = pack_bf16x2(m[6], m[7]);
-            *reinterpret_cast<uint4*>(chunk0 + (size_t)a * slice_bytes + off) = pk;
+    for (int a = 0; a < GP_MAX_SLICES; ++a) {
+        if (a >= ns) break;
+        uint8_t* base = chunk0 + (size_t)a * slice_bytes;
+        const uint4 p0 = next_slice8(xh[0], xl[0], w);
+        if (NC == 16) {
+            const uint4 p1 = next_slice8(xh[NC / 8 - 1], xl[NC / 8 - 1], w);
+            if (off0 < off1) st_global_v8(base + off0, p0, p1);
+            else             st_global_v8(base + off1, p1, p0);
+        } else {
+            *reinterpret_cast<uint4*>(base + off0) = p0;
         }
+        w = __fmul_rn(w, 0.00390625f);
     }
 }
 
@@ -404,39 +429,36 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_panel(MixedBatch b, int
 // update: row r of row block I = J + 2 + blockIdx.x / 4 spans tiles (I, J) and
 // (I, J + 1) and gets one exponent for all 256 columns, so the products of
 // both panels accumulate in the same tensor-memory groups.  A CTA takes a
-// quarter tile (32 rows); thread (r, part) owns the same 16-byte piece (8
-// columns) of each panel and keeps both panels' values in registers for the
-// row maximum and the slicing.
+// quarter tile (32 rows); thread (r, part) owns 16 columns of one panel
+// (parts 0-7 panel J, 8-15 panel J + 1; the same two pieces of an image
+// chunk as in k_split_panel), so every tile is read once and every slice
+// written in 32-byte stores; the row maximum spans all 16 parts.
 __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int J) {
     __shared__ float pmax[kFusedParts][kFusedRows];
     __shared__ dfl xs[2][GP_NB];
-    __shared__ dfl red[kFusedParts][2][kFusedRows];
+    __shared__ dfl red[kFusedParts / 2][2][kFusedRows];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     const int I = J + 2 + blockIdx.x / 4;
     const int rl = threadIdx.x % kFusedRows, part = threadIdx.x / kFusedRows;
-    const int q = part >> 2, c0 = kFusedCols * part;
+    const int panel = part >> 3, lp = part & 7;
+    const int q = lp >> 1, u = lp & 1, c0 = kSplitCols * lp;
     const int r = (blockIdx.x & 3) * kFusedRows + rl;
     if (b.fwd && threadIdx.x < 2 * GP_NB) {
         // x_{J+1}: the panel J term was applied by k_split_panel
         const int k = threadIdx.x >> 7, c = threadIdx.x & 127;
         xs[k][c] = df_load(b.Z + (size_t)t * b.z_stride + (size_t)k * b.nt * GP_NB + (size_t)(J + 1) * GP_NB + c);
     }
-    const float2* src0 = df_tile(b, b.A, t, I, J);
-    const float2* src1 = df_tile(b, b.A, t, I, J + 1);
-    // both panels' values stay in registers: each tile is read once
-    float2 v0[kFusedCols], v1[kFusedCols];
+    const float2* src = df_tile(b, b.A, t, I, J + panel);
+    float2 v[kSplitCols];
 #pragma unroll
-    for (int j = 0; j < kFusedCols; ++j) {
-        v0[j] = src0[(size_t)(c0 + j) * GP_NB + r];
-        v1[j] = src1[(size_t)(c0 + j) * GP_NB + r];
-    }
+    for (int j = 0; j < kSplitCols; ++j) v[j] = src[(size_t)(c0 + j) * GP_NB + r];
     float mx = 0.f;
 #pragma unroll
-    for (int j = 0; j < kFusedCols; ++j) mx = fmaxf(mx, fmaxf(fabsf(v0[j].x), fabsf(v1[j].x)));
+    for (int j = 0; j < kSplitCols; ++j) mx = fmaxf(mx, fabsf(v[j].x));
     pmax[part][rl] = mx;
     __syncthreads();
-    if (b.fwd) fwd_partials(v1, xs, c0, part, rl, red);
+    if (b.fwd && panel == 1) fwd_partials(v, xs, c0, lp, rl, red);
 #pragma unroll
     for (int k = 0; k < kFusedParts; ++k) mx = fmaxf(mx, pmax[k][rl]);
     const int E = exponent_of(mx);
@@ -445,11 +467,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_fused(MixedBatch b, int
     slice_scale(E, sa, sb);
     const size_t slice_bytes = (size_t)2 * kChunks * kChunkBytes;
     uint8_t* base = reinterpret_cast<uint8_t*>(pf_block(b, t, I));
-    slice_pieces(v0, sa, sb, r, c0 & 31, b.s, base + (size_t)q * kChunkElems * 2, slice_bytes);
-    slice_pieces(v1, sa, sb, r, c0 & 31, b.s, base + (size_t)(4 + q) * kChunkElems * 2, slice_bytes);
+    slice_pieces(v, sa, sb, r, 16 * u, b.s, base + (size_t)(4 * panel + q) * kChunkElems * 2, slice_bytes);
     if (b.fwd) {
         __syncthreads();
-        fwd_apply<kFusedParts>(b, t, I, r, part, rl, red);
+        fwd_apply<kFusedParts / 2>(b, t, I, r, part, rl, red);
     }
 }
 
