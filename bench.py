@@ -311,7 +311,8 @@ def run_gp(args):
                 "traffic": stored_traffic("k_split_gemm<update>", ["k_gemm.cu", "mixed_common.cuh"], units),
                 "units_per_launch": units,
                 "algorithmic_bytes_per_launch": units * NB * NB * 8,
-                "peak_source": f"bf16 dense sustained, {pk_src} (MEASURED_PEAKS.json)",
+                "peak_source": ("bf16 dense sustained, measured (MEASURED_PEAKS.json)" if pk_src == "measured"
+                                else "bf16 dense sustained, fallback (1.7 PFLOP/s; MEASURED_PEAKS.json absent)"),
                 "flops_counted": f"executed bf16 slice products: {tiles} 128x128 tiles per "
                                  f"instance x {prods} products x 2*128^3",
                 "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
