@@ -394,6 +394,35 @@ void gp_model_free(gp_model* model);
 /* Device bytes a model holds (0 for NULL). */
 size_t gp_model_bytes(const gp_model* model);
 
+/* Calls whose device memory gp_call_bytes reports. */
+typedef enum {
+    GP_CALL_NLL_BATCH = 0,  /* gp_nll_batch / gp_nll_batch_ex at precision prec, count = T */
+    GP_CALL_NLL_GRAD = 1,   /* gp_nll_grad_batch, count = T */
+    GP_CALL_FIT = 2,        /* gp_fit: the model's bytes (gp_model_bytes); count unused */
+    GP_CALL_PREDICT = 3     /* gp_predict with variances (s2 != NULL), count = N test
+                               points, n and d those of the model */
+} gp_call;
+
+/* Device bytes a call would allocate for these sizes: for GP_CALL_FIT the model,
+ * otherwise the workspace the call grows the context's arena to (what
+ * gp_workspace_bytes reports after the call on a context whose arena was
+ * smaller).  The candidates of a batch are processed in chunks that fit the
+ * budget, as the calls themselves do, so the figure is for one chunk.
+ * GP_AUTO gives an upper bound: the largest workspace of its three tiers plus
+ * its routing buffers.  Per candidate these are the buffers of Section 3's
+ * work (one R, its factor, the solves), so they grow like n^2 / 2.
+ * Host arithmetic only: no device access and no allocation, so it works
+ * without a GPU.
+ *   ctx    the context whose options, budget and device (SM count) the call
+ *          would use, or NULL: default options, no budget limit, 152 SMs.
+ *   call   a gp_call.  prec: a gp_precision, read for GP_CALL_NLL_BATCH only.
+ *   bytes  out (host).
+ * Returns GP_OK; GP_EINVAL for sizes the call rejects (n, d, count) or an
+ * unknown call or precision; GP_ENOTSUP where the call is not built for the
+ * sizes (gradient with d > 16); GP_ENOMEM where the call would fail for the
+ * context's budget. */
+int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size_t* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 
 struct gp_ctx {
     int device = 0;
+    int sms = 1;                // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     size_t budget = 0;          // bytes the context and its models may hold
     size_t models_bytes = 0;    // held by live models
@@ -156,6 +157,27 @@ size_t per_instance_bytes_f64(int n) {
            align256((size_t)2 * nt * GP_NB * sizeof(double)) + align256(sizeof(gp::InstState));
 }
 
+// Candidates per chunk of a batched call and the workspace it grows to:
+// `per` bytes per candidate plus `extra`, within the budget left next to the
+// models, the max_batch option and the grid.y bound (65535) of the
+// per-candidate launches.  False when not even one candidate fits.
+struct Chunking {
+    int Tc = 0;
+    size_t bytes = 0;
+};
+
+bool chunk_batch(const gp_options& opt, size_t budget, size_t held, size_t per, size_t extra, int T,
+                 Chunking* out) {
+    const size_t avail = budget > held ? budget - held : 0;
+    long long cap = (long long)((avail > extra ? avail - extra : 0) / per);
+    if (opt.max_batch > 0 && cap > opt.max_batch) cap = opt.max_batch;
+    if (cap > 65535) cap = 65535;
+    if (cap < 1) return false;
+    out->Tc = (int)(cap < T ? cap : T);
+    out->bytes = per * (size_t)out->Tc + extra;
+    return true;
+}
+
 // Factor and solve `b.count` instances already assembled in b.A.
 int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
     for (int J = 0; J < b.nt; ++J) {
@@ -180,6 +202,9 @@ int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
 struct MixedSizes {
     size_t A, PS, PE, WS, WE, PF, FE, WT, Z, RP, SC, st, per;   // WT also sizes WR
 };
+
+// Bytes after the instances of a split-precision batch: its error flag.
+constexpr size_t kMixedTail = 256;
 
 MixedSizes mixed_sizes(int n, int s) {
     const int nt = gp::num_tiles(n);
@@ -361,13 +386,11 @@ int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y,
                     const double* theta, double p, double delta, double* nll, double* mu,
                     double* sigma2, double* logdet, int* status, int slices, double* cond) {
     const MixedSizes z = mixed_sizes(n, slices);
-    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
-    long long cap = (long long)((avail > 256 ? avail - 256 : 0) / z.per);
-    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
-    if (cap > 65535) cap = 65535;
-    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", z.per);
-    const int Tc = (int)(cap < T ? cap : T);
-    int rc = ensure_ws(ctx, z.per * (size_t)Tc + 256);
+    Chunking ch;
+    if (!chunk_batch(ctx->opt, ctx->budget, ctx->models_bytes, z.per, kMixedTail, T, &ch))
+        return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", z.per);
+    const int Tc = ch.Tc;
+    int rc = ensure_ws(ctx, ch.bytes);
     if (rc) return rc;
     for (int c0 = 0; c0 < T; c0 += Tc) {
         const int cnt = (T - c0 < Tc) ? (T - c0) : Tc;
@@ -391,13 +414,11 @@ int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
                    double* sigma2_hat, double* logdet, int* status) {
     const int nt = gp::num_tiles(n);
     const size_t per = per_instance_bytes_f64(n);
-    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
-    long long cap = (long long)(avail / per);
-    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
-    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
-    if (cap > 65535) cap = 65535;  // grid.y bound of the per-instance launches
-    const int Tc = (int)(cap < T ? cap : T);
-    int rc = ensure_ws(ctx, per * (size_t)Tc);
+    Chunking ch;
+    if (!chunk_batch(ctx->opt, ctx->budget, ctx->models_bytes, per, 0, T, &ch))
+        return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
+    const int Tc = ch.Tc;
+    int rc = ensure_ws(ctx, ch.bytes);
     if (rc) return rc;
     char* base = (char*)ctx->ws;
     const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
@@ -434,17 +455,24 @@ int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
 // bound leaves a margin of 10 or more.
 double split_error_per_cond(int s) { return std::ldexp(1.0, -(8 * s + 6)); }
 
+// GP_AUTO's routing buffers (allocated beside the workspace): compacted theta
+// and the outputs of a re-evaluated subset, indices, and cond / prec_used when
+// the caller passed none.
+size_t auto_staging_bytes(int T, int d) {
+    const size_t bT = align256((size_t)T * sizeof(double));
+    const size_t bI = align256((size_t)T * sizeof(int));
+    return align256((size_t)T * d * sizeof(double)) + 6 * bT + 4 * bI;
+}
+
 // GP_AUTO: route every candidate to the cheapest arithmetic whose bound
 // meets auto_tol (GP_FP32, then GP_MIXED, then GP_FP64); see gp.h.
 int auto_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                    const double* theta, double p, double delta, double* nll, double* mu,
                    double* sigma2, double* logdet, int* status, double* cond, int* prec_used) {
     const double tol = ctx->opt.auto_tol;
-    // staging: compacted theta and outputs of a re-evaluated subset, indices,
-    // and cond / prec_used when the caller passed none
     const size_t bT = align256((size_t)T * sizeof(double));
     const size_t bI = align256((size_t)T * sizeof(int));
-    const size_t total = align256((size_t)T * d * sizeof(double)) + 6 * bT + 4 * bI;
+    const size_t total = auto_staging_bytes(T, d);
     void* dev = nullptr;
     if (cudaMallocAsync(&dev, total, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -526,6 +554,65 @@ int auto_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
     return done(GP_OK);
 }
 
+// Workspace per candidate of gp_nll_grad_batch: the factor, L^-1, R^-1,
+// [a | w], its record, tile partial sums, and mu / sigma2 / log|R| (which
+// the caller does not ask for).
+struct GradSizes {
+    size_t a, z, st, part, sc, per;
+};
+
+GradSizes grad_sizes(int n, int d) {
+    const int nt = gp::num_tiles(n);
+    GradSizes g;
+    g.a = align256(gp::packed_elems(n) * sizeof(double));
+    g.z = align256((size_t)2 * nt * GP_NB * sizeof(double));
+    g.st = align256(sizeof(gp::InstState));
+    g.part = align256((size_t)gp::packed_tiles(nt) * d * sizeof(double));
+    g.sc = align256(3 * sizeof(double));
+    g.per = 3 * g.a + g.z + g.st + g.part + g.sc;
+    return g;
+}
+
+// One allocation per model: the factor, [a | w], x, theta, the scalars, the
+// status and the instance record.
+struct ModelSizes {
+    size_t L, Z, x, th, sc, stat, st, total;
+};
+
+ModelSizes model_sizes(int n, int d) {
+    const int nt = gp::num_tiles(n);
+    ModelSizes m;
+    m.L = align256(gp::packed_elems(n) * sizeof(double));
+    m.Z = align256((size_t)2 * nt * GP_NB * sizeof(double));
+    m.x = align256((size_t)n * d * sizeof(double));
+    m.th = align256((size_t)d * sizeof(double));
+    m.sc = align256(8 * sizeof(double));
+    m.stat = align256(sizeof(int));
+    m.st = align256(sizeof(gp::InstState));
+    m.total = m.L + m.Z + m.x + m.th + m.sc + m.stat + m.st;
+    return m;
+}
+
+// Launch shape and workspace of gp_predict: test points per CTA, CTAs in
+// all, CTAs per launch (at most four waves, fewer when their scratch would
+// not fit `avail`), and the scratch those CTAs take when variances are asked
+// for (else a token 256 bytes).
+struct PredictShape {
+    int ppc, blocks, chunk;
+    size_t per_cta, bytes;
+};
+
+PredictShape predict_shape(int nt, int N, int sms, size_t avail, bool variances) {
+    PredictShape s;
+    s.ppc = gp::predict_points_per_cta(N, sms);
+    s.per_cta = gp::predict_work_per_cta(nt, s.ppc);
+    s.blocks = (N + s.ppc - 1) / s.ppc;
+    s.chunk = s.blocks < 4 * sms ? s.blocks : 4 * sms;
+    while (s.chunk > 1 && s.per_cta * s.chunk > avail) s.chunk /= 2;
+    s.bytes = variances ? s.per_cta * s.chunk : 256;
+    return s;
+}
+
 }  // namespace
 
 namespace gp {
@@ -588,6 +675,11 @@ int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stre
         return GP_ECUDA;
     }
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (free_b / 4) * 3;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+        ctx->sms = sms;
+    else
+        cudaGetLastError();
     *out = ctx;
     return GP_OK;
 }
@@ -744,7 +836,7 @@ int gp_cholesky(gp_ctx* ctx, int n, int d, const double* x, const double* theta,
     } else {
         const int slices = prec == GP_FP32 ? 3 : ctx->opt.slices;
         const MixedSizes z = mixed_sizes(n, slices);
-        rc = ensure_ws(ctx, z.per + 256);
+        rc = ensure_ws(ctx, z.per + kMixedTail);
         if (rc) return rc;
         gp::MixedBatch mb = mixed_layout(ctx, n, 1, nullptr, (char*)ctx->ws, z, 1, slices);
         rc = run_mixed_factor(ctx, mb, d, x, theta, p, delta);
@@ -792,22 +884,13 @@ int gp_nll_grad_batch(gp_ctx* ctx, int n, int d, const double* x, const double* 
     if (!x || !y || !theta || !nll || !grad || !status) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int nt = gp::num_tiles(n);
-    const long long ntiles = gp::packed_tiles(nt);
-    const size_t a_bytes = align256(gp::packed_elems(n) * sizeof(double));
-    const size_t z_bytes = align256((size_t)2 * nt * GP_NB * sizeof(double));
-    const size_t st_bytes = align256(sizeof(gp::InstState));
-    const size_t part_bytes = align256((size_t)ntiles * d * sizeof(double));
-    const size_t sc_bytes = align256(3 * sizeof(double));
-    // per instance: the factor, L^-1, R^-1, [a | w], its record, tile partial
-    // sums and mu / sigma2 / log|R| (which the caller does not ask for)
-    const size_t per = 3 * a_bytes + z_bytes + st_bytes + part_bytes + sc_bytes;
-    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
-    long long cap = (long long)(avail / per);
-    if (ctx->opt.max_batch > 0 && cap > ctx->opt.max_batch) cap = ctx->opt.max_batch;
-    if (cap > 65535) cap = 65535;
-    if (cap < 1) return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
-    const int Tc = (int)(cap < T ? cap : T);
-    rc = ensure_ws(ctx, per * (size_t)Tc);
+    const GradSizes g = grad_sizes(n, d);
+    const size_t a_bytes = g.a, z_bytes = g.z, st_bytes = g.st, part_bytes = g.part;
+    Chunking ch;
+    if (!chunk_batch(ctx->opt, ctx->budget, ctx->models_bytes, g.per, 0, T, &ch))
+        return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", g.per);
+    const int Tc = ch.Tc;
+    rc = ensure_ws(ctx, ch.bytes);
     if (rc) return rc;
     char* c = (char*)ctx->ws;
     double* A = (double*)c; c += a_bytes * Tc;
@@ -1122,14 +1205,9 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int nt = gp::num_tiles(n);
     const int npad = nt * GP_NB;
-    const size_t bL = align256(gp::packed_elems(n) * sizeof(double));
-    const size_t bZ = align256((size_t)2 * npad * sizeof(double));
-    const size_t bx = align256((size_t)n * d * sizeof(double));
-    const size_t bth = align256((size_t)d * sizeof(double));
-    const size_t bsc = align256(8 * sizeof(double));
-    const size_t bstat = align256(sizeof(int));
-    const size_t bst = align256(sizeof(gp::InstState));
-    const size_t total = bL + bZ + bx + bth + bsc + bstat + bst;
+    const ModelSizes ms = model_sizes(n, d);
+    const size_t bL = ms.L, bZ = ms.Z, bx = ms.x, bth = ms.th, bsc = ms.sc, bstat = ms.stat;
+    const size_t total = ms.total;
     if (total + ctx->models_bytes + ctx->ws_bytes > ctx->budget)
         return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
     gp_model* m = new gp_model();
@@ -1212,18 +1290,10 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int npad = m->nt * GP_NB;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms <= 0) {
-        cudaGetLastError();
-        sms = 1;
-    }
-    const int ppc = gp::predict_points_per_cta(N, sms);
-    const size_t per_cta = gp::predict_work_per_cta(m->nt, ppc);
-    const int blocks_total = (N + ppc - 1) / ppc;
-    int chunk = blocks_total < 4 * sms ? blocks_total : 4 * sms;
-    size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
-    while (chunk > 1 && per_cta * chunk > avail) chunk /= 2;
-    int rc = ensure_ws(ctx, s2 ? per_cta * chunk : 256);
+    const size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    const PredictShape sh = predict_shape(m->nt, N, ctx->sms, avail, s2 != nullptr);
+    const int ppc = sh.ppc, blocks_total = sh.blocks, chunk = sh.chunk;
+    int rc = ensure_ws(ctx, sh.bytes);
     if (rc) return rc;
     const double c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
     const float2* Ldf = reinterpret_cast<const float2*>(m->L);
@@ -1256,5 +1326,72 @@ void gp_model_free(gp_model* m) {
 }
 
 size_t gp_model_bytes(const gp_model* m) { return m ? m->bytes : 0; }
+
+int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size_t* bytes) {
+    if (!bytes) return fail(ctx, GP_EINVAL, "null bytes pointer");
+    *bytes = 0;
+    gp_options opt;
+    size_t budget = SIZE_MAX, held = 0, ws = 0;
+    int sms = 152;
+    if (ctx) {
+        opt = ctx->opt;
+        budget = ctx->budget;
+        held = ctx->models_bytes;
+        ws = ctx->ws_bytes;
+        sms = ctx->sms;
+    } else {
+        gp_default_options(&opt);
+    }
+    if (n < 1 || n > (1 << 20)) return fail(ctx, GP_EINVAL, "n = %d out of range [1, 2^20]", n);
+    if (d < 1 || d > GP_MAX_D) return fail(ctx, GP_EINVAL, "d = %d out of range [1, %d]", d, GP_MAX_D);
+    const size_t avail = budget > held ? budget - held : 0;
+    // a workspace larger than the arena must fit the budget next to the models
+    auto grow = [&](size_t need) {
+        if (need > ws && need > avail)
+            return fail(ctx, GP_ENOMEM, "workspace of %zu bytes exceeds the HBM budget", need);
+        *bytes = need;
+        return (int)GP_OK;
+    };
+    auto batch = [&](size_t per, size_t extra, size_t* out) {
+        Chunking ch;
+        if (!chunk_batch(opt, budget, held, per, extra, count, &ch))
+            return fail(ctx, GP_ENOMEM, "one instance (%zu bytes) exceeds the HBM budget", per);
+        *out = ch.bytes;
+        return (int)GP_OK;
+    };
+    switch (call) {
+    case GP_CALL_NLL_BATCH: {
+        if (count < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", count);
+        if (prec < GP_FP64 || prec > GP_AUTO) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
+        size_t b64 = 0, bsplit = 0, b32 = 0;
+        int rc = GP_OK;
+        if (prec == GP_FP64 || prec == GP_AUTO) rc = batch(per_instance_bytes_f64(n), 0, &b64);
+        if (rc == GP_OK && (prec == GP_MIXED || prec == GP_AUTO))
+            rc = batch(mixed_sizes(n, opt.slices).per, kMixedTail, &bsplit);
+        if (rc == GP_OK && (prec == GP_FP32 || prec == GP_AUTO))
+            rc = batch(mixed_sizes(n, 3).per, kMixedTail, &b32);
+        if (rc) return rc;
+        *bytes = std::max(b64, std::max(bsplit, b32)) + (prec == GP_AUTO ? auto_staging_bytes(count, d) : 0);
+        return GP_OK;
+    }
+    case GP_CALL_NLL_GRAD: {
+        if (count < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", count);
+        if (d > 16) return fail(ctx, GP_ENOTSUP, "the gradient is built for d <= 16 (d = %d)", d);
+        return batch(grad_sizes(n, d).per, 0, bytes);
+    }
+    case GP_CALL_FIT: {
+        const size_t total = model_sizes(n, d).total;
+        if (total + held + ws > budget) return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
+        *bytes = total;
+        return GP_OK;
+    }
+    case GP_CALL_PREDICT:
+        if (count < 0) return fail(ctx, GP_EINVAL, "N = %d must be >= 0", count);
+        if (count == 0) return GP_OK;
+        return grow(predict_shape(gp::num_tiles(n), count, sms, avail, true).bytes);
+    default:
+        return fail(ctx, GP_EINVAL, "unknown call %d", call);
+    }
+}
 
 }  // extern "C"

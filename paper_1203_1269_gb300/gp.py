@@ -22,6 +22,8 @@ PRECISIONS = {"fp64": GP_FP64, "mixed": GP_MIXED, "fp32": GP_FP32, "auto": GP_AU
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 # gp_correlation: eq. (2)'s power-exponential family and the Matern family
 CORRELATIONS = {"powexp": 0, "matern12": 1, "matern32": 2, "matern52": 3}
+# gp_call: the calls whose device memory gp_call_bytes reports
+CALLS = {"nll_batch": 0, "nll_grad": 1, "fit": 2, "predict": 3}
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ENOTPD", -4: "ECUDA", -5: "ETIMEOUT",
           -6: "EDEGENERATE", -7: "ENOTSUP"}
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTPD, GP_ECUDA, GP_ETIMEOUT, GP_EDEGENERATE, GP_ENOTSUP = \
@@ -111,12 +113,29 @@ def load(path=None):
     lib.gp_model_free.restype = None
     lib.gp_model_bytes.argtypes = [P]
     lib.gp_model_bytes.restype = _c_size
+    lib.gp_call_bytes.argtypes = [P, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_size)]
     _lib = lib
     return lib
 
 
 def _ptr(t):
     return None if t is None else _vp(t.data_ptr())
+
+
+def call_bytes(call, n, d, count=1, prec="mixed", ctx=None):
+    """Device bytes a call would allocate (gp_call_bytes): the workspace of
+    "nll_batch" (count = T, at precision prec), "nll_grad" (count = T) or
+    "predict" (count = N, with variances; n, d of the model), or the model of
+    "fit".  Host arithmetic only, so it needs no GPU; ctx=None sizes with the
+    default options and no budget limit."""
+    lib = ctx._lib if ctx is not None else load()
+    h = ctx._h if ctx is not None else None
+    out = _c_size()
+    rc = lib.gp_call_bytes(h, CALLS[call], int(n), int(d), int(count), _prec(prec), ctypes.byref(out))
+    if rc != 0:
+        msg = lib.gp_last_error(h).decode() if h is not None else "gp_call_bytes"
+        raise GPError(rc, msg)
+    return int(out.value)
 
 
 def _dev_f64(t, name, shape=None, device=None):
@@ -263,6 +282,10 @@ class Context:
 
     def workspace_bytes(self):
         return int(self._lib.gp_workspace_bytes(self._h))
+
+    def call_bytes(self, call, n, d, count=1, prec="mixed"):
+        """gp_call_bytes with this context's options and budget."""
+        return call_bytes(call, n, d, count, prec, ctx=self)
 
     def close(self):
         if getattr(self, "_h", None):

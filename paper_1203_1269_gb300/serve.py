@@ -33,25 +33,20 @@ from . import gp, inputs
 _MB = 1 << 20
 
 
-def mixed_bytes(n, T=32, slices=5):
-    """Workspace gp_nll_batch(GP_MIXED) asks for T candidates of size n."""
-    nt = (n + 127) // 128
-    tiles = nt * (nt + 1) // 2
-    a = tiles * 16384 * 8
-    per = (2 * a + nt * 7 * 16384 * 2 + nt * 128 * 4 + 7 * 16384 * 2 + 512 + nt * slices * 2 * 16384 * 2
-           + nt * 128 * 4 + nt * 16384 * 8 + 5 * nt * 128 * 8 + 256)
-    return T * per + 256
+FIT_CANDIDATES = 32   # theta candidates evaluated per fit request (inputs.request_data)
+
+
+def eval_bytes(n, d, prec, T=FIT_CANDIDATES):
+    """Workspace of gp_nll_batch for T candidates, as the library sizes it."""
+    return gp.call_bytes("nll_batch", n, d, T, prec)
 
 
 def model_bytes(n, d):
-    nt = (n + 127) // 128
-    return nt * (nt + 1) // 2 * 16384 * 8 + 2 * nt * 128 * 8 + n * d * 8 + 4096
+    return gp.call_bytes("fit", n, d)
 
 
-def predict_bytes(n, N):
-    nt = (n + 127) // 128
-    blocks = min((N + 31) // 32, 4 * 152)
-    return blocks * nt * 128 * 32 * 8
+def predict_bytes(n, d, N):
+    return gp.call_bytes("predict", n, d, N)
 
 
 class Result:
@@ -102,9 +97,9 @@ class Server:
 
     def _need(self, req):
         if req.kind == "fit":
-            return mixed_bytes(req.n) + model_bytes(req.n, req.d)
+            return eval_bytes(req.n, req.d, self.prec) + model_bytes(req.n, req.d)
         tgt = self.requests[req.target]
-        return predict_bytes(tgt.n, self.N_pred) + model_bytes(tgt.n, tgt.d)
+        return predict_bytes(tgt.n, tgt.d, self.N_pred) + model_bytes(tgt.n, tgt.d)
 
     # -- submission ----------------------------------------------------------
     def submit(self, req):
