@@ -237,6 +237,42 @@ def test_fit_predict_matches_oracle(ctx):
     model.free()
 
 
+def test_predict_in_many_launches():
+    """N = 20000 test points take several launches (at most four waves of
+    CTAs each), and a budget that leaves room for few CTAs' scratch takes
+    many more: the predictions are the same bits either way, and sampled
+    points (both ends, the launch boundaries) match the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_1269_gb300 import gp
+    g = np.random.default_rng(81)
+    n, d, N = 200, 3, 20000
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    theta = np.array([2.0, 4.0, 3.0])
+    xs = g.random((N, d))
+    out = {}
+    for budget in (0, 2 << 20):
+        c = gp.Context(0, hbm_budget_bytes=budget)
+        try:
+            model = c.fit(dev(x), dev(y), dev(theta), 1.95, 1e-8, "fp64")
+            before = c.launch_count()
+            yh, s2 = c.predict(model, dev(xs))
+            out[budget] = (host(yh), host(s2), c.launch_count() - before)
+            model.free()
+        finally:
+            c.close()
+    (y0, v0, l0), (y1, v1, l1) = out[0], out[2 << 20]
+    assert l0 >= 2 and l1 > l0
+    assert np.array_equal(y0, y1) and np.array_equal(v0, v1)
+    idx = np.unique(np.r_[0, 1, N - 1, np.arange(9700, 9760), np.arange(19440, 19470),
+                          g.integers(0, N, 200)])
+    yo, so, st = oracle.predict(x, y, theta, 1.95, 1e-8, xs[idx])
+    o, _ = oracle.nll(x, y, theta, 1.95, 1e-8, want_cond=True)
+    assert np.max(np.abs(y0[idx] - yo)) <= 1e-8 * max(1.0, np.max(np.abs(yo)))
+    assert np.max(np.abs(v0[idx] - so)) <= 1e-8 * o["sigma2"]
+
+
 @pytest.mark.parametrize("n", [1, 129, 260])
 def test_fit_predict_ragged_and_interpolation(ctx, n):
     g = np.random.default_rng(n + 5)
