@@ -151,3 +151,18 @@ def test_prec_used_reports_fixed_precision(ctx):
                    logdet=torch.empty(8, **kw), status=torch.empty(8, dtype=torch.int32, device="cuda"))
         ctx.nll_batch(dev(w.x), dev(w.y), dev(w.thetas[:8]), w.p, w.delta, name, out=out)
         assert np.all(host(out["prec_used"]) == gp.PRECISIONS[name])
+
+
+def test_auto_chunked_matches_one_chunk(ctx):
+    """GP_AUTO over a batch split into chunks of 5 (max_batch): every
+    candidate's estimate, route and values are the same bits as in one chunk."""
+    x, y, th, p, delta = spread_case()
+    base = ctx.options()
+    try:
+        one = ctx.nll_batch(dev(x), dev(y), dev(th), p, delta, "auto", cond=True)
+        ctx.set_options(max_batch=5)
+        many = ctx.nll_batch(dev(x), dev(y), dev(th), p, delta, "auto", cond=True)
+    finally:
+        ctx.set_options(**base)
+    for k in ("nll", "mu", "sigma2", "logdet", "status", "cond", "prec_used"):
+        assert np.array_equal(host(many[k]), host(one[k]), equal_nan=True), k

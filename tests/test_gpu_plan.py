@@ -62,6 +62,33 @@ def test_plan_replays_the_call(ctx, prec, cond):
     plan.free()
 
 
+def test_plan_of_a_chunked_batch(ctx):
+    """A batch processed in chunks (max_batch = 4 of T = 10) records every
+    chunk's launches in the graph and replays to the same bits."""
+    g = np.random.default_rng(503)
+    x = dev(inputs.random_lhd(g, 300, 3))
+    y = dev(inputs.y_sinsum(host(x)))
+    th = dev(inputs.log_uniform_thetas(g, 10, 3, lo=-0.5, hi=1.0))
+    base = ctx.options()
+    try:
+        ctx.set_options(max_batch=4)
+        l0 = ctx.launch_count()
+        direct = ctx.nll_batch(x, y, th, 1.95, 1e-6, "mixed")
+        torch.cuda.synchronize()
+        per_call = ctx.launch_count() - l0
+        plan = ctx.plan_nll_batch(x, y, th, 1.95, 1e-6, "mixed")
+    finally:
+        ctx.set_options(**base)
+    assert plan.kernels == per_call
+    for k in KEYS:
+        plan.out[k].fill_(0)
+    plan.launch()
+    torch.cuda.synchronize()
+    for k in KEYS:
+        assert np.array_equal(host(plan.out[k]), host(direct[k]), equal_nan=True), k
+    plan.free()
+
+
 def test_plan_owns_its_workspace(ctx):
     """Calls that regrow the context's workspace leave the plan intact."""
     g = np.random.default_rng(502)
