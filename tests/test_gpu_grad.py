@@ -115,3 +115,25 @@ def test_grad_chunked_matches_one_chunk(ctx):
     for k in ("nll", "grad", "status"):
         assert np.array_equal(host(got[k]), host(ref[k]), equal_nan=True), k
 
+
+
+def test_grad_at_max_d(ctx):
+    """d = 16, the largest d the gradient is built for, against the oracle;
+    d = 17 is refused with GP_ENOTSUP."""
+    from paper_1203_1269_gb300 import gp
+    g = np.random.default_rng(65)
+    n, d, delta = 200, 16, 1e-6
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 2, d, lo=-1.0, hi=0.0)
+    res = ctx.nll_grad_batch(dev(x), dev(y), dev(th), 1.95, delta)
+    assert np.all(host(res["status"]) == 0)
+    G = host(res["grad"])
+    for t in range(len(th)):
+        go, _, st = oracle.nll_grad(x, y, th[t], 1.95, delta)
+        assert st == 0
+        assert np.max(np.abs(G[t] - go)) <= 1e-8 * max(np.max(np.abs(go)), 1.0)
+    x17 = g.random((n, 17))
+    with pytest.raises(gp.GPError) as e:
+        ctx.nll_grad_batch(dev(x17), dev(y), dev(g.random((1, 17))), 1.95, delta)
+    assert e.value.code == gp.GP_ENOTSUP

@@ -273,6 +273,38 @@ def test_predict_in_many_launches():
     assert np.max(np.abs(v0[idx] - so)) <= 1e-8 * o["sigma2"]
 
 
+@pytest.mark.parametrize("d", [17, 64])
+def test_wide_designs_up_to_max_d(ctx, d):
+    """d just past the assembly kernels' register-bounded variants (17) and
+    the largest d the library accepts (64): -2logL at both precisions and
+    kriging against the oracle; d = 65 is rejected."""
+    from paper_1203_1269_gb300 import gp
+    g = np.random.default_rng(90 + d)
+    n, T, p, delta = 300, 4, 1.95, 1e-6
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, T, d, lo=-1.5, hi=-0.5)
+    ref, st = oracle.nll_batch(x, y, th, p, delta, want_cond=True)
+    assert np.all(st == 0) and np.all(ref[:, 6] <= 1e8)
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-6)):
+        res = ctx.nll_batch(dev(x), dev(y), dev(th), p, delta, prec)
+        assert np.all(host(res["status"]) == 0)
+        rel = np.abs(host(res["nll"]) - ref[:, 0]) / np.abs(ref[:, 0])
+        assert rel.max() <= tol, (prec, rel.max())
+    model = ctx.fit(dev(x), dev(y), dev(th[0]), p, delta, "fp64")
+    xs = g.random((50, d))
+    yh, s2 = ctx.predict(model, dev(xs))
+    yo, so, _ = oracle.predict(x, y, th[0], p, delta, xs)
+    assert np.max(np.abs(host(yh) - yo)) <= 1e-8 * max(1.0, np.max(np.abs(yo)))
+    assert np.max(np.abs(host(s2) - so)) <= 1e-8 * model.sigma2
+    model.free()
+    if d == 64:
+        x65 = g.random((n, 65))
+        with pytest.raises(gp.GPError) as e:
+            ctx.nll_batch(dev(x65), dev(y), dev(g.random((1, 65))), p, delta, "fp64")
+        assert e.value.code == gp.GP_EINVAL
+
+
 @pytest.mark.parametrize("n", [1, 129, 260])
 def test_fit_predict_ragged_and_interpolation(ctx, n):
     g = np.random.default_rng(n + 5)
