@@ -21,6 +21,7 @@ are identical alone and in the mix (tests/test_gpu_serve.py checks this).
 """
 import argparse
 import collections
+import functools
 import json
 import threading
 import time
@@ -36,15 +37,20 @@ _MB = 1 << 20
 FIT_CANDIDATES = 32   # theta candidates evaluated per fit request (inputs.request_data)
 
 
+# The scheduler sizes every queued request at each pick: the library's figures
+# depend only on these arguments (default options, no budget), so keep them.
+@functools.lru_cache(maxsize=4096)
 def eval_bytes(n, d, prec, T=FIT_CANDIDATES):
     """Workspace of gp_nll_batch for T candidates, as the library sizes it."""
     return gp.call_bytes("nll_batch", n, d, T, prec)
 
 
+@functools.lru_cache(maxsize=4096)
 def model_bytes(n, d):
     return gp.call_bytes("fit", n, d)
 
 
+@functools.lru_cache(maxsize=4096)
 def predict_bytes(n, d, N):
     return gp.call_bytes("predict", n, d, N)
 

@@ -95,3 +95,12 @@ def test_errors(gp):
     import ctypes
     out = ctypes.c_size_t()
     assert lib.gp_call_bytes(None, 7, 100, 6, 1, 1, ctypes.byref(out)) == gp.GP_EINVAL
+
+
+def test_serving_admission_uses_the_library_sizes(gp):
+    from paper_1203_1269_gb300 import serve
+    for n, d in ((256, 2), (1000, 6), (8192, 12)):
+        for prec in ("mixed", "fp64"):
+            assert serve.eval_bytes(n, d, prec) == gp.call_bytes("nll_batch", n, d, serve.FIT_CANDIDATES, prec)
+        assert serve.model_bytes(n, d) == gp.call_bytes("fit", n, d)
+        assert serve.predict_bytes(n, d, 1000) == gp.call_bytes("predict", n, d, 1000)
