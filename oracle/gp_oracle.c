@@ -28,9 +28,24 @@
  *     sigma2 [ c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1) ] with
  *     c0 = 1 + delta (nugget counted in the process variance) or c0 = 1.
  */
-#include <math.h>
+#include <float.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+
+/* The arithmetic type.  The oracle proper is built in IEEE double.  Built
+ * with -DGPO_EXTENDED the same definitions run in long double (64-bit
+ * significand on x86_64, 113-bit on aarch64): that build exists only to
+ * bound the double build's own rounding error on small cases.  The math
+ * calls are type-generic (tgmath.h), so each runs in the arithmetic type. */
+#ifdef GPO_EXTENDED
+typedef long double real;
+#define GPO_UNIT_ROUNDOFF (LDBL_EPSILON / 2)
+#else
+typedef double real;
+#define GPO_UNIT_ROUNDOFF (DBL_EPSILON / 2)
+#endif
+#define GPO_PI ((real)3.141592653589793238462643383279502884L)
 
 #define GPO_OK 0
 #define GPO_NOTPD (-3)
@@ -55,15 +70,15 @@
 #define GPO_MATERN52 3
 
 /* One dimension's factor of the correlation. */
-static double gpo_corr_1d(double diff, double theta, double p, int fam) {
-    double a = fabs(diff);
+static real gpo_corr_1d(real diff, real theta, real p, int fam) {
+    real a = fabs(diff);
     if (fam == GPO_MATERN12) return exp(-theta * a);
     if (fam == GPO_MATERN32) {
-        double h = sqrt(3.0) * theta * a;
+        real h = sqrt((real)3) * theta * a;
         return (1.0 + h) * exp(-h);
     }
     if (fam == GPO_MATERN52) {
-        double h = sqrt(5.0) * theta * a;
+        real h = sqrt((real)5) * theta * a;
         return (1.0 + h + h * h / 3.0) * exp(-h);
     }
     return exp(-theta * pow(a, p));
@@ -71,19 +86,19 @@ static double gpo_corr_1d(double diff, double theta, double p, int fam) {
 
 /* Correlation between two points: the product over the d input dimensions
  * (eq. 2 for the power-exponential family). */
-static double gpo_corr_pair(int d, const double* xi, const double* xj,
-                            const double* theta, double p, int fam) {
-    double r = 1.0;
+static real gpo_corr_pair(int d, const real* xi, const real* xj,
+                            const real* theta, real p, int fam) {
+    real r = 1.0;
     for (int k = 0; k < d; ++k) r *= gpo_corr_1d(xi[k] - xj[k], theta[k], p, fam);
     return r;
 }
 
 /* R(theta), full n x n, plus the nugget delta on the diagonal. */
-void gpo_corr_matrix(int n, int d, const double* x, const double* theta,
-                     double p, int fam, double delta, double* R) {
+void gpo_corr_matrix(int n, int d, const real* x, const real* theta,
+                     real p, int fam, real delta, real* R) {
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j < n; ++j) {
-            double v = gpo_corr_pair(d, x + (size_t)i * d, x + (size_t)j * d, theta, p, fam);
+            real v = gpo_corr_pair(d, x + (size_t)i * d, x + (size_t)j * d, theta, p, fam);
             if (i == j) v += delta;
             R[(size_t)i * n + j] = v;
         }
@@ -91,8 +106,8 @@ void gpo_corr_matrix(int n, int d, const double* x, const double* theta,
 }
 
 /* Cross-correlations r_i(x*) = corr(z(x*), z(x_i)) by eq. (2); no nugget. */
-void gpo_cross_corr(int n, int d, const double* x, const double* xs,
-                    const double* theta, double p, int fam, double* r) {
+void gpo_cross_corr(int n, int d, const real* x, const real* xs,
+                    const real* theta, real p, int fam, real* r) {
     for (int i = 0; i < n; ++i)
         r[i] = gpo_corr_pair(d, xs, x + (size_t)i * d, theta, p, fam);
 }
@@ -101,11 +116,11 @@ void gpo_cross_corr(int n, int d, const double* x, const double* xs,
  * L is written to the lower triangle of L (upper set to zero).  The paper's
  * CPU path factors R by Cholesky (Section 3).  Returns 0, or (k+1) where k
  * is the first column whose pivot is not positive and finite. */
-int gpo_cholesky(int n, const double* R, double* L) {
-    memset(L, 0, sizeof(double) * (size_t)n * n);
+int gpo_cholesky(int n, const real* R, real* L) {
+    memset(L, 0, sizeof(real) * (size_t)n * n);
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j <= i; ++j) {
-            double s = R[(size_t)i * n + j];
+            real s = R[(size_t)i * n + j];
             for (int k = 0; k < j; ++k)
                 s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
             if (i == j) {
@@ -120,18 +135,18 @@ int gpo_cholesky(int n, const double* R, double* L) {
 }
 
 /* Forward substitution L z = b. */
-void gpo_forward(int n, const double* L, const double* b, double* z) {
+void gpo_forward(int n, const real* L, const real* b, real* z) {
     for (int i = 0; i < n; ++i) {
-        double s = b[i];
+        real s = b[i];
         for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * z[k];
         z[i] = s / L[(size_t)i * n + i];
     }
 }
 
 /* Back substitution L' w = e. */
-void gpo_backward(int n, const double* L, const double* e, double* w) {
+void gpo_backward(int n, const real* L, const real* e, real* w) {
     for (int i = n - 1; i >= 0; --i) {
-        double s = e[i];
+        real s = e[i];
         for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * w[k];
         w[i] = s / L[(size_t)i * n + i];
     }
@@ -142,22 +157,22 @@ void gpo_backward(int n, const double* L, const double* e, double* w) {
  * (W. W. Hager, "Condition estimates", SIAM J. Sci. Stat. Comput. 5, 1984),
  * at most 5 steps, using solves with L only.  The estimate is a lower bound
  * of the true condition number. */
-double gpo_cond1_est(int n, const double* A, const double* L) {
-    double* work = (double*)malloc(sizeof(double) * 5 * (size_t)n);
+real gpo_cond1_est(int n, const real* A, const real* L) {
+    real* work = (real*)malloc(sizeof(real) * 5 * (size_t)n);
     if (!work) return NAN;
-    double* v = work;
-    double* yv = work + n;
-    double* z = work + 2 * n;
-    double* t = work + 3 * n;
-    double* sg = work + 4 * n;
-    double anorm = 0.0;
+    real* v = work;
+    real* yv = work + n;
+    real* z = work + 2 * n;
+    real* t = work + 3 * n;
+    real* sg = work + 4 * n;
+    real anorm = 0.0;
     for (int j = 0; j < n; ++j) {
-        double c = 0.0;
+        real c = 0.0;
         for (int i = 0; i < n; ++i) c += fabs(A[(size_t)i * n + j]);
         if (c > anorm) anorm = c;
     }
     for (int i = 0; i < n; ++i) v[i] = 1.0 / n;
-    double est = 0.0;
+    real est = 0.0;
     int jprev = -1;
     for (int iter = 0; iter < 5; ++iter) {
         gpo_forward(n, L, v, t);
@@ -168,10 +183,10 @@ double gpo_cond1_est(int n, const double* A, const double* L) {
         gpo_forward(n, L, sg, t);
         gpo_backward(n, L, t, z);           /* z = A^-T sign(yv), A symmetric */
         int jmax = 0;
-        double zmax = fabs(z[0]);
+        real zmax = fabs(z[0]);
         for (int i = 1; i < n; ++i)
             if (fabs(z[i]) > zmax) { zmax = fabs(z[i]); jmax = i; }
-        double ztv = 0.0;
+        real ztv = 0.0;
         for (int i = 0; i < n; ++i) ztv += z[i] * v[i];
         if (zmax <= ztv || jmax == jprev) break;
         for (int i = 0; i < n; ++i) v[i] = 0.0;
@@ -185,9 +200,10 @@ double gpo_cond1_est(int n, const double* A, const double* L) {
 /* Q = e'e is zero in exact arithmetic when Y lies in the span of 1 (always
  * so for n = 1).  In floating point e = b - mu a then holds only rounding
  * noise of size ~u |b|, so Q is taken as zero when it is no larger than
- * 16 n u^2 b'b (u = 2^-53), which includes Q == 0 exactly. */
-static int gpo_q_is_zero(int n, double Q, double bb) {
-    const double u = 1.1102230246251565e-16;
+ * 16 n u^2 b'b (u the unit roundoff: 2^-53 in double), which includes
+ * Q == 0 exactly. */
+static int gpo_q_is_zero(int n, real Q, real bb) {
+    const real u = GPO_UNIT_ROUNDOFF;
     return Q <= 16.0 * n * u * u * bb;
 }
 
@@ -205,17 +221,17 @@ static int gpo_q_is_zero(int n, double Q, double bb) {
  * Route: R by eq. (2) -> Cholesky R = L L' -> a = L^-1 1, b = L^-1 Y, so that
  * 1'R^-1 1 = a'a and 1'R^-1 Y = a'b; e = b - mu a = L^-1 (Y - 1 mu) and
  * Q = e'e. */
-int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
-            double p, int fam, double delta, int want_cond, double* out) {
-    const double nan = NAN;
+int gpo_nll(int n, int d, const real* x, const real* y, const real* theta,
+            real p, int fam, real delta, int want_cond, real* out) {
+    const real nan = NAN;
     for (int i = 0; i < 7; ++i) out[i] = nan;
     out[6] = 0.0;
-    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
-    double* a = (double*)malloc(sizeof(double) * (size_t)n);
-    double* b = (double*)malloc(sizeof(double) * (size_t)n);
-    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    real* R = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* L = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* ones = (real*)malloc(sizeof(real) * (size_t)n);
+    real* a = (real*)malloc(sizeof(real) * (size_t)n);
+    real* b = (real*)malloc(sizeof(real) * (size_t)n);
+    real* e = (real*)malloc(sizeof(real) * (size_t)n);
     int status = GPO_OK;
     if (!R || !L || !ones || !a || !b || !e) { status = GPO_ENOMEM; goto done; }
 
@@ -229,15 +245,15 @@ int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
     for (int i = 0; i < n; ++i) ones[i] = 1.0;
     gpo_forward(n, L, ones, a);
     gpo_forward(n, L, y, b);
-    double aa = 0.0, ab = 0.0;
+    real aa = 0.0, ab = 0.0;
     for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
-    double mu = ab / aa;
-    double Q = 0.0, bb = 0.0;
+    real mu = ab / aa;
+    real Q = 0.0, bb = 0.0;
     for (int i = 0; i < n; ++i) { e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; bb += b[i] * b[i]; }
-    double logdet = 0.0;
+    real logdet = 0.0;
     for (int i = 0; i < n; ++i) logdet += log(L[(size_t)i * n + i]);
     logdet *= 2.0;
-    double sigma2 = Q / n;
+    real sigma2 = Q / n;
     out[1] = mu;
     out[2] = sigma2;
     out[3] = logdet;
@@ -248,7 +264,7 @@ int gpo_nll(int n, int d, const double* x, const double* y, const double* theta,
         out[5] = -INFINITY;
     } else {
         out[0] = logdet + n * log(Q);
-        out[5] = logdet + n * log(sigma2) + n * (1.0 + log(2.0 * M_PI));
+        out[5] = logdet + n * log(sigma2) + n * (1.0 + log(2 * GPO_PI));
     }
     if (want_cond) out[6] = gpo_cond1_est(n, R, L);
 done:
@@ -259,9 +275,9 @@ done:
 /* -2 log L at T candidate theta vectors (theta is T x d row-major); the
  * candidates are independent, so they are spread over host threads.  Each
  * evaluation is the single-threaded gpo_nll above.  out is T x 7. */
-void gpo_nll_batch(int n, int d, const double* x, const double* y, int T,
-                   const double* theta, double p, int fam, double delta, int want_cond,
-                   double* out, int* status) {
+void gpo_nll_batch(int n, int d, const real* x, const real* y, int T,
+                   const real* theta, real p, int fam, real delta, int want_cond,
+                   real* out, int* status) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < T; ++t)
         status[t] = gpo_nll(n, d, x, y, theta + (size_t)t * d, p, fam, delta,
@@ -274,16 +290,16 @@ void gpo_nll_batch(int n, int d, const double* x, const double* y, int T,
  * where v = L^-1 r gives r'R^-1 r = v'v and 1'R^-1 r = a'v, and
  * c0 = 1 + delta if nugget_in_var else 1.  s2 may be NULL.
  * Returns the status of the fit. */
-int gpo_predict(int n, int d, const double* x, const double* y, const double* theta,
-                double p, int fam, double delta, int N, const double* xs, int nugget_in_var,
-                double* yhat, double* s2) {
-    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
-    double* a = (double*)malloc(sizeof(double) * (size_t)n);
-    double* b = (double*)malloc(sizeof(double) * (size_t)n);
-    double* e = (double*)malloc(sizeof(double) * (size_t)n);
-    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+int gpo_predict(int n, int d, const real* x, const real* y, const real* theta,
+                real p, int fam, real delta, int N, const real* xs, int nugget_in_var,
+                real* yhat, real* s2) {
+    real* R = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* L = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* ones = (real*)malloc(sizeof(real) * (size_t)n);
+    real* a = (real*)malloc(sizeof(real) * (size_t)n);
+    real* b = (real*)malloc(sizeof(real) * (size_t)n);
+    real* e = (real*)malloc(sizeof(real) * (size_t)n);
+    real* w = (real*)malloc(sizeof(real) * (size_t)n);
     int status = GPO_OK;
     if (!R || !L || !ones || !a || !b || !e || !w) { status = GPO_ENOMEM; goto done; }
     gpo_corr_matrix(n, d, x, theta, p, fam, delta, R);
@@ -295,30 +311,30 @@ int gpo_predict(int n, int d, const double* x, const double* y, const double* th
     for (int i = 0; i < n; ++i) ones[i] = 1.0;
     gpo_forward(n, L, ones, a);
     gpo_forward(n, L, y, b);
-    double aa = 0.0, ab = 0.0;
+    real aa = 0.0, ab = 0.0;
     for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
-    double mu = ab / aa;
-    double Q = 0.0;
+    real mu = ab / aa;
+    real Q = 0.0;
     for (int i = 0; i < n; ++i) { e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; }
-    double sigma2 = Q / n;
+    real sigma2 = Q / n;
     gpo_backward(n, L, e, w);
-    double c0 = nugget_in_var ? 1.0 + delta : 1.0;
+    real c0 = nugget_in_var ? 1.0 + delta : 1.0;
 #pragma omp parallel
     {
-        double* r = (double*)malloc(sizeof(double) * (size_t)n);
-        double* v = (double*)malloc(sizeof(double) * (size_t)n);
+        real* r = (real*)malloc(sizeof(real) * (size_t)n);
+        real* v = (real*)malloc(sizeof(real) * (size_t)n);
 #pragma omp for schedule(static)
         for (int m = 0; m < N; ++m) {
             if (!r || !v) { yhat[m] = NAN; if (s2) s2[m] = NAN; continue; }
             gpo_cross_corr(n, d, x, xs + (size_t)m * d, theta, p, fam, r);
-            double yh = 0.0;
+            real yh = 0.0;
             for (int i = 0; i < n; ++i) yh += r[i] * w[i];
             yhat[m] = mu + yh;
             if (s2) {
                 gpo_forward(n, L, r, v);
-                double vv = 0.0, av = 0.0;
+                real vv = 0.0, av = 0.0;
                 for (int i = 0; i < n; ++i) { vv += v[i] * v[i]; av += a[i] * v[i]; }
-                double g = 1.0 - av;
+                real g = 1.0 - av;
                 s2[m] = sigma2 * (c0 - vv + g * g / aa);
             }
         }
@@ -332,20 +348,20 @@ done:
 /* The factor and the solve vectors of one fit, for tests that check the
  * intermediate quantities: L (n x n), a = L^-1 1, b = L^-1 Y, w = R^-1(Y-1mu).
  * Returns the status. */
-int gpo_fit_parts(int n, int d, const double* x, const double* y, const double* theta,
-                  double p, int fam, double delta, double* R, double* L, double* a, double* b,
-                  double* w) {
+int gpo_fit_parts(int n, int d, const real* x, const real* y, const real* theta,
+                  real p, int fam, real delta, real* R, real* L, real* a, real* b,
+                  real* w) {
     gpo_corr_matrix(n, d, x, theta, p, fam, delta, R);
     if (gpo_cholesky(n, R, L) != 0) return GPO_NOTPD;
-    double* ones = (double*)malloc(sizeof(double) * (size_t)n);
-    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    real* ones = (real*)malloc(sizeof(real) * (size_t)n);
+    real* e = (real*)malloc(sizeof(real) * (size_t)n);
     if (!ones || !e) { free(ones); free(e); return GPO_ENOMEM; }
     for (int i = 0; i < n; ++i) ones[i] = 1.0;
     gpo_forward(n, L, ones, a);
     gpo_forward(n, L, y, b);
-    double aa = 0.0, ab = 0.0;
+    real aa = 0.0, ab = 0.0;
     for (int i = 0; i < n; ++i) { aa += a[i] * a[i]; ab += a[i] * b[i]; }
-    double mu = ab / aa;
+    real mu = ab / aa;
     for (int i = 0; i < n; ++i) e[i] = b[i] - mu * a[i];
     gpo_backward(n, L, e, w);
     free(ones); free(e);
@@ -358,16 +374,16 @@ int gpo_fit_parts(int n, int d, const double* x, const double* y, const double* 
  *   nu = 1/2:  -|dx|
  *   nu = 3/2:  rho' / rho = -h / (1 + h) * sqrt(3) |dx|
  *   nu = 5/2:  rho' / rho = -h (1 + h) / (3 (1 + h + h^2/3)) * sqrt(5) |dx| */
-static double gpo_dlog_corr_1d(double diff, double theta, double p, int fam) {
-    double a = fabs(diff);
+static real gpo_dlog_corr_1d(real diff, real theta, real p, int fam) {
+    real a = fabs(diff);
     if (fam == GPO_MATERN12) return -a;
     if (fam == GPO_MATERN32) {
-        double h = sqrt(3.0) * theta * a;
-        return -h / (1.0 + h) * sqrt(3.0) * a;
+        real h = sqrt((real)3) * theta * a;
+        return -h / (1.0 + h) * sqrt((real)3) * a;
     }
     if (fam == GPO_MATERN52) {
-        double h = sqrt(5.0) * theta * a;
-        return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(5.0) * a;
+        real h = sqrt((real)5) * theta * a;
+        return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt((real)5) * a;
     }
     return -pow(a, p);
 }
@@ -380,19 +396,19 @@ static double gpo_dlog_corr_1d(double diff, double theta, double p, int fam) {
  * nugget and the unit diagonal do not depend on theta).  R^-1 is formed
  * column by column by two triangular solves of e_j.  grad has d entries;
  * out is filled as by gpo_nll.  Returns the status (grad NaN if not OK). */
-int gpo_nll_grad(int n, int d, const double* x, const double* y, const double* theta,
-                 double p, int fam, double delta, double* grad, double* out) {
+int gpo_nll_grad(int n, int d, const real* x, const real* y, const real* theta,
+                 real p, int fam, real delta, real* grad, real* out) {
     int status = gpo_nll(n, d, x, y, theta, p, fam, delta, 0, out);
     for (int k = 0; k < d; ++k) grad[k] = NAN;
     if (status != GPO_OK) return status;
-    double* R = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* L = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* Ri = (double*)malloc(sizeof(double) * (size_t)n * n);
-    double* a = (double*)malloc(sizeof(double) * (size_t)n);
-    double* b = (double*)malloc(sizeof(double) * (size_t)n);
-    double* w = (double*)malloc(sizeof(double) * (size_t)n);
-    double* col = (double*)malloc(sizeof(double) * (size_t)n);
-    double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+    real* R = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* L = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* Ri = (real*)malloc(sizeof(real) * (size_t)n * n);
+    real* a = (real*)malloc(sizeof(real) * (size_t)n);
+    real* b = (real*)malloc(sizeof(real) * (size_t)n);
+    real* w = (real*)malloc(sizeof(real) * (size_t)n);
+    real* col = (real*)malloc(sizeof(real) * (size_t)n);
+    real* tmp = (real*)malloc(sizeof(real) * (size_t)n);
     if (!R || !L || !Ri || !a || !b || !w || !col || !tmp) {
         status = GPO_ENOMEM;
         goto done;
@@ -406,15 +422,15 @@ int gpo_nll_grad(int n, int d, const double* x, const double* y, const double* t
         for (int i = 0; i < n; ++i) Ri[(size_t)i * n + j] = col[i];
     }
     {
-        const double Q = out[4];
+        const real Q = out[4];
         for (int k = 0; k < d; ++k) {
-            double tr = 0.0, quad = 0.0;
+            real tr = 0.0, quad = 0.0;
             for (int i = 0; i < n; ++i) {
                 for (int j = 0; j < n; ++j) {
                     if (i == j) continue;
-                    const double* xi = x + (size_t)i * d;
-                    const double* xj = x + (size_t)j * d;
-                    const double dR = R[(size_t)i * n + j] * gpo_dlog_corr_1d(xi[k] - xj[k], theta[k], p, fam);
+                    const real* xi = x + (size_t)i * d;
+                    const real* xj = x + (size_t)j * d;
+                    const real dR = R[(size_t)i * n + j] * gpo_dlog_corr_1d(xi[k] - xj[k], theta[k], p, fam);
                     tr += Ri[(size_t)j * n + i] * dR;
                     quad += w[i] * dR * w[j];
                 }

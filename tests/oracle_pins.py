@@ -534,3 +534,107 @@ ALL_CHECKS = [
     check_fit_parts, check_matern_half_is_exponential, check_matern_bessel, check_matern_n2,
     check_matern_predict, check_grad_finite_differences, check_grad_n2,
 ]
+
+
+# ----------------------------------------- the oracle's own rounding error --
+#
+# The long-double build of the oracle (oracle.extended()) runs the same
+# definitions with a 64-bit significand.  It is pinned to the exact KMS closed
+# form at 50 digits, and then bounds the double oracle's own rounding error on
+# cases without a closed form.  These checks take both builds, so they stay out
+# of ALL_CHECKS (a planted mistake in the double build alone would disagree
+# with the intact extended build and tell nothing about the pins).
+
+def _ld_to_mpf(v, mpmath):
+    """Exact value of a numpy.longdouble as an mpmath number (a sum of three
+    doubles covers the 64- and the 113-bit significand)."""
+    v = np.longdouble(v)
+    total = mpmath.mpf(0)
+    for _ in range(3):
+        h = float(v)
+        total += mpmath.mpf(h)
+        v = v - np.longdouble(h)
+    return total
+
+
+def _kms_exact(n, theta, h, y, mpmath):
+    """-2logL, sigma2, log|R| of the KMS case in 50-digit arithmetic, for the
+    rho the double inputs define: rho = exp(-theta h) with theta and h exact."""
+    mpmath.mp.dps = 50
+    rho = mpmath.exp(-mpmath.mpf(theta) * mpmath.mpf(h))
+    c = 1 / (1 - rho * rho)
+    ys = [mpmath.mpf(float(v)) for v in y]
+    one = [mpmath.mpf(1)] * n
+
+    def qf(u, v):
+        s = mpmath.mpf(0)
+        for i in range(n):
+            s += u[i] * (1 if i in (0, n - 1) else 1 + rho * rho) * v[i]
+        for i in range(1, n):
+            s -= rho * (u[i] * v[i - 1] + u[i - 1] * v[i])
+        return c * s
+    A, B, C = qf(one, one), qf(one, ys), qf(ys, ys)
+    Q = C - B * B / A
+    logdet = (n - 1) * mpmath.log(1 - rho * rho)
+    return {"nll": logdet + n * mpmath.log(Q), "mu": B / A, "sigma2": Q / n, "logdet": logdet}
+
+
+def check_extended_kms_exact(ext, mpmath, seed=61):
+    """The extended build within n cond(R) 2^-64 of the exact KMS values,
+    relative to max(|value|, 1), for n = 2 to 120 and rho = 0.5 to 0.99, with
+    cond(R) <= ((1 + rho) / (1 - rho))^2 (the KMS eigenvalue bounds).  That is
+    2^11 below the double arithmetic's n cond u, whose evaluation is off by
+    1e-17 to 2e-13 on these cases: the extended arithmetic is at work."""
+    g = np.random.default_rng(seed)
+    h = 1.0 / 1024.0
+    for n in (2, 5, 33, 120):
+        for rho in (0.5, 0.9, 0.99):
+            theta = -math.log(rho) / h
+            x = (np.arange(n, dtype=np.float64) * h).reshape(n, 1)
+            y = g.standard_normal(n)
+            exact = _kms_exact(n, theta, h, y, mpmath)
+            out, st = ext.nll(x, y, [theta], 1.0, 0.0)
+            assert st == 0
+            bound = n * ((1 + rho) / (1 - rho)) ** 2 * 2.0 ** -64
+            for k in ("nll", "mu", "sigma2", "logdet"):
+                err = abs((_ld_to_mpf(out[k], mpmath) - exact[k]) / max(abs(exact[k]), 1))
+                assert err <= bound, (n, rho, k, float(err), bound)
+
+
+def check_double_within_rounding_bound(orc, ext, seed=7):
+    """The double oracle's own error, measured against the extended build:
+    -2logL, mu_hat, sigma2_hat, log|R|, kriging and the gradient within
+    8 n cond_1(R) u (u = 2^-53) of the extended values, relative to
+    max(|value|, 1) (sigma2_hat for the variance), for every family.  The
+    largest ratio seen is about one."""
+    from paper_1203_1269_gb300 import inputs
+    u = 2.0 ** -53
+    g = np.random.default_rng(seed)
+    ratios = []
+    for corr in ("powexp", "matern12", "matern32", "matern52"):
+        for n, d in ((3, 1), (10, 2), (40, 3), (100, 4)):
+            x = inputs.random_lhd(g, n, d)
+            y = inputs.y_sinsum(x)
+            for th in inputs.log_uniform_thetas(g, 4, d, lo=-1.0, hi=1.0):
+                od, sd = orc.nll(x, y, th, 1.95, 1e-8, want_cond=True, corr=corr)
+                oe, se = ext.nll(x, y, th, 1.95, 1e-8, corr=corr)
+                assert sd == se
+                if sd != 0:
+                    continue
+                bound = n * od["cond1"] * u
+                for k in ("nll", "mu", "sigma2", "logdet"):
+                    e = float(oe[k])
+                    ratios.append(abs(od[k] - e) / max(abs(e), 1.0) / bound)
+                xs = g.random((5, d))
+                yd, vd, _ = orc.predict(x, y, th, 1.95, 1e-8, xs, corr=corr)
+                ye, ve, _ = ext.predict(x, y, th, 1.95, 1e-8, xs, corr=corr)
+                ye, ve = ye.astype(np.float64), ve.astype(np.float64)
+                ratios.append(np.max(np.abs(yd - ye)) / max(1.0, np.max(np.abs(ye))) / bound)
+                ratios.append(np.max(np.abs(vd - ve)) / float(oe["sigma2"]) / bound)
+                if n > 1:
+                    gd, _, _ = orc.nll_grad(x, y, th, 1.95, 1e-8, corr=corr)
+                    ge, _, _ = ext.nll_grad(x, y, th, 1.95, 1e-8, corr=corr)
+                    ge = ge.astype(np.float64)
+                    ratios.append(np.max(np.abs(gd - ge)) / max(1.0, np.max(np.abs(ge))) / bound)
+    assert max(ratios) <= 8.0, max(ratios)
+    return max(ratios)

@@ -21,10 +21,10 @@ MUTANTS = {
     "corr_sign": ("return exp(-theta * pow(a, p));", "return exp(theta * pow(a, p));"),
     "matern12_squares": ("if (fam == GPO_MATERN12) return exp(-theta * a);",
                          "if (fam == GPO_MATERN12) return exp(-theta * a * a);"),
-    "matern32_constant": ("double h = sqrt(3.0) * theta * a;", "double h = sqrt(5.0) * theta * a;"),
+    "matern32_constant": ("real h = sqrt((real)3) * theta * a;", "real h = sqrt((real)5) * theta * a;"),
     "matern32_linear_coeff": ("return (1.0 + h) * exp(-h);", "return (1.0 + 0.5 * h) * exp(-h);"),
     "q_zero_threshold_off": ("return Q <= 16.0 * n * u * u * bb;", "return Q <= 0.0;"),
-    "predict_nugget_ignored": ("double c0 = nugget_in_var ? 1.0 + delta : 1.0;", "double c0 = 1.0;"),
+    "predict_nugget_ignored": ("real c0 = nugget_in_var ? 1.0 + delta : 1.0;", "real c0 = 1.0;"),
     "matern52_drops_quadratic": ("return (1.0 + h + h * h / 3.0) * exp(-h);", "return (1.0 + h) * exp(-h);"),
     "matern52_quadratic_coeff": ("return (1.0 + h + h * h / 3.0) * exp(-h);",
                                  "return (1.0 + h + h * h / 2.0) * exp(-h);"),
@@ -38,12 +38,12 @@ MUTANTS = {
                            "for (int k = 0; k < i; ++k) s -= L[(size_t)k * n + i] * z[k];"),
     "backward_transposed": ("for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * w[k];",
                             "for (int k = i + 1; k < n; ++k) s -= L[(size_t)i * n + k] * w[k];"),
-    "mu_inverted": ("double mu = ab / aa;\n    double Q = 0.0, bb", "double mu = aa / ab;\n    double Q = 0.0, bb"),
+    "mu_inverted": ("real mu = ab / aa;\n    real Q = 0.0, bb", "real mu = aa / ab;\n    real Q = 0.0, bb"),
     "residual_sign": ("e[i] = b[i] - mu * a[i]; Q += e[i] * e[i]; bb", "e[i] = b[i] + mu * a[i]; Q += e[i] * e[i]; bb"),
-    "logdet_not_doubled": ("    logdet *= 2.0;\n    double sigma2", "    double sigma2"),
+    "logdet_not_doubled": ("    logdet *= 2.0;\n    real sigma2", "    real sigma2"),
     "nll_uses_sigma2": ("out[0] = logdet + n * log(Q);", "out[0] = logdet + n * log(Q / n);"),
     "nll_drops_n": ("out[0] = logdet + n * log(Q);", "out[0] = logdet + log(Q);"),
-    "sigma2_not_over_n": ("double sigma2 = Q / n;\n    out[1]", "double sigma2 = Q;\n    out[1]"),
+    "sigma2_not_over_n": ("real sigma2 = Q / n;\n    out[1]", "real sigma2 = Q;\n    out[1]"),
     "predict_drops_mu": ("yhat[m] = mu + yh;", "yhat[m] = yh;"),
     "predict_var_sign": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 + vv + g * g / aa);"),
     "predict_var_unsquared": ("s2[m] = sigma2 * (c0 - vv + g * g / aa);", "s2[m] = sigma2 * (c0 - vv + g / aa);"),
@@ -56,9 +56,9 @@ MUTANTS = {
     "grad_trace_sign": ("tr += Ri[(size_t)j * n + i] * dR;", "tr -= Ri[(size_t)j * n + i] * dR;"),
     "grad_drops_n_over_q": ("grad[k] = tr - n / Q * quad;", "grad[k] = tr - quad;"),
     "grad_power_wrong": ("    return -pow(a, p);", "    return -pow(a, p - 1.0);"),
-    "grad_matern32_dlog": ("return -h / (1.0 + h) * sqrt(3.0) * a;", "return -h * sqrt(3.0) * a;"),
-    "grad_matern52_dlog": ("return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(5.0) * a;",
-                           "return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt(3.0) * a;"),
+    "grad_matern32_dlog": ("return -h / (1.0 + h) * sqrt((real)3) * a;", "return -h * sqrt((real)3) * a;"),
+    "grad_matern52_dlog": ("return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt((real)5) * a;",
+                           "return -h * (1.0 + h) / (3.0 * (1.0 + h + h * h / 3.0)) * sqrt((real)3) * a;"),
     "grad_quad_one_sided": ("quad += w[i] * dR * w[j];", "quad += w[i] * dR * w[i];"),
     "grad_exponential_dlog": ("if (fam == GPO_MATERN12) return -a;", "if (fam == GPO_MATERN12) return -a * a;"),
 }

@@ -29,3 +29,17 @@ def test_batch_matches_single(orc):
         o, s = orc.nll(w.x, w.y, w.thetas[t], w.p, w.delta, want_cond=True)
         assert s == st[t]
         assert np.array_equal(np.array([o[k] for k in oracle.NLL_FIELDS]), out[t])
+
+
+def test_extended_build_matches_exact_kms():
+    """The long-double build of the oracle against the KMS closed form in
+    50-digit arithmetic."""
+    mpmath = pytest.importorskip("mpmath")
+    pins.check_extended_kms_exact(oracle.extended(), mpmath)
+
+
+def test_double_oracle_error_within_rounding_bound(orc):
+    """The double oracle's own rounding error, bounded through the extended
+    build: within 8 n cond_1(R) u everywhere it is compared."""
+    worst = pins.check_double_within_rounding_bound(orc, oracle.extended())
+    print(f"\nworst |double - extended| / (n cond u): {worst:.2f}")
