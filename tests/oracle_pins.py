@@ -10,7 +10,8 @@ oracle's own code:
     form and a tridiagonal inverse, so mu_hat, Q and -2logL follow in O(n).
   * hand derivations for n = 1, 2 (with a nugget) and n = 3 (adjugate).
   * log|R| against the eigenvalues from LAPACK's symmetric eigensolver.
-  * mu_hat, sigma2_hat, Q and kriging against LAPACK's general solver.
+  * mu_hat, sigma2_hat, Q and kriging against LAPACK's general solver, and
+    for n <= 16 against long-double Gauss-Jordan elimination.
   * invariants: row permutation, scaling and shifting of y, Hadamard's
     inequality, symmetry and unit diagonal.
   * the form of eq. (4) against the printed rows of Tables 1-2.
@@ -233,6 +234,54 @@ def check_solve_estimates(orc, seed=13):
         assert _rel(out["sigma2"], Q / n) < 1e-9
         assert _rel(out["nll"], ld + n * math.log(Q)) < 1e-9
         assert _rel(out["nll_full"], ld + n * math.log(Q / n) + n * (1 + math.log(2 * math.pi))) < 1e-9
+
+
+def _gauss_jordan_ld(A):
+    """R^-1 and log|det R| by Gauss-Jordan elimination with partial pivoting
+    in numpy.longdouble, plain loops: an elimination unrelated to the
+    oracle's Cholesky route, in wider arithmetic."""
+    n = A.shape[0]
+    M = np.hstack([np.asarray(A, dtype=np.longdouble), np.eye(n, dtype=np.longdouble)])
+    logdet = np.longdouble(0)
+    for c in range(n):
+        piv = c + int(np.argmax(np.abs(M[c:, c])))
+        if piv != c:
+            M[[c, piv]] = M[[piv, c]]
+        pv = M[c, c]
+        logdet += np.log(np.abs(pv))
+        M[c] = M[c] / pv
+        for r in range(n):
+            if r != c:
+                M[r] = M[r] - M[r, c] * M[c]
+    return M[:, n:], logdet
+
+
+def check_gauss_jordan_estimates(orc, seed=53):
+    """n <= 16: mu_hat, Q, sigma2_hat, log|R| and -2logL against R^-1 and
+    |det R| by long-double Gauss-Jordan elimination on the oracle's own R,
+    within 8 n cond(R) u of them."""
+    g = np.random.default_rng(seed)
+    u = 2.0 ** -53
+    for (n, d, p, delta) in [(2, 1, 2.0, 0.0), (3, 2, 1.5, 1e-6), (7, 2, 1.95, 1e-8), (16, 3, 1.95, 1e-6)]:
+        x = g.random((n, d))
+        th = 10 ** g.uniform(-0.5, 1, d)
+        y = np.cos(4 * x).sum(axis=1) + 0.1 * g.standard_normal(n)
+        R = orc.corr_matrix(x, th, p, delta)
+        Ri, logdet = _gauss_jordan_ld(R)
+        one = np.ones(n, dtype=np.longdouble)
+        yl = y.astype(np.longdouble)
+        A, B, C = one @ Ri @ one, one @ Ri @ yl, yl @ Ri @ yl
+        mu = B / A
+        Q = C - B * B / A
+        with np.errstate(invalid="ignore", divide="ignore"):   # a broken R gives Q <= 0
+            nll = logdet + n * np.log(Q)
+        want = {"mu": mu, "Q": Q, "sigma2": Q / n, "logdet": logdet, "nll": nll}
+        out, st = orc.nll(x, y, th, p, delta)
+        assert st == 0
+        tol = 8 * n * np.linalg.cond(R) * u
+        for k, v in want.items():
+            v = float(v)
+            assert abs(out[k] - v) <= tol * max(abs(v), 1.0), (n, k, out[k], v)
 
 
 def check_cholesky_reconstructs(orc, seed=17):
@@ -532,7 +581,7 @@ ALL_CHECKS = [
     check_n3, check_eig_logdet, check_solve_estimates, check_cholesky_reconstructs,
     check_notpd, check_cond_estimate, check_invariants, check_table_form, check_predict,
     check_fit_parts, check_matern_half_is_exponential, check_matern_bessel, check_matern_n2,
-    check_matern_predict, check_grad_finite_differences, check_grad_n2,
+    check_matern_predict, check_grad_finite_differences, check_grad_n2, check_gauss_jordan_estimates,
 ]
 
 
