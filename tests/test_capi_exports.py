@@ -52,3 +52,17 @@ def test_create_without_gpu_fails_cleanly(lib):
 def test_oracle_builds_and_loads():
     import oracle
     assert oracle.num_threads() >= 1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU or PyTorch fallback: with libgp.so absent the binding raises,
+    for the sizing query as for the compute calls."""
+    from paper_1203_1269_gb300 import gp
+    monkeypatch.setattr(gp, "_lib", None)
+    monkeypatch.setattr(gp._build, "LIB", str(tmp_path / "libgp.so"))
+    with pytest.raises(RuntimeError, match="libgp.so not found"):
+        gp.load()
+    with pytest.raises(RuntimeError, match="libgp.so not found"):
+        gp.call_bytes("fit", 100, 2)
+    with pytest.raises(RuntimeError, match="libgp.so not found"):
+        gp.Context(0)
