@@ -34,6 +34,10 @@
  *     not positive gives status GP_ENOTPD and -2logL = +inf; Q at rounding
  *     level (Y in the span of 1, e.g. n = 1) gives GP_EDEGENERATE and
  *     -2logL = -inf.
+ *   - Threads: a context, and the models and plans made from it, are used by
+ *     one host thread at a time.  Separate contexts are independent: one per
+ *     thread and stream runs their work concurrently on the GPU (the serving
+ *     loop does so).
  */
 #ifndef GP_H
 #define GP_H
