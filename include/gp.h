@@ -386,6 +386,7 @@ int gp_model_scalars(const gp_model* model, double* out_host);
  *   s2[m]   = sigma2_hat [c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1)]
  * with r_i = corr(z(x*_m), z(x_i)) by eq. (2), c0 = 1 + delta (or 1 when
  * the context's nugget_in_var is 0).  s2 may be NULL (mean only).
+ * 0 <= N <= 2^30 per call (GP_EINVAL beyond: split larger sets).
  * Asynchronous; the model must outlive the enqueued work. */
 int gp_predict(gp_ctx* ctx, const gp_model* model, int N, const double* xstar,
                double* yhat, double* s2);

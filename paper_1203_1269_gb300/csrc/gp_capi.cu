@@ -593,6 +593,10 @@ ModelSizes model_sizes(int n, int d) {
     return m;
 }
 
+// Test points one gp_predict call takes: the launch arithmetic (point
+// indices, CTA counts rounded up) stays in int with room to spare.
+constexpr int kMaxPredictPoints = 1 << 30;
+
 // Launch shape and workspace of gp_predict: test points per CTA, CTAs in
 // all, CTAs per launch (at most four waves, fewer when their scratch would
 // not fit `avail`), and the scratch those CTAs take when variances are asked
@@ -1285,7 +1289,8 @@ int gp_model_scalars(const gp_model* m, double* out) {
 
 int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, double* yhat, double* s2) {
     if (!ctx || !m) return GP_EINVAL;
-    if (N < 0) return fail(ctx, GP_EINVAL, "N = %d must be >= 0", N);
+    if (N < 0 || N > kMaxPredictPoints)
+        return fail(ctx, GP_EINVAL, "N = %d outside [0, 2^30] test points per call", N);
     if (N == 0) return GP_OK;
     if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1386,7 +1391,8 @@ int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size
         return GP_OK;
     }
     case GP_CALL_PREDICT:
-        if (count < 0) return fail(ctx, GP_EINVAL, "N = %d must be >= 0", count);
+        if (count < 0 || count > kMaxPredictPoints)
+            return fail(ctx, GP_EINVAL, "N = %d outside [0, 2^30] test points per call", count);
         if (count == 0) return GP_OK;
         return grow(predict_shape(gp::num_tiles(n), count, sms, avail, true).bytes);
     default:
