@@ -25,9 +25,10 @@
  *     only argument and launch errors in their return value.
  *   - Return value: GP_OK or a negative gp_status.  The message of the last
  *     failure is available from gp_last_error().
- *   - Arguments are validated: n >= 1, d >= 1, T >= 1, 0 < p <= 2 (for the
- *     power-exponential family; Matern families ignore p), delta >= 0 and
- *     finite.  theta values are checked on the device: a
+ *   - Arguments are validated: 1 <= n <= 2^20, 1 <= d <= 64,
+ *     1 <= T <= 2^30, 0 < p <= 2 (for the power-exponential family; Matern
+ *     families ignore p), delta >= 0 and finite.  theta values are checked
+ *     on the device: a
  *     theta_k that is negative or not finite makes that candidate's status
  *     GP_EINVAL and its outputs NaN; the rest of the batch completes.
  *   - Per-candidate failures never fail the call: a Cholesky pivot that is

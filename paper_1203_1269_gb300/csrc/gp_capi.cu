@@ -859,7 +859,7 @@ int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y,
                     int* prec_used) {
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
-    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (T < 1 || T > gp::kMaxCandidates) return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
     if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
         return fail(ctx, GP_EINVAL, "null pointer argument");
     if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32 && prec != GP_AUTO)
@@ -883,7 +883,7 @@ int gp_nll_grad_batch(gp_ctx* ctx, int n, int d, const double* x, const double* 
                       const double* theta, double p, double delta, double* nll, double* grad, int* status) {
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
-    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (T < 1 || T > gp::kMaxCandidates) return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
     if (d > 16) return fail(ctx, GP_ENOTSUP, "the gradient is built for d <= 16 (d = %d)", d);
     if (!x || !y || !theta || !nll || !grad || !status) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -946,7 +946,7 @@ int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int
     if (ntrials) *ntrials = 0;
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
-    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (T < 1 || T > gp::kMaxCandidates) return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
     if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
     if (prec != GP_MIXED && prec != GP_FP32)
         return fail(ctx, GP_ENOTSUP, "the autotuner chooses split-precision launch shapes only");
@@ -1150,7 +1150,7 @@ int gp_nll_batch_host(gp_ctx* ctx, int n, int d, const double* x_host, const dou
                       int* status_host) {
     int rc = check_common(ctx, n, d, p, delta);
     if (rc) return rc;
-    if (T < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", T);
+    if (T < 1 || T > gp::kMaxCandidates) return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
     if (!x_host || !y_host || !theta_host || !nll_host || !mu_hat_host || !sigma2_hat_host ||
         !status_host)
         return fail(ctx, GP_EINVAL, "null pointer argument");
@@ -1366,7 +1366,8 @@ int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size
     };
     switch (call) {
     case GP_CALL_NLL_BATCH: {
-        if (count < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", count);
+        if (count < 1 || count > gp::kMaxCandidates)
+            return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", count);
         if (prec < GP_FP64 || prec > GP_AUTO) return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
         size_t b64 = 0, bsplit = 0, b32 = 0;
         int rc = GP_OK;
@@ -1380,7 +1381,8 @@ int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size
         return GP_OK;
     }
     case GP_CALL_NLL_GRAD: {
-        if (count < 1) return fail(ctx, GP_EINVAL, "T = %d must be >= 1", count);
+        if (count < 1 || count > gp::kMaxCandidates)
+            return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", count);
         if (d > 16) return fail(ctx, GP_ENOTSUP, "the gradient is built for d <= 16 (d = %d)", d);
         return batch(grad_sizes(n, d).per, 0, bytes);
     }

@@ -26,6 +26,9 @@
 
 namespace gp {
 
+// Candidates one call takes: the chunk loops over them stay in int.
+constexpr int kMaxCandidates = 1 << 30;
+
 __host__ __device__ inline int num_tiles(int n) { return (n + GP_NB - 1) / GP_NB; }
 
 __host__ __device__ inline long long tile_index(int I, int J, int nt) {

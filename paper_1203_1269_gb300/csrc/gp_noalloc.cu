@@ -44,8 +44,8 @@ extern "C" int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, 
                                     const double* theta, double p, double delta, double* nll,
                                     double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
     if (!ctx) return GP_EINVAL;
-    if (n < 1 || d < 1 || d > GP_MAX_D || T < 1)
-        return gp::ctx_fail(ctx, GP_EINVAL, "n, d and T must be >= 1 (d <= 64)");
+    if (n < 1 || d < 1 || d > GP_MAX_D || T < 1 || T > gp::kMaxCandidates)
+        return gp::ctx_fail(ctx, GP_EINVAL, "n, d and T must be >= 1 (d <= 64, T <= 2^30)");
     if (gp::ctx_correlation(ctx) == GP_CORR_POWEXP && !(p > 0.0 && p <= 2.0))
         return gp::ctx_fail(ctx, GP_EINVAL, "p outside (0, 2]");
     if (!(delta >= 0.0) || !(delta <= 1e300)) return gp::ctx_fail(ctx, GP_EINVAL, "delta must be finite and >= 0");

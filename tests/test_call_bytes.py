@@ -84,6 +84,8 @@ def test_errors(gp):
            ("nll_batch", 100, 0, 1, "mixed", gp.GP_EINVAL),
            ("nll_batch", 100, 65, 1, "mixed", gp.GP_EINVAL),
            ("nll_batch", 100, 6, 0, "mixed", gp.GP_EINVAL),
+           ("nll_batch", 100, 6, 2 ** 30 + 1, "fp64", gp.GP_EINVAL),
+           ("nll_grad", 100, 6, 2 ** 30 + 1, "fp64", gp.GP_EINVAL),
            ("nll_batch", 100, 6, 1, 9, gp.GP_EINVAL),
            ("nll_grad", 100, 17, 1, "fp64", gp.GP_ENOTSUP),
            ("predict", 100, 6, -1, "fp64", gp.GP_EINVAL),
