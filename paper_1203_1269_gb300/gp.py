@@ -154,6 +154,63 @@ def _dev_f64(t, name, shape=None, device=None):
     return t
 
 
+def _out_tensor(t, name, shape, dtype, device):
+    """A caller-supplied output: the library writes prod(shape) elements of
+    `dtype` through its pointer, so everything about it is checked first.
+    device=None means a host (CPU) tensor."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"out[{name!r}] must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"out[{name!r}] must be {dtype}, got {t.dtype}")
+    if device is None:
+        if t.is_cuda:
+            raise ValueError(f"out[{name!r}] must be a CPU tensor")
+    elif t.device != device:
+        raise ValueError(f"out[{name!r}] is on {t.device}, the context uses {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"out[{name!r}] must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"out[{name!r}] has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+_INT_OUTPUTS = ("status", "prec_used")
+
+
+def _check_outs(out, required, optional, T, device, shapes=None):
+    """Validate a caller's `out` dict: the `required` keys must be there, the
+    `optional` ones may be; each is (T,) (or shapes[key]) of int32 for the
+    status-like keys and float64 otherwise."""
+    if not isinstance(out, dict):
+        raise TypeError("out must be a dict of tensors")
+    for k in required:
+        if out.get(k) is None:
+            raise ValueError(f"out lacks {k!r}")
+    for k in tuple(required) + tuple(optional):
+        if out.get(k) is not None:
+            dtype = torch.int32 if k in _INT_OUTPUTS else torch.float64
+            _out_tensor(out[k], k, (shapes or {}).get(k, (T,)), dtype, device)
+    return out
+
+
+def _host_batch_args(x, y, thetas):
+    """(n, d, T) of a host-buffer batch after checking x (n x d), y (n) and
+    thetas (T x d): the library copies exactly those bytes from them."""
+    def host(t, name):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU torch.float64 tensor")
+        return t
+    host(x, "x"); host(y, "y"); host(thetas, "thetas")
+    if x.dim() != 2:
+        raise ValueError("x must be n x d")
+    n, d = x.shape
+    if tuple(y.shape) != (n,):
+        raise ValueError(f"y has shape {tuple(y.shape)}, expected {(n,)}")
+    if thetas.dim() != 2 or thetas.shape[1] != d:
+        raise ValueError("thetas must be T x d")
+    return n, d, thetas.shape[0]
+
+
 def _prec(prec):
     if isinstance(prec, str):
         return PRECISIONS[prec]
@@ -347,6 +404,9 @@ class Context:
             out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw),
                        sigma2=torch.empty(T, **kw), logdet=torch.empty(T, **kw),
                        status=torch.empty(T, dtype=torch.int32, device=self.device))
+        else:
+            _check_outs(out, ("nll", "mu", "sigma2", "status"), ("logdet", "cond", "prec_used"), T,
+                        self.device)
         pc = _prec(prec)
         if cond and "cond" not in out:
             out["cond"] = torch.empty(T, dtype=torch.float64, device=self.device)
@@ -394,6 +454,8 @@ class Context:
             kw = dict(dtype=torch.float64, device=self.device)
             out = dict(nll=torch.empty(T, **kw), grad=torch.empty((T, d), **kw),
                        status=torch.empty(T, dtype=torch.int32, device=self.device))
+        else:
+            _check_outs(out, ("nll", "grad", "status"), (), T, self.device, shapes={"grad": (T, d)})
         self._check(self._lib.gp_nll_grad_batch(
             self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta),
             _ptr(out["nll"]), _ptr(out["grad"]), _ptr(out["status"])))
@@ -437,6 +499,8 @@ class Context:
             out = dict(nll=torch.empty(T, **kw), mu=torch.empty(T, **kw),
                        sigma2=torch.empty(T, **kw), logdet=torch.empty(T, **kw),
                        status=torch.empty(T, dtype=torch.int32, device=self.device))
+        else:
+            _check_outs(out, ("nll", "mu", "sigma2", "status"), ("logdet",), T, self.device)
         self._check(self._lib.gp_nll_batch_noalloc(
             self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta),
             _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
@@ -445,20 +509,14 @@ class Context:
 
     def nll_batch_host(self, x, y, thetas, p, delta, prec="fp64", out=None):
         """gp_nll_batch_host: host (CPU, optionally pinned) tensors in and out."""
-        def host(t, name, dtype=torch.float64):
-            if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
-                raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor")
-            return t
-        x = host(x, "x")
-        n, d = x.shape
-        y = host(y, "y")
-        thetas = host(thetas, "thetas")
-        T = thetas.shape[0]
+        n, d, T = _host_batch_args(x, y, thetas)
         if out is None:
             out = dict(nll=torch.empty(T, dtype=torch.float64), mu=torch.empty(T, dtype=torch.float64),
                        sigma2=torch.empty(T, dtype=torch.float64),
                        logdet=torch.empty(T, dtype=torch.float64),
                        status=torch.empty(T, dtype=torch.int32))
+        else:
+            _check_outs(out, ("nll", "mu", "sigma2", "status"), ("logdet",), T, None)
         self._check(self._lib.gp_nll_batch_host(
             self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta), _prec(prec),
             _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]), _ptr(out.get("logdet")),
@@ -485,8 +543,12 @@ class Context:
             raise ValueError("xs must be N x d")
         if yhat is None:
             yhat = torch.empty(N, dtype=torch.float64, device=self.device)
+        else:
+            _out_tensor(yhat, "yhat", (N,), torch.float64, self.device)
         if want_var and s2 is None:
             s2 = torch.empty(N, dtype=torch.float64, device=self.device)
+        elif want_var:
+            _out_tensor(s2, "s2", (N,), torch.float64, self.device)
         self._check(self._lib.gp_predict(self._h, model._h, N, _ptr(xs), _ptr(yhat),
                                          _ptr(s2) if want_var else None))
         return yhat, (s2 if want_var else None)
