@@ -66,3 +66,35 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
         gp.call_bytes("fit", 100, 2)
     with pytest.raises(RuntimeError, match="libgp.so not found"):
         gp.Context(0)
+
+
+def _declared_params():
+    """Parameter count of every gp_* function gp.h declares."""
+    out = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(gp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the Python binding calls has argtypes of the length
+    gp.h declares (a drifted signature would pass arguments in the wrong
+    registers)."""
+    from paper_1203_1269_gb300 import gp
+    lib = gp.load()
+    declared = _declared_params()
+    bound = {name: len(getattr(lib, name).argtypes) for name in declared
+             if getattr(getattr(lib, name), "argtypes", None) is not None}
+    assert len(bound) >= 25, sorted(bound)
+    wrong = {k: (v, declared[k]) for k, v in bound.items() if v != declared[k]}
+    assert not wrong, wrong
+    # and the binding sets argtypes for every call it makes
+    src = open(os.path.join(ROOT, "paper_1203_1269_gb300", "gp.py")).read()
+    called = set(re.findall(r"_lib\.(gp_[a-z0-9_]+)\(", src)) | set(re.findall(r"\blib\.(gp_[a-z0-9_]+)\(", src))
+    assert called <= set(bound), sorted(called - set(bound))
