@@ -98,3 +98,23 @@ def test_binding_signatures_match_the_header():
     src = open(os.path.join(ROOT, "paper_1203_1269_gb300", "gp.py")).read()
     called = set(re.findall(r"_lib\.(gp_[a-z0-9_]+)\(", src)) | set(re.findall(r"\blib\.(gp_[a-z0-9_]+)\(", src))
     assert called <= set(bound), sorted(called - set(bound))
+
+
+def _declared_struct(name):
+    """(field, C type) pairs of the typedef struct `name` in gp.h, in order."""
+    src = open(os.path.join(ROOT, "include", "gp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef\s+struct\s*\{([^}]*)\}\s*" + name + r"\s*;", src, flags=re.S)
+    assert m, name
+    return re.findall(r"\b(int|double)\s+([a-z_0-9]+)\s*;", m.group(1))
+
+
+@pytest.mark.parametrize("cname,pyname", [("gp_options", "Options"), ("gp_tune_trial", "TuneTrial")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes structures the binding passes by pointer have gp.h's
+    fields, in its order and with its types."""
+    import ctypes
+    from paper_1203_1269_gb300 import gp
+    want = [(f, {"int": ctypes.c_int, "double": ctypes.c_double}[t]) for t, f in _declared_struct(cname)]
+    assert len(want) >= 5
+    assert list(getattr(gp, pyname)._fields_) == want
