@@ -118,3 +118,19 @@ def test_binding_structs_match_the_header(cname, pyname):
     want = [(f, {"int": ctypes.c_int, "double": ctypes.c_double}[t]) for t, f in _declared_struct(cname)]
     assert len(want) >= 5
     assert list(getattr(gp, pyname)._fields_) == want
+
+
+def test_oracle_wrapper_signatures_match_the_source():
+    """The oracle's ctypes wrapper passes as many arguments as each exported
+    gpo_* function of gp_oracle.c takes, in both of its builds."""
+    import oracle
+    src = open(os.path.join(ROOT, "oracle", "gp_oracle.c")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    declared = {}
+    for m in re.finditer(r"^(?!static)[a-z][a-z ]*\b(gpo_[a-z0-9_]+)\s*\(([^)]*)\)\s*\{", src, flags=re.M):
+        params = m.group(2).strip()
+        declared[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    assert len(declared) >= 10, declared
+    for orc in (oracle.default(), oracle.extended()):
+        for name, count in declared.items():
+            assert len(getattr(orc.lib, name).argtypes or ()) == count, name
