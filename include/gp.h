@@ -134,13 +134,6 @@ typedef struct {
     int correlation;      /* gp_correlation of every call that builds R or r, default
                              GP_CORR_POWEXP; a fit keeps the family it was made with,
                              and its predictions use that one */
-    int pair_update;      /* split path, default 0: 1 runs the fused trailing updates
-                             on clusters of two CTAs that share their row panel (each
-                             copies half of it, multicast to both: a quarter less
-                             operand traffic per SM); same results.  At n = 4000 it is
-                             16% slower (fewer SMs hold a cluster pair, and the update is
-                             not bound by operand traffic); the autotuner tries it.  Used
-                             with update_tile = 128 and fuse_panels = 1 */
 } gp_options;
 
 void gp_default_options(gp_options* opt);
@@ -282,12 +275,10 @@ int gp_nll_batch_ex(gp_ctx* ctx, int n, int d, const double* x, const double* y,
                     int* status, double* cond1, int* prec_used);
 
 /* Launch-shape autotuner.  Times gp_nll_batch(prec) on the caller's batch
- * for every combination of update_tile (128, 64), fuse_panels (1, 0),
- * pair_update (0, 1; with 128 and fuse only) and assemble_cols (16, 32) --
- * one untimed call, then `reps` calls timed with
+ * for every combination of update_tile (128, 64), fuse_panels (1, 0) and
+ * assemble_cols (16, 32) -- one untimed call, then `reps` calls timed with
  * CUDA events on the context's stream, median -- and keeps the fastest as
- * the context's options.  update_tile, pair_update and assemble_cols never
- * change results; fuse_panels changes the rounding of the trailing updates (both
+ * the context's options.  update_tile and assemble_cols never change results; fuse_panels changes the rounding of the trailing updates (both
  * settings meet the split path's accuracy).  trials (may be NULL) receives
  * up to max_trials entries and *ntrials the number of combinations timed.
  * prec: GP_MIXED or GP_FP32 (GP_ENOTSUP otherwise: the FP64 path has no
@@ -296,7 +287,6 @@ typedef struct {
     int update_tile;
     int fuse_panels;
     int assemble_cols;
-    int pair_update;
     double ms;            /* median device time of one gp_nll_batch call */
 } gp_tune_trial;
 int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,

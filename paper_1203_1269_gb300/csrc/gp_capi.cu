@@ -252,7 +252,6 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.ug = ctx->opt.update_groups;
     mb.inject_timeout = ctx->opt.inject_timeout;
     mb.update_tile = ctx->opt.update_tile;
-    mb.pair_update = ctx->opt.pair_update;
     mb.sp = mb.s > mb.ps ? mb.s : mb.ps;
     mb.inst_stride = z.A / sizeof(float2);
     mb.ps_stride = z.PS / sizeof(__nv_bfloat16);
@@ -655,7 +654,6 @@ void gp_default_options(gp_options* opt) {
     opt->auto_tol = 1e-6;
     opt->update_tile = 128;
     opt->assemble_cols = 16;
-    opt->pair_update = 0;
     opt->correlation = GP_CORR_POWEXP;
 }
 
@@ -734,8 +732,6 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
         return fail(ctx, GP_EINVAL, "update_tile = 64 needs update_groups = 4");
     if (opt->assemble_cols != 16 && opt->assemble_cols != 32)
         return fail(ctx, GP_EINVAL, "assemble_cols must be 16 or 32");
-    if (opt->pair_update != 0 && opt->pair_update != 1)
-        return fail(ctx, GP_EINVAL, "pair_update must be 0 or 1");
     if (opt->correlation < GP_CORR_POWEXP || opt->correlation > GP_CORR_MATERN52)
         return fail(ctx, GP_EINVAL, "correlation = %d is not a gp_correlation", opt->correlation);
     ctx->opt = *opt;
@@ -972,14 +968,11 @@ int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int
     int count = 0;
     for (int ut : {128, 64}) {
         for (int fuse : {1, 0}) {
-            for (int pair : {0, 1}) {
             for (int ac : {16, 32}) {
                 if (base.update_groups != 4 && (fuse || ut == 64)) continue;
-                if (pair && !(fuse && ut == 128)) continue;   // pairs run the fused 128-wide update only
                 gp_options o = base;
                 o.update_tile = ut;
                 o.fuse_panels = fuse;
-                o.pair_update = pair;
                 o.assemble_cols = ac;
                 ctx->opt = o;
                 std::vector<float> ms;
@@ -996,14 +989,12 @@ int gp_autotune(gp_ctx* ctx, int n, int d, const double* x, const double* y, int
                 if (rc) break;
                 std::sort(ms.begin(), ms.end());
                 const double med = ms[ms.size() / 2];
-                if (trials && count < max_trials) trials[count] = gp_tune_trial{ut, fuse, ac, pair, med};
+                if (trials && count < max_trials) trials[count] = gp_tune_trial{ut, fuse, ac, med};
                 ++count;
                 if (med < best_ms) {
                     best_ms = med;
                     best = o;
                 }
-            }
-            if (rc) break;
             }
             if (rc) break;
         }

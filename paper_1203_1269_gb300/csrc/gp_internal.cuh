@@ -99,7 +99,6 @@ struct MixedBatch {
     int ug;                       // accumulator groups of the trailing update (3, 4 or 7)
     int inject_timeout;           // test hook: one split-GEMM CTA waits on a barrier nothing signals
     int update_tile;              // columns of a trailing-update output tile (128 or 64)
-    int pair_update;              // 1: fused updates by CTA pairs sharing their row panel
     int sp;                       // slice slots per row block in PS (max(s, ps))
     float2* A;                    // working matrix -> factor (double-float tiles)
     float2* Rc;                   // copy of R (double-float tiles), for residuals

@@ -1,6 +1,6 @@
 // k_gemm.cu -- the split GEMMs of the split-precision (GP_MIXED) factorisation
 // on the tensor cores: the panel solve L_IJ = A_IJ W_J^T and the trailing
-// updates A_IK -= L_IJ L_KJ^T (single panels, fused panel pairs, CTA pairs),
+// updates A_IK -= L_IJ L_KJ^T (single panels and fused panel pairs),
 // each over bf16 slices (mixed_common.cuh) with fp32 accumulation in tensor
 // memory and the exact recombination and application in double-float.
 // The slicing, the diagonal blocks and the solves are in k_mixed.cu.
@@ -484,248 +484,6 @@ __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
 }
 
-// Row-pair decode for the fused update run by CTA pairs: the trailing
-// triangle's row ii holds tiles kk = 0 .. ii, taken two at a time, so row ii
-// has ii / 2 + 1 pairs and rows 0 .. ii - 1 hold h (h + 1) pairs (ii = 2h) or
-// h^2 (ii = 2h - 1).  q -> (ii, pair in the row).
-__device__ __forceinline__ void pair_decode(int q, int& ii, int& pr) {
-    int h = (int)sqrtf((float)q);
-    while (h * h > q) --h;
-    while ((h + 1) * (h + 1) <= q) ++h;
-    if (q >= h * (h + 1)) {
-        ii = 2 * h;
-        pr = q - h * (h + 1);
-    } else {
-        ii = 2 * h - 1;
-        pr = q - h * h;
-    }
-}
-
-__host__ __device__ __forceinline__ int pairs_in_triangle(int m) {
-    const int h = m / 2;
-    return (m % 2 == 0) ? h * (h + 1) : (h + 1) * (h + 1);
-}
-
-// The fused (K = 256) trailing update of a panel pair by clusters of two
-// CTAs.  The two CTAs of a cluster take the tiles (I, K) and (I, K + 1) of
-// one row: they share the A operand (the two-panel slices of row block I),
-// so each CTA bulk-copies half of A's slices, multicast into both CTAs'
-// shared memory, and its own B; per SM that is three quarters of the
-// operand traffic of k_split_gemm, whose trailing updates are bound by it.
-// A stage is refilled only when both CTAs' MMAs have read it: every MMA
-// commit arrives on both CTAs' empty barriers.  When a row has an odd number
-// of tiles, the second CTA of its last pair only supplies its half of A.
-// Everything else (MMA groups, exact recombination, bounded waits) is that of
-// k_split_gemm<1, 128, 4>.
-__global__ void __launch_bounds__(kGemmThreads, 1) k_split_gemm_pair(MixedBatch b, int J, int pairs_per_inst) {
-    constexpr int NT = 128, NG = 4;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[2];
-    __shared__ __align__(8) uint64_t empty_bar[2];
-    __shared__ __align__(8) uint64_t tfull_bar;
-    __shared__ __align__(8) uint64_t tempty_bar;
-    __shared__ __align__(8) uint64_t drain_bar;
-    __shared__ uint32_t tmem_base;
-    __shared__ volatile int abort_flag;
-
-    const int ns = b.s;
-    constexpr int nch = 2 * kChunks;                             // K = 256
-    constexpr uint32_t kBBytes = kChunkBytes;                    // NT = 128: whole chunk rows
-    const uint32_t a_bytes = (uint32_t)ns * kChunkBytes;
-    const uint32_t stage_bytes = a_bytes + (uint32_t)ns * kBBytes;
-    constexpr uint32_t idesc = idesc_bf16(NT);
-    constexpr uint16_t kPair = 0x3;
-    const int rank = (int)cluster_ctarank();
-    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-    const int total = pairs_per_inst * b.count;
-
-    // pair item -> (instance, I, K, this CTA's tile exists)
-    auto decode = [&](int w, int& t, int& I, int& K, bool& valid) {
-        t = w / pairs_per_inst;
-        int ii, pr;
-        pair_decode(w - t * pairs_per_inst, ii, pr);
-        const int kk = 2 * pr + rank;
-        valid = (kk <= ii);
-        I = J + 2 + ii;
-        K = J + 2 + (valid ? kk : ii);
-    };
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        mbar_init(&full_bar[0], 1);
-        mbar_init(&full_bar[1], 1);
-        mbar_init(&empty_bar[0], 2);   // both CTAs' MMAs
-        mbar_init(&empty_bar[1], 2);
-        mbar_init(&tfull_bar, 1);
-        mbar_init(&tempty_bar, kEpiThreads);
-        mbar_init(&drain_bar, 1);
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    // the partner's barriers exist before any copy or commit targets them
-    cluster_sync_all();
-    tc_fence_after();
-    const uint32_t tbase = tmem_base;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            int g = 0;
-            for (int w = cid; w < total && !abort_flag; w += ncl) {
-                int t, I, K;
-                bool valid;
-                decode(w, t, I, K, valid);
-                if (b.st[t].status != GP_OK) continue;       // the partner skips it too
-                const __nv_bfloat16* gA = pf_block(b, t, I);
-                const uint8_t* gB = reinterpret_cast<const uint8_t*>(pf_block(b, t, K));
-                for (int kc = 0; kc < nch; ++kc, ++g) {
-                    const int st = g & 1;
-                    if (g >= 2 && !mbar_wait(&empty_bar[st], ((g >> 1) - 1) & 1, &abort_flag)) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    uint8_t* sa = smem + st * stage_bytes;
-                    uint8_t* sb = sa + a_bytes;
-                    // this CTA receives all of A (half from each CTA) and its own B
-                    mbar_expect_tx(&full_bar[st], a_bytes + (valid ? (uint32_t)ns * kBBytes : 0u));
-                    for (int a = rank; a < ns; a += 2)
-                        bulk_g2s_mc(sa + a * kChunkBytes, gA + (size_t)(a * nch + kc) * kChunkElems, kChunkBytes,
-                                    &full_bar[st], kPair);
-                    if (valid)
-                        for (int a = 0; a < ns; ++a)
-                            bulk_g2s(sb + a * kBBytes, gB + (size_t)(a * nch + kc) * kChunkBytes, kBBytes,
-                                     &full_bar[st]);
-                }
-            }
-            // every copy into this CTA (its own and the partner's) has landed,
-            // and both CTAs' commits for the last stages have arrived here,
-            // before the CTA retires
-            for (int k = (g > 2 ? g - 2 : 0); k < g; ++k) mbar_wait(&full_bar[k & 1], (k >> 1) & 1);
-            for (int k = (g > 2 ? g - 2 : 0); k < g; ++k) mbar_wait(&empty_bar[k & 1], (k >> 1) & 1);
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            int g = 0, i = 0;
-            for (int w = cid; w < total && !abort_flag; w += ncl) {
-                int t, I, K;
-                bool valid;
-                decode(w, t, I, K, valid);
-                if (b.st[t].status != GP_OK) continue;
-                if (valid && i >= 1 && !mbar_wait(&tempty_bar, (i - 1) & 1, &abort_flag)) {
-                    abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                for (int kc = 0; kc < nch; ++kc, ++g) {
-                    const int st = g & 1;
-                    if (!mbar_wait(&full_bar[st], (g >> 1) & 1, &abort_flag)) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    tc_fence_after();
-                    if (valid) {
-                        const uint32_t sa = smem_u32(smem + st * stage_bytes);
-                        const uint32_t sb = sa + a_bytes;
-                        const uint64_t ad0 = smem_desc(sa, 16, 512, 4), bd0 = smem_desc(sb, 16, 512, 4);
-                        issue_stage_ns<NG, NT, kBBytes>(ns, kc == 0, tbase, ad0, bd0, idesc);
-                    }
-                    // this stage may be refilled in both CTAs once both have read it
-                    mma_commit_mc(&empty_bar[st], kPair);
-                }
-                if (abort_flag) break;
-                if (valid) {
-                    mma_commit(&tfull_bar);
-                    ++i;
-                }
-            }
-            mma_commit(&drain_bar);
-            mbar_wait(&drain_bar, 0);
-        }
-    } else {
-        const int q = warp & 3;
-        const int part = (warp - 2) >> 2;
-        const int r = q * 32 + lane;
-        const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-        constexpr int kPartCols = NT / kEpiParts;
-        constexpr int CB = 16;
-        const int ng_used = ns < NG ? ns : NG;
-        int i = 0;
-        for (int w = cid; w < total && !abort_flag; w += ncl) {
-            int t, I, K;
-            bool valid;
-            decode(w, t, I, K, valid);
-            if (b.st[t].status != GP_OK || !valid) continue;
-            float2* C = df_tile(b, b.A, t, I, K);
-            if (threadIdx.x == 64) prefetch_l2(C, (uint32_t)(NT * GP_NB * sizeof(float2)));
-            if (!mbar_wait(&tfull_bar, i & 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            tc_fence_after();
-            const int eA = fe_block(b, t, I)[r];
-            const int* eBp = fe_block(b, t, K);
-            for (int c0 = part * kPartCols; c0 < (part + 1) * kPartCols; c0 += CB) {
-                float2 cv[CB];
-#pragma unroll
-                for (int j = 0; j < CB; ++j) cv[j] = C[(size_t)(c0 + j) * GP_NB + r];
-                float d[NG][CB];
-#pragma unroll
-                for (int gq = 0; gq < NG; ++gq) {
-                    if (gq < ng_used) {
-                        tmem_ld16(lane_addr + gq * NT + c0, d[gq]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < CB; ++j) d[gq][j] = 0.f;
-                    }
-                }
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < CB; ++j) {
-                    const int c = c0 + j;
-                    // groups 0 .. 2 exact, the last (weight <= 2^-24) in the low word
-                    float h, l;
-                    two_sum(d[0][j], d[1][j], h, l);
-                    {
-                        float s2, e2;
-                        two_sum(h, d[2][j], s2, e2);
-                        h = s2;
-                        l = __fadd_rn(l, e2);
-                    }
-                    l = __fadd_rn(l, d[3][j]);
-                    two_sum(h, l, h, l);
-                    const int e = eA + __ldg(eBp + c) - 14;
-                    const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
-                    h = __fmul_rn(h, sc);
-                    l = __fmul_rn(l, sc);
-                    float sh, se;
-                    two_sum(cv[j].x, -h, sh, se);
-                    se = __fadd_rn(se, __fsub_rn(cv[j].y, l));
-                    two_sum(sh, se, sh, se);
-                    C[(size_t)c * GP_NB + r] = make_float2(sh, se);
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&tempty_bar);
-            ++i;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    // neither CTA leaves while the other may still copy into it or arrive on it
-    cluster_sync_all();
-    tc_fence_after();
-    if (abort_flag && threadIdx.x == 0) {
-        atomicExch(b.err, GP_ETIMEOUT);
-        for (int w = cid; w < total; w += ncl) b.st[w / pairs_per_inst].status = GP_ETIMEOUT;
-    }
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
-}
-
 }  // namespace
 
 // SMs of the current device (looked up once per device ordinal)
@@ -802,47 +560,10 @@ cudaError_t launch_gemm_update_column(const MixedBatch& b, int J, cudaStream_t s
     return launch_update128(b, J, m, b.s, s, 1);
 }
 
-// The fused update by CTA pairs (k_split_gemm_pair): a cluster launch whose
-// grid is as many pairs as can be resident at once (looked up per device).
-static cudaError_t launch_gemm_pair(const MixedBatch& b, int J, int m, cudaStream_t s) {
-    const size_t smem = (size_t)2 * b.s * (2 * kChunkBytes) + 1024;
-    static std::atomic<size_t> attr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_split_gemm_pair, smem, attr);
-    if (e != cudaSuccess) return e;
-    const int ppi = pairs_in_triangle(m);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kGemmThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    static std::atomic<int> clusters[kMaxDevices];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int nc = (dev >= 0 && dev < kMaxDevices) ? clusters[dev].load(std::memory_order_relaxed) : 0;
-    if (nc == 0) {
-        cfg.gridDim = dim3(2 * sm_count());
-        e = cudaOccupancyMaxActiveClusters(&nc, k_split_gemm_pair, &cfg);
-        if (e != cudaSuccess) return e;
-        if (nc < 1) return cudaErrorInvalidConfiguration;
-        if (dev >= 0 && dev < kMaxDevices) clusters[dev].store(nc, std::memory_order_relaxed);
-    }
-    const long long total = (long long)ppi * b.count;
-    const int ncl = (int)(total < nc ? total : nc);
-    cfg.gridDim = dim3(2 * ncl);
-    return cudaLaunchKernelEx(&cfg, k_split_gemm_pair, b, J, ppi);
-}
-
 cudaError_t launch_gemm_update_fused(const MixedBatch& b, int J, cudaStream_t s) {
     const int m = b.nt - J - 2;
     if (m <= 0) return cudaSuccess;
     if (b.update_tile == 64) return launch_gemm<1, 64, 4>(b, J, m * (m + 1), b.s, s, 2);
-    if (b.pair_update) return launch_gemm_pair(b, J, m, s);
     return launch_update128(b, J, m * (m + 1) / 2, b.s, s, 2);
 }
 

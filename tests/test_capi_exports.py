@@ -116,7 +116,7 @@ def test_binding_structs_match_the_header(cname, pyname):
     import ctypes
     from paper_1203_1269_gb300 import gp
     want = [(f, {"int": ctypes.c_int, "double": ctypes.c_double}[t]) for t, f in _declared_struct(cname)]
-    assert len(want) >= 5
+    assert len(want) >= 4
     assert list(getattr(gp, pyname)._fields_) == want
 
 

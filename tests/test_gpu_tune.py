@@ -44,14 +44,12 @@ def test_shape_options_leave_results_unchanged(ctx, fuse):
     X, Y, TH = dev(x), dev(y), dev(th)
     base_opts = ctx.options()
     try:
-        ctx.set_options(fuse_panels=fuse, update_tile=128, assemble_cols=16, pair_update=0)
+        ctx.set_options(fuse_panels=fuse, update_tile=128, assemble_cols=16)
         ref = ctx.nll_batch(X, Y, TH, p, delta, "mixed")
         variants = [dict(update_tile=64), dict(assemble_cols=32), dict(update_tile=64, assemble_cols=32)]
-        if fuse:
-            variants.append(dict(pair_update=1))    # CTA pairs sharing the row panel
         for kw in variants:
             ctx.set_options(fuse_panels=fuse, update_tile=kw.get("update_tile", 128),
-                            assemble_cols=kw.get("assemble_cols", 16), pair_update=kw.get("pair_update", 0))
+                            assemble_cols=kw.get("assemble_cols", 16))
             got = ctx.nll_batch(X, Y, TH, p, delta, "mixed")
             for k in KEYS:
                 assert np.array_equal(host(got[k]), host(ref[k]), equal_nan=True), (kw, k)
@@ -65,11 +63,11 @@ def test_autotune_keeps_fastest(ctx):
     base_opts = ctx.options()
     try:
         trials, chosen = ctx.autotune(X, Y, TH, p, delta, "mixed", reps=2)
-        assert len(trials) == 10
+        assert len(trials) == 8
         best = min(trials, key=lambda t: t["ms"])
-        for k in ("update_tile", "fuse_panels", "assemble_cols", "pair_update"):
+        for k in ("update_tile", "fuse_panels", "assemble_cols"):
             assert chosen[k] == best[k]
-        print("\nautotune n=900 T=16:", [(t["update_tile"], t["fuse_panels"], t["pair_update"], t["assemble_cols"],
+        print("\nautotune n=900 T=16:", [(t["update_tile"], t["fuse_panels"], t["assemble_cols"],
                                           round(t["ms"], 3)) for t in trials])
         # the tuned context still meets the split path's tolerance
         ref, st = oracle.nll_batch(x, y, th, p, delta, want_cond=True)
