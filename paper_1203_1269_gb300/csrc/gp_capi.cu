@@ -633,6 +633,10 @@ int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...) {
 
 int ctx_device(const gp_ctx* ctx) { return ctx->device; }
 
+int ctx_check_common(gp_ctx* ctx, int n, int d, double p, double delta) {
+    return check_common(ctx, n, d, p, delta);
+}
+
 int ctx_correlation(const gp_ctx* ctx) { return ctx->opt.correlation; }
 
 cudaStream_t ctx_stream(const gp_ctx* ctx) { return ctx->stream; }

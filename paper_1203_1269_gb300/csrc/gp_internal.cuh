@@ -161,6 +161,8 @@ inline cudaError_t raise_smem_limit(Kernel* kernel, size_t bytes, std::atomic<si
 // ---- context accessors (gp_capi.cu) ----------------------------------------
 int ctx_fail(gp_ctx* ctx, int code, const char* fmt, ...);
 int ctx_device(const gp_ctx* ctx);
+// the argument checks every entry point shares: n, d, p (for eq. 2's family), delta
+int ctx_check_common(gp_ctx* ctx, int n, int d, double p, double delta);
 int ctx_correlation(const gp_ctx* ctx);
 cudaStream_t ctx_stream(const gp_ctx* ctx);
 

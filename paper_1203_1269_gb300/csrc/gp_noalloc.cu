@@ -43,12 +43,9 @@ cudaError_t scratch_address(int device, void** out) {
 extern "C" int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                                     const double* theta, double p, double delta, double* nll,
                                     double* mu_hat, double* sigma2_hat, double* logdet, int* status) {
-    if (!ctx) return GP_EINVAL;
-    if (n < 1 || d < 1 || d > GP_MAX_D || T < 1 || T > gp::kMaxCandidates)
-        return gp::ctx_fail(ctx, GP_EINVAL, "n, d and T must be >= 1 (d <= 64, T <= 2^30)");
-    if (gp::ctx_correlation(ctx) == GP_CORR_POWEXP && !(p > 0.0 && p <= 2.0))
-        return gp::ctx_fail(ctx, GP_EINVAL, "p outside (0, 2]");
-    if (!(delta >= 0.0) || !(delta <= 1e300)) return gp::ctx_fail(ctx, GP_EINVAL, "delta must be finite and >= 0");
+    const int rc = gp::ctx_check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1 || T > gp::kMaxCandidates) return gp::ctx_fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
     if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
         return gp::ctx_fail(ctx, GP_EINVAL, "null pointer argument");
     const int device = gp::ctx_device(ctx);
