@@ -68,6 +68,27 @@ def chol_flops(n):
     return n ** 3 / 3.0
 
 
+def fp64_dgemm_tflops(dev, m=4096, reps=5):
+    """The FP64 peak this GPU reaches in a dense library GEMM (cuBLAS DGEMM
+    through torch.matmul, best of `reps`, CUDA events): the denominator of
+    the FP64 path's roofline, measured in the same run."""
+    import torch
+    a = torch.randn(m, m, dtype=torch.float64, device=dev)
+    b = torch.randn(m, m, dtype=torch.float64, device=dev)
+    a @ b
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * m ** 3 / (best / 1e3) / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -179,7 +200,26 @@ def cpu_baseline_sample(w, max_theta=None, timeout_s=60.0):
     return {"value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} of the {w.T} candidates at n={w.n}, d={w.d} "
                       f"(one single-threaded evaluation per core, {dt:.1f} s)",
-            "seconds": dt}
+            "seconds": dt}, out, st
+
+
+def oracle_errors(o_out, o_st, mixed, fp64):
+    """Both GPU arms against the oracle on the oracle's own sample (the
+    first candidates of the batch): relative error of -2logL per candidate."""
+    k = len(o_st)
+    mix = mixed["nll"][:k].cpu().numpy()
+    f64 = fp64["nll"][:k].cpu().numpy()
+    rows, wm, wf = [], 0.0, 0.0
+    for t in range(k):
+        if o_st[t] != 0:
+            continue
+        ref = o_out[t, 0]
+        em = abs(mix[t] - ref) / abs(ref)
+        ef = abs(f64[t] - ref) / abs(ref)
+        wm, wf = max(wm, em), max(wf, ef)
+        rows.append([t, float(f"{em:.3g}"), float(f"{ef:.3g}")])
+    return {"candidates": k, "mixed_max_rel_err_nll": wm, "fp64_max_rel_err_nll": wf,
+            "per_candidate_t_mixed_fp64": rows}
 
 
 def run_reference(args):
@@ -284,12 +324,12 @@ def run_gp(args):
         upd_ms, upd_n = phases["update"]
         flops = update_flops(w.n) * w.T * args.steps
         achieved = flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
-        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        fp64_peak = fp64_dgemm_tflops(dev)
         roof = {"kernel": "k_update_f64", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None,
                 "traffic": stored_traffic("k_update_f64", ["k_chol_f64.cu"]),
-                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock "
-                               "(unit counts and clock of the profiling recipe)",
+                "peak_source": "FP64 dense, measured in this run: cuBLAS DGEMM (torch.matmul, "
+                               "4096^3, best of 5, CUDA events)",
                 "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
                 "algorithmic_flops_per_launch": flops / max(upd_n, 1)}
     else:
@@ -299,9 +339,14 @@ def run_gp(args):
         prods = s * (s + 1) // 2
         nt = (w.n + NB - 1) // NB
         tiles = sum(m * (m + 1) // 2 for m in range(1, nt))          # trailing tiles per instance
-        exec_flops = float(tiles) * prods * 2 * NB ** 3 * w.T * args.steps
-        achieved = exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
         peak = pk["bf16_tflops_sustained"]
+        # the method's own work: the trailing updates of one Cholesky of the n
+        # real rows (update_flops), each executed as `prods` bf16 slice
+        # products of the same shape
+        alg_flops = update_flops(w.n) * prods * w.T * args.steps
+        exec_flops = float(tiles) * prods * 2 * NB ** 3 * w.T * args.steps
+        achieved = alg_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+        executed = exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
         # one unit = one 128 x 128 tile updated by one 128-wide panel; a launch
         # updates tiles * T * steps / launches of them on average (the fused
         # launches apply two panels per tile)
@@ -313,10 +358,14 @@ def run_gp(args):
                 "algorithmic_bytes_per_launch": units * NB * NB * 8,
                 "peak_source": ("bf16 dense sustained, measured (MEASURED_PEAKS.json)" if pk_src == "measured"
                                 else "bf16 dense sustained, fallback (1.7 PFLOP/s; MEASURED_PEAKS.json absent)"),
-                "flops_counted": f"executed bf16 slice products: {tiles} 128x128 tiles per "
-                                 f"instance x {prods} products x 2*128^3",
+                "flops_counted": f"algorithmic: the trailing updates of the {w.n} real rows "
+                                 f"(sum over block steps of 128 m (m + 1)) x {prods} slice products",
+                "frac_executed": (executed / peak) if executed else None,
+                "executed_flops_note": f"executed: {tiles} whole 128x128 tiles per instance x {prods} "
+                                       f"products x 2*128^3; the padded rows and the upper halves of the "
+                                       f"diagonal tiles are {100.0 * (1.0 - alg_flops / exec_flops):.1f}% of it",
                 "launches_timed": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1),
-                "flops_per_launch": exec_flops / max(upd_n, 1),
+                "flops_per_launch": alg_flops / max(upd_n, 1),
                 "fp64_equivalent_tflops": update_flops(w.n) * w.T * args.steps / (upd_ms / 1e3) / 1e12}
 
     # ---- end to end through the host-buffer entry point ---------------------
@@ -347,16 +396,22 @@ def run_gp(args):
 
     # ---- secondary precision (the other arm of the metric) -------------------
     other = None
+    fp64_out = None
     if args.compare and prec == "mixed":
         o = ctx.nll_batch(x, y, th, w.p, w.delta, "fp64")
         torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.phase_times()
         a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(args.compare_steps):
             o = ctx.nll_batch(x, y, th, w.p, w.delta, "fp64", out=o)
         a1.record(stream)
         torch.cuda.synchronize()
+        ph64 = ctx.phase_times()
+        ctx.set_timing(False)
         ms = a0.elapsed_time(a1)
+        fp64_out = o
         ref = o["nll"].cpu().numpy()
         got = out["nll"].cpu().numpy()
         # the tolerance applies where cond_1(R) <= 1e8: take the library's own
@@ -365,18 +420,31 @@ def run_gp(args):
         fin = np.isfinite(ref) & np.isfinite(got)
         rel = np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])
         wc = cnd[fin] <= 1e8
+        # beyond cond_1 = 1e8 the error is reported against the rounding bound
+        # n cond_1 u (u = 2^-53) of a factorisation in double
+        ratio = rel / (w.n * cnd[fin] * 2.0 ** -53)
+        upd64_ms = ph64["update"][0]
+        upd64 = update_flops(w.n) * w.T * args.compare_steps / (upd64_ms / 1e3) / 1e12 if upd64_ms else None
+        dg = fp64_dgemm_tflops(dev)
         other = {"prec": "fp64", "value": world * w.T * args.compare_steps / (ms / 1e3),
                  "steps": args.compare_steps,
+                 "update_fp64_tflops": upd64, "fp64_dgemm_tflops_measured": dg,
+                 "update_frac_of_dgemm": (upd64 / dg) if upd64 else None,
                  "mixed_vs_fp64_rel_err_nll": {
                      "max": float(rel.max()) if rel.size else None,
                      "median": float(np.median(rel)) if rel.size else None,
                      "max_where_cond1_le_1e8": float(rel[wc].max()) if wc.any() else None,
                      "candidates_cond1_le_1e8": int(wc.sum()),
-                     "cond1_range": [float(np.nanmin(cnd)), float(np.nanmax(cnd))]}}
+                     "cond1_range": [float(np.nanmin(cnd)), float(np.nanmax(cnd))],
+                     "max_err_over_n_cond1_u": float(ratio.max()) if ratio.size else None,
+                     "per_candidate_cond1_err": [[float(f"{c:.3g}"), float(f"{e:.3g}")]
+                                                 for c, e in zip(cnd[fin], rel)]}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(w)
+        cpu, o_out, o_st = cpu_baseline_sample(w)
+        if other is not None:
+            other["vs_oracle"] = oracle_errors(o_out, o_st, out, fp64_out)
 
     if rank == 0:
         pct = lambda q: float(np.percentile(step_ms, q))

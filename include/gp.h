@@ -55,11 +55,17 @@ typedef struct gp_plan gp_plan;
 
 /* Arithmetic of the factorisation.
  * GP_FP64:  assembly, Cholesky and solves in IEEE double.
- * GP_MIXED: assembly, diagonal-block factorisation and inversion, log-det
- *           and the iterative-refinement residuals in double; the panel and
- *           trailing updates of the blocked Cholesky on the tensor cores with
- *           double operands split into bf16 slices and exact fp32
- *           accumulation (Ozaki-style), recombined in double-float.
+ * GP_MIXED: the panel solves and trailing updates of the blocked Cholesky
+ *           on the tensor cores: operands split into bf16 slices, exact fp32
+ *           accumulation of the product groups (Ozaki-style), recombined in
+ *           double-float (a pair of floats, ~48 significant bits).  Everything
+ *           else runs in double-float on the FP32 pipes, not in IEEE double:
+ *           the assembly of R (a table-driven exp, ~46 bits), the factor and
+ *           inverse of each diagonal block, the forward and backward
+ *           substitutions, and the iterative refinement, whose residual
+ *           b - R x is formed against a double-float copy of R.  Only the
+ *           logarithms of the pivots (log|R|) and the last scalar steps
+ *           (mu_hat, Q, -2logL from the double-float sums) are IEEE double.
  * GP_FP32:  the GP_MIXED factorisation with 3 slices in the trailing
  *           updates: 24 significant bits, the precision of an FP32 factor,
  *           at 6 tensor-core products per tile update instead of 15.  Meant
