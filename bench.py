@@ -421,8 +421,11 @@ def run_gp(args):
         rel = np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])
         wc = cnd[fin] <= 1e8
         # beyond cond_1 = 1e8 the error is reported against the rounding bound
-        # n cond_1 u (u = 2^-53) of a factorisation in double
-        ratio = rel / (w.n * cnd[fin] * 2.0 ** -53)
+        # n cond_1 u (u = 2^-53) of a factorisation in double, in absolute
+        # terms: log|R| and n log Q carry absolute errors, and -2logL itself
+        # may be close to zero
+        absd = np.abs(got[fin] - ref[fin])
+        ratio = absd / (w.n * cnd[fin] * 2.0 ** -53)
         upd64_ms = ph64["update"][0]
         upd64 = update_flops(w.n) * w.T * args.compare_steps / (upd64_ms / 1e3) / 1e12 if upd64_ms else None
         dg = fp64_dgemm_tflops(dev)
@@ -436,9 +439,10 @@ def run_gp(args):
                      "max_where_cond1_le_1e8": float(rel[wc].max()) if wc.any() else None,
                      "candidates_cond1_le_1e8": int(wc.sum()),
                      "cond1_range": [float(np.nanmin(cnd)), float(np.nanmax(cnd))],
-                     "max_err_over_n_cond1_u": float(ratio.max()) if ratio.size else None,
-                     "per_candidate_cond1_err": [[float(f"{c:.3g}"), float(f"{e:.3g}")]
-                                                 for c, e in zip(cnd[fin], rel)]}}
+                     "max_abs": float(absd.max()) if absd.size else None,
+                     "max_abs_err_over_n_cond1_u": float(ratio.max()) if ratio.size else None,
+                     "per_candidate_cond1_rel_abs": [[float(f"{c:.3g}"), float(f"{e:.3g}"), float(f"{a:.3g}")]
+                                                     for c, e, a in zip(cnd[fin], rel, absd)]}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -114,7 +114,12 @@ typedef struct {
     int slices;           /* GP_MIXED: bf16 slices per double operand (2..6), default 5 */
     int panel_slices;     /* GP_MIXED: slices of the panel-solve GEMM; fixed at 7 (all
                              product groups exact), other values are rejected */
-    int refine_iters;     /* GP_MIXED: iterative-refinement steps of the solves, default 1 */
+    int refine_iters;     /* GP_MIXED: most iterative-refinement steps of the solves
+                             (0..10), default 1.  Each candidate stops earlier once the
+                             error its -2logL has left from Q falls below the error of
+                             its log|R|, which no refinement changes: an estimate from
+                             its own pivots, 2^-40 (1 + delta) sum_i 1 / L_ii^2.  Steps
+                             that no candidate takes still cost their launches */
     int nugget_in_var;    /* kriging variance uses 1 + delta (1) or 1 (0), default 1 */
     int max_batch;        /* instances factored concurrently (0 = from the budget) */
     int update_groups;    /* GP_MIXED: fp32 accumulators of the trailing update: 3 or 4

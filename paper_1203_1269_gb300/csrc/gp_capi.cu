@@ -31,6 +31,10 @@ struct gp_ctx {
     std::vector<gp_plan*> plans;     // live plans (likewise)
     long long phase_launches[GP_NUM_PHASES] = {0};
     long long launches = 0;
+    // a second stream for work that overlaps the main stream inside a call
+    // (forked from and joined back to it with the two events)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 struct gp_model {
@@ -270,6 +274,20 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     return mb;
 }
 
+// The context's second stream and its fork / join events (made on first use).
+int ensure_aux(gp_ctx* ctx) {
+    if (ctx->aux) return GP_OK;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GP_ECUDA, "creating the auxiliary stream failed");
+    }
+    return GP_OK;
+}
+
 // Assemble and factor (split precision) the instances of `mb`.
 int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, const double* theta, double p,
                      double delta) {
@@ -280,6 +298,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
     b.inst_stride = mb.inst_stride; b.st = mb.st;
     b.asm_cols = ctx->opt.assemble_cols;
     mb.d = d;
+    mb.delta = delta;
     GP_CUDA(ctx, cudaMemsetAsync(mb.err, 0, sizeof(int), ctx->stream));
     {
         PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, mb.fwd ? 3 : 2);
@@ -288,23 +307,39 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
         if (mb.fwd) GP_CUDA(ctx, gp::launch_rhs_init(mb, ctx->stream));
     }
     const int nt = mb.nt;
-    auto diag = [&](int J) -> int {
-        PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
-        GP_CUDA(ctx, gp::launch_diag_mixed(mb, J, ctx->stream));
+    int rc = ensure_aux(ctx);
+    if (rc) return rc;
+    // Diagonal block J and the slices of panel J's tiles for the panel solve
+    // touch disjoint buffers: the slicing runs on the second stream while
+    // the diagonal kernel (latency-bound, about one CTA per SM) runs on the
+    // main one, and the panel solve waits for both.
+    auto diag_and_slices = [&](int J) -> int {
+        const bool slices = J + 1 < nt;
+        if (slices) GP_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+        {
+            PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
+            GP_CUDA(ctx, gp::launch_diag_mixed(mb, J, ctx->stream));
+        }
+        if (slices) {
+            GP_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+            ctx->launches += 1;
+            ctx->phase_launches[GP_PHASE_SPLIT] += 1;
+            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, 0, ctx->aux));
+            GP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
+            // the time the main stream waits here is the slicing left exposed
+            PhaseScope ps(ctx, GP_PHASE_SPLIT, 0);
+            GP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+        }
         return GP_OK;
     };
     auto panel = [&](int J) -> int {
-        {
-            PhaseScope ps(ctx, GP_PHASE_SPLIT, 1);
-            GP_CUDA(ctx, gp::launch_split_panel(mb, J, mb.ps, 0, ctx->stream));
-        }
         PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
         GP_CUDA(ctx, gp::launch_gemm_panel(mb, J, ctx->stream));
         return GP_OK;
     };
     int J = 0;
     while (J < nt) {
-        int rc = diag(J);
+        rc = diag_and_slices(J);
         if (rc) return rc;
         if (J + 1 == nt) break;
         rc = panel(J);
@@ -321,7 +356,7 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
                 PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
                 GP_CUDA(ctx, gp::launch_gemm_update_column(mb, J, ctx->stream));
             }
-            rc = diag(J + 1);
+            rc = diag_and_slices(J + 1);
             if (rc) return rc;
             rc = panel(J + 1);
             if (rc) return rc;
@@ -343,18 +378,28 @@ int run_mixed_factor(gp_ctx* ctx, gp::MixedBatch& mb, int d, const double* x, co
     return GP_OK;
 }
 
-// Solves with refinement and the likelihood for the factored instances.
+// Solves with refinement and the likelihood for the factored instances: the
+// backward substitution x = L^-T [a b] of the forward solve's results, then
+// up to refine_iters refinement steps (residual and forward correction; the
+// correction's backward substitution only when another step follows), each
+// closed by k_refine_check, which forms the sums of eq. 3 and stops the
+// candidates whose -2logL no further step can improve (k_mixed.cu).
 int run_mixed_solve(gp_ctx* ctx, const gp::MixedBatch& mb, double* nll, double* mu, double* sigma2,
                     double* logdet, int* status) {
     const int sp = gp::subst_launches(mb.nt);
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, (mb.fwd ? 0 : 1 + sp) + sp + ctx->opt.refine_iters * (2 + 2 * sp) + 1);
+    const int steps = ctx->opt.refine_iters;
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, (mb.fwd ? 0 : 1 + sp) + 1 + sp + 1 + steps * (sp + 3) +
+                                           (steps > 1 ? (steps - 1) * sp : 0) + 1);
     // with mb.fwd the factorisation has already done the first forward solve
     if (!mb.fwd) GP_CUDA(ctx, gp::launch_df_forward(mb, 0, 1, ctx->stream));
+    GP_CUDA(ctx, gp::launch_keep_forward(mb, ctx->stream));
     GP_CUDA(ctx, gp::launch_df_backward(mb, 0, -1, ctx->stream));
-    for (int it = 0; it < ctx->opt.refine_iters; ++it) {
+    GP_CUDA(ctx, gp::launch_refine_check(mb, 0, ctx->stream));
+    for (int k = 1; k <= steps; ++k) {
+        if (k > 1) GP_CUDA(ctx, gp::launch_df_backward(mb, 2, 0, ctx->stream));   // x += L^-T z
         GP_CUDA(ctx, gp::launch_df_residual(mb, ctx->stream));
         GP_CUDA(ctx, gp::launch_df_forward(mb, 2, 0, ctx->stream));
-        GP_CUDA(ctx, gp::launch_df_backward(mb, 2, 0, ctx->stream));
+        GP_CUDA(ctx, gp::launch_refine_check(mb, k, ctx->stream));
     }
     GP_CUDA(ctx, gp::launch_df_finalize(mb, nll, mu, sigma2, logdet, status, ctx->stream));
     return GP_OK;
@@ -703,6 +748,12 @@ void gp_destroy(gp_ctx* ctx) {
     for (auto& o : ctx->ev_open) {
         cudaEventDestroy(o.second.first);
         cudaEventDestroy(o.second.second);
+    }
+    if (ctx->aux) {
+        cudaStreamSynchronize(ctx->aux);
+        cudaStreamDestroy(ctx->aux);
+        cudaEventDestroy(ctx->ev_fork);
+        cudaEventDestroy(ctx->ev_join);
     }
     delete ctx;
 }

@@ -72,6 +72,10 @@ struct InstState {
     int hager_iter;
     int hager_jprev;
     int hager_done;   // 1: the estimate has stopped; the solve kernels skip the instance
+    // iterative refinement of the split path (k_mixed.cu)
+    double piv_inv;   // sum_i 1 / L_ii^2 over the factor's pivots
+    double dq_prev;   // change of n log Q made by the previous refinement step
+    int refine_done;  // 1: the refinement has stopped; the solve kernels skip the instance
 };
 
 // Batched problem description handed to the kernels (by value).
@@ -94,6 +98,7 @@ struct Batch {
 // slice images of the current panel and of W = L_JJ^-1, solve vectors).
 struct MixedBatch {
     int n, d, nt, count;
+    double delta;                 // the nugget (the refinement's log-det error estimate)
     int s;                        // slices of the trailing update operands
     int ps;                       // slices of the panel solve operands (GP_PANEL_SLICES)
     int ug;                       // accumulator groups of the trailing update (3, 4 or 7)
@@ -117,9 +122,10 @@ struct MixedBatch {
     float2* WR;                   // the same, row-major (its transpose column-major), stride wt_stride
     size_t wt_stride;
     size_t ps_stride, pe_stride, ws_stride, we_stride;
-    float2* Z;                    // 8 columns of npad double-float values: x_1, x_y, two
-                                  // residual columns, 1 / L_ii, two condition-estimate
-                                  // columns, |R| row sums
+    float2* Z;                    // 10 columns of npad double-float values: x_1, x_y, two
+                                  // residual / correction columns, 1 / L_ii, two
+                                  // condition-estimate columns, |R| row sums, and
+                                  // a = L^-1 1, b = L^-1 Y (kept from the forward solve)
     size_t z_stride;
     float2* RP;                   // per-tile partial sums of the tile-parallel solves and residual
     size_t rp_stride;
@@ -130,7 +136,7 @@ struct MixedBatch {
     int* err;                     // set when a bounded device wait gave up
 };
 
-constexpr int kZCols = 8;
+constexpr int kZCols = 10;
 // kernel launches of one forward or backward substitution pass (the first
 // block's diagonal step, then a tile step per further block column that
 // also finishes the next block)
@@ -211,6 +217,8 @@ cudaError_t launch_scatter(int m, const int* idx, const double* src, double* dst
 cudaError_t launch_scatter_int(int m, const int* idx, const int* src, int* dst, cudaStream_t s);
 cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2,
                                double* logdet, int* status, cudaStream_t s);
+cudaError_t launch_keep_forward(const MixedBatch& b, cudaStream_t s);
+cudaError_t launch_refine_check(const MixedBatch& b, int step, cudaStream_t s);
 cudaError_t launch_df_to_double(const float2* src, double* dst, size_t count, cudaStream_t s);
 
 }  // namespace gp

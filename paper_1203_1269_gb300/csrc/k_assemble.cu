@@ -75,6 +75,7 @@ __global__ void k_validate_theta(Batch b) {
     s.fail_col = -1;
     s.anorm = 0.0; s.est = 0.0;
     s.hager_iter = 0; s.hager_jprev = -1; s.hager_done = 0;
+    s.piv_inv = 0.0; s.dq_prev = 0.0; s.refine_done = 0;
     b.st[t] = s;
 }
 

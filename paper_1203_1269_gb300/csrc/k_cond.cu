@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_hager(MixedBatch b, int phase, dou
                 st->hager_iter = 0;
                 st->hager_jprev = -1;
                 st->hager_done = 0;
+                st->refine_done = 0;   // the estimate's solves run for every instance
             }
         }
         return;

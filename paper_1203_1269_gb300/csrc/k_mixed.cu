@@ -20,9 +20,11 @@
 // factorisation (the diagonal kernel and the slicing of each solved panel).
 //
 // Solves: the backward substitution with the double-float factor, two
-// right-hand sides, then one step of iterative refinement against the
-// double-float copy of R (residual r = b - R x, forward and backward
-// correction), all tile-parallel; then the profile likelihood.
+// right-hand sides, then iterative refinement against the double-float copy
+// of R (residual r = b - R x, forward correction z = L^-1 r), all
+// tile-parallel, with the sums of eq. 3 taken from forward-only identities
+// (k_refine_check) and a per-candidate stopping rule; then the profile
+// likelihood.
 #include "mixed_common.cuh"
 
 namespace gp {
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     __shared__ dfl bj[2][GP_NB];
     __shared__ dfl xpart[2][GP_NB];
     __shared__ double lsum[GP_NB / 32];
+    __shared__ double psum[GP_NB / 32];
     __shared__ int failed;
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
@@ -175,18 +178,32 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     }
     // log-det: sum of log L_cc over the block in a fixed order (warp trees,
     // then the four warp sums in turn); reciprocal diagonal out
+    // and the sum of 1 / L_cc^2 over the block's real rows (the refinement's
+    // estimate of the log-det's own error, k_refine_check)
     if (threadIdx.x < GP_NB) {
         double v = log(df_to_double(lcc[threadIdx.x]));
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) lsum[warp] = v;
+        const double di = df_to_double(dinv[threadIdx.x]);
+        double q = (J * GP_NB + (int)threadIdx.x < b.n) ? di * di : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_down_sync(0xffffffffu, v, o);
+            q += __shfl_down_sync(0xffffffffu, q, o);
+        }
+        if (lane == 0) {
+            lsum[warp] = v;
+            psum[warp] = q;
+        }
         float2* rinv = b.Z + (size_t)t * b.z_stride + (size_t)4 * b.nt * GP_NB + J * GP_NB;
         df_store(rinv + threadIdx.x, dinv[threadIdx.x]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double ld = 0.0;
-        for (int w = 0; w < GP_NB / 32; ++w) ld += lsum[w];
+        double ld = 0.0, pq = 0.0;
+        for (int w = 0; w < GP_NB / 32; ++w) {
+            ld += lsum[w];
+            pq += psum[w];
+        }
         b.st[t].logdet += 2.0 * ld;
+        b.st[t].piv_inv += pq;
     }
     // W as a double-float tile (column-major, zeros above the diagonal) for
     // the diagonal-block products of the solves
@@ -537,7 +554,7 @@ __global__ void k_rhs_init(MixedBatch b) {
 constexpr int kSubThreads = 256;
 
 __device__ __forceinline__ bool sub_active(const MixedBatch& b, int t) {
-    return b.st[t].status == GP_OK && !b.st[t].hager_done;
+    return b.st[t].status == GP_OK && !b.st[t].hager_done && !b.st[t].refine_done;
 }
 
 __device__ __forceinline__ float2* rp_part(const MixedBatch& b, int t, int I, int J) {
@@ -779,7 +796,7 @@ __global__ void __launch_bounds__(kResThreads) k_resid_tiles(MixedBatch b) {
     __shared__ dfl xb[2][GP_NB];                // x_I
     __shared__ dfl part[2 * 2 * GP_NB];           // U: [2][2][128], then V: [4][2][64]
     const int t = blockIdx.y;
-    if (b.st[t].status != GP_OK) return;
+    if (b.st[t].status != GP_OK || b.st[t].refine_done) return;
     const int nt = b.nt;
     const int q = blockIdx.x >> 1, hc = blockIdx.x & 1;
     int J = 0, rem = q;
@@ -844,7 +861,7 @@ __global__ void __launch_bounds__(kResThreads) k_resid_tiles(MixedBatch b) {
 // so r = 0.  One CTA per (row block I, instance).
 __global__ void __launch_bounds__(kResThreads) k_resid_reduce(MixedBatch b) {
     const int t = blockIdx.y, I = blockIdx.x;
-    if (b.st[t].status != GP_OK) return;
+    if (b.st[t].status != GP_OK || b.st[t].refine_done) return;
     const int nt = b.nt, n = b.n;
     const int k = threadIdx.x >> 7, r = threadIdx.x & 127;
     const float2* rp = b.RP + (size_t)t * b.rp_stride;
@@ -864,37 +881,63 @@ __global__ void __launch_bounds__(kResThreads) k_resid_reduce(MixedBatch b) {
     df_store(zcol(b, t, 2 + k) + gi, (gi < n) ? df_sub(bq, y) : dfl{0.f, 0.f});
 }
 
-// mu_hat = 1'x_y / 1'x_1, w = x_y - mu x_1 = R^-1 (Y - 1 mu), Q = (Y - 1 mu)'w,
-// -2logL = log|R| + n log Q; column 1 becomes w (for kriging), column 0 keeps
-// x_1 = R^-1 1.  Q is taken as zero when Q <= 16 n eps^2 Y'x_y with
-// eps = 2^-40, the accuracy unit of the split factorisation.
-__global__ void __launch_bounds__(kSolveThreads) k_df_finalize(MixedBatch b, double* nll, double* mu,
-                                                               double* sigma2, double* logdet, int* status) {
+// a = L^-1 1 and b = L^-1 Y (Z columns 0, 1 after the forward solve) into
+// columns 8, 9, where the refinement's sums read them
+__global__ void k_keep_forward(MixedBatch b) {
+    const int t = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npad = b.nt * GP_NB;
+    if (b.st[t].status != GP_OK || i >= 2 * npad) return;
+    const int k = i / npad, r = i - k * npad;
+    zcol(b, t, 8 + k)[r] = zcol(b, t, k)[r];
+}
+
+// The sums of eq. 3 after refinement step `step` (0: the first solve, before
+// any correction), and whether the candidate refines further.
+//
+// With the factor L (L L' ~ R), x = [x_1 x_y] the current solution of
+// R x = [1 Y], r = [1 Y] - R x its residual and z = L^-1 r (Z columns 2, 3),
+// the refined solution is x + L^-T z, and every sum eq. 3 needs follows
+// without that backward substitution, since v' L^-T z = (L^-1 v)' z:
+//   1'R^-1 1 = 1'x_1 + a'z_1,   1'R^-1 Y = 1'x_y + a'z_y,   mu = their ratio,
+//   Q = (Y - 1 mu)'(x_y - mu x_1) + (b - mu a)'(z_y - mu z_1),
+//   Y'R^-1 Y = Y'x_y + b'z_y,
+// a = L^-1 1, b = L^-1 Y (columns 8, 9).  A further step first applies the
+// backward substitution to z and adds it to x.
+//
+// Stopping rule.  The factor's pivots carry an absolute error of about
+// 2^-40 (1 + delta) each (a row of L has norm^2 R_ii = 1 + delta and the
+// split products are exact to about 2^-40 of it), so log|R| = sum log L_ii^2
+// is uncertain by about e_ld = 2^-40 (1 + delta) sum_i 1 / L_ii^2.  Step k
+// changes n log Q by dq_k; with the contraction rho of the iteration (1/16
+// assumed after the first step, then dq_k / dq_{k-1}) the error of n log Q
+// left is about dq_k rho / (1 - rho).  Once that is below e_ld, further steps
+// cannot make -2logL more accurate, and the candidate stops.
+__global__ void __launch_bounds__(kSolveThreads) k_refine_check(MixedBatch b, int step) {
     __shared__ dfl red[kSolveThreads / 32];
     const int t = blockIdx.x;
-    InstState st = b.st[t];
+    InstState* st = b.st + t;
+    if (st->status != GP_OK || st->refine_done) return;
     const int n = b.n;
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    if (st.status != GP_OK) {
-        if (threadIdx.x == 0) {
-            nll[t] = (st.status == GP_ENOTPD) ? inf : nan;
-            mu[t] = nan;
-            sigma2[t] = nan;
-            if (logdet) logdet[t] = (st.status == GP_ENOTPD) ? nan : nan;
-            status[t] = st.status;
-        }
-        return;
-    }
-    float2* x1 = zcol(b, t, 0);
-    float2* xy = zcol(b, t, 1);
+    const float2* x1 = zcol(b, t, 0);
+    const float2* xy = zcol(b, t, 1);
+    const float2* z1 = zcol(b, t, 2);
+    const float2* zy = zcol(b, t, 3);
+    const float2* av = zcol(b, t, 8);
+    const float2* bv = zcol(b, t, 9);
+    const bool corr = step > 0;
     dfl sa = {0.f, 0.f}, sb = {0.f, 0.f}, sc = {0.f, 0.f};
     for (int i = threadIdx.x; i < n; i += kSolveThreads) {
-        const dfl a = df_load(x1 + i), c = df_load(xy + i);
-        const dfl yi = df_from_double(b.y[i]);
-        sa = df_add(sa, a);
+        const dfl c = df_load(xy + i);
+        sa = df_add(sa, df_load(x1 + i));
         sb = df_add(sb, c);
-        sc = df_fma(yi, c, sc);
+        sc = df_fma(df_from_double(b.y[i]), c, sc);
+        if (corr) {
+            const dfl ai = df_load(av + i), zyi = df_load(zy + i);
+            sa = df_fma(ai, df_load(z1 + i), sa);
+            sb = df_fma(ai, zyi, sb);
+            sc = df_fma(df_load(bv + i), zyi, sc);
+        }
     }
     const double A = df_to_double(block_sum_df(sa, red));
     const double B = df_to_double(block_sum_df(sb, red));
@@ -903,27 +946,62 @@ __global__ void __launch_bounds__(kSolveThreads) k_df_finalize(MixedBatch b, dou
     const dfl md = df_from_double(m);
     dfl sq = {0.f, 0.f};
     for (int i = threadIdx.x; i < n; i += kSolveThreads) {
-        const dfl wv = df_fms(md, df_load(x1 + i), df_load(xy + i));
-        df_store(xy + i, wv);
         const dfl e = df_sub(df_from_double(b.y[i]), md);
-        sq = df_fma(e, wv, sq);
+        sq = df_fma(e, df_fms(md, df_load(x1 + i), df_load(xy + i)), sq);
+        if (corr) {
+            const dfl u = df_fms(md, df_load(av + i), df_load(bv + i));
+            sq = df_fma(u, df_fms(md, df_load(z1 + i), df_load(zy + i)), sq);
+        }
     }
     const double Q = df_to_double(block_sum_df(sq, red));
     if (threadIdx.x == 0) {
-        const double eps = 9.094947017729282e-13;   // 2^-40
-        const bool degenerate = Q <= 16.0 * n * eps * eps * fabs(C);
-        nll[t] = degenerate ? -inf : st.logdet + n * log(Q);
-        mu[t] = m;
-        sigma2[t] = Q / n;
-        if (logdet) logdet[t] = st.logdet;
-        status[t] = degenerate ? GP_EDEGENERATE : GP_OK;
-        st.aa = A;
-        st.ab = B;
-        st.bb = C;
-        st.mu = m;
-        st.Q = Q;
-        b.st[t] = st;
+        const double Qprev = st->Q;
+        st->aa = A;
+        st->ab = B;
+        st->bb = C;
+        st->mu = m;
+        st->Q = Q;
+        if (!(Q > 0.0)) {
+            st->refine_done = 1;            // degenerate: the finalisation reports it
+        } else if (corr) {
+            const double dq = n * fabs(log(Q) - log(Qprev));
+            double rho = 0.0625;
+            if (step > 1 && st->dq_prev > 0.0) rho = fmin(0.5, fmax(dq / st->dq_prev, 1.52587890625e-05));
+            const double rest = dq * rho / (1.0 - rho);
+            const double e_ld = 9.094947017729282e-13 * (1.0 + b.delta) * st->piv_inv;   // 2^-40
+            st->dq_prev = dq;
+            if (rest <= e_ld) st->refine_done = 1;
+        }
     }
+}
+
+// -2logL = log|R| + n log Q from the sums of the last refinement check; Q is
+// taken as zero when Q <= 16 n eps^2 Y'R^-1 Y with eps = 2^-40, the accuracy
+// unit of the split factorisation.
+__global__ void k_df_finalize(MixedBatch b, double* nll, double* mu, double* sigma2, double* logdet,
+                              int* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.count) return;
+    const InstState st = b.st[t];
+    const int n = b.n;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    if (st.status != GP_OK) {
+        nll[t] = (st.status == GP_ENOTPD) ? inf : nan;
+        mu[t] = nan;
+        sigma2[t] = nan;
+        if (logdet) logdet[t] = nan;
+        status[t] = st.status;
+        return;
+    }
+    const double eps = 9.094947017729282e-13;   // 2^-40
+    const double Q = st.Q;
+    const bool degenerate = !(Q > 16.0 * n * eps * eps * fabs(st.bb));
+    nll[t] = degenerate ? -inf : st.logdet + n * log(Q);
+    mu[t] = st.mu;
+    sigma2[t] = Q / n;
+    if (logdet) logdet[t] = st.logdet;
+    status[t] = degenerate ? GP_EDEGENERATE : GP_OK;
 }
 
 // Convert the double-float factor and solve vectors of one fitted instance
@@ -1008,7 +1086,18 @@ cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
 
 cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2, double* logdet,
                                int* status, cudaStream_t s) {
-    k_df_finalize<<<b.count, kSolveThreads, 0, s>>>(b, nll, mu, sigma2, logdet, status);
+    k_df_finalize<<<(b.count + 127) / 128, 128, 0, s>>>(b, nll, mu, sigma2, logdet, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keep_forward(const MixedBatch& b, cudaStream_t s) {
+    const int npad = b.nt * GP_NB;
+    k_keep_forward<<<dim3((2 * npad + 255) / 256, b.count), 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_check(const MixedBatch& b, int step, cudaStream_t s) {
+    k_refine_check<<<b.count, kSolveThreads, 0, s>>>(b, step);
     return cudaGetLastError();
 }
 
