@@ -69,7 +69,17 @@ __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) {
 // c - a * b
 __device__ __forceinline__ dfl df_fms(dfl a, dfl b, dfl c) { return df_fma(df_neg(a), b, c); }
 
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) { return df_fma(a, b, dfl{0.f, 0.f}); }
+// a * b: the exact product of the high words, its error and the cross terms
+// (what df_fma gives with c = 0, without the additions of zero)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s, t;
+    fast_two_sum(p, e, s, t);
+    return {s, t};
+}
 
 // a / b to about 46 bits: one Newton correction of the float quotient
 __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
@@ -94,45 +104,48 @@ __device__ __forceinline__ dfl df_load(const float2* p) {
 
 __device__ __forceinline__ void df_store(float2* p, dfl a) { *p = make_float2(a.hi, a.lo); }
 
-// exp(-S) for S >= 0 to about 46 bits, after P. T. P. Tang, "Table-driven
+// Entries of the table of 2^(-j/N) that df_exp_neg reads (N = 1024: 8 KB
+// of double-float values in shared memory).
+constexpr int kExpTabBits = 10;
+constexpr int kExpTab = 1 << kExpTabBits;
+
+// exp(-S) to about 46 bits, after P. T. P. Tang, "Table-driven
 // implementation of the exponential function in IEEE floating-point
-// arithmetic", ACM TOMS 15 (1989):
-//   k = round(S * 64 / ln 2),  r = S - k ln2/64  (|r| <= ln2/128, Cody-Waite
-//   reduction with ln2/64 held as two floats), exp(-S) = 2^(-k/64) exp(-r),
-//   2^(-k/64) = 2^(-m) tab[j] with k = 64 m + j, and exp(-r) by its Taylor
-//   series to r^5 (the r^6 term is below 2^-54 for |r| <= ln2/128).
-// tab[j] = 2^(-j/64) as double-float (filled by fill_exp2_table).  Results
+// arithmetic", ACM TOMS 15 (1989), with a table of N = 1024 entries:
+//   k = round(S N / ln 2),  r = S - k ln2/N  (|r| <= ln2/(2N) = 3.4e-4, a
+//   Cody-Waite reduction with ln2/N held as two floats),
+//   exp(-S) = 2^(-k/N) exp(-r),  2^(-k/N) = 2^(-m) tab[j] for k = N m + j,
+//   exp(-r) = 1 - r + q,  q = r^2/2 - r^3/6 (the r^4 term is below 2^-50).
+// q < 6e-8 is needed to float precision only, so past the reduction the
+// only double-float steps are 1 - r and the product with the table.  S may
+// be negative down to -83 (the logarithms of df_log's Newton step).
+// tab[j] = 2^(-j/N) as double-float (filled by fill_exp2_table).  Results
 // below 2^-125 (S > 86.6) are returned as zero.
 __device__ __forceinline__ dfl df_exp_neg(dfl S, const dfl* tab) {
-    constexpr double kLn2Over64 = 0.693147180559945309417232121458176568 / 64.0;
-    constexpr float kCHi = (float)kLn2Over64;
-    constexpr float kCLo = (float)(kLn2Over64 - (double)kCHi);
-    constexpr float k64OverLn2 = (float)(64.0 / 0.693147180559945309417232121458176568);
+    constexpr double kLn2OverN = 0.693147180559945309417232121458176568 / kExpTab;
+    constexpr float kCHi = (float)kLn2OverN;
+    constexpr float kCLo = (float)(kLn2OverN - (double)kCHi);
+    constexpr float kNOverLn2 = (float)(kExpTab / 0.693147180559945309417232121458176568);
     if (!(S.hi < 86.6f)) return {0.f, 0.f};
-    const float kf = rintf(__fmul_rn(S.hi, k64OverLn2));
+    const float kf = rintf(__fmul_rn(S.hi, kNOverLn2));
     const int k = (int)kf;
-    // r = S - k (C_hi + C_lo); k C_hi exactly as p1 + e1
+    // r = S - k (C_hi + C_lo); k C_hi as p1 + e1 exactly
     const float p1 = __fmul_rn(kf, kCHi);
     const float e1 = __fmaf_rn(kf, kCHi, -p1);
     const float p2 = __fmul_rn(kf, kCLo);
     float rh = __fsub_rn(S.hi, p1);   // exact: p1 is within a factor 2 of S.hi, or 0
     float rl = __fsub_rn(__fsub_rn(S.lo, e1), p2);
     two_sum(rh, rl, rh, rl);
-    // exp(-r) = 1 - r + r^2/2 + q3,  q3 = -r^3/6 + r^4/24 - r^5/120 (|q3| < 3e-8)
-    const dfl r = {rh, rl};
-    dfl r2 = df_mul(r, r);
-    r2.hi = __fmul_rn(r2.hi, 0.5f);
-    r2.lo = __fmul_rn(r2.lo, 0.5f);
-    const float q3 = __fmul_rn(__fmul_rn(rh, __fmul_rn(rh, rh)),
-                               __fmaf_rn(rh, __fmaf_rn(rh, -1.f / 120.f, 1.f / 24.f), -1.f / 6.f));
+    // q = rh^2/2 - rh^3/6 + rh rl  (r^2/2 to first order in rl)
+    float q = __fmaf_rn(rh, -1.f / 6.f, 0.5f);
+    q = __fmaf_rn(rh, q, rl);
+    q = __fmul_rn(rh, q);
     float s, t;
-    two_sum(1.f, -rh, s, t);
-    t = __fsub_rn(t, rl);
+    fast_two_sum(1.f, -rh, s, t);     // |rh| < 1
+    t = __fadd_rn(__fsub_rn(t, rl), q);
     fast_two_sum(s, t, s, t);
-    dfl e = df_add(dfl{s, t}, r2);
-    e.lo = __fadd_rn(e.lo, q3);
-    e = df_mul(e, tab[k & 63]);
-    const float sc = __int_as_float((127 - (k >> 6)) << 23);   // 2^-m, m <= 125
+    dfl e = df_mul(dfl{s, t}, tab[k & (kExpTab - 1)]);
+    const float sc = __int_as_float((127 - (k >> kExpTabBits)) << 23);   // 2^-m, -120 <= m <= 125
     e.hi = __fmul_rn(e.hi, sc);
     e.lo = __fmul_rn(e.lo, sc);
     return e;
@@ -172,9 +185,11 @@ __device__ __forceinline__ dfl df_powabs(dfl d, int mode, double p, dfl pd, cons
     return df_exp_neg(df_neg(df_mul(pd, df_log(d, tab))), tab);
 }
 
-// tab[j] = 2^(-j/64), j = 0..63, as double-float (threads 0..63 of a block).
+// tab[j] = 2^(-j/N), j = 0 .. N - 1, as double-float (the block's threads in
+// turn; the caller synchronises before the table is read).
 __device__ __forceinline__ void fill_exp2_table(dfl* tab) {
-    if (threadIdx.x < 64) tab[threadIdx.x] = df_from_double(exp2(-(double)threadIdx.x / 64.0));
+    for (int j = threadIdx.x; j < kExpTab; j += blockDim.x)
+        tab[j] = df_from_double(exp2(-(double)j / (double)kExpTab));
 }
 
 }  // namespace gp

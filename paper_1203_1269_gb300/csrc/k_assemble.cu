@@ -178,8 +178,8 @@ k_assemble_tiles_df(Batch b, int group) {
     double* xs_r = dsm;                                  // GP_NB * DB
     double* xs_c = xs_r + GP_NB * DB;                    // kColsDf * DB
     dfl* th = reinterpret_cast<dfl*>(xs_c + kColsDf * DB); // group * DB
-    dfl* tab = th + (size_t)group * DB;                  // 64
-    int* live = reinterpret_cast<int*>(tab + 64);        // group
+    dfl* tab = th + (size_t)group * DB;                  // kExpTab
+    int* live = reinterpret_cast<int*>(tab + kExpTab);   // group
     const int nt = b.nt, n = b.n, d = b.d;
     const int tile_lin = blockIdx.x / kSplitDf;
     const int part = blockIdx.x % kSplitDf;
@@ -378,7 +378,7 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
         grid = dim3((unsigned)(tiles * split), (unsigned)g_df);
         const int DB = b.d <= 4 ? 4 : (b.d <= 8 ? 8 : 16);
         const size_t smem = (size_t)(GP_NB + cols) * DB * sizeof(double) +
-                            ((size_t)group * DB + 64) * sizeof(dfl) + (size_t)group * sizeof(int);
+                            ((size_t)group * DB + kExpTab) * sizeof(dfl) + (size_t)group * sizeof(int);
         cudaError_t e = cudaSuccess;
         auto go = [&](auto kern) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -283,7 +283,7 @@ template <int DB>
 __global__ void __launch_bounds__(kThreads) k_grad_tiles(Batch b, const float2* Ri, const double* Z, size_t zs,
                                                          double* partial, int ntiles) {
     __shared__ double red[kThreads / 32][DB];
-    __shared__ dfl tab[64];
+    __shared__ dfl tab[kExpTab];
     fill_exp2_table(tab);
     __syncthreads();
     const int t = blockIdx.y, nt = b.nt, n = b.n, d = b.d;

@@ -45,7 +45,7 @@ struct PredArgs {
 };
 
 // NR test points per CTA, PT = NR / 2 per thread (two threads per row).
-// dynamic shared memory: rhs[NR][NB] + vs[NB][NR] (dfl) + xs[NR][d] + th[d] (dfl) + tab[64]
+// dynamic shared memory: rhs[NR][NB] + vs[NB][NR] (dfl) + xs[NR][d] + th[d] (dfl) + tab[kExpTab]
 template <int NR>
 __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
     constexpr int PT = NR / 2;
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_predict(PredArgs g) {
     dfl* vs = rhs + NR * GP_NB;                    // [NB][NR]
     dfl* xsm = vs + GP_NB * NR;                    // [NR][d]
     dfl* th = xsm + NR * g.d;                      // [d]
-    dfl* tab = th + g.d;                           // [64]
+    dfl* tab = th + g.d;                           // [kExpTab]
     __shared__ dfl red[3][NR][4];
     const int d = g.d, n = g.n, nt = g.nt;
     const int npad = nt * GP_NB;
@@ -225,7 +225,7 @@ int predict_points_per_cta(int N, int sms) { return (N + 15) / 16 < 2 * sms ? 8 
 
 template <int NR>
 static cudaError_t launch_predict_nr(const PredArgs& g0, int d, int N, int chunk, cudaStream_t s) {
-    const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + 64) * sizeof(dfl);
+    const size_t smem = (size_t)(2 * NR * GP_NB + NR * d + d + kExpTab) * sizeof(dfl);
     static std::atomic<size_t> attr[kMaxDevices];
     cudaError_t e = raise_smem_limit(k_predict<NR>, smem, attr);
     if (e != cudaSuccess) return e;
