@@ -145,25 +145,50 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
         __syncthreads();
         if (c + 1 == GP_NB) break;
         // phase 2: rows i > c, X_ip += L_ic V_p (p <= i), a warp per row; warp
-        // 0 takes only row c + 1 and its pivot, the others deal the rest
+        // 0 takes only row c + 1 and its pivot, the others deal the rest two
+        // rows at a time (both rows' loads first: eight independent
+        // multiply-adds per lane).  A row i reaches only the 32-column blocks
+        // j <= i / 32, a test that is uniform across the warp.
         dfl vl[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) vl[j] = V[lane + 32 * j];
-        const int i0 = (warp == 0) ? c + 1 : c + 1 + warp;
-        const int di = (warp == 0) ? GP_NB : kWarps - 1;
-        for (int i = i0; i < GP_NB; i += di) {
+        if (warp == 0) {
+            const int i = c + 1;
             const dfl m = df_neg(V[i]);    // L_ic
             dfl* row = P + prow(i);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int p = lane + 32 * j;
-                if (p <= i) {
+                if (32 * j <= i && p <= i) {
                     const dfl x0 = (p == c) ? dfl{0.f, 0.f} : row[p];
                     const dfl x = df_fma(m, vl[j], x0);
-                    if (p == c + 1 && i == c + 1)
+                    if (p == c + 1)
                         take_pivot(c + 1, x);
                     else
                         row[p] = x;
+                }
+            }
+        } else {
+            constexpr int kRowStep = kWarps - 1;
+            for (int i = c + 1 + warp; i < GP_NB; i += 2 * kRowStep) {
+                const int i2 = i + kRowStep;
+                const bool two = i2 < GP_NB;
+                const dfl m1 = df_neg(V[i]);
+                const dfl m2 = two ? df_neg(V[i2]) : dfl{0.f, 0.f};
+                dfl* r1 = P + prow(i);
+                dfl* r2 = P + prow(two ? i2 : i);
+                dfl x1[4], x2[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int p = lane + 32 * j;
+                    if (32 * j <= i) x1[j] = (p <= i && p != c) ? r1[p] : dfl{0.f, 0.f};
+                    if (two && 32 * j <= i2) x2[j] = (p <= i2 && p != c) ? r2[p] : dfl{0.f, 0.f};
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int p = lane + 32 * j;
+                    if (32 * j <= i && p <= i) r1[p] = df_fma(m1, vl[j], x1[j]);
+                    if (two && 32 * j <= i2 && p <= i2) r2[p] = df_fma(m2, vl[j], x2[j]);
                 }
             }
         }
