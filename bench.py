@@ -144,11 +144,24 @@ def dist_setup():
     return world, rank, local
 
 
-def workload_for_rank(rank, n=4000, T=256):
-    w = inputs.hartman_shape(n=n, T=T)
+# The workloads a step can run: the benchmark (the Hartman-shaped n = 4000
+# batch) and, for measurement beside it, the batched n = 2048 case and the
+# large n = 16384 instance of the other configurations.
+WORKLOADS = ("hartman", "batched", "large")
+
+
+def workload_for_rank(rank, n=4000, T=256, name="hartman"):
+    if name == "batched":
+        w = inputs.batched_split()
+        seed = inputs.BASE_SEED + 2
+    elif name == "large":
+        w = inputs.large_instance()
+        seed = inputs.BASE_SEED + 3
+    else:
+        w = inputs.hartman_shape(n=n, T=T)
+        seed = inputs.BASE_SEED + 1
     if rank > 0:
-        w.thetas = inputs.log_uniform_thetas(inputs.rng(inputs.BASE_SEED + 1 + 1000 * rank),
-                                             w.T, w.d)
+        w.thetas = inputs.log_uniform_thetas(inputs.rng(seed + 1000 * rank), w.T, w.d)
     return w
 
 
@@ -226,7 +239,7 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
-    w = workload_for_rank(0, args.n, args.T)
+    w = workload_for_rank(0, args.n, args.T, args.workload)
     import oracle
     cores = oracle.num_threads()
     k = max(1, min(w.T, cores))
@@ -265,7 +278,7 @@ def run_gp(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = workload_for_rank(rank, args.n, args.T)
+    w = workload_for_rank(rank, args.n, args.T, args.workload)
     prec = args.prec
     ctx = gp.Context(local)
     f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -444,15 +457,46 @@ def run_gp(args):
                      "per_candidate_cond1_rel_abs": [[float(f"{c:.3g}"), float(f"{e:.3g}"), float(f"{a:.3g}")]
                                                      for c, e, a in zip(cnd[fin], rel, absd)]}}
 
+    # ---- kriging at the best candidate (the large instance's N = 1e5 points) --
+    kriging = None
+    if args.workload == "large" and w.xs is not None:
+        st_h = out["status"].cpu().numpy()
+        nll_h = out["nll"].cpu().numpy()
+        okc = np.where(st_h == 0)[0]
+        best = int(okc[np.argmin(nll_h[okc])])
+        torch.cuda.synchronize()
+        k0 = time.perf_counter()
+        model = ctx.fit(x, y, th[best].contiguous(), w.p, w.delta, "fp64")
+        torch.cuda.synchronize()
+        t_fit = time.perf_counter() - k0
+        xs = f64(w.xs)
+        ctx.predict(model, xs[:1000])
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True); p1 = torch.cuda.Event(enable_timing=True)
+        p2 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        ctx.predict(model, xs, want_var=False)
+        p1.record(stream)
+        ctx.predict(model, xs)
+        p2.record(stream)
+        torch.cuda.synchronize()
+        kriging = {"N": int(xs.shape[0]), "candidate": best, "fit_s": t_fit,
+                   "mean_only_s": p0.elapsed_time(p1) / 1e3, "mean_and_variance_s": p1.elapsed_time(p2) / 1e3}
+        model.free()
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.workload == "large":
+        pass   # one oracle evaluation at n = 16384 takes minutes: no bounded sample
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, o_out, o_st = cpu_baseline_sample(w)
         if other is not None:
             other["vs_oracle"] = oracle_errors(o_out, o_st, out, fp64_out)
 
     if rank == 0:
         pct = lambda q: float(np.percentile(step_ms, q))
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        metric = METRIC if args.workload == "hartman" else \
+            f"GP -2logL evals/s at n={w.n} (d={w.d}, T={w.T} theta batch)"
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == "fp64" else "bf16-split/f64",
@@ -462,13 +506,15 @@ def run_gp(args):
                            "l2": "no flush: the batch's factor storage "
                                  f"({w.T * ((w.n + NB - 1) // NB) * ((w.n + NB - 1) // NB + 1) // 2 * NB * NB * 8 / 1e9:.1f} GB) "
                                  "exceeds L2 (129 MB)"},
-                "latency_ms": {"p50": pct(50), "p99": pct(99), "unit": "ms per 256-candidate batch"},
+                "latency_ms": {"p50": pct(50), "p99": pct(99), "unit": f"ms per {w.T}-candidate batch"},
                 "statuses_ok": ok,
                 "roofline": roof, "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()
                                                          if v[1]},
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         if other:
             line["compare"] = other
+        if kriging:
+            line["kriging"] = kriging
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -490,6 +536,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=4000, help="design size (profiling cases only)")
     ap.add_argument("--T", type=int, default=256, help="candidates per step (profiling cases only)")
+    ap.add_argument("--workload", default="hartman", choices=WORKLOADS,
+                    help="hartman: the benchmark (n = 4000, d = 6, T = 256); batched: n = 2048, "
+                         "d = 8, T = 1024; large: n = 16384, d = 10, T = 32 with kriging at 1e5 points")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -85,7 +85,7 @@ def test_clock_sampler_without_nvidia_smi():
 def test_reference_arm_line(capsys):
     """The reference arm (the oracle on the host) prints one JSON line with
     the contract's keys, on a small case."""
-    args = SimpleNamespace(n=96, T=8, steps=2, warmup=1, gpus=1)
+    args = SimpleNamespace(n=96, T=8, steps=2, warmup=1, gpus=1, workload="hartman")
     assert bench.run_reference(args) == 0
     lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
     assert len(lines) == 1
