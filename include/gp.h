@@ -368,16 +368,46 @@ int gp_nll_batch_noalloc(gp_ctx* ctx, int n, int d, const double* x, const doubl
                          double* mu_hat, double* sigma2_hat, double* logdet, int* status);
 
 /* Fit at one theta (length d): assemble, factor, solve, and keep on the
- * device what prediction needs.  The fit is always factored in IEEE double
- * whatever `prec` asks (any gp_precision value is accepted): a fit is one
- * factorisation, and the kriging variance needs r'R^-1 r to full precision.
+ * device what kriging needs (Section 3: one factorisation, then solves per
+ * test point).  prec:
+ *   GP_FP64 (and GP_AUTO): the factor in IEEE double; kriging means and
+ *       variances to double precision (the paper, too, refines its final
+ *       fit with double-precision runs, Sections 4-5).
+ *   GP_MIXED, GP_FP32: the split-precision factor of gp_nll_batch, with its
+ *       iterative refinement: kriging means carry about cond(R) 2^-46 of
+ *       relative error (w is refined), variances about cond(R) 2^-40 (the
+ *       solve v = L^-1 r uses the split factor); several times faster than
+ *       GP_FP64 from n ~ 4000 on.  The context's workspace grows as for
+ *       gp_nll_batch with T = 1.
  * Kept on the device: the factor L, w = R^-1 (Y - 1 mu_hat), a = L^-1 1 and a
- * copy of x, converted after the solves to double-float pairs (hi + lo floats,
- * ~48 bits) for the kriging kernel, and the scalars.  Synchronises.  On GP_OK,
- * *model owns that device memory until gp_model_free.  A fit whose R is
- * not positive definite returns GP_ENOTPD and no model. */
+ * copy of x, as double-float pairs (hi + lo floats, ~48 bits) for the
+ * kriging kernel, and the scalars.  Synchronises.  On GP_OK (or
+ * GP_EDEGENERATE: the mean is still usable), *model owns that device memory
+ * until gp_model_free.  A fit whose R is not positive definite returns
+ * GP_ENOTPD and no model. */
 int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y,
            const double* theta, double p, double delta, int prec, gp_model** model);
+
+/* gp_nll_batch at T candidates, then a fit (as gp_fit) at the best of them:
+ * the one with the smallest -2logL among those with status GP_OK (ties: the
+ * first).  The model is built from that candidate's own factor, which the
+ * batch has just computed, with no second factorisation (unless the batch ran
+ * in several chunks and the best one's factor was overwritten: then it is
+ * factored again, with the same result).  This is the last step of a
+ * multi-start search (Section 4: the paper's GA ends with the best
+ * candidate's fit and its predictions).
+ *   prec: GP_FP64, GP_MIXED or GP_FP32 (GP_ENOTSUP for GP_AUTO); the model
+ *         carries that precision (gp_fit).
+ *   nll .. status: as gp_nll_batch (device arrays of length T, logdet may be
+ *         NULL).
+ *   *best_host: index of the best candidate, or -1 if none gave GP_OK (the
+ *         call then returns GP_ENOTPD and no model).
+ * Synchronises.  Returns GP_OK or GP_EDEGENERATE with *model set, or an
+ * error. */
+int gp_fit_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
+                 const double* theta, double p, double delta, int prec, double* nll,
+                 double* mu_hat, double* sigma2_hat, double* logdet, int* status,
+                 int* best_host, gp_model** model);
 
 /* Scalars of a fit: out[0..5] = -2logL, mu_hat, sigma2_hat, log|R|, Q, a'a. */
 int gp_model_scalars(const gp_model* model, double* out_host);

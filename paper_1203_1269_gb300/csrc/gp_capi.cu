@@ -2,6 +2,7 @@
 // argument checks, the device workspace, batching of theta candidates and
 // the sequence of kernel launches for each call.
 #include <algorithm>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -426,9 +427,22 @@ int run_mixed_cond(gp_ctx* ctx, const gp::MixedBatch& mb, double* cond) {
     return GP_OK;
 }
 
+// Where the last chunk of a batched call left its candidates in the
+// workspace: gp_fit_batch builds a model from one of them.
+struct LastChunk {
+    int c0 = 0, cnt = 0;
+    bool split = false;
+    gp::MixedBatch mb{};          // split path
+    double* A = nullptr;          // FP64 path: factors, [a | b] solve vectors, records
+    double* Z = nullptr;
+    gp::InstState* st = nullptr;
+    size_t a_stride = 0, z_stride = 0;
+};
+
 int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                     const double* theta, double p, double delta, double* nll, double* mu,
-                    double* sigma2, double* logdet, int* status, int slices, double* cond) {
+                    double* sigma2, double* logdet, int* status, int slices, double* cond,
+                    LastChunk* last = nullptr) {
     const MixedSizes z = mixed_sizes(n, slices);
     Chunking ch;
     if (!chunk_batch(ctx->opt, ctx->budget, ctx->models_bytes, z.per, kMixedTail, T, &ch))
@@ -448,6 +462,12 @@ int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y,
             rc = run_mixed_cond(ctx, mb, cond + c0);
             if (rc) return rc;
         }
+        if (last) {
+            last->c0 = c0;
+            last->cnt = cnt;
+            last->split = true;
+            last->mb = mb;
+        }
     }
     return GP_OK;
 }
@@ -455,7 +475,7 @@ int mixed_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y,
 // -2logL in IEEE double for T candidates (batches sized by the budget).
 int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T,
                    const double* theta, double p, double delta, double* nll, double* mu_hat,
-                   double* sigma2_hat, double* logdet, int* status) {
+                   double* sigma2_hat, double* logdet, int* status, LastChunk* last = nullptr) {
     const int nt = gp::num_tiles(n);
     const size_t per = per_instance_bytes_f64(n);
     Chunking ch;
@@ -488,6 +508,16 @@ int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
         GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
         GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, mu_hat + c0, sigma2_hat + c0,
                                          logdet ? logdet + c0 : nullptr, status + c0, ctx->stream));
+        if (last) {
+            last->c0 = c0;
+            last->cnt = cnt;
+            last->split = false;
+            last->A = A;
+            last->Z = Z;
+            last->st = st;
+            last->a_stride = a_bytes / sizeof(double);
+            last->z_stride = zs;
+        }
     }
     return GP_OK;
 }
@@ -659,6 +689,134 @@ PredictShape predict_shape(int nt, int N, int sms, size_t avail, bool variances)
     while (s.chunk > 1 && s.per_cta * s.chunk > avail) s.chunk /= 2;
     s.bytes = variances ? s.per_cta * s.chunk : 256;
     return s;
+}
+
+// A model's device memory (one allocation, ModelSizes), counted against the
+// context's budget next to its workspace.
+int model_alloc(gp_ctx* ctx, int n, int d, double p, double delta, int prec, gp_model** out) {
+    *out = nullptr;
+    const ModelSizes ms = model_sizes(n, d);
+    if (ms.total + ctx->models_bytes + ctx->ws_bytes > ctx->budget)
+        return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", ms.total);
+    gp_model* m = new gp_model();
+    m->ctx = ctx; m->n = n; m->d = d; m->nt = gp::num_tiles(n); m->p = p; m->delta = delta; m->prec = prec;
+    m->corr = ctx->opt.correlation;
+    if (cudaMallocAsync(&m->mem, ms.total, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return fail(ctx, GP_ENOMEM, "allocation of %zu bytes for the model failed", ms.total);
+    }
+    m->bytes = ms.total;
+    char* c = (char*)m->mem;
+    m->L = (double*)c; c += ms.L;
+    m->Z = (double*)c; c += ms.Z;
+    m->x = (double*)c; c += ms.x;
+    m->theta = (double*)c; c += ms.th;
+    m->scalars = (double*)c; c += ms.sc;
+    m->status = (int*)c; c += ms.stat;
+    m->st = (gp::InstState*)c;
+    ctx->models_bytes += ms.total;
+    *out = m;
+    return GP_OK;
+}
+
+// Release a model that was never handed out (a failed fit).
+int model_discard(gp_ctx* ctx, gp_model* m, int code) {
+    cudaFreeAsync(m->mem, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->models_bytes -= m->bytes;
+    delete m;
+    return code;
+}
+
+// The kriging kernel reads the factor, [a | w] and x as double-float pairs:
+// convert what is still in double, copy x and theta in, read the status and
+// the scalars back, and hand the model out (GP_OK or GP_EDEGENERATE).
+int model_finish(gp_ctx* ctx, gp_model* m, const double* x, const double* theta, bool df_factor,
+                 gp_model** out) {
+    const size_t npad = (size_t)m->nt * GP_NB;
+    if (cudaMemcpyAsync(m->x, x, (size_t)m->n * m->d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) ||
+        cudaMemcpyAsync(m->theta, theta, (size_t)m->d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) ||
+        (!df_factor && gp::launch_to_df_inplace(m->L, gp::packed_elems(m->n), ctx->stream)) ||
+        (!df_factor && gp::launch_to_df_inplace(m->Z, 2 * npad, ctx->stream)) ||
+        gp::launch_to_df_inplace(m->x, (size_t)m->n * m->d, ctx->stream))
+        return model_discard(ctx, m, fail(ctx, GP_ECUDA, "model conversion failed"));
+    int hstatus = 0;
+    cudaError_t e = cudaMemcpyAsync(&hstatus, m->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->host_scalars, m->scalars, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return model_discard(ctx, m, fail(ctx, GP_ECUDA, "fit: %s", cudaGetErrorString(e)));
+    if (hstatus != GP_OK && hstatus != GP_EDEGENERATE)
+        return model_discard(ctx, m, fail(ctx, hstatus, "fit failed with status %d", hstatus));
+    ctx->models.push_back(m);
+    *out = m;
+    return hstatus;
+}
+
+// Model of candidate t (0-based inside the last chunk) of an FP64 batch: its
+// factor and [a | b] copied out of the workspace, then w = L^-T (b - mu a)
+// as gp_fit forms it.
+int model_from_fp64(gp_ctx* ctx, gp_model* m, const LastChunk& lc, int t, const double* nll, const double* mu, const double* sigma2, const double* logdet,
+                    const int* status) {
+    const size_t npad = (size_t)m->nt * GP_NB;
+    cudaStream_t s = ctx->stream;
+    if (cudaMemcpyAsync(m->L, lc.A + (size_t)t * lc.a_stride, gp::packed_elems(m->n) * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(m->Z, lc.Z + (size_t)t * lc.z_stride, 2 * npad * sizeof(double), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(m->st, lc.st + t, sizeof(gp::InstState), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(m->scalars + 0, nll, sizeof(double), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(m->scalars + 1, mu, sizeof(double), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(m->scalars + 2, sigma2, sizeof(double), cudaMemcpyDeviceToDevice, s) ||
+        (logdet && cudaMemcpyAsync(m->scalars + 3, logdet, sizeof(double), cudaMemcpyDeviceToDevice, s)) ||
+        cudaMemcpyAsync(m->status, status, sizeof(int), cudaMemcpyDeviceToDevice, s))
+        return fail(ctx, GP_ECUDA, "copy of the factor into the model failed");
+    gp::Batch b{};
+    b.n = m->n; b.nt = m->nt; b.count = 1; b.st = m->st; b.A = m->L; b.inst_stride = gp::packed_elems(m->n);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+    if (gp::launch_fit_finish(b, m->Z, 2 * npad, m->scalars, s) ||
+        gp::launch_backward_solve(b, m->Z, 2 * npad, 1, s))
+        return fail(ctx, GP_ECUDA, "solve launch failed");
+    return GP_OK;
+}
+
+// The one-candidate view of candidate t of a split batch.
+gp::MixedBatch mixed_view(const gp::MixedBatch& mb, int t) {
+    gp::MixedBatch v = mb;
+    v.count = 1;
+    v.A += (size_t)t * mb.inst_stride;
+    v.Rc += (size_t)t * mb.inst_stride;
+    v.PS += (size_t)t * mb.ps_stride;
+    v.PE += (size_t)t * mb.pe_stride;
+    v.WS += (size_t)t * mb.ws_stride;
+    v.WE += (size_t)t * mb.we_stride;
+    v.PF += (size_t)t * mb.pf_stride;
+    v.FE += (size_t)t * mb.fe_stride;
+    v.WT += (size_t)t * mb.wt_stride;
+    v.WR += (size_t)t * mb.wt_stride;
+    v.Z += (size_t)t * mb.z_stride;
+    v.RP += (size_t)t * mb.rp_stride;
+    v.SC += (size_t)t * mb.sc_stride;
+    v.st += t;
+    return v;
+}
+
+// Model of candidate t of a split batch: its double-float factor as it is,
+// the last refinement correction applied (x += L^-T z, as a further step
+// would), then [a | w] with w = x_y - mu x_1 (k_split_model).
+int model_from_split(gp_ctx* ctx, gp_model* m, const LastChunk& lc, int t, const double* nll,
+                     const int* status) {
+    const gp::MixedBatch v = mixed_view(lc.mb, t);
+    cudaStream_t s = ctx->stream;
+    if (cudaMemcpyAsync(m->L, v.A, gp::packed_elems(m->n) * sizeof(float2), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemsetAsync(reinterpret_cast<char*>(v.st) + offsetof(gp::InstState, refine_done), 0, sizeof(int), s))
+        return fail(ctx, GP_ECUDA, "copy of the factor into the model failed");
+    const int sp = gp::subst_launches(v.nt);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, (ctx->opt.refine_iters > 0 ? sp : 0) + 1);
+    if ((ctx->opt.refine_iters > 0 && gp::launch_df_backward(v, 2, 0, s)) ||
+        gp::launch_split_model(v, reinterpret_cast<float2*>(m->Z), m->scalars, nll, status, m->status, s))
+        return fail(ctx, GP_ECUDA, "model launch failed");
+    return GP_OK;
 }
 
 }  // namespace
@@ -1248,83 +1406,100 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     if (!x || !y || !theta) return fail(ctx, GP_EINVAL, "null pointer argument");
     if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32 && prec != GP_AUTO)
         return fail(ctx, GP_EINVAL, "unknown precision %d", prec);
-    // The model is always factored in double: one factorisation per fit, and
-    // the kriging variance needs r'R^-1 r to full precision (the paper, too,
-    // refines the final fit with double-precision runs, Sections 4-5).
-    prec = GP_FP64;
+    if (prec == GP_AUTO) prec = GP_FP64;
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int nt = gp::num_tiles(n);
-    const int npad = nt * GP_NB;
-    const ModelSizes ms = model_sizes(n, d);
-    const size_t bL = ms.L, bZ = ms.Z, bx = ms.x, bth = ms.th, bsc = ms.sc, bstat = ms.stat;
-    const size_t total = ms.total;
-    if (total + ctx->models_bytes + ctx->ws_bytes > ctx->budget)
-        return fail(ctx, GP_ENOMEM, "model of %zu bytes exceeds the HBM budget", total);
-    gp_model* m = new gp_model();
-    m->ctx = ctx; m->n = n; m->d = d; m->nt = nt; m->p = p; m->delta = delta; m->prec = prec;
-    m->corr = ctx->opt.correlation;
-    cudaError_t e = cudaMallocAsync(&m->mem, total, ctx->stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete m;
-        return fail(ctx, GP_ENOMEM, "allocation of %zu bytes for the model failed", total);
+    gp_model* m = nullptr;
+    rc = model_alloc(ctx, n, d, p, delta, prec, &m);
+    if (rc) return rc;
+    const int npad = m->nt * GP_NB;
+    if (prec != GP_FP64) {
+        // the split factorisation of this one candidate in the workspace (its
+        // outputs straight into the model's scalars), then the model from it
+        LastChunk lc;
+        rc = mixed_nll_batch(ctx, n, d, x, y, 1, theta, p, delta, m->scalars + 0, m->scalars + 1,
+                             m->scalars + 2, m->scalars + 3, m->status, prec == GP_FP32 ? 3 : ctx->opt.slices,
+                             nullptr, &lc);
+        if (rc == GP_OK) rc = model_from_split(ctx, m, lc, 0, m->scalars + 0, m->status);
+        if (rc) return model_discard(ctx, m, rc);
+        return model_finish(ctx, m, x, theta, true, model);
     }
-    m->bytes = total;
-    char* c = (char*)m->mem;
-    m->L = (double*)c; c += bL;
-    m->Z = (double*)c; c += bZ;
-    m->x = (double*)c; c += bx;
-    m->theta = (double*)c; c += bth;
-    m->scalars = (double*)c; c += bsc;
-    m->status = (int*)c; c += bstat;
-    m->st = (gp::InstState*)c;
-    ctx->models_bytes += total;
-    auto bail = [&](int code) {
-        cudaFreeAsync(m->mem, ctx->stream);
-        cudaStreamSynchronize(ctx->stream);
-        ctx->models_bytes -= m->bytes;
-        delete m;
-        return code;
-    };
-    if (cudaMemcpyAsync(m->x, x, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) ||
-        cudaMemcpyAsync(m->theta, theta, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream))
-        return bail(fail(ctx, GP_ECUDA, "copy of x/theta into the model failed"));
+    // double: assembled and factored in the model's own storage
+    if (cudaMemcpyAsync(m->theta, theta, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream))
+        return model_discard(ctx, m, fail(ctx, GP_ECUDA, "copy of theta into the model failed"));
     gp::Batch b{};
-    b.n = n; b.d = d; b.nt = nt; b.count = 1; b.p = p; b.delta = delta; b.corr = m->corr;
-    b.x = m->x; b.y = y; b.theta = m->theta; b.A = m->L; b.inst_stride = bL / sizeof(double);
+    b.n = n; b.d = d; b.nt = m->nt; b.count = 1; b.p = p; b.delta = delta; b.corr = m->corr;
+    b.x = x; b.y = y; b.theta = m->theta; b.A = m->L; b.inst_stride = gp::packed_elems(n);
     b.st = m->st;
     {
         PhaseScope ps(ctx, GP_PHASE_ASSEMBLE, 2);
         if (gp::launch_validate_theta(b, ctx->stream) || gp::launch_assemble_tiles(b, ctx->stream))
-            return bail(fail(ctx, GP_ECUDA, "assembly launch failed"));
+            return model_discard(ctx, m, fail(ctx, GP_ECUDA, "assembly launch failed"));
     }
     rc = run_factor_f64(ctx, b);
-    if (rc) return bail(rc);
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, 4);
-    if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream))
-        return bail(fail(ctx, GP_ECUDA, "forward solve launch failed"));
-    if (gp::launch_finalize(b, m->Z, (size_t)2 * npad, m->scalars + 0, m->scalars + 1, m->scalars + 2,
-                            m->scalars + 3, m->status, ctx->stream) ||
-        gp::launch_fit_finish(b, m->Z, (size_t)2 * npad, m->scalars, ctx->stream) ||
-        gp::launch_backward_solve(b, m->Z, (size_t)2 * npad, 1, ctx->stream))
-        return bail(fail(ctx, GP_ECUDA, "solve launch failed"));
-    // the kriging kernel reads the factor, [a | w] and x as double-float pairs
-    if (gp::launch_to_df_inplace(m->L, gp::packed_elems(n), ctx->stream) ||
-        gp::launch_to_df_inplace(m->Z, (size_t)2 * npad, ctx->stream) ||
-        gp::launch_to_df_inplace(m->x, (size_t)n * d, ctx->stream))
-        return bail(fail(ctx, GP_ECUDA, "model conversion launch failed"));
-    int hstatus = 0;
-    e = cudaMemcpyAsync(&hstatus, m->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->host_scalars, m->scalars, 6 * sizeof(double), cudaMemcpyDeviceToHost,
-                            ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return bail(fail(ctx, GP_ECUDA, "fit: %s", cudaGetErrorString(e)));
-    if (hstatus == GP_ENOTPD || hstatus == GP_EINVAL)
-        return bail(fail(ctx, hstatus, "fit failed with status %d", hstatus));
-    ctx->models.push_back(m);
-    *model = m;
-    return hstatus;  // GP_OK or GP_EDEGENERATE (model still usable for the mean)
+    if (rc) return model_discard(ctx, m, rc);
+    {
+        PhaseScope ps(ctx, GP_PHASE_SOLVE, 4);
+        if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream) ||
+            gp::launch_finalize(b, m->Z, (size_t)2 * npad, m->scalars + 0, m->scalars + 1, m->scalars + 2,
+                                m->scalars + 3, m->status, ctx->stream) ||
+            gp::launch_fit_finish(b, m->Z, (size_t)2 * npad, m->scalars, ctx->stream) ||
+            gp::launch_backward_solve(b, m->Z, (size_t)2 * npad, 1, ctx->stream))
+            return model_discard(ctx, m, fail(ctx, GP_ECUDA, "solve launch failed"));
+    }
+    return model_finish(ctx, m, x, theta, false, model);
+}
+
+int gp_fit_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, int T, const double* theta,
+                 double p, double delta, int prec, double* nll, double* mu_hat, double* sigma2_hat,
+                 double* logdet, int* status, int* best_host, gp_model** model) {
+    if (!model || !best_host) return fail(ctx, GP_EINVAL, "null model or best pointer");
+    *model = nullptr;
+    *best_host = -1;
+    int rc = check_common(ctx, n, d, p, delta);
+    if (rc) return rc;
+    if (T < 1 || T > gp::kMaxCandidates) return fail(ctx, GP_EINVAL, "T = %d outside [1, 2^30]", T);
+    if (!x || !y || !theta || !nll || !mu_hat || !sigma2_hat || !status)
+        return fail(ctx, GP_EINVAL, "null pointer argument");
+    if (prec != GP_FP64 && prec != GP_MIXED && prec != GP_FP32)
+        return fail(ctx, prec == GP_AUTO ? GP_ENOTSUP : GP_EINVAL,
+                    "gp_fit_batch takes GP_FP64, GP_MIXED or GP_FP32 (precision %d)", prec);
+    GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    LastChunk lc;
+    if (prec == GP_FP64)
+        rc = fp64_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status, &lc);
+    else
+        rc = mixed_nll_batch(ctx, n, d, x, y, T, theta, p, delta, nll, mu_hat, sigma2_hat, logdet, status,
+                             prec == GP_FP32 ? 3 : ctx->opt.slices, nullptr, &lc);
+    if (rc) return rc;
+    std::vector<double> hn(T);
+    std::vector<int> hs(T);
+    GP_CUDA(ctx, cudaMemcpyAsync(hn.data(), nll, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaMemcpyAsync(hs.data(), status, (size_t)T * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int best = -1;
+    for (int t = 0; t < T; ++t)
+        if (hs[t] == GP_OK && (best < 0 || hn[t] < hn[best])) best = t;
+    if (best < 0) return fail(ctx, GP_ENOTPD, "no candidate gave a likelihood (status of the first: %d)", hs[0]);
+    *best_host = best;
+    const double* th = theta + (size_t)best * d;
+    if (best < lc.c0 || best >= lc.c0 + lc.cnt)   // its factor was overwritten by a later chunk
+        return gp_fit(ctx, n, d, x, y, th, p, delta, prec, model);
+    gp_model* m = nullptr;
+    rc = model_alloc(ctx, n, d, p, delta, prec, &m);
+    if (rc) return rc;
+    const int t = best - lc.c0;
+    if (prec == GP_FP64)
+        rc = model_from_fp64(ctx, m, lc, t, nll + best, mu_hat + best, sigma2_hat + best,
+                             logdet ? logdet + best : nullptr, status + best);
+    else
+        rc = model_from_split(ctx, m, lc, t, nll + best, status + best);
+    if (rc) return model_discard(ctx, m, rc);
+    if (prec == GP_FP64 && !logdet) {
+        // log|R| was not asked for: the instance record has it
+        const char* rec = reinterpret_cast<const char*>(lc.st + t) + offsetof(gp::InstState, logdet);
+        GP_CUDA(ctx, cudaMemcpyAsync(m->scalars + 3, rec, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return model_finish(ctx, m, x, th, prec != GP_FP64, model);
 }
 
 int gp_model_scalars(const gp_model* m, double* out) {

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <atomic>
+#include <mutex>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -147,20 +148,27 @@ constexpr int kRpTile = 2 * 2 * GP_NB + 2 * 2 * (GP_NB / 2);
 
 // A kernel's dynamic shared-memory limit is a per-device attribute: each
 // launcher keeps the largest size it has set on every device ordinal and
-// raises the limit once per device (and again when it needs more).
+// raises the limit once per device (and again when it needs more).  Threads
+// that launch the same kernel with different sizes (contexts on several
+// streams) take a lock around the check and the attribute call, so the
+// attribute only ever grows: without it, a thread setting a smaller size
+// after another set a larger one would leave the larger launches refused.
 constexpr int kMaxDevices = 64;
+inline std::mutex& smem_limit_mutex() {
+    static std::mutex m;
+    return m;
+}
 template <typename Kernel>
 inline cudaError_t raise_smem_limit(Kernel* kernel, size_t bytes, std::atomic<size_t> (&done)[kMaxDevices]) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < kMaxDevices && bytes <= done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    if (cached && bytes <= done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(smem_limit_mutex());
+    if (cached && bytes <= done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) {
-        size_t cur = done[dev].load(std::memory_order_relaxed);
-        while (cur < bytes && !done[dev].compare_exchange_weak(cur, bytes)) {
-        }
-    }
+    if (e == cudaSuccess && cached) done[dev].store(bytes, std::memory_order_release);
     return e;
 }
 
@@ -219,6 +227,8 @@ cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, dou
                                double* logdet, int* status, cudaStream_t s);
 cudaError_t launch_keep_forward(const MixedBatch& b, cudaStream_t s);
 cudaError_t launch_refine_check(const MixedBatch& b, int step, cudaStream_t s);
+cudaError_t launch_split_model(const MixedBatch& v, float2* Zm, double* scalars, const double* nll,
+                               const int* status, int* status_out, cudaStream_t s);
 cudaError_t launch_df_to_double(const float2* src, double* dst, size_t count, cudaStream_t s);
 
 }  // namespace gp

@@ -351,6 +351,18 @@ __global__ void k_assemble_dense(int n, int d, const double* __restrict__ x,
 
 }  // namespace
 
+// The double-float assembly for one (DB, COLS, family): its shared-memory
+// limit raised once per device and size (raise_smem_limit, safe when
+// contexts on several threads assemble at once), then the launch.
+template <int DB, int COLS, bool M>
+static cudaError_t launch_asm_df(dim3 grid, size_t smem, cudaStream_t s, const Batch& b, int group) {
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_assemble_tiles_df<DB, COLS, M>, smem, attr);
+    if (e != cudaSuccess) return e;
+    k_assemble_tiles_df<DB, COLS, M><<<grid, kThreads, smem, s>>>(b, group);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate_theta(const Batch& b, cudaStream_t s) {
     k_validate_theta<<<(b.count + 127) / 128, 128, 0, s>>>(b);
     return cudaGetLastError();
@@ -379,23 +391,18 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
         const int DB = b.d <= 4 ? 4 : (b.d <= 8 ? 8 : 16);
         const size_t smem = (size_t)(GP_NB + cols) * DB * sizeof(double) +
                             ((size_t)group * DB + kExpTab) * sizeof(dfl) + (size_t)group * sizeof(int);
-        cudaError_t e = cudaSuccess;
-        auto go = [&](auto kern) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) kern<<<grid, kThreads, smem, s>>>(b, group);
-        };
         const bool m = corr_is_matern(b.corr);
+        cudaError_t e;
         if (cols == 16) {
-            if (DB == 4) m ? go(k_assemble_tiles_df<4, 16, true>) : go(k_assemble_tiles_df<4, 16, false>);
-            else if (DB == 8) m ? go(k_assemble_tiles_df<8, 16, true>) : go(k_assemble_tiles_df<8, 16, false>);
-            else m ? go(k_assemble_tiles_df<16, 16, true>) : go(k_assemble_tiles_df<16, 16, false>);
+            if (DB == 4) e = m ? launch_asm_df<4, 16, true>(grid, smem, s, b, group) : launch_asm_df<4, 16, false>(grid, smem, s, b, group);
+            else if (DB == 8) e = m ? launch_asm_df<8, 16, true>(grid, smem, s, b, group) : launch_asm_df<8, 16, false>(grid, smem, s, b, group);
+            else e = m ? launch_asm_df<16, 16, true>(grid, smem, s, b, group) : launch_asm_df<16, 16, false>(grid, smem, s, b, group);
         } else {
-            if (DB == 4) m ? go(k_assemble_tiles_df<4, 32, true>) : go(k_assemble_tiles_df<4, 32, false>);
-            else if (DB == 8) m ? go(k_assemble_tiles_df<8, 32, true>) : go(k_assemble_tiles_df<8, 32, false>);
-            else m ? go(k_assemble_tiles_df<16, 32, true>) : go(k_assemble_tiles_df<16, 32, false>);
+            if (DB == 4) e = m ? launch_asm_df<4, 32, true>(grid, smem, s, b, group) : launch_asm_df<4, 32, false>(grid, smem, s, b, group);
+            else if (DB == 8) e = m ? launch_asm_df<8, 32, true>(grid, smem, s, b, group) : launch_asm_df<8, 32, false>(grid, smem, s, b, group);
+            else e = m ? launch_asm_df<16, 32, true>(grid, smem, s, b, group) : launch_asm_df<16, 32, false>(grid, smem, s, b, group);
         }
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
+        return e;
     }
     if (b.d <= 4)
         k_assemble_tiles<4><<<grid, kThreads, 0, s>>>(b, group);

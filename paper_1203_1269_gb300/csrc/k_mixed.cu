@@ -1029,6 +1029,34 @@ __global__ void k_df_finalize(MixedBatch b, double* nll, double* mu, double* sig
     status[t] = degenerate ? GP_EDEGENERATE : GP_OK;
 }
 
+// The kriging weights of one split-precision candidate (v: its one-candidate
+// view, the last correction already applied to x): [a | w] as the
+// double-float pairs the kriging kernel reads, a = L^-1 1 (column 8) and
+// w = x_y - mu x_1 = R^-1 (Y - 1 mu), and the fit's scalars [-2logL, mu,
+// sigma2, log|R|, Q, 1'R^-1 1].
+__global__ void k_split_model(MixedBatch v, float2* Zm, double* scalars, const double* nll, const int* status,
+                              int* status_out) {
+    const InstState st = v.st[0];
+    const int npad = v.nt * GP_NB;
+    const float2* x1 = zcol(v, 0, 0);
+    const float2* xy = zcol(v, 0, 1);
+    const float2* av = zcol(v, 0, 8);
+    const dfl md = df_from_double(st.mu);
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+        Zm[i] = av[i];
+        df_store(Zm + npad + i, df_fms(md, df_load(x1 + i), df_load(xy + i)));
+    }
+    if (threadIdx.x == 0) {
+        scalars[0] = *nll;
+        scalars[1] = st.mu;
+        scalars[2] = st.Q / v.n;
+        scalars[3] = st.logdet;
+        scalars[4] = st.Q;
+        scalars[5] = st.aa;
+        *status_out = *status;
+    }
+}
+
 // Convert the double-float factor and solve vectors of one fitted instance
 // into the double layout that the kriging kernel reads: L (tiles), a = L^-1 1
 // is not needed by the mixed fit, so column 0 of Zd gets x_1 = R^-1 1 and
@@ -1112,6 +1140,12 @@ cudaError_t launch_df_residual(const MixedBatch& b, cudaStream_t s) {
 cudaError_t launch_df_finalize(const MixedBatch& b, double* nll, double* mu, double* sigma2, double* logdet,
                                int* status, cudaStream_t s) {
     k_df_finalize<<<(b.count + 127) / 128, 128, 0, s>>>(b, nll, mu, sigma2, logdet, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_model(const MixedBatch& v, float2* Zm, double* scalars, const double* nll,
+                               const int* status, int* status_out, cudaStream_t s) {
+    k_split_model<<<1, 512, 0, s>>>(v, Zm, scalars, nll, status, status_out);
     return cudaGetLastError();
 }
 

@@ -106,6 +106,8 @@ def load(path=None):
                                          P, P, P, P, P]
     lib.gp_fit.argtypes = [P, _c_int, _c_int, P, P, P, _c_double, _c_double, _c_int,
                            ctypes.POINTER(P)]
+    lib.gp_fit_batch.argtypes = [P, _c_int, _c_int, P, P, _c_int, P, _c_double, _c_double, _c_int,
+                                 P, P, P, P, P, ctypes.POINTER(_c_int), ctypes.POINTER(P)]
     lib.gp_model_scalars.argtypes = [P, ctypes.POINTER(_c_double)]
     lib.gp_predict.argtypes = [P, P, _c_int, P, P, P]
     lib.gp_model_free.argtypes = [P]
@@ -534,6 +536,35 @@ class Context:
         if rc not in (GP_OK, GP_EDEGENERATE):
             self._check(rc)
         return Model(self, h, n, d)
+
+    def fit_batch(self, x, y, thetas, p, delta, prec="fp64", out=None):
+        """gp_fit_batch: -2logL at every row of thetas (T x d), then a fit at
+        the best candidate built from its own factor.  Returns (out, best,
+        model); model is None when no candidate gave a likelihood."""
+        x = _dev_f64(x, "x", device=self.device)
+        n, d = x.shape
+        y = _dev_f64(y, "y", (n,), self.device)
+        thetas = _dev_f64(thetas, "thetas", device=self.device)
+        if thetas.dim() != 2 or thetas.shape[1] != d:
+            raise ValueError("thetas must be T x d")
+        T = thetas.shape[0]
+        if out is None:
+            f = lambda: torch.empty(T, dtype=torch.float64, device=self.device)
+            out = dict(nll=f(), mu=f(), sigma2=f(), logdet=f(),
+                       status=torch.empty(T, dtype=torch.int32, device=self.device))
+        else:
+            _check_outs(out, ("nll", "mu", "sigma2", "status"), ("logdet",), T, self.device)
+        best = _c_int(-1)
+        h = _vp()
+        rc = self._lib.gp_fit_batch(self._h, n, d, _ptr(x), _ptr(y), T, _ptr(thetas), float(p), float(delta),
+                                    _prec(prec), _ptr(out["nll"]), _ptr(out["mu"]), _ptr(out["sigma2"]),
+                                    _ptr(out.get("logdet")), _ptr(out["status"]), ctypes.byref(best),
+                                    ctypes.byref(h))
+        if rc == GP_ENOTPD and best.value < 0:
+            return out, -1, None
+        if rc not in (GP_OK, GP_EDEGENERATE):
+            self._check(rc)
+        return out, best.value, Model(self, h, n, d)
 
     def predict(self, model, xs, want_var=True, yhat=None, s2=None):
         xs = _dev_f64(xs, "xs", device=self.device)

@@ -1,8 +1,11 @@
 """Continuous-batching request server over libgp.
 
-Requests are fits (the -2logL of a request's 32 theta candidates through
-gp_nll_batch, then gp_fit at the best one, whose factor stays resident on the
-device) and predictions (gp_predict against a resident fit).  Work runs on
+Requests are fits (the -2logL of a request's 32 theta candidates and the fit
+of the best one from its own factor, gp_fit_batch, whose factor then stays
+resident on the device) and predictions (gp_predict against a resident fit).
+Everything runs at the server's precision: with "mixed" the resident factors
+are the split-precision ones (kriging variances to about cond(R) 2^-40), with
+"fp64" double ones.  Work runs on
 `workers` CUDA streams at once, one libgp context per stream, so requests of
 different n and d overlap on the GPU.  A request is admitted as soon as a
 stream is free and its device memory fits the HBM budget next to what is
@@ -57,7 +60,7 @@ def predict_bytes(n, d, N):
 
 class Result:
     __slots__ = ("rid", "kind", "arrival", "start", "done", "theta", "nll", "mu", "sigma2",
-                 "best", "yhat", "s2", "status", "refit", "t_eval", "t_fit", "t_pred")
+                 "best", "yhat", "s2", "status", "error", "refit", "t_eval", "t_fit", "t_pred")
 
     def __init__(self, rid, kind):
         self.rid, self.kind = rid, kind
@@ -65,6 +68,7 @@ class Result:
         self.theta = self.nll = self.mu = self.sigma2 = self.best = None
         self.yhat = self.s2 = None
         self.status = None
+        self.error = None
         self.refit = False
         self.t_eval = self.t_fit = self.t_pred = 0.0
 
@@ -168,6 +172,7 @@ class Server:
                         self._predict(ctx, req, res)
             except gp.GPError as e:
                 res.status = e.code
+                res.error = str(e)
             res.done = time.perf_counter()
             with self.lock:
                 self.busy[i] = False
@@ -184,21 +189,18 @@ class Server:
     def _fit(self, ctx, req, res):
         x, y, th, _ = inputs.request_data(req, self.N_pred)
         xd, yd, thd = self._device(x), self._device(y), self._device(th)
+        # the candidates' -2logL and the fit of the best one, from its own
+        # factor (gp_fit_batch: no second factorisation)
         t0 = time.perf_counter()
-        out = ctx.nll_batch(xd, yd, thd, req.p, req.delta, self.prec)
-        nll = out["nll"].cpu().numpy()
+        out, best, model = ctx.fit_batch(xd, yd, thd, req.p, req.delta, self.prec)
         res.t_eval = time.perf_counter() - t0
+        res.nll = out["nll"].cpu().numpy()
         st = out["status"].cpu().numpy()
-        ok = np.where(st == 0)[0]
-        res.nll = nll
-        res.status = int(0 if ok.size else st[0])
-        if not ok.size:
+        if model is None:
+            res.status = int(st[0])
             return
-        best = int(ok[np.argmin(nll[ok])])
+        res.status = 0
         res.best, res.theta = best, th[best]
-        t0 = time.perf_counter()
-        model = ctx.fit(xd, yd, thd[best].contiguous(), req.p, req.delta, "fp64")
-        res.t_fit = time.perf_counter() - t0
         res.mu, res.sigma2 = model.mu, model.sigma2
         with self.lock:
             self._evict_for(model.bytes, keep=req.rid)
@@ -218,7 +220,9 @@ class Server:
         if entry is None:
             # released: refit at the chosen theta (same factor, same result)
             x, y, _, _ = inputs.request_data(src, self.N_pred)
-            model = ctx.fit(self._device(x), self._device(y), self._device(fit.theta), src.p, src.delta, "fp64")
+            t0 = time.perf_counter()
+            model = ctx.fit(self._device(x), self._device(y), self._device(fit.theta), src.p, src.delta, self.prec)
+            res.t_fit = time.perf_counter() - t0
             res.refit = True
             with self.lock:
                 self._evict_for(model.bytes, keep=req.target)
@@ -270,10 +274,12 @@ def summarize(results, requests):
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
             "refits": sum(r.refit for r in results.values()),
-            "busy_s": {"evals": sum(r.t_eval for r in results.values()),
-                       "final_fits": sum(r.t_fit for r in results.values()),
+            "busy_s": {"evals_and_fits": sum(r.t_eval for r in results.values()),
+                       "refits": sum(r.t_fit for r in results.values()),
                        "predicts": sum(r.t_pred for r in results.values())},
-            "failed": sum(1 for r in results.values() if r.status not in (0, None))}
+            "failed": sum(1 for r in results.values() if r.status not in (0, None)),
+            "errors": dict(collections.Counter(f"{r.kind}: {r.error or r.status}" for r in results.values()
+                                               if r.status not in (0, None)).most_common(5))}
 
 
 def main():
