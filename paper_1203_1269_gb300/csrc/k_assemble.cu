@@ -239,26 +239,32 @@ k_assemble_tiles_df(Batch b, int group) {
                 const dfl* tt = th + (size_t)(t - t0) * DB;
                 float sh = 0.f, sl = 0.f;
                 dfl qp = {1.f, 0.f};                // Matern: prod_k q(h_k)
+                // k >= d is uniform across the warp: leave the unrolled loop
+                // there rather than issue its predicated-off iterations; the
+                // first term enters S exactly (the TwoSum of 0 and it is exact)
 #pragma unroll
                 for (int k = 0; k < DB; ++k) {
-                    if (k < d) {
-                        const dfl a = tt[k];
-                        float ph = __fmul_rn(a.hi, D[k].hi);
-                        if (matern) {
-                            // h_k = a D_k itself is needed for q(h_k): its high
-                            // word enters the TwoSum, its low word sl
-                            const float pe = __fmaf_rn(a.hi, D[k].hi, -ph);
-                            const float pl = __fmaf_rn(a.hi, D[k].lo, __fmul_rn(a.lo, D[k].hi));
-                            dfl h;
-                            fast_two_sum(ph, __fadd_rn(pe, pl), h.hi, h.lo);
-                            qp = df_mul(qp, matern_q_df(h, b.corr, third));
-                            ph = h.hi;
-                            sl = __fadd_rn(sl, h.lo);
-                        } else {
-                            sl = __fadd_rn(sl, __fmaf_rn(a.hi, D[k].hi, -ph));
-                            sl = __fmaf_rn(a.hi, D[k].lo, sl);
-                            sl = __fmaf_rn(a.lo, D[k].hi, sl);
-                        }
+                    if (k >= d) break;
+                    const dfl a = tt[k];
+                    float ph = __fmul_rn(a.hi, D[k].hi);
+                    if (matern) {
+                        // h_k = a D_k itself is needed for q(h_k): its high
+                        // word enters the TwoSum, its low word sl
+                        const float pe = __fmaf_rn(a.hi, D[k].hi, -ph);
+                        const float pl = __fmaf_rn(a.hi, D[k].lo, __fmul_rn(a.lo, D[k].hi));
+                        dfl h;
+                        fast_two_sum(ph, __fadd_rn(pe, pl), h.hi, h.lo);
+                        qp = df_mul(qp, matern_q_df(h, b.corr, third));
+                        ph = h.hi;
+                        sl = __fadd_rn(sl, h.lo);
+                    } else {
+                        sl = __fadd_rn(sl, __fmaf_rn(a.hi, D[k].hi, -ph));
+                        sl = __fmaf_rn(a.hi, D[k].lo, sl);
+                        sl = __fmaf_rn(a.lo, D[k].hi, sl);
+                    }
+                    if (k == 0) {
+                        sh = ph;
+                    } else {
                         float s2, e2;
                         two_sum(sh, ph, s2, e2);
                         sh = s2;
