@@ -91,11 +91,17 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kDiagThreads / 32;
-    // pivot c: 1 / sqrt(a) from a float seed (about 22 correct bits) and two
-    // Newton steps in double-float, y <- y + y (1 - a y^2) / 2 (44, then
-    // about 48 bits), L_cc = a y; all on the FP32 pipes, since this chain is
-    // the sweep's critical path.  Pivots outside [2^-100, 2^100] (the float
-    // seed's comfortable range) take the double route.
+    // pivot c: 1 / sqrt(a) from rsqrtf's seed (about 22 correct bits), one
+    // float Newton step to y1 (about 24 bits), then y = y1 (1 + e/2 + 3 e^2/8)
+    // with e = 1 - a y1^2: Newton's step with its second-order term, the next
+    // term (5 e^3 / 16) being below 2^-65.  e is about 2^-23 and needed to
+    // float precision only, so it comes from the exact products a.hi y1 and
+    // (a.hi y1) y1 (1 - q_h is exact, q_h lying within 2^-22 of 1), and y is
+    // the exact sum y1 + corr: about 2^-46 relative, as two double-float
+    // Newton steps give, in a quarter of their dependent chain, which matters
+    // since the pivot is the sweep's critical path.  Pivots outside
+    // [2^-100, 2^100] (the float seed's comfortable range) take the double
+    // route.
     auto take_pivot = [&](int c, dfl a) {
         dfl y, l;
         if (!(a.hi > 0.f) || !isfinite(a.hi)) {
@@ -104,12 +110,17 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             l = y;
         } else if (a.hi > 7.9e-31f && a.hi < 1.26e30f) {
             const float y0 = rsqrtf(a.hi);
-            y = dfl{y0, 0.f};
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const dfl e = df_sub(dfl{1.f, 0.f}, df_mul(df_mul(a, y), y));
-                y = df_fma(df_mul(dfl{0.5f, 0.f}, y), e, y);
-            }
+            const float p0 = __fmul_rn(a.hi, y0);
+            const float y1 = __fmaf_rn(__fmul_rn(y0, 0.5f), __fmaf_rn(-p0, y0, 1.f), y0);
+            const float ph = __fmul_rn(a.hi, y1);
+            const float pl = __fmaf_rn(a.hi, y1, -ph);
+            const float qh = __fmul_rn(ph, y1);
+            const float ql = __fmaf_rn(pl, y1, __fmaf_rn(ph, y1, -qh));
+            const float rl = __fmul_rn(__fmul_rn(a.lo, y1), y1);
+            const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.f, qh), ql), rl);
+            const float h = __fmul_rn(y1, 0.5f);
+            const float corr = __fmaf_rn(h, e, __fmul_rn(__fmul_rn(h, __fmul_rn(e, e)), 0.75f));
+            fast_two_sum(y1, corr, y.hi, y.lo);
             l = df_mul(a, y);
         } else {
             const double piv = df_to_double(a);
