@@ -125,11 +125,13 @@ typedef struct {
     int update_groups;    /* GP_MIXED: fp32 accumulators of the trailing update: 3 or 4
                              (128-wide tiles, the last group rounded) or 7 (64-wide
                              tiles, every group exact) */
-    int inject_timeout;   /* test hook, default 0: when 1, the first CTA of the first
+    int inject_timeout;   /* test hook, default 0, bits: 1 = the first CTA of the first
                              trailing-update launch of each GP_MIXED batch waits 5 ms on
                              a barrier nothing signals, gives up, and the instances it
-                             would have updated come back GP_ETIMEOUT (the bounded-wait
-                             failure path, exercised without faulting the GPU) */
+                             would have updated come back GP_ETIMEOUT; 2 = the first CTA
+                             of each tensor-core variance pass of gp_predict does the
+                             same and its points' s2 come back NaN (the bounded-wait
+                             failure paths, exercised without faulting the GPU) */
     int fuse_panels;      /* GP_MIXED, default 1: panels are factored in pairs with a
                              one-panel look-ahead and both applied to the trailing tiles
                              in one 256-wide pass (half the passes over the trailing
@@ -145,6 +147,12 @@ typedef struct {
     int correlation;      /* gp_correlation of every call that builds R or r, default
                              GP_CORR_POWEXP; a fit keeps the family it was made with,
                              and its predictions use that one */
+    int predict_tc;       /* gp_predict, default 1: v = L^-1 r for the variances as a
+                             block forward substitution of split bf16 GEMMs on the tensor
+                             cores (5 slices in the updates, 7 in the diagonal steps,
+                             double-float accumulation; variance error ~1e-10 sigma2_hat
+                             where cond(R) <= 5e8); 0: the substitution in double-float
+                             on the FP32 pipes.  Means are r'w in double-float either way */
 } gp_options;
 
 void gp_default_options(gp_options* opt);
@@ -418,6 +426,11 @@ int gp_model_scalars(const gp_model* model, double* out_host);
  *   s2[m]   = sigma2_hat [c0 - r'R^-1 r + (1 - 1'R^-1 r)^2 / (1'R^-1 1)]
  * with r_i = corr(z(x*_m), z(x_i)) by eq. (2), c0 = 1 + delta (or 1 when
  * the context's nugget_in_var is 0).  s2 may be NULL (mean only).
+ * With predict_tc (the default) the call first cuts the model's factor into
+ * bf16 slices in its workspace (gp_call_bytes counts them) and then forms
+ * v = L^-1 r 128 points at a time on the tensor cores; yhat has the same
+ * bits with or without s2.  A variance pass that gives up on a bounded wait
+ * leaves NaN in the s2 of the points it had not finished.
  * 0 <= N <= 2^30 per call (GP_EINVAL beyond: split larger sets).
  * Asynchronous; the model must outlive the enqueued work. */
 int gp_predict(gp_ctx* ctx, const gp_model* model, int N, const double* xstar,

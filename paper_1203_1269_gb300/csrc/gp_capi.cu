@@ -255,7 +255,7 @@ gp::MixedBatch mixed_layout(gp_ctx* ctx, int n, int cnt, const double* y, char* 
     mb.n = n; mb.nt = gp::num_tiles(n); mb.count = cnt; mb.s = slices;
     mb.ps = GP_PANEL_SLICES;
     mb.ug = ctx->opt.update_groups;
-    mb.inject_timeout = ctx->opt.inject_timeout;
+    mb.inject_timeout = ctx->opt.inject_timeout & 1;
     mb.update_tile = ctx->opt.update_tile;
     mb.sp = mb.s > mb.ps ? mb.s : mb.ps;
     mb.inst_stride = z.A / sizeof(float2);
@@ -691,6 +691,34 @@ PredictShape predict_shape(int nt, int N, int sms, size_t avail, bool variances)
     return s;
 }
 
+// Workspace of gp_predict on the tensor-core path (predict_tc): with
+// variances the slice tables of the model, then an error flag, the r
+// values (with variances) and partial means of a chunk of 128-point
+// blocks, and per CTA of the tensor-core pass the slices of V and of C_J.
+// A chunk is one wave of that pass (one block per SM; four waves' partial
+// means without variances), fewer blocks when the budget is short.
+struct VarPlan {
+    int blocks, chunk, grid;
+    size_t tables, per_block, bytes;
+};
+
+VarPlan var_plan(int nt, int N, int sms, size_t avail, bool variances) {
+    VarPlan v;
+    v.blocks = (N + GP_NB - 1) / GP_NB;
+    v.tables = variances ? align256(gp::var_table_bytes(nt)) : 0;
+    v.per_block = (variances ? gp::var_rx_bytes(nt) : 0) + gp::var_mp_bytes(nt);
+    const size_t per_cta = variances ? gp::var_cta_bytes(nt) : 0;
+    auto total = [&](int c) {
+        return v.tables + 256 + (size_t)c * v.per_block + (size_t)(c < sms ? c : sms) * per_cta;
+    };
+    const int cap = variances ? sms : 4 * sms;
+    v.chunk = v.blocks < cap ? v.blocks : cap;
+    while (v.chunk > 1 && total(v.chunk) > avail) v.chunk -= (v.chunk / 4 > 1 ? v.chunk / 4 : 1);
+    v.grid = v.chunk < sms ? v.chunk : sms;
+    v.bytes = total(v.chunk);
+    return v;
+}
+
 // A model's device memory (one allocation, ModelSizes), counted against the
 // context's budget next to its workspace.
 int model_alloc(gp_ctx* ctx, int n, int d, double p, double delta, int prec, gp_model** out) {
@@ -846,6 +874,66 @@ cudaStream_t ctx_stream(const gp_ctx* ctx) { return ctx->stream; }
 
 }  // namespace gp
 
+namespace {
+
+// gp_predict on the tensor-core path: the tables of the model (with
+// variances), then per chunk of point blocks r and the partial means, yhat,
+// and the tensor-core pass for s2 (k_var_tc.cu).
+int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, double* yhat, double* s2) {
+    const bool var = s2 != nullptr;
+    const int nt = m->nt, npad = nt * GP_NB;
+    const size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
+    const VarPlan v = var_plan(nt, N, ctx->sms, avail, var);
+    int rc = ensure_ws(ctx, v.bytes);
+    if (rc) return rc;
+    char* c = static_cast<char*>(ctx->ws);
+    gp::VarCall call{};
+    if (var) call.t = gp::var_tables_at(c, nt);
+    c += v.tables;
+    call.err = reinterpret_cast<int*>(c);
+    c += 256;
+    call.RX = reinterpret_cast<float2*>(c);
+    if (var) c += (size_t)v.chunk * gp::var_rx_bytes(nt);
+    call.MP = reinterpret_cast<float2*>(c);
+    c += (size_t)v.chunk * gp::var_mp_bytes(nt);
+    call.VS = reinterpret_cast<__nv_bfloat16*>(c);
+    if (var) c += (size_t)v.grid * gp::var_vs_bytes(nt);
+    call.CS = reinterpret_cast<__nv_bfloat16*>(c);
+    call.n = m->n; call.d = m->d; call.nt = nt; call.N = N; call.corr = m->corr;
+    call.p = m->p;
+    call.c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
+    // |v_i|^2 <= v'v <= 1 + delta: the V slices' exponent E with
+    // sqrt(1 + delta) < 2^E
+    int ev = 0;
+    std::frexp(std::sqrt(1.0 + m->delta) * (1.0 + 0x1p-20), &ev);
+    call.ev = ev;
+    call.grid = v.grid;
+    call.inject_timeout = (ctx->opt.inject_timeout & 2) != 0;
+    const float2* Zdf = reinterpret_cast<const float2*>(m->Z);
+    call.x = reinterpret_cast<const float2*>(m->x);
+    call.theta = m->theta; call.w = Zdf + npad; call.a = Zdf; call.sc = m->scalars;
+    call.xs = xstar; call.yhat = yhat; call.s2 = s2;
+    PhaseScope ps(ctx, GP_PHASE_PREDICT, 0);
+    int k = 0;
+    if (var) {
+        const cudaError_t e = gp::launch_var_tables(reinterpret_cast<const float2*>(m->L), nt, call.t, ctx->stream, &k);
+        ps.kernels += k;
+        GP_CUDA(ctx, e);
+    }
+    for (int b0 = 0; b0 < v.blocks; b0 += v.chunk) {
+        const int nb = v.blocks - b0 < v.chunk ? v.blocks - b0 : v.chunk;
+        const cudaError_t e = gp::launch_var_chunk(call, b0 * GP_NB, nb, ctx->stream, &k);
+        ps.kernels += k;
+        if (e == cudaErrorNotSupported)
+            return fail(ctx, GP_ENOTSUP, "the tensor-core variance kernel was built with too few registers "
+                                         "for its register split: set predict_tc = 0");
+        GP_CUDA(ctx, e);
+    }
+    return GP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gp_default_options(gp_options* opt) {
@@ -862,6 +950,7 @@ void gp_default_options(gp_options* opt) {
     opt->update_tile = 128;
     opt->assemble_cols = 16;
     opt->correlation = GP_CORR_POWEXP;
+    opt->predict_tc = 1;
 }
 
 int gp_create(gp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
@@ -947,6 +1036,9 @@ int gp_set_options(gp_ctx* ctx, const gp_options* opt) {
         return fail(ctx, GP_EINVAL, "assemble_cols must be 16 or 32");
     if (opt->correlation < GP_CORR_POWEXP || opt->correlation > GP_CORR_MATERN52)
         return fail(ctx, GP_EINVAL, "correlation = %d is not a gp_correlation", opt->correlation);
+    if (opt->predict_tc != 0 && opt->predict_tc != 1) return fail(ctx, GP_EINVAL, "predict_tc must be 0 or 1");
+    if (opt->inject_timeout < 0 || opt->inject_timeout > 3)
+        return fail(ctx, GP_EINVAL, "inject_timeout = %d outside [0, 3]", opt->inject_timeout);
     ctx->opt = *opt;
     return GP_OK;
 }
@@ -1515,6 +1607,7 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, doubl
     if (N == 0) return GP_OK;
     if (!xstar || !yhat) return fail(ctx, GP_EINVAL, "null pointer argument");
     GP_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (ctx->opt.predict_tc) return predict_tensor(ctx, m, N, xstar, yhat, s2);
     const int npad = m->nt * GP_NB;
     const size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
     const PredictShape sh = predict_shape(m->nt, N, ctx->sms, avail, s2 != nullptr);
@@ -1617,6 +1710,7 @@ int gp_call_bytes(gp_ctx* ctx, int call, int n, int d, int count, int prec, size
         if (count < 0 || count > kMaxPredictPoints)
             return fail(ctx, GP_EINVAL, "N = %d outside [0, 2^30] test points per call", count);
         if (count == 0) return GP_OK;
+        if (opt.predict_tc) return grow(var_plan(gp::num_tiles(n), count, sms, avail, true).bytes);
         return grow(predict_shape(gp::num_tiles(n), count, sms, avail, true).bytes);
     default:
         return fail(ctx, GP_EINVAL, "unknown call %d", call);

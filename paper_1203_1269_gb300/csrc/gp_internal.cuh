@@ -196,6 +196,43 @@ cudaError_t launch_fit_finish(const Batch& b, double* Z, size_t z_stride, double
                               cudaStream_t s);
 cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t z_stride, int col,
                                   cudaStream_t s);
+// Kriging with the variance's solve on the tensor cores (k_var_tc.cu).
+struct VarTables {
+    __nv_bfloat16* LS;            // slices of the rows of L left of the diagonal blocks
+    __nv_bfloat16* WS;            // slices of the rows of W_J = L_JJ^-1
+    int* LE;                      // npad row exponents of LS
+    int* WE;                      // npad row exponents of WS
+    int* lbits;                   // npad scratch: row maxima as float bits
+};
+struct VarCall {
+    int n, d, nt, N, corr;
+    double p, c0;
+    int ev;                       // fixed exponent of the slices of v = L^-1 r
+    int grid;                     // CTAs of the tensor-core pass
+    int inject_timeout;
+    const float2* x;              // n x d design points (double-float)
+    const double* theta;
+    const float2* w;              // npad: R^-1 (Y - 1 mu_hat)
+    const float2* a;              // npad: L^-1 1
+    const double* sc;             // model scalars
+    const double* xs;             // N x d
+    double* yhat;
+    double* s2;                   // null: means only
+    VarTables t;
+    float2* RX;                   // chunk x npad x 128 values of r
+    float2* MP;                   // chunk x nt x 128 partial r'w
+    __nv_bfloat16* VS;            // grid x var_cta_bytes: slices of V, then of C_J
+    __nv_bfloat16* CS;
+    int* err;
+};
+size_t var_table_bytes(int nt);
+size_t var_rx_bytes(int nt);      // per point block
+size_t var_mp_bytes(int nt);      // per point block
+size_t var_vs_bytes(int nt);      // per CTA: the slices of V
+size_t var_cta_bytes(int nt);     // per CTA of the tensor-core pass: V's and C_J's slices
+VarTables var_tables_at(void* base, int nt);
+cudaError_t launch_var_tables(const float2* L, int nt, const VarTables& t, cudaStream_t s, int* kernels);
+cudaError_t launch_var_chunk(const VarCall& c, int m0, int npb, cudaStream_t s, int* kernels);
 cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
                            const double* xs, double* yhat, double* s2, float2* work, int chunk, int nr,

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
     _fields_ = [("slices", _c_int), ("panel_slices", _c_int), ("refine_iters", _c_int),
                 ("nugget_in_var", _c_int), ("max_batch", _c_int), ("update_groups", _c_int),
                 ("inject_timeout", _c_int), ("fuse_panels", _c_int), ("auto_tol", _c_double),
-                ("update_tile", _c_int), ("assemble_cols", _c_int), ("correlation", _c_int)]
+                ("update_tile", _c_int), ("assemble_cols", _c_int), ("correlation", _c_int),
+                ("predict_tc", _c_int)]
 
 
 class TuneTrial(ctypes.Structure):
