@@ -19,9 +19,9 @@
 //     0, 1, 2 exact and >= 3 rounded, weight <= 2^-24).  V has one fixed
 //     exponent: |v_i| <= ||v|| and v'v = r'R^-1 r <= c0 = 1 + delta, since
 //     [R r; r' 1 + delta] is a correlation matrix plus delta I.  A group
-//     sum stays exact in fp32 (below 2^24 in units of its weight) for K <=
-//     256 (3 pairs x 2^14 x 256), so the accumulators are drained into
-//     double-float registers every 256 columns of K;
+//     sum stays exact in fp32 (below 2^24 in units of its weight) for K <
+//     341 (3 pairs x 2^14 x K), so the accumulators are drained into
+//     double-float registers every 320 columns of K;
 //   - the diagonal step with 7 slices and every group exact (its error
 //     scales with |C| |W|, which exceeds |V_J| when L_JJ is ill-conditioned),
 //     in two 64-column halves (7 groups x 64 of the 512 tensor-memory
@@ -56,6 +56,10 @@ namespace {
 constexpr int kVarSlices = 5;                        // update operands
 constexpr int kVarWSlices = GP_PANEL_SLICES;         // diagonal step operands (7)
 constexpr uint32_t kHalfBytes = kChunkBytes / 2;     // 64 rows of a 128 x 32 chunk
+// K chunks (of 32) between drains of the update's accumulators: the group of
+// a + b = 2 (three slice pairs, |q_a q_b| <= 2^14) stays below 2^24 for 320
+constexpr int kDrainChunks = 10;
+static_assert(3 * 16384 * 32 * kDrainChunks < (1 << 24), "exact accumulator groups");
 
 // Layouts (bf16 images of 128 x 32 chunks, as the factorisation's slices):
 //   LS: row block J >= 1: [slice a][chunk k < 4J], first chunk 10 J (J - 1)
@@ -371,11 +375,13 @@ __global__ void __launch_bounds__(kVarThreads, 1) k_var_tc(VarArgs g) {
             dfl vv = {0.f, 0.f}, av = {0.f, 0.f};
             const float2* rx = g.RX + (size_t)pb * nt * GP_NB * GP_NB + row;
             for (int J = 0; ok && J < nt; ++J) {
-                // update: S = sum over the drained K blocks of V_K L_JK^T
+                // update: S = sum over the drained K blocks of V_K L_JK^T, kept
+                // unscaled (the scale 2^(ev + E_L - 14) of a column is a power
+                // of two, the same in every drain: applied once at the end)
                 float2 c[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) c[j] = make_float2(0.f, 0.f);
-                for (int k0 = 0; k0 < 4 * J; k0 += 8) {
+                for (int k0 = 0; k0 < 4 * J; k0 += kDrainChunks) {
                     if (!mbar_wait(&tfull_bar, use & 1, &abort_flag)) {
                         ok = false;
                         break;
@@ -389,18 +395,17 @@ __global__ void __launch_bounds__(kVarThreads, 1) k_var_tc(VarArgs g) {
                         tmem_wait_ld();
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            // groups 0 .. 2 exact, group 3 (weight <= 2^-24) rounded
-                            float h, l, s2, e2;
+                            // groups 0 .. 2 exact, group 3 (weight <= 2^-24)
+                            // rounded, straight into the running double-float
+                            // sum, renormalised once per drain
+                            float h, l, e2, s, t;
                             two_sum(d[0][j], d[1][j], h, l);
-                            two_sum(h, d[2][j], s2, e2);
-                            h = s2;
+                            two_sum(h, d[2][j], h, e2);
                             l = __fadd_rn(__fadd_rn(l, e2), d[3][j]);
-                            two_sum(h, l, h, l);
-                            const int e = g.ev + __ldg(g.LE + J * GP_NB + 32 * part + 4 * cb + j) - 14;
-                            const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
-                            const dfl t = df_add(dfl{c[4 * cb + j].x, c[4 * cb + j].y},
-                                                 dfl{__fmul_rn(h, sc), __fmul_rn(l, sc)});
-                            c[4 * cb + j] = make_float2(t.hi, t.lo);
+                            two_sum(c[4 * cb + j].x, h, s, t);
+                            t = __fadd_rn(c[4 * cb + j].y, __fadd_rn(t, l));
+                            two_sum(s, t, s, t);
+                            c[4 * cb + j] = make_float2(s, t);
                         }
                     }
                     tc_fence_before();
@@ -413,7 +418,12 @@ __global__ void __launch_bounds__(kVarThreads, 1) k_var_tc(VarArgs g) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float2 rv = rx[(size_t)(J * GP_NB + 32 * part + j) * GP_NB];
-                    const dfl t = df_sub(dfl{rv.x, rv.y}, dfl{c[j].x, c[j].y});
+                    float sc = 0.f;
+                    if (J > 0) {
+                        const int e = g.ev + __ldg(g.LE + J * GP_NB + 32 * part + j) - 14;
+                        sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
+                    }
+                    const dfl t = df_sub(dfl{rv.x, rv.y}, dfl{__fmul_rn(c[j].x, sc), __fmul_rn(c[j].y, sc)});
                     c[j] = make_float2(t.hi, t.lo);
                     mx = fmaxf(mx, fabsf(t.hi));
                 }
@@ -591,9 +601,9 @@ __global__ void __launch_bounds__(kVarThreads, 1) k_var_tc(VarArgs g) {
             };
             for (int pb = blockIdx.x; ok && pb < g.npb; pb += gridDim.x) {
                 for (int J = 0; ok && J < nt; ++J) {
-                    for (int k0 = 0; ok && k0 < 4 * J; k0 += 8) {
+                    for (int k0 = 0; ok && k0 < 4 * J; k0 += kDrainChunks) {
                         if (!(ok = tmem_free())) break;
-                        const int k1 = (k0 + 8 < 4 * J) ? k0 + 8 : 4 * J;
+                        const int k1 = (k0 + kDrainChunks < 4 * J) ? k0 + kDrainChunks : 4 * J;
                         for (int k = k0; k < k1; ++k) {
                             uint32_t sa;
                             if (!(ok = take(sa))) break;
