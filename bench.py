@@ -52,6 +52,18 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def variance_flops(n, N, nb=NB):
+    """The kriging variance's solve v = L^-1 r for N points: n^2 / 2
+    multiply-adds per point (the method's work, 2 flops each), and the split
+    GEMMs the tensor-core pass executes for it (per 128-point block and tile
+    row J: the update, 15 slice products x 2 x 128^2 x 128 J, and the
+    diagonal step, 28 products x 2 x 128^3)."""
+    nt = -(-n // nb)
+    blocks = -(-N // nb)
+    executed = blocks * (15 * 2 * nb ** 3 * nt * (nt - 1) // 2 + 28 * 2 * nb ** 3 * nt)
+    return float(n) * n * N, float(executed)
+
+
 def update_flops(n, nb=NB):
     """Algorithmic flops of the trailing updates of one Cholesky (real rows
     only): sum over block steps of nb * m (m + 1), m = rows below the panel."""
@@ -480,8 +492,27 @@ def run_gp(args):
         ctx.predict(model, xs)
         p2.record(stream)
         torch.cuda.synchronize()
+        t_mean, t_var = p0.elapsed_time(p1) / 1e3, p1.elapsed_time(p2) / 1e3
+        method, executed = variance_flops(w.n, int(xs.shape[0]))
+        pk, _ = peaks()
+        t_tc = t_var - t_mean   # the tables and the tensor-core pass (r is formed by both calls)
+        # the double-float substitution on the FP32 pipes, on the first 1e4 points
+        ctx.set_options(predict_tc=0)
+        q0 = torch.cuda.Event(enable_timing=True); q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        ctx.predict(model, xs[:10000])
+        q1.record(stream)
+        torch.cuda.synchronize()
+        ctx.set_options(predict_tc=1)
         kriging = {"N": int(xs.shape[0]), "candidate": best, "fit_s": t_fit,
-                   "mean_only_s": p0.elapsed_time(p1) / 1e3, "mean_and_variance_s": p1.elapsed_time(p2) / 1e3}
+                   "mean_only_s": t_mean, "mean_and_variance_s": t_var,
+                   "variance_solve": {"tensor_core_pass_s": t_tc,
+                                      "method_tflops": method / t_tc / 1e12,
+                                      "executed_split_tflops": executed / t_tc / 1e12,
+                                      "executed_frac_of_sustained_bf16": executed / t_tc / 1e12 / pk["bf16_tflops_sustained"],
+                                      "flops_counted": "method: n^2 N (v = L^-1 r); executed: the split GEMMs "
+                                                       "(15 products in the updates, 28 in the diagonal steps)"},
+                   "fp32_pipes_mean_and_variance_1e4_points_s": q0.elapsed_time(q1) / 1e3}
         model.free()
 
     cpu = None

@@ -25,7 +25,7 @@
 // tile-parallel, with the sums of eq. 3 taken from forward-only identities
 // (k_refine_check) and a per-candidate stopping rule; then the profile
 // likelihood.
-#include "mixed_common.cuh"
+#include "slices.cuh"
 
 namespace gp {
 

@@ -47,11 +47,21 @@
 // All of it is rebuilt per call from the model (the tables take about 1 ms
 // at n = 16384), so a model holds only its factor.
 #include "corr.cuh"
-#include "mixed_common.cuh"
+#include "slices.cuh"
 
 namespace gp {
 
 namespace {
+
+// 32 lanes x 32 bits x 4 columns of tensor memory
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 constexpr int kVarSlices = 5;                        // update operands
 constexpr int kVarWSlices = GP_PANEL_SLICES;         // diagonal step operands (7)

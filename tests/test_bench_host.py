@@ -111,3 +111,18 @@ def test_bench_help_runs_without_a_gpu():
     r = subprocess.run([sys.executable, bench.os.path.join(bench.ROOT, "bench.py"), "--help"],
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and "--impl" in r.stdout
+
+
+def test_variance_flops_counts_every_block_and_tile_row():
+    """The variance solve's flop counts against an explicit sum: per point
+    block and tile row J the update is 15 products of 128 x 128 x 128 J, the
+    diagonal step 28 products of 128 x 128 x 128; the method's n^2 N."""
+    import bench
+    for n, N in ((1, 1), (128, 128), (300, 129), (4000, 1000)):
+        nt, blocks = -(-n // 128), -(-N // 128)
+        want = 0
+        for _ in range(blocks):
+            for J in range(nt):
+                want += 15 * 2 * 128 * 128 * (128 * J) + 28 * 2 * 128 ** 3
+        method, executed = bench.variance_flops(n, N)
+        assert executed == want and method == float(n) * n * N
