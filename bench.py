@@ -553,6 +553,54 @@ def run_gp(args):
     return 0
 
 
+def run_kriging(args):
+    """Kriging alone: the large instance's design (random Latin hypercube,
+    d = 10, p = 1.9, delta = 1e-6) at n = --n (16384 unless given), its first
+    candidate fitted in FP64, then gp_predict at --points uniform test points:
+    means only, means and variances (the variance's solve on the tensor
+    cores), each timed with CUDA events after --warmup calls."""
+    import torch
+    from paper_1203_1269_gb300 import gp
+    n = args.n if args.n != 4000 else 16384
+    w = inputs.large_instance(n=n, T=1, N=args.points)
+    ctx = gp.Context(0)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    model = ctx.fit(dev(w.x), dev(w.y), dev(w.thetas[0]), w.p, w.delta, "fp64")
+    xs = dev(w.xs)
+    stream = torch.cuda.current_stream()
+
+    def timed(want_var):
+        for _ in range(args.warmup):
+            ctx.predict(model, xs, want_var=want_var)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = ctx.predict(model, xs, want_var=want_var)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / args.steps, out
+
+    t_mean, _ = timed(False)
+    t_var, (_, s2) = timed(True)
+    method, executed = variance_flops(n, args.points)
+    pk, _ = peaks()
+    t_tc = t_var - t_mean
+    print(json.dumps({"metric": f"kriging points/s (mean and variance) at n={n}, d={w.d}",
+                      "value": args.points / t_var, "unit": "points/s", "higher_is_better": True,
+                      "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+                      "config": {"workload": f"kriging n={n} d={w.d} N={args.points}", "p": w.p, "delta": w.delta},
+                      "mean_only_s": t_mean, "mean_and_variance_s": t_var,
+                      "variance_nan": int(torch.isnan(s2).sum()),
+                      "variance_solve": {"tensor_core_pass_s": t_tc, "method_tflops": method / t_tc / 1e12,
+                                         "executed_split_tflops": executed / t_tc / 1e12,
+                                         "executed_frac_of_sustained_bf16":
+                                             executed / t_tc / 1e12 / pk["bf16_tflops_sustained"]}}))
+    model.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,11 +618,17 @@ def main():
     ap.add_argument("--workload", default="hartman", choices=WORKLOADS,
                     help="hartman: the benchmark (n = 4000, d = 6, T = 256); batched: n = 2048, "
                          "d = 8, T = 1024; large: n = 16384, d = 10, T = 32 with kriging at 1e5 points")
+    ap.add_argument("--kriging-only", action="store_true",
+                    help="fit one candidate of the large instance at --n (default 16384) design points "
+                         "and time gp_predict at --points test points; one JSON line")
+    ap.add_argument("--points", type=int, default=100000, help="test points of --kriging-only")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.kriging_only:
+        return run_kriging(args)
     return run_gp(args)
 
 

@@ -70,6 +70,12 @@ constexpr uint32_t kHalfBytes = kChunkBytes / 2;     // 64 rows of a 128 x 32 ch
 // a + b = 2 (three slice pairs, |q_a q_b| <= 2^14) stays below 2^24 for 320
 constexpr int kDrainChunks = 10;
 static_assert(3 * 16384 * 32 * kDrainChunks < (1 << 24), "exact accumulator groups");
+// The update's stages ahead of the ring whose operands the copy thread
+// prefetches into L2: a stage's V slices come from HBM (each CTA streams its
+// own block's V) and a two-slot ring of 80 KB stages alone leaves the
+// tensor pipe waiting on that latency
+constexpr int kPrefetch = 2;
+static_assert(kPrefetch <= 4, "a prefetch reaches at most into the next tile row's first 4 chunks");
 
 // Layouts (bf16 images of 128 x 32 chunks, as the factorisation's slices):
 //   LS: row block J >= 1: [slice a][chunk k < 4J], first chunk 10 J (J - 1)
@@ -567,6 +573,21 @@ __global__ void __launch_bounds__(kVarThreads, 1) k_var_tc(VarArgs g) {
                                 break;
                             }
                             ++vn;
+                        }
+                        {
+                            // L2 prefetch of chunk k + kPrefetch, or of the next
+                            // tile row's first chunks (a hint: L2 stays coherent
+                            // with the epilogue's later writes of V)
+                            int kp = k + kPrefetch, Jp = J;
+                            if (kp >= 4 * J) {
+                                kp -= 4 * J;
+                                Jp = J + 1;
+                            }
+                            if (Jp < nt)
+                                for (int a = 0; a < kVarSlices; ++a) {
+                                    prefetch_l2(VSb + ((size_t)a * 4 * nt + kp) * kChunkBytes, kChunkBytes);
+                                    prefetch_l2(LSb + ls_chunk(Jp, a, kp) * kChunkBytes, kChunkBytes);
+                                }
                         }
                         ok = stage(kVarSlices, VSb + (size_t)k * kChunkBytes, (size_t)4 * nt * kChunkBytes,
                                    kVarSlices, LSb + ls_chunk(J, 0, k) * kChunkBytes, (size_t)4 * J * kChunkBytes,
