@@ -118,7 +118,8 @@ typedef struct {
                              (0..10), default 1.  Each candidate stops earlier once the
                              error its -2logL has left from Q falls below the error of
                              its log|R|, which no refinement changes: an estimate from
-                             its own pivots, 2^-40 (1 + delta) sum_i 1 / L_ii^2.  Steps
+                             its own pivots, 2^-8s (1 + delta) sum_i 1 / L_ii^2 for s
+                             slices (2^-40 at the default 5).  Steps
                              that no candidate takes still cost their launches */
     int nugget_in_var;    /* kriging variance uses 1 + delta (1) or 1 (0), default 1 */
     int max_batch;        /* instances factored concurrently (0 = from the budget) */

@@ -857,13 +857,19 @@ __global__ void k_keep_forward(MixedBatch b) {
 // backward substitution to z and adds it to x.
 //
 // Stopping rule.  The factor's pivots carry an absolute error of about
-// 2^-40 (1 + delta) each (a row of L has norm^2 R_ii = 1 + delta and the
-// split products are exact to about 2^-40 of it), so log|R| = sum log L_ii^2
-// is uncertain by about e_ld = 2^-40 (1 + delta) sum_i 1 / L_ii^2.  Step k
+// u (1 + delta) each, u = 2^-8s for s slices in the trailing updates (2^-40
+// at the default 5: a row of L has norm^2 R_ii = 1 + delta and the split
+// products are exact to about u of it), so log|R| = sum log L_ii^2 is
+// uncertain by about e_ld = u (1 + delta) sum_i 1 / L_ii^2.  Step k
 // changes n log Q by dq_k; with the contraction rho of the iteration (1/16
 // assumed after the first step, then dq_k / dq_{k-1}) the error of n log Q
 // left is about dq_k rho / (1 - rho).  Once that is below e_ld, further steps
 // cannot make -2logL more accurate, and the candidate stops.
+// 2^-8s, the accuracy unit of a factor with s slices in its trailing updates
+__device__ __forceinline__ double split_unit(int s) {
+    return __longlong_as_double((long long)(1023 - 8 * s) << 52);
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_refine_check(MixedBatch b, int step) {
     __shared__ dfl red[kSolveThreads / 32];
     const int t = blockIdx.x;
@@ -919,7 +925,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_refine_check(MixedBatch b, in
             double rho = 0.0625;
             if (step > 1 && st->dq_prev > 0.0) rho = fmin(0.5, fmax(dq / st->dq_prev, 1.52587890625e-05));
             const double rest = dq * rho / (1.0 - rho);
-            const double e_ld = 9.094947017729282e-13 * (1.0 + b.delta) * st->piv_inv;   // 2^-40
+            const double e_ld = split_unit(b.s) * (1.0 + b.delta) * st->piv_inv;
             st->dq_prev = dq;
             if (rest <= e_ld) st->refine_done = 1;
         }
@@ -927,8 +933,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_refine_check(MixedBatch b, in
 }
 
 // -2logL = log|R| + n log Q from the sums of the last refinement check; Q is
-// taken as zero when Q <= 16 n eps^2 Y'R^-1 Y with eps = 2^-40, the accuracy
-// unit of the split factorisation.
+// taken as zero when Q <= 16 n eps^2 Y'R^-1 Y with eps = 2^-8s, the accuracy
+// unit of the split factorisation (2^-40 at 5 slices).
 __global__ void k_df_finalize(MixedBatch b, double* nll, double* mu, double* sigma2, double* logdet,
                               int* status) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -945,7 +951,7 @@ __global__ void k_df_finalize(MixedBatch b, double* nll, double* mu, double* sig
         status[t] = st.status;
         return;
     }
-    const double eps = 9.094947017729282e-13;   // 2^-40
+    const double eps = split_unit(b.s);
     const double Q = st.Q;
     const bool degenerate = !(Q > 16.0 * n * eps * eps * fabs(st.bb));
     nll[t] = degenerate ? -inf : st.logdet + n * log(Q);
