@@ -37,7 +37,7 @@ namespace {
 // instruction costs about 64 FP32 ones here): L_JJ = chol(A_JJ), log-det,
 // the reciprocal diagonal, and W = L_JJ^-1 with the slices of W's rows.
 // The block lives in shared memory as a packed lower triangle (row-major,
-// P[r(r+1)/2 + c]), 66 KB, so that three CTAs share an SM.
+// P[r(r+1)/2 + c]), 66 KB; two 512-thread CTAs share an SM.
 //
 // Factor and inverse run in one right-looking sweep over c = 0 .. 127.  At
 // step c, position (i, p) of the triangle holds, for rows i > c,
@@ -51,7 +51,8 @@ namespace {
 //   X_ip += L_ic V_p for p <= i   (X_ic = L_ic V_c: the first term of acc_ic),
 // which is the Cholesky update a_ip -= L_ic L_pc for p > c and the inverse's
 // acc_ip += L_ic W_cp for p <= c.  The lane that finishes a_{c+1,c+1} takes
-// the next pivot: 1 / sqrt by a float seed and three Newton steps in double.
+// the next pivot (1 / sqrt from a float seed, refined on the FP32 pipes; see
+// take_pivot).
 // After step 127 the triangle holds W.
 constexpr int kDiagThreads = 512;
 constexpr int kPacked = GP_NB * (GP_NB + 1) / 2;
