@@ -96,6 +96,31 @@ __device__ __forceinline__ bool issue_first_stage_er(int ns, int i, uint32_t tac
     return true;
 }
 
+// The panel solve's accumulator groups (each exact in fp32) summed into a
+// double-float: groups 0 .. 3 through TwoSums, groups 4 .. NG - 1 (weights
+// 2^-32 and below of group 0's unit) as one float sum, whose rounding, about
+// 2^-56 of that unit, is the slices' own truncation level; one TwoSum
+// normalises at the end (h may be small under cancellation).  29 operations
+// for 7 groups where a TwoSum and a renormalisation per group took 56, and
+// the whole sum precedes the release of tensor memory to the next tile.
+template <int NG, int CB>
+__device__ __forceinline__ void sum_panel_groups(const float (&d)[NG][CB], int j, float& h, float& l) {
+    float e;
+    two_sum(d[0][j], d[1][j], h, l);
+#pragma unroll
+    for (int g = 2; g < NG && g < 4; ++g) {
+        two_sum(h, d[g][j], h, e);
+        l = __fadd_rn(l, e);
+    }
+    if (NG > 4) {
+        float tail = d[NG - 1][j];
+#pragma unroll
+        for (int g = NG - 2; g >= 4; --g) tail = __fadd_rn(tail, d[g][j]);
+        l = __fadd_rn(l, tail);
+    }
+    two_sum(h, l, h, l);
+}
+
 // Split GEMM over 128 x NT output tiles with NG accumulator groups (group g
 // gathers the products with a + b = g, the last one all a + b >= g).
 // MODE 0 (panel):  A_IJ(:, cols)  =  PS_I . WS(cols)^T   NT = 64, ps slices,
@@ -297,19 +322,7 @@ __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
                     }
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < CB1; ++j) {
-                        float h, l;
-                        two_sum(d[0][j], d[1][j], h, l);
-#pragma unroll
-                        for (int g = 2; g < NG; ++g) {
-                            float s2, e2;
-                            two_sum(h, d[g][j], s2, e2);
-                            l = __fadd_rn(l, e2);
-                            fast_two_sum(s2, l, h, l);
-                        }
-                        hv[cb + j] = h;
-                        lv[cb + j] = l;
-                    }
+                    for (int j = 0; j < CB1; ++j) sum_panel_groups<NG>(d, j, hv[cb + j], lv[cb + j]);
                 }
                 // tensor memory is free for the next tile's MMAs
                 tc_fence_before();
@@ -508,13 +521,7 @@ __global__ void __launch_bounds__(ER ? kGemmThreadsER : kGemmThreads, 1)
                         // assuming |h| >= |l|
                         two_sum(h, l, h, l);
                     } else {
-#pragma unroll
-                        for (int g = 2; g < NG; ++g) {
-                            float s2, e2;
-                            two_sum(h, d[g][j], s2, e2);
-                            l = __fadd_rn(l, e2);
-                            fast_two_sum(s2, l, h, l);
-                        }
+                        sum_panel_groups<NG>(d, j, h, l);
                     }
                     const int e = eA + __ldg(eBp + c) - 14;
                     const float sc = (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
