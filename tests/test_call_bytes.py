@@ -107,3 +107,25 @@ def test_serving_admission_uses_the_library_sizes(gp):
             assert serve.eval_bytes(n, d, prec) == gp.call_bytes("nll_batch", n, d, serve.FIT_CANDIDATES, prec)
         assert serve.model_bytes(n, d) == gp.call_bytes("fit", n, d)
         assert serve.predict_bytes(n, d, 1000) == gp.call_bytes("predict", n, d, 1000)
+
+
+def test_predict_workspace_of_the_tensor_core_path(gp):
+    """The default predict path (predict_tc = 1): the slice tables of the
+    factor (5 slices of the rows of L left of their diagonal blocks, 7 of each
+    W_J = L_JJ^-1, three npad int arrays), an error flag, per 128-point block
+    of a chunk its r values (npad x 128 double-floats) and partial r'w
+    (nt x 128), per CTA of the tensor-core pass the slices of V (5 x 4 nt
+    chunks) and of C_J (7 x 4 chunks); a chunk is at most one wave of 152
+    blocks."""
+    al = lambda v: (v + 255) // 256 * 256
+    chunk = 128 * 32 * 2
+    for n, d in ((1, 2), (300, 3), (4000, 6), (16384, 10)):
+        nt = (n + 127) // 128
+        npad = nt * 128
+        tables = al(al(10 * nt * (nt - 1) * chunk) + al(nt * 28 * chunk) + 3 * al(npad * 4))
+        per_block = npad * 128 * 8 + nt * 128 * 8
+        per_cta = (5 * 4 * nt + 28) * chunk
+        for N in (1, 128, 129, 5000, 152 * 128, 10 ** 6):
+            B = min((N + 127) // 128, 152)
+            want = tables + 256 + B * per_block + min(B, 152) * per_cta
+            assert gp.call_bytes("predict", n, d, N) == want, (n, N)

@@ -177,3 +177,24 @@ def test_tc_bounded_wait_gives_nan_not_a_hang(ctx):
     assert np.all(np.isfinite(host(s22)))
     assert np.array_equal(host(yh2), yh)
     model.free()
+
+
+def test_bench_kriging_only_runs():
+    """bench.py --kriging-only (the entry the variance-pass profiles name)
+    at a small size: one JSON line, finite times, no NaN variances, and the
+    variance solve's executed rate below the bf16 peak."""
+    import json
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--kriging-only", "--n", "300", "--points", "1000",
+                        "--steps", "1", "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["unit"] == "points/s" and line["value"] > 0
+    assert line["variance_nan"] == 0
+    assert 0 < line["mean_only_s"] and 0 < line["mean_and_variance_s"]
+    assert line["variance_solve"]["executed_frac_of_sustained_bf16"] < 1.5
