@@ -592,10 +592,13 @@ def run_kriging(args):
                       "config": {"workload": f"kriging n={n} d={w.d} N={args.points}", "p": w.p, "delta": w.delta},
                       "mean_only_s": t_mean, "mean_and_variance_s": t_var,
                       "variance_nan": int(torch.isnan(s2).sum()),
-                      "variance_solve": {"tensor_core_pass_s": t_tc, "method_tflops": method / t_tc / 1e12,
-                                         "executed_split_tflops": executed / t_tc / 1e12,
+                      # the pass is the difference of two timings: too short a pass to
+                      # resolve (tiny n or N) reports no rate
+                      "variance_solve": {"tensor_core_pass_s": t_tc,
+                                         "method_tflops": method / t_tc / 1e12 if t_tc > 0 else None,
+                                         "executed_split_tflops": executed / t_tc / 1e12 if t_tc > 0 else None,
                                          "executed_frac_of_sustained_bf16":
-                                             executed / t_tc / 1e12 / pk["bf16_tflops_sustained"]}}))
+                                             executed / t_tc / 1e12 / pk["bf16_tflops_sustained"] if t_tc > 0 else None}}))
     model.free()
     ctx.close()
     return 0
