@@ -117,6 +117,35 @@ def test_kriging_at_n16384_closed_form(ctx):
     model.free()
 
 
+def test_split_fit_kriging_at_n16384_closed_form(ctx):
+    """The same Markov case fitted in split precision (GP_MIXED): -2logL within
+    1e-8 of the closed form (cond(R) is about 19, so the split factor's 2^-40
+    per pivot dominates), kriging means and tensor-core variances within
+    1e-8, and the two variance paths of gp_predict within 2e-9 sigma2."""
+    n = 16384
+    theta = -math.log(0.9) / H
+    x = (np.arange(n) * H).reshape(n, 1)
+    y = np.random.default_rng(6).standard_normal(n)
+    model = ctx.fit(dev(x), dev(y), dev([theta]), 1.0, 0.0, "mixed")
+    f = kms(n, math.exp(-theta * H), y)
+    assert abs(model.nll - f["nll"]) <= 1e-8 * abs(f["nll"])
+    rng = np.random.default_rng(7)
+    js = rng.integers(0, n - 1, 1000)
+    xs = (js + rng.uniform(0.05, 0.95, 1000)) * H
+    yh, s2 = ctx.predict(model, dev(xs.reshape(-1, 1)))
+    ry, rs = ou_predict(theta, y, xs, f)
+    yh, s2 = yh.cpu().numpy(), s2.cpu().numpy()
+    assert np.max(np.abs(yh - ry)) <= 1e-8 * np.max(np.abs(y))
+    assert np.max(np.abs(s2 - rs)) <= 1e-8 * f["sigma2"]
+    ctx.set_options(predict_tc=0)
+    try:
+        _, s0 = ctx.predict(model, dev(xs.reshape(-1, 1)))
+    finally:
+        ctx.set_options(predict_tc=1)
+    assert np.max(np.abs(s0.cpu().numpy() - s2)) <= 2e-9 * f["sigma2"]
+    model.free()
+
+
 @pytest.mark.skipif(not __import__("os").environ.get("GP_SLOW_TESTS"),
                     reason="one oracle evaluation at n = 16384 takes about 12 minutes: set GP_SLOW_TESTS=1")
 def test_large_instance_one_theta_against_oracle(ctx):
