@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
                 const dfl l = df_mul(P[prow(p) + c], di);
                 df_store(T + (size_t)c * GP_NB + p, l);
                 V[p] = df_neg(l);
+                P[prow(p) + c] = dfl{0.f, 0.f};   // restarts in phase 2 as acc_pc = L_pc V_c
             }
         }
         __syncthreads();
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
             for (int j = 0; j < 4; ++j) {
                 const int p = lane + 32 * j;
                 if (32 * j <= i && p <= i) {
-                    const dfl x0 = (p == c) ? dfl{0.f, 0.f} : row[p];
+                    const dfl x0 = row[p];
                     const dfl x = df_fma(m, vl[j], x0);
                     if (p == c + 1)
                         take_pivot(c + 1, x);
@@ -182,8 +183,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_mixed(MixedBatch b, int J
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int p = lane + 32 * j;
-                    if (32 * j <= i) x1[j] = (p <= i && p != c) ? r1[p] : dfl{0.f, 0.f};
-                    if (two && 32 * j <= i2) x2[j] = (p <= i2 && p != c) ? r2[p] : dfl{0.f, 0.f};
+                    if (32 * j <= i) x1[j] = (p <= i) ? r1[p] : dfl{0.f, 0.f};
+                    if (two && 32 * j <= i2) x2[j] = (p <= i2) ? r2[p] : dfl{0.f, 0.f};
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
