@@ -884,6 +884,11 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
     const int nt = m->nt, npad = nt * GP_NB;
     const size_t avail = ctx->budget > ctx->models_bytes ? ctx->budget - ctx->models_bytes : 0;
     const VarPlan v = var_plan(nt, N, ctx->sms, avail, var);
+    if (var && v.bytes > ctx->ws_bytes && v.bytes + ctx->models_bytes > ctx->budget)
+        return fail(ctx, GP_ENOMEM,
+                    "the tensor-core variance needs %zu bytes of workspace (the factor's slices and one "
+                    "128-point block), beyond the HBM budget (%zu, %zu held by models): set predict_tc = 0",
+                    v.bytes, ctx->budget, ctx->models_bytes);
     int rc = ensure_ws(ctx, v.bytes);
     if (rc) return rc;
     char* c = static_cast<char*>(ctx->ws);
