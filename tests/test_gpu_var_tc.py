@@ -197,3 +197,34 @@ def test_bench_kriging_only_runs():
     assert line["variance_nan"] == 0
     assert 0 < line["mean_only_s"] and 0 < line["mean_and_variance_s"]
     assert "tensor_core_pass_s" in line["variance_solve"]
+
+
+def test_tc_workspace_beyond_budget_names_the_fp32_path():
+    """A budget that holds the fit and the FP32-pipe prediction's scratch but
+    not the tensor-core pass's slice tables: gp_predict with variances fails
+    with GP_ENOMEM naming predict_tc, and succeeds with predict_tc = 0."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_1269_gb300 import gp
+    n, d, N = 2048, 3, 500
+    model_b = gp.call_bytes("fit", n, d)
+    fit_ws = gp.call_bytes("nll_batch", n, d, 1, "fp64")
+    tc_ws = gp.call_bytes("predict", n, d, N)
+    budget = model_b + fit_ws + (4 << 20)
+    assert tc_ws + model_b > budget
+    g = np.random.default_rng(21)
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    c = gp.Context(0, hbm_budget_bytes=budget)
+    try:
+        model = c.fit(dev(x), dev(y), dev([2.0, 3.0, 4.0]), 1.95, 1e-8, "fp64")
+        xs = dev(g.random((N, d)))
+        with pytest.raises(gp.GPError) as e:
+            c.predict(model, xs)
+        assert e.value.code == gp.GP_ENOMEM and "predict_tc" in str(e.value)
+        c.set_options(predict_tc=0)
+        yh, s2 = c.predict(model, xs)
+        assert torch.isfinite(s2).all() and torch.isfinite(yh).all()
+        model.free()
+    finally:
+        c.close()
