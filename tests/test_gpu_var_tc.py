@@ -50,9 +50,12 @@ def both_paths(ctx, model, xs, want_var=True):
 
 
 # (n, d, N, p, delta, theta scale): ragged n (one tile row, several, a
-# ragged last one), ragged N (one point, a partial block, several blocks)
+# ragged last one), ragged N (one point, a partial block, several blocks), a
+# large nugget (|v_i|^2 <= 1 + delta = 4: the slices of v take exponent 2),
+# p below 1
 CASES = [(1, 2, 5, 1.95, 1e-6, 1.0), (100, 3, 129, 1.95, 1e-8, 4.0), (129, 1, 1, 2.0, 1e-6, 20.0),
-         (260, 3, 300, 1.95, 0.0, 4.0), (700, 6, 257, 1.9, 1e-6, 1.0), (1100, 4, 64, 2.0, 1e-6, 2.0)]
+         (260, 3, 300, 1.95, 0.0, 4.0), (700, 6, 257, 1.9, 1e-6, 1.0), (1100, 4, 64, 2.0, 1e-6, 2.0),
+         (400, 2, 200, 2.0, 3.0, 2.0), (300, 3, 150, 0.7, 1e-6, 2.0)]
 
 
 @pytest.mark.parametrize("n,d,N,p,delta,ts", CASES)
