@@ -696,10 +696,15 @@ PredictShape predict_shape(int nt, int N, int sms, size_t avail, bool variances)
 // values (with variances) and partial means of a chunk of 128-point
 // blocks, and per CTA of the tensor-core pass the slices of V and of C_J.
 // A chunk is one wave of that pass (one block per SM; four waves' partial
-// means without variances), fewer blocks when the budget is short.
+// means without variances), fewer blocks when the budget is short.  With
+// variances and more than one chunk, the blocks past the last whole chunk
+// (the remainder, rem < chunk) get their own r values and CTA slices: their
+// pass runs on the context's second stream while the main stream forms the
+// r values of the whole chunks, one chunk ahead of its passes in a second
+// slot, so that the remainder's partial wave is not a round of its own.
 struct VarPlan {
-    int blocks, chunk, grid;
-    size_t tables, per_block, bytes;
+    int blocks, chunk, grid, rem, slots;
+    size_t tables, per_block, per_cta, bytes;
 };
 
 VarPlan var_plan(int nt, int N, int sms, size_t avail, bool variances) {
@@ -707,14 +712,22 @@ VarPlan var_plan(int nt, int N, int sms, size_t avail, bool variances) {
     v.blocks = (N + GP_NB - 1) / GP_NB;
     v.tables = variances ? align256(gp::var_table_bytes(nt)) : 0;
     v.per_block = (variances ? gp::var_rx_bytes(nt) : 0) + gp::var_mp_bytes(nt);
-    const size_t per_cta = variances ? gp::var_cta_bytes(nt) : 0;
+    v.per_cta = variances ? gp::var_cta_bytes(nt) : 0;
+    auto shape = [&](int c, int& rem, int& slots) {
+        rem = (variances && v.blocks > c) ? v.blocks % c : 0;
+        slots = (rem > 0 && (v.blocks - rem) / c >= 2) ? 2 : 1;
+    };
     auto total = [&](int c) {
-        return v.tables + 256 + (size_t)c * v.per_block + (size_t)(c < sms ? c : sms) * per_cta;
+        int rem, slots;
+        shape(c, rem, slots);
+        return v.tables + 256 + (size_t)slots * c * v.per_block + (size_t)(c < sms ? c : sms) * v.per_cta +
+               (size_t)rem * (v.per_block + v.per_cta);
     };
     const int cap = variances ? sms : 4 * sms;
     v.chunk = v.blocks < cap ? v.blocks : cap;
     while (v.chunk > 1 && total(v.chunk) > avail) v.chunk -= (v.chunk / 4 > 1 ? v.chunk / 4 : 1);
     v.grid = v.chunk < sms ? v.chunk : sms;
+    shape(v.chunk, v.rem, v.slots);
     v.bytes = total(v.chunk);
     return v;
 }
@@ -891,19 +904,35 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
                     v.bytes, ctx->budget, ctx->models_bytes);
     int rc = ensure_ws(ctx, v.bytes);
     if (rc) return rc;
+    if (v.rem > 0 && (rc = ensure_aux(ctx))) return rc;
+    // the workspace, in the order var_plan counts it
     char* c = static_cast<char*>(ctx->ws);
     gp::VarCall call{};
     if (var) call.t = gp::var_tables_at(c, nt);
     c += v.tables;
     call.err = reinterpret_cast<int*>(c);
     c += 256;
-    call.RX = reinterpret_cast<float2*>(c);
-    if (var) c += (size_t)v.chunk * gp::var_rx_bytes(nt);
-    call.MP = reinterpret_cast<float2*>(c);
-    c += (size_t)v.chunk * gp::var_mp_bytes(nt);
-    call.VS = reinterpret_cast<__nv_bfloat16*>(c);
-    if (var) c += (size_t)v.grid * gp::var_vs_bytes(nt);
-    call.CS = reinterpret_cast<__nv_bfloat16*>(c);
+    const size_t rx = var ? gp::var_rx_bytes(nt) : 0, mp = gp::var_mp_bytes(nt);
+    const size_t vs = var ? gp::var_vs_bytes(nt) : 0, cs = var ? gp::var_cta_bytes(nt) - gp::var_vs_bytes(nt) : 0;
+    float2* RX[2];
+    float2* MP[2];
+    for (int q = 0; q < v.slots; ++q, c += (size_t)v.chunk * rx) RX[q] = reinterpret_cast<float2*>(c);
+    for (int q = 0; q < v.slots; ++q, c += (size_t)v.chunk * mp) MP[q] = reinterpret_cast<float2*>(c);
+    if (v.slots == 1) {
+        RX[1] = RX[0];
+        MP[1] = MP[0];
+    }
+    __nv_bfloat16* VS = reinterpret_cast<__nv_bfloat16*>(c);
+    c += (size_t)v.grid * vs;
+    __nv_bfloat16* CS = reinterpret_cast<__nv_bfloat16*>(c);
+    c += (size_t)v.grid * cs;
+    float2* RXr = reinterpret_cast<float2*>(c);
+    c += (size_t)v.rem * rx;
+    float2* MPr = reinterpret_cast<float2*>(c);
+    c += (size_t)v.rem * mp;
+    __nv_bfloat16* VSr = reinterpret_cast<__nv_bfloat16*>(c);
+    c += (size_t)v.rem * vs;
+    __nv_bfloat16* CSr = reinterpret_cast<__nv_bfloat16*>(c);
     call.n = m->n; call.d = m->d; call.nt = nt; call.N = N; call.corr = m->corr;
     call.p = m->p;
     call.c0 = ctx->opt.nugget_in_var ? 1.0 + m->delta : 1.0;
@@ -912,7 +941,6 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
     int ev = 0;
     std::frexp(std::sqrt(1.0 + m->delta) * (1.0 + 0x1p-20), &ev);
     call.ev = ev;
-    call.grid = v.grid;
     call.inject_timeout = (ctx->opt.inject_timeout & 2) != 0;
     const float2* Zdf = reinterpret_cast<const float2*>(m->Z);
     call.x = reinterpret_cast<const float2*>(m->x);
@@ -920,20 +948,57 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
     call.xs = xstar; call.yhat = yhat; call.s2 = s2;
     PhaseScope ps(ctx, GP_PHASE_PREDICT, 0);
     int k = 0;
-    if (var) {
-        const cudaError_t e = gp::launch_var_tables(reinterpret_cast<const float2*>(m->L), nt, call.t, ctx->stream, &k);
+    auto points = [&](int b0, int nb, float2* rxp, float2* mpp) -> int {
+        const cudaError_t e = gp::launch_var_points(call, b0 * GP_NB, nb, var ? rxp : nullptr, mpp, ctx->stream, &k);
         ps.kernels += k;
         GP_CUDA(ctx, e);
-    }
-    for (int b0 = 0; b0 < v.blocks; b0 += v.chunk) {
-        const int nb = v.blocks - b0 < v.chunk ? v.blocks - b0 : v.chunk;
-        const cudaError_t e = gp::launch_var_chunk(call, b0 * GP_NB, nb, ctx->stream, &k);
+        return GP_OK;
+    };
+    auto pass = [&](int b0, int nb, const float2* rxp, __nv_bfloat16* vsp, __nv_bfloat16* csp, int grid,
+                    cudaStream_t st) -> int {
+        const cudaError_t e = gp::launch_var_pass(call, b0 * GP_NB, nb, rxp, vsp, csp, grid, st, &k);
         ps.kernels += k;
         if (e == cudaErrorNotSupported)
             return fail(ctx, GP_ENOTSUP, "the tensor-core variance kernel was built with too few registers "
                                          "for its register split: set predict_tc = 0");
         GP_CUDA(ctx, e);
+        return GP_OK;
+    };
+    if (!var) {
+        for (int b0 = 0; b0 < v.blocks; b0 += v.chunk)
+            if ((rc = points(b0, v.blocks - b0 < v.chunk ? v.blocks - b0 : v.chunk, nullptr, MP[0]))) return rc;
+        return GP_OK;
     }
+    {
+        const cudaError_t e = gp::launch_var_tables(reinterpret_cast<const float2*>(m->L), nt, call.t, ctx->stream, &k);
+        ps.kernels += k;
+        GP_CUDA(ctx, e);
+    }
+    const int full = v.blocks - v.rem;             // whole chunks
+    const int chunks = (full + v.chunk - 1) / v.chunk;
+    if (v.rem > 0) {
+        // the remainder's r, then its pass on the second stream
+        if ((rc = points(full, v.rem, RXr, MPr))) return rc;
+        GP_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+        GP_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        if ((rc = pass(full, v.rem, RXr, VSr, CSr, v.rem, ctx->aux))) return rc;
+        GP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
+    }
+    // whole chunks: with two slots the r of chunk q + 1 is formed before the
+    // pass of chunk q (in-order on the main stream, so a slot is rewritten
+    // only after the pass that read it)
+    for (int q = 0; q < chunks; ++q) {
+        const int b0 = q * v.chunk, nb = full - b0 < v.chunk ? full - b0 : v.chunk;
+        if (v.slots == 1 || q == 0)
+            if ((rc = points(b0, nb, RX[q & 1], MP[q & 1]))) return rc;
+        if (v.slots == 2 && q + 1 < chunks) {
+            const int b1 = b0 + v.chunk;
+            if ((rc = points(b1, full - b1 < v.chunk ? full - b1 : v.chunk, RX[(q + 1) & 1], MP[(q + 1) & 1])))
+                return rc;
+        }
+        if ((rc = pass(b0, nb, RX[q & 1], VS, CS, v.grid, ctx->stream))) return rc;
+    }
+    if (v.rem > 0) GP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     return GP_OK;
 }
 

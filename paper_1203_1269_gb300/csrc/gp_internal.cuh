@@ -208,7 +208,6 @@ struct VarCall {
     int n, d, nt, N, corr;
     double p, c0;
     int ev;                       // fixed exponent of the slices of v = L^-1 r
-    int grid;                     // CTAs of the tensor-core pass
     int inject_timeout;
     const float2* x;              // n x d design points (double-float)
     const double* theta;
@@ -219,10 +218,6 @@ struct VarCall {
     double* yhat;
     double* s2;                   // null: means only
     VarTables t;
-    float2* RX;                   // chunk x npad x 128 values of r
-    float2* MP;                   // chunk x nt x 128 partial r'w
-    __nv_bfloat16* VS;            // grid x var_cta_bytes: slices of V, then of C_J
-    __nv_bfloat16* CS;
     int* err;
 };
 size_t var_table_bytes(int nt);
@@ -232,7 +227,10 @@ size_t var_vs_bytes(int nt);      // per CTA: the slices of V
 size_t var_cta_bytes(int nt);     // per CTA of the tensor-core pass: V's and C_J's slices
 VarTables var_tables_at(void* base, int nt);
 cudaError_t launch_var_tables(const float2* L, int nt, const VarTables& t, cudaStream_t s, int* kernels);
-cudaError_t launch_var_chunk(const VarCall& c, int m0, int npb, cudaStream_t s, int* kernels);
+cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, float2* MP, cudaStream_t s,
+                              int* kernels);
+cudaError_t launch_var_pass(const VarCall& c, int m0, int npb, const float2* RX, __nv_bfloat16* VS,
+                            __nv_bfloat16* CS, int grid, cudaStream_t s, int* kernels);
 cudaError_t launch_predict(int n, int d, int nt, const float2* x, const double* theta, double p, int corr, double c0,
                            const float2* L, const float2* w, const float2* a, const double* scalars, int N,
                            const double* xs, double* yhat, double* s2, float2* work, int chunk, int nr,

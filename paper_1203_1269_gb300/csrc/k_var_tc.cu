@@ -754,39 +754,47 @@ static bool var_tc_fits() {
     return v == 1;
 }
 
-// One chunk of npb point blocks from point m0: r and the partial means,
-// yhat, then (with variances) the tensor-core pass on `grid` CTAs.
-cudaError_t launch_var_chunk(const VarCall& c, int m0, int npb, cudaStream_t s, int* kernels) {
+// r and the partial means of npb point blocks from point m0 (RX null: means
+// only), then yhat: 2 kernels.
+cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, float2* MP, cudaStream_t s,
+                              int* kernels) {
     *kernels = 0;
-    const bool var = c.s2 != nullptr;
-    if (var && !var_tc_fits()) return cudaErrorNotSupported;
     RhsArgs r;
     r.n = c.n; r.d = c.d; r.nt = c.nt; r.N = c.N; r.m0 = m0;
     r.x = c.x; r.theta = c.theta; r.p = c.p; r.corr = c.corr; r.xs = c.xs; r.w = c.w;
-    r.RX = var ? c.RX : nullptr;
-    r.MP = c.MP;
+    r.RX = RX;
+    r.MP = MP;
     const size_t rsmem = (size_t)(2 * GP_NB * c.d + c.d + kExpTab) * sizeof(dfl);
     static std::atomic<size_t> rattr[kMaxDevices];
     cudaError_t e = raise_smem_limit(k_var_rhs, rsmem, rattr);
     if (e != cudaSuccess) return e;
     k_var_rhs<<<dim3(c.nt, npb), 2 * GP_NB, rsmem, s>>>(r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_var_mean<<<(npb * GP_NB + 255) / 256, 256, 0, s>>>(c.MP, c.nt, c.N, m0, npb, c.sc, c.yhat);
+    k_var_mean<<<(npb * GP_NB + 255) / 256, 256, 0, s>>>(MP, c.nt, c.N, m0, npb, c.sc, c.yhat);
     *kernels = 2;
-    if ((e = cudaGetLastError()) != cudaSuccess || !var) return e;
+    return cudaGetLastError();
+}
+
+// The tensor-core pass over npb point blocks from point m0, whose r values
+// are in RX, on min(npb, grid) CTAs with their slices of V and C_J in VS and
+// CS: 1 kernel.
+cudaError_t launch_var_pass(const VarCall& c, int m0, int npb, const float2* RX, __nv_bfloat16* VS,
+                            __nv_bfloat16* CS, int grid, cudaStream_t s, int* kernels) {
+    *kernels = 0;
+    if (!var_tc_fits()) return cudaErrorNotSupported;
     VarArgs g;
     g.nt = c.nt; g.npb = npb; g.N = c.N; g.m0 = m0; g.ev = c.ev;
     g.LS = c.t.LS; g.LE = c.t.LE; g.WS = c.t.WS; g.WE = c.t.WE;
-    g.a = c.a; g.sc = c.sc; g.c0 = c.c0; g.RX = c.RX;
-    g.VS = c.VS; g.CS = c.CS;
+    g.a = c.a; g.sc = c.sc; g.c0 = c.c0; g.RX = RX;
+    g.VS = VS; g.CS = CS;
     g.vs_stride = (size_t)kVarSlices * 4 * c.nt * kChunkElems;
     g.cs_stride = (size_t)kVarWSlices * 4 * kChunkElems;
     g.s2 = c.s2; g.err = c.err; g.inject_timeout = c.inject_timeout;
     static std::atomic<size_t> tattr[kMaxDevices];
-    if ((e = raise_smem_limit(k_var_tc, kVarSmem, tattr)) != cudaSuccess) return e;
-    const int grid = npb < c.grid ? npb : c.grid;
-    k_var_tc<<<grid, kVarThreads, kVarSmem, s>>>(g);
-    *kernels = 3;
+    cudaError_t e = raise_smem_limit(k_var_tc, kVarSmem, tattr);
+    if (e != cudaSuccess) return e;
+    k_var_tc<<<npb < grid ? npb : grid, kVarThreads, kVarSmem, s>>>(g);
+    *kernels = 1;
     return cudaGetLastError();
 }
 

@@ -75,8 +75,10 @@ def test_predict_scratch(gp):
     for N in (1, 100, 1000, 4000):
         # every point's solve column (a double-float pair per row) in one pass
         assert gp.call_bytes("predict", n, d, N) >= N * npad * 8
-    big = [gp.call_bytes("predict", n, d, N) for N in (100000, 200000, 10 ** 6)]
-    assert big[0] == big[1] == big[2]   # at most four waves of CTAs at once
+    # bounded in N: one wave of blocks, a second slot of r values and at most
+    # 151 remainder blocks, whatever the number of points
+    big = [gp.call_bytes("predict", n, d, N) for N in (100000, 200000, 10 ** 6, 2 ** 30)]
+    assert max(big) <= 2 * gp.call_bytes("predict", n, d, 152 * 128) + 151 * npad * 128 * 8 * 4
 
 
 def test_errors(gp):
@@ -116,7 +118,9 @@ def test_predict_workspace_of_the_tensor_core_path(gp):
     of a chunk its r values (npad x 128 double-floats) and partial r'w
     (nt x 128), per CTA of the tensor-core pass the slices of V (5 x 4 nt
     chunks) and of C_J (7 x 4 chunks); a chunk is at most one wave of 152
-    blocks."""
+    blocks.  Past one chunk the remainder blocks (blocks mod 152) get their
+    own r values and CTA slices, and with two or more whole chunks the r
+    values take a second slot."""
     al = lambda v: (v + 255) // 256 * 256
     chunk = 128 * 32 * 2
     for n, d in ((1, 2), (300, 3), (4000, 6), (16384, 10)):
@@ -125,7 +129,10 @@ def test_predict_workspace_of_the_tensor_core_path(gp):
         tables = al(al(10 * nt * (nt - 1) * chunk) + al(nt * 28 * chunk) + 3 * al(npad * 4))
         per_block = npad * 128 * 8 + nt * 128 * 8
         per_cta = (5 * 4 * nt + 28) * chunk
-        for N in (1, 128, 129, 5000, 152 * 128, 10 ** 6):
-            B = min((N + 127) // 128, 152)
-            want = tables + 256 + B * per_block + min(B, 152) * per_cta
+        for N in (1, 128, 129, 5000, 152 * 128, 152 * 128 + 1, 2 * 152 * 128 + 300, 10 ** 6):
+            blocks = (N + 127) // 128
+            C = min(blocks, 152)
+            rem = blocks % C if blocks > C else 0
+            slots = 2 if rem > 0 and (blocks - rem) // C >= 2 else 1
+            want = tables + 256 + slots * C * per_block + C * per_cta + rem * (per_block + per_cta)
             assert gp.call_bytes("predict", n, d, N) == want, (n, N)

@@ -231,3 +231,37 @@ def test_tc_workspace_beyond_budget_names_the_fp32_path():
         model.free()
     finally:
         c.close()
+
+
+def test_tc_remainder_on_the_second_stream_gives_the_same_bits():
+    """N = 2 x 152 x 128 + 300 points: two whole chunks (the second r slot)
+    and a 3-block remainder whose pass runs on the context's second stream.
+    The same bits as a budget that allows one block per chunk (no remainder
+    path), every variance finite, sampled points against the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_1269_gb300 import gp
+    g = np.random.default_rng(31)
+    n, d, N = 300, 3, 2 * 152 * 128 + 300
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    theta = np.array([2.0, 4.0, 3.0])
+    xs = g.random((N, d))
+    out = []
+    for budget in (0, 6 << 20):
+        c = gp.Context(0, hbm_budget_bytes=budget)
+        try:
+            model = c.fit(dev(x), dev(y), dev(theta), 1.95, 1e-8, "fp64")
+            yh, s2 = c.predict(model, dev(xs))
+            out.append((host(yh), host(s2)))
+            model.free()
+        finally:
+            c.close()
+    (y0, v0), (y1, v1) = out
+    assert np.all(np.isfinite(v0))
+    assert np.array_equal(y0, y1) and np.array_equal(v0, v1)
+    idx = np.unique(np.r_[0, N - 1, np.arange(2 * 152 * 128 - 5, 2 * 152 * 128 + 5), g.integers(0, N, 100)])
+    yo, so, _ = oracle.predict(x, y, theta, 1.95, 1e-8, xs[idx])
+    o, _ = oracle.nll(x, y, theta, 1.95, 1e-8)
+    assert np.max(np.abs(y0[idx] - yo)) <= 1e-8 * max(1.0, np.max(np.abs(yo)))
+    assert np.max(np.abs(v0[idx] - so)) <= 1e-8 * o["sigma2"]
