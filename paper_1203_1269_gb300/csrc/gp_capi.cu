@@ -720,7 +720,7 @@ VarPlan var_plan(int nt, int N, int sms, size_t avail, bool variances) {
     auto total = [&](int c) {
         int rem, slots;
         shape(c, rem, slots);
-        return v.tables + 256 + (size_t)slots * c * v.per_block + (size_t)(c < sms ? c : sms) * v.per_cta +
+        return v.tables + 256 + gp::var_rhs_tab_bytes() + (size_t)slots * c * v.per_block + (size_t)(c < sms ? c : sms) * v.per_cta +
                (size_t)rem * (v.per_block + v.per_cta);
     };
     const int cap = variances ? sms : 4 * sms;
@@ -912,6 +912,8 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
     c += v.tables;
     call.err = reinterpret_cast<int*>(c);
     c += 256;
+    call.rtab = reinterpret_cast<float2*>(c);
+    c += gp::var_rhs_tab_bytes();
     const size_t rx = var ? gp::var_rx_bytes(nt) : 0, mp = gp::var_mp_bytes(nt);
     const size_t vs = var ? gp::var_vs_bytes(nt) : 0, cs = var ? gp::var_cta_bytes(nt) - gp::var_vs_bytes(nt) : 0;
     float2* RX[2];
@@ -948,6 +950,11 @@ int predict_tensor(gp_ctx* ctx, const gp_model* m, int N, const double* xstar, d
     call.xs = xstar; call.yhat = yhat; call.s2 = s2;
     PhaseScope ps(ctx, GP_PHASE_PREDICT, 0);
     int k = 0;
+    {
+        const cudaError_t e = gp::launch_var_rhs_tables(call, ctx->stream, &k);
+        ps.kernels += k;
+        GP_CUDA(ctx, e);
+    }
     auto points = [&](int b0, int nb, float2* rxp, float2* mpp) -> int {
         const cudaError_t e = gp::launch_var_points(call, b0 * GP_NB, nb, var ? rxp : nullptr, mpp, ctx->stream, &k);
         ps.kernels += k;

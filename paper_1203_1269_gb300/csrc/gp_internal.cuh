@@ -219,13 +219,16 @@ struct VarCall {
     double* s2;                   // null: means only
     VarTables t;
     int* err;
+    float2* rtab;                 // var_rhs_tab_bytes(): the r kernel's tables
 };
 size_t var_table_bytes(int nt);
 size_t var_rx_bytes(int nt);      // per point block
 size_t var_mp_bytes(int nt);      // per point block
 size_t var_vs_bytes(int nt);      // per CTA: the slices of V
 size_t var_cta_bytes(int nt);     // per CTA of the tensor-core pass: V's and C_J's slices
+size_t var_rhs_tab_bytes();
 VarTables var_tables_at(void* base, int nt);
+cudaError_t launch_var_rhs_tables(const VarCall& c, cudaStream_t s, int* kernels);
 cudaError_t launch_var_tables(const float2* L, int nt, const VarTables& t, cudaStream_t s, int* kernels);
 cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, float2* MP, cudaStream_t s,
                               int* kernels);

@@ -186,6 +186,95 @@ __global__ void __launch_bounds__(2 * GP_NB) k_var_lslice(const float2* L, int n
 
 // --------------------------------------------------------------- r ---------
 
+// |dx|^p for a general p without a logarithm or an exponential (the
+// table-driven reduction of P. T. P. Tang, ACM TOMS 16 (1990), applied to
+// the power): |dx| = 2^m F_j (1 + u), F_j = 1 + j/kPowN the table point
+// nearest to the mantissa (|u| <= 2^-8), so that
+//   theta_k |dx|^p = [theta_k 2^(m p)] F_j^p (1 + u)^p
+// with 2^(m p) (m = -kPowM .. kPowM) and F_j^p from tables in double-float
+// and (1 + u)^p by its binomial series to u^5 (the u^6 term is below
+// 2^-53 for p in (0, 2]).  The tables depend on p alone and are built once
+// per call (k_var_rhs_tables), with the exponential's 2^(-j/1024).
+constexpr int kPowNBits = 7;
+constexpr int kPowN = 1 << kPowNBits;
+constexpr int kPowM = 60;                            // |dx| in [2^-60, 2^60]
+constexpr int kPowMs = 2 * kPowM + 1;
+constexpr int kPowMaxD = 16;                         // above: the general routine per term
+// the table image, in float2 units: 2^(-j/1024), 2^(m p), F_j^p, then
+// 1/F_j as floats
+constexpr int kTabExp = 0;
+constexpr int kTabTwo = kExpTab;
+constexpr int kTabF = kTabTwo + kPowMs;
+constexpr int kTabInv = kTabF + kPowN;
+constexpr int kTabLen = kTabInv + kPowN / 2;
+
+__global__ void k_var_rhs_tables(double p, float2* tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v;
+    if (i < kTabTwo) {
+        v = exp2(-(double)i / (double)kExpTab);      // as fill_exp2_table
+    } else if (i < kTabF) {
+        v = exp2((double)(i - kTabTwo - kPowM) * p);
+    } else if (i < kTabInv) {
+        v = pow(1.0 + (double)(i - kTabF) / kPowN, p);
+    } else {
+        if (i < kTabInv + kPowN)
+            reinterpret_cast<float*>(tab + kTabInv)[i - kTabInv] =
+                (float)(1.0 / (1.0 + (double)(i - kTabInv) / kPowN));
+        return;
+    }
+    const dfl t = df_from_double(v);
+    tab[i] = make_float2(t.hi, t.lo);
+}
+
+// (1 + u)^p = 1 + p u + c2 u^2 + (c3 + c4 u + c5 u^2) u^3 for u = uh + ul,
+// |u| <= 2^-8, |ul| <= 2^-24 (it carries the argument's low word): p u and
+// c2 u^2 as exact products of the high words plus their cross terms, the
+// rest in float (it is below 2^-26) with u^3 = uh^2 (uh + 3 ul)
+__device__ __forceinline__ dfl pow_series(float uh, float ul, dfl pd, dfl c2, float c3, float c4, float c5) {
+    const float t1 = __fmul_rn(pd.hi, uh);
+    float t1e = __fmaf_rn(pd.hi, uh, -t1);
+    t1e = __fmaf_rn(pd.hi, ul, t1e);
+    t1e = __fmaf_rn(pd.lo, uh, t1e);
+    const float sq = __fmul_rn(uh, uh);
+    float sqe = __fmaf_rn(uh, uh, -sq);
+    sqe = __fmaf_rn(__fadd_rn(uh, uh), ul, sqe);
+    const float t2 = __fmul_rn(c2.hi, sq);
+    float t2e = __fmaf_rn(c2.hi, sq, -t2);
+    t2e = __fmaf_rn(c2.hi, sqe, t2e);
+    t2e = __fmaf_rn(c2.lo, sq, t2e);
+    float q = __fmaf_rn(uh, c5, c4);
+    q = __fmaf_rn(uh, q, c3);
+    const float t3 = __fmul_rn(__fmul_rn(sq, __fmaf_rn(3.f, ul, uh)), q);
+    float a, al, b, bl;
+    fast_two_sum(1.f, t1, a, al);
+    fast_two_sum(a, t2, b, bl);
+    const float lo = __fadd_rn(__fadd_rn(al, bl), __fadd_rn(__fadd_rn(t1e, t2e), t3));
+    dfl P;
+    fast_two_sum(b, lo, P.hi, P.lo);
+    return P;
+}
+
+// theta_k |x|^p for x = (xh, xl), 2^-60 <= xh <= 2^60, from the tables:
+// thm = theta_k 2^(m p) for this k (indexed by m + kPowM), fp = F_j^p,
+// inv = 1/F_j (rounded; the residual of the division is formed exactly)
+__device__ __forceinline__ dfl pow_tab(float xh, float xl, const dfl* thm, const dfl* fp, const float* inv,
+                                       dfl pd, dfl c2, float c3, float c4, float c5, dfl& P) {
+    const int rb = __float_as_int(xh) + (1 << (22 - kPowNBits));   // mantissa rounded to kPowNBits bits
+    const int e = rb >> 23;                                          // biased exponent of 2^m F_j
+    const int j = (rb >> (23 - kPowNBits)) & (kPowN - 1);
+    const float Fm = __int_as_float(rb & ~((1 << (23 - kPowNBits)) - 1));   // 2^m F_j
+    const float g = __int_as_float((254 - e) << 23);                          // 2^-m
+    const float fh = __fmul_rn(__fsub_rn(xh, Fm), g);                        // exact (Sterbenz)
+    const float fl = __fmul_rn(xl, g);
+    const float F = __fmul_rn(Fm, g);
+    const float iv = inv[j];
+    const float uh = __fmul_rn(fh, iv);
+    const float ul = __fmul_rn(__fadd_rn(__fmaf_rn(-uh, F, fh), fl), iv);
+    P = pow_series(uh, ul, pd, c2, c3, c4, c5);
+    return df_mul(thm[e - 127 + kPowM], fp[j]);
+}
+
 struct RhsArgs {
     int n, d, nt, N, m0;          // m0: first point of the launch (point block 0)
     const float2* x;              // n x d design points (double-float)
@@ -196,16 +285,23 @@ struct RhsArgs {
     const float2* w;              // npad: R^-1 (Y - 1 mu_hat)
     float2* RX;                   // [pb][npad][128] or null (mean only)
     float2* MP;                   // [pb][nt][128] partial r'w
+    const float2* tab;            // k_var_rhs_tables' image
+    int tabpow;                   // 1: general p, power-exponential, d <= kPowMaxD
+    double c2;                    // binomial coefficients of (1 + u)^p
+    float c3, c4, c5;
 };
 
 // r for point block blockIdx.y (128 points) and tile row blockIdx.x (128
-// design points) in double-float, each entry as the assembly and the
-// prediction kernel form it: S = sum_k theta_k |dx_k|^p (compensated, in
-// dimension order), r = exp(-S) (times the Matern polynomials).  Thread
-// (r, h) takes design points h, h + 2, ..., so one warp writes 32
+// design points) in double-float: S = sum_k theta_k |dx_k|^p (compensated,
+// in dimension order), r = exp(-S) (times the Matern polynomials).  A
+// general p on the power-exponential family takes the powers from the
+// tables (pow_tab) and sums S as the assembly does (one TwoSum per term
+// on the high words, all terms being >= 0); p = 1, 2, the Matern family and
+// d > kPowMaxD form each term as the assembly's double-float routines do.
+// Thread (r, h) takes design points h, h + 2, ..., so one warp writes 32
 // consecutive points of one design point.  Dynamic shared memory: the
 // points' coordinates [d][128], the design points' [128][d], theta, the
-// exp table.
+// exp table, and with the tables theta_k 2^(m p) [d][kPowMs], F_j^p and 1/F_j.
 __global__ void __launch_bounds__(2 * GP_NB) k_var_rhs(RhsArgs g) {
     extern __shared__ dfl rsm[];
     const int d = g.d;
@@ -213,9 +309,13 @@ __global__ void __launch_bounds__(2 * GP_NB) k_var_rhs(RhsArgs g) {
     dfl* xd = xsT + d * GP_NB;             // [128][d]
     dfl* th = xd + GP_NB * d;              // [d]
     dfl* tab = th + d;                     // [kExpTab]
+    dfl* thm = tab + kExpTab;              // [d][kPowMs]   (tabpow)
+    dfl* fp = thm + d * kPowMs;            // [kPowN]        (tabpow)
+    float* inv = reinterpret_cast<float*>(fp + kPowN);   // [kPowN] (tabpow)
     __shared__ dfl part[2][GP_NB];
     const int J = blockIdx.x, pb = blockIdx.y;
     const int mb = g.m0 + pb * GP_NB;
+    const bool tabpow = g.tabpow != 0;
     for (int q = threadIdx.x; q < GP_NB * d; q += blockDim.x) {
         const int m = q / d, k = q % d;
         xsT[k * GP_NB + m] = (mb + m < g.N) ? df_from_double(g.xs[(size_t)(mb + m) * d + k]) : dfl{0.f, 0.f};
@@ -223,32 +323,77 @@ __global__ void __launch_bounds__(2 * GP_NB) k_var_rhs(RhsArgs g) {
         xd[q] = (i < g.n) ? df_load(g.x + (size_t)i * d + k) : dfl{0.f, 0.f};
     }
     for (int q = threadIdx.x; q < d; q += blockDim.x) th[q] = df_from_double(corr_theta_scale(g.corr) * g.theta[q]);
-    fill_exp2_table(tab);
+    for (int q = threadIdx.x; q < kExpTab; q += blockDim.x) tab[q] = df_load(g.tab + kTabExp + q);
+    if (tabpow) {
+        for (int q = threadIdx.x; q < kPowN; q += blockDim.x) {
+            fp[q] = df_load(g.tab + kTabF + q);
+            inv[q] = reinterpret_cast<const float*>(g.tab + kTabInv)[q];
+        }
+        __syncthreads();                   // th
+        for (int q = threadIdx.x; q < d * kPowMs; q += blockDim.x)
+            thm[q] = df_mul(th[q / kPowMs], df_load(g.tab + kTabTwo + q % kPowMs));
+    }
     __syncthreads();
     const dfl pd = df_from_double(g.p);
     const bool matern = corr_is_matern(g.corr);
     const int pmode = matern ? kPowOne : pow_mode(g.p);
     const dfl third = df_from_double(1.0 / 3.0);
+    const dfl c2 = df_from_double(g.c2);
     const int r = threadIdx.x & (GP_NB - 1), h = threadIdx.x >> 7;
     const bool point_ok = mb + r < g.N;
     float2* out = g.RX ? g.RX + ((size_t)pb * g.nt * GP_NB + (size_t)J * GP_NB) * GP_NB + r : nullptr;
     dfl mean = {0.f, 0.f};
-    for (int c = h; c < GP_NB; c += 2) {
-        const int i = J * GP_NB + c;
-        dfl v = {0.f, 0.f};
-        if (point_ok && i < g.n) {
-            dfl s = {0.f, 0.f}, qp = {1.f, 0.f};
-            for (int k = 0; k < d; ++k) {
-                const dfl dx = df_sub(xsT[k * GP_NB + r], xd[c * d + k]);
-                const dfl hk = df_mul(th[k], df_powabs(dx, pmode, g.p, pd, tab));
-                s = df_add(s, hk);
-                if (matern) qp = df_mul(qp, matern_q_df(hk, g.corr, third));
+    if (tabpow) {
+        for (int c = h; c < GP_NB; c += 2) {
+            const int i = J * GP_NB + c;
+            dfl v = {0.f, 0.f};
+            if (point_ok && i < g.n) {
+                float sh = 0.f, sl = 0.f;
+                for (int k = 0; k < d; ++k) {
+                    dfl dx = df_sub(xsT[k * GP_NB + r], xd[c * d + k]);
+                    if (dx.hi < 0.f) dx = df_neg(dx);
+                    dfl A, P;
+                    if (dx.hi >= 0x1p-60f && dx.hi <= 0x1p60f) {
+                        A = pow_tab(dx.hi, dx.lo, thm + k * kPowMs, fp, inv, pd, c2, g.c3, g.c4, g.c5, P);
+                    } else {
+                        A = df_mul(th[k], df_powabs(dx, kPowGeneral, g.p, pd, tab));   // 0 at dx = 0
+                        P = {1.f, 0.f};
+                    }
+                    // theta_k |dx_k|^p = A P into S
+                    const float ph = __fmul_rn(A.hi, P.hi);
+                    sl = __fadd_rn(sl, __fmaf_rn(A.hi, P.hi, -ph));
+                    sl = __fmaf_rn(A.hi, P.lo, sl);
+                    sl = __fmaf_rn(A.lo, P.hi, sl);
+                    float s2, e2;
+                    two_sum(sh, ph, s2, e2);
+                    sh = s2;
+                    sl = __fadd_rn(sl, e2);
+                }
+                dfl S;
+                fast_two_sum(sh, sl, S.hi, S.lo);
+                v = df_exp_neg(S, tab);
+                mean = df_fma(v, df_load(g.w + i), mean);
             }
-            v = df_exp_neg(s, tab);
-            if (matern) v = df_mul(v, qp);
-            mean = df_fma(v, df_load(g.w + i), mean);
+            if (out) out[(size_t)c * GP_NB] = make_float2(v.hi, v.lo);
         }
-        if (out) out[(size_t)c * GP_NB] = make_float2(v.hi, v.lo);
+    } else {
+        for (int c = h; c < GP_NB; c += 2) {
+            const int i = J * GP_NB + c;
+            dfl v = {0.f, 0.f};
+            if (point_ok && i < g.n) {
+                dfl s = {0.f, 0.f}, qp = {1.f, 0.f};
+                for (int k = 0; k < d; ++k) {
+                    const dfl dx = df_sub(xsT[k * GP_NB + r], xd[c * d + k]);
+                    const dfl hk = df_mul(th[k], df_powabs(dx, pmode, g.p, pd, tab));
+                    s = df_add(s, hk);
+                    if (matern) qp = df_mul(qp, matern_q_df(hk, g.corr, third));
+                }
+                v = df_exp_neg(s, tab);
+                if (matern) v = df_mul(v, qp);
+                mean = df_fma(v, df_load(g.w + i), mean);
+            }
+            if (out) out[(size_t)c * GP_NB] = make_float2(v.hi, v.lo);
+        }
     }
     part[h][r] = mean;
     __syncthreads();
@@ -764,7 +909,16 @@ cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, flo
     r.x = c.x; r.theta = c.theta; r.p = c.p; r.corr = c.corr; r.xs = c.xs; r.w = c.w;
     r.RX = RX;
     r.MP = MP;
-    const size_t rsmem = (size_t)(2 * GP_NB * c.d + c.d + kExpTab) * sizeof(dfl);
+    r.tab = c.rtab;
+    r.tabpow = !corr_is_matern(c.corr) && pow_mode(c.p) == kPowGeneral && c.d <= kPowMaxD;
+    // binomial coefficients C(p, k) of (1 + u)^p
+    const double b2 = c.p * (c.p - 1.0) / 2.0, b3 = b2 * (c.p - 2.0) / 3.0, b4 = b3 * (c.p - 3.0) / 4.0;
+    r.c2 = b2;
+    r.c3 = (float)b3;
+    r.c4 = (float)b4;
+    r.c5 = (float)(b4 * (c.p - 4.0) / 5.0);
+    const size_t rsmem = (size_t)(2 * GP_NB * c.d + c.d + kExpTab) * sizeof(dfl) +
+                         (r.tabpow ? (size_t)(c.d * kPowMs + kPowN) * sizeof(dfl) + kPowN * sizeof(float) : 0);
     static std::atomic<size_t> rattr[kMaxDevices];
     cudaError_t e = raise_smem_limit(k_var_rhs, rsmem, rattr);
     if (e != cudaSuccess) return e;
@@ -772,6 +926,15 @@ cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, flo
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_var_mean<<<(npb * GP_NB + 255) / 256, 256, 0, s>>>(MP, c.nt, c.N, m0, npb, c.sc, c.yhat);
     *kernels = 2;
+    return cudaGetLastError();
+}
+
+size_t var_rhs_tab_bytes() { return ((size_t)kTabLen * sizeof(float2) + 255) & ~(size_t)255; }
+
+// The r kernel's tables (they depend on p alone): 1 kernel.
+cudaError_t launch_var_rhs_tables(const VarCall& c, cudaStream_t s, int* kernels) {
+    k_var_rhs_tables<<<(kTabInv + kPowN + 255) / 256, 256, 0, s>>>(c.p, c.rtab);
+    *kernels = 1;
     return cudaGetLastError();
 }
 

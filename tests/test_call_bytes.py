@@ -114,7 +114,9 @@ def test_serving_admission_uses_the_library_sizes(gp):
 def test_predict_workspace_of_the_tensor_core_path(gp):
     """The default predict path (predict_tc = 1): the slice tables of the
     factor (5 slices of the rows of L left of their diagonal blocks, 7 of each
-    W_J = L_JJ^-1, three npad int arrays), an error flag, per 128-point block
+    W_J = L_JJ^-1, three npad int arrays), an error flag, the r kernel's
+    tables (2^(-j/1024) for j < 1024, 2^(m p) for |m| <= 60, F_j^p and 1/F_j
+    for the 128 points F_j = 1 + j/128), per 128-point block
     of a chunk its r values (npad x 128 double-floats) and partial r'w
     (nt x 128), per CTA of the tensor-core pass the slices of V (5 x 4 nt
     chunks) and of C_J (7 x 4 chunks); a chunk is at most one wave of 152
@@ -123,6 +125,7 @@ def test_predict_workspace_of_the_tensor_core_path(gp):
     values take a second slot."""
     al = lambda v: (v + 255) // 256 * 256
     chunk = 128 * 32 * 2
+    rtab = al((1024 + 121 + 128) * 8 + 128 * 4)
     for n, d in ((1, 2), (300, 3), (4000, 6), (16384, 10)):
         nt = (n + 127) // 128
         npad = nt * 128
@@ -134,5 +137,5 @@ def test_predict_workspace_of_the_tensor_core_path(gp):
             C = min(blocks, 152)
             rem = blocks % C if blocks > C else 0
             slots = 2 if rem > 0 and (blocks - rem) // C >= 2 else 1
-            want = tables + 256 + slots * C * per_block + C * per_cta + rem * (per_block + per_cta)
+            want = tables + 256 + rtab + slots * C * per_block + C * per_cta + rem * (per_block + per_cta)
             assert gp.call_bytes("predict", n, d, N) == want, (n, N)
