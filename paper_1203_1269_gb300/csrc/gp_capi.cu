@@ -504,7 +504,7 @@ int fp64_nll_batch(gp_ctx* ctx, int n, int d, const double* x, const double* y, 
         rc = run_factor_f64(ctx, b);
         if (rc) return rc;
         const size_t zs = z_bytes / sizeof(double);
-        PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+        PhaseScope ps(ctx, GP_PHASE_SOLVE, gp::solve_f64_launches(b.nt, false) + 1);
         GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
         GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, mu_hat + c0, sigma2_hat + c0,
                                          logdet ? logdet + c0 : nullptr, status + c0, ctx->stream));
@@ -814,7 +814,7 @@ int model_from_fp64(gp_ctx* ctx, gp_model* m, const LastChunk& lc, int t, const 
         return fail(ctx, GP_ECUDA, "copy of the factor into the model failed");
     gp::Batch b{};
     b.n = m->n; b.nt = m->nt; b.count = 1; b.st = m->st; b.A = m->L; b.inst_stride = gp::packed_elems(m->n);
-    PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+    PhaseScope ps(ctx, GP_PHASE_SOLVE, 1 + gp::solve_f64_launches(b.nt, true));
     if (gp::launch_fit_finish(b, m->Z, 2 * npad, m->scalars, s) ||
         gp::launch_backward_solve(b, m->Z, 2 * npad, 1, s))
         return fail(ctx, GP_ECUDA, "solve launch failed");
@@ -1297,7 +1297,7 @@ int gp_nll_grad_batch(gp_ctx* ctx, int n, int d, const double* x, const double* 
         if (rc) return rc;
         const size_t zs = z_bytes / sizeof(double);
         {
-            PhaseScope ps(ctx, GP_PHASE_SOLVE, 2);
+            PhaseScope ps(ctx, GP_PHASE_SOLVE, gp::solve_f64_launches(b.nt, false) + 1);
             GP_CUDA(ctx, gp::launch_forward_solve(b, Z, zs, ctx->stream));
             GP_CUDA(ctx, gp::launch_finalize(b, Z, zs, nll + c0, sc, sc + Tc, sc + 2 * Tc, status + c0,
                                              ctx->stream));
@@ -1607,7 +1607,8 @@ int gp_fit(gp_ctx* ctx, int n, int d, const double* x, const double* y, const do
     rc = run_factor_f64(ctx, b);
     if (rc) return model_discard(ctx, m, rc);
     {
-        PhaseScope ps(ctx, GP_PHASE_SOLVE, 4);
+        PhaseScope ps(ctx, GP_PHASE_SOLVE,
+                      gp::solve_f64_launches(b.nt, false) + 2 + gp::solve_f64_launches(b.nt, true));
         if (gp::launch_forward_solve(b, m->Z, (size_t)2 * npad, ctx->stream) ||
             gp::launch_finalize(b, m->Z, (size_t)2 * npad, m->scalars + 0, m->scalars + 1, m->scalars + 2,
                                 m->scalars + 3, m->status, ctx->stream) ||

@@ -196,6 +196,8 @@ cudaError_t launch_fit_finish(const Batch& b, double* Z, size_t z_stride, double
                               cudaStream_t s);
 cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t z_stride, int col,
                                   cudaStream_t s);
+// kernels that launch_forward_solve (backward = false) or launch_backward_solve launch
+int solve_f64_launches(int nt, bool backward);
 // Kriging with the variance's solve on the tensor cores (k_var_tc.cu).
 struct VarTables {
     __nv_bfloat16* LS;            // slices of the rows of L left of the diagonal blocks

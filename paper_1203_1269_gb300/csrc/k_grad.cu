@@ -382,7 +382,7 @@ cudaError_t launch_grad(const Batch& b, double* Z, size_t zs, double* X, double*
     ++k;
     cudaError_t e = launch_backward_solve(b, Z, zs, 1, s);   // w = L^-T (b - mu a), double factor
     if (e != cudaSuccess) return e;
-    ++k;
+    k += solve_f64_launches(nt, true);
     // from here on the factor, X and R^-1 are double-float tiles
     const size_t elems = (size_t)ntiles * GP_TILE_ELEMS;
     k_factor_to_df<<<dim3(64, b.count), kThreads, 0, s>>>(b, elems);

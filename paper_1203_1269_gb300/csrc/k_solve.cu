@@ -9,9 +9,9 @@
 // backward: w = L^-T z  (for the kriging weights R^-1 (Y - 1 mu_hat))
 //
 // Z holds, per instance, two columns of length npad = nt*NB: Z[0..npad) and
-// Z[npad..2 npad).  Each instance is solved by one CTA, tile row by tile
-// row; reductions run in a fixed order so results do not depend on what
-// else is in the batch.
+// Z[npad..2 npad).  The solves are tile-parallel (below); every reduction
+// runs in a fixed order, so results do not depend on what else is in the
+// batch.
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -42,102 +42,152 @@ __device__ double block_sum(double v, double* red) {
     return s;
 }
 
-// Forward solve of both right-hand sides for one instance per CTA.
-__global__ void __launch_bounds__(kThreads) k_forward(Batch b, double* Z, size_t zs) {
-    __shared__ double xj[2][GP_NB];
-    __shared__ double part[2][2][GP_NB];
-    __shared__ double rhs[2][GP_NB];
-    const int t = blockIdx.x;
-    if (b.st[t].status != GP_OK) return;
-    const int nt = b.nt, n = b.n;
-    const int npad = nt * GP_NB;
-    double* z0 = Z + (size_t)t * zs;
-    double* z1 = z0 + npad;
-    const int r = threadIdx.x % GP_NB;
-    const int h = threadIdx.x / GP_NB;
-    for (int I = 0; I < nt; ++I) {
-        const int gi = I * GP_NB + r;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int Jt = 0; Jt < I; ++Jt) {
-            __syncthreads();
-            if (h == 0) xj[0][r] = z0[Jt * GP_NB + r];
-            else        xj[1][r] = z1[Jt * GP_NB + r];
-            __syncthreads();
-            const double* L = tile_ptr(b, t, I, Jt);
-            // columns c of parity h; thread reads row r of column c (coalesced)
-            for (int c = h; c < GP_NB; c += 2) {
-                const double l = __ldg(L + c * GP_NB + r);
-                acc0 = fma(l, xj[0][c], acc0);
-                acc1 = fma(l, xj[1][c], acc1);
-            }
-        }
-        part[h][0][r] = acc0;
-        part[h][1][r] = acc1;
-        __syncthreads();
-        if (h == 0) {
-            const double b0 = (gi < n) ? 1.0 : 0.0;
-            const double b1 = (gi < n) ? b.y[gi] : 0.0;
-            rhs[0][r] = b0 - (part[0][0][r] + part[1][0][r]);
-            rhs[1][r] = b1 - (part[0][1][r] + part[1][1][r]);
-        }
-        __syncthreads();
-        // triangular solve with the diagonal tile (lower part holds L_II)
-        const double* D = tile_ptr(b, t, I, I);
-        for (int c = 0; c < GP_NB; ++c) {
-            const double inv = 1.0 / __ldg(D + c * GP_NB + c);
-            const double x0 = rhs[0][c] * inv;
-            const double x1 = rhs[1][c] * inv;
-            __syncthreads();
-            if (threadIdx.x < GP_NB && r > c) {
-                const double l = __ldg(D + c * GP_NB + r);
-                rhs[0][r] = fma(-l, x0, rhs[0][r]);
-                rhs[1][r] = fma(-l, x1, rhs[1][r]);
-            }
-            if (threadIdx.x == 0) { rhs[0][c] = x0; rhs[1][c] = x1; }
-            __syncthreads();
-        }
-        if (h == 0) z0[I * GP_NB + r] = rhs[0][r];
-        else        z1[I * GP_NB + r] = rhs[1][r];
-        __syncthreads();
+// The triangular solves are tile-parallel, one launch per block column (so
+// that a single instance, as gp_fit has, still spreads its factor over
+// every SM): a diagonal step per instance solves with the diagonal tile,
+// staged in shared memory, and a tile step subtracts the products of the
+// next tiles from the right-hand sides in Z, every tile of the block column
+// at once, one CTA per tile.  A block's right-hand side takes the products
+// in block-column order, so the results are the same bits at any batch size.
+constexpr int kTileThreads = 1024;
+constexpr int kDiagStride = GP_NB + 1;        // staged diagonal tile: D[c * kDiagStride + r] = L_rc
+constexpr size_t kDiagSmem = (size_t)GP_NB * kDiagStride * sizeof(double);
+
+__device__ __forceinline__ void stage_diag(const double* L, double* D) {
+    for (int e = threadIdx.x; e < GP_TILE_ELEMS; e += blockDim.x) D[(e >> 7) * kDiagStride + (e & 127)] = __ldg(L + e);
+}
+
+// Z <- [1 Y] (padded rows zero), the forward solve's right-hand sides
+__global__ void k_rhs_f64(Batch b, double* Z, size_t zs) {
+    const int npad = b.nt * GP_NB;
+    double* z0 = Z + (size_t)blockIdx.y * zs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+        const bool in = i < b.n;
+        z0[i] = in ? 1.0 : 0.0;
+        z0[npad + i] = in ? b.y[i] : 0.0;
     }
 }
 
-// Backward solve L^T w = z for column `col` of Z (in place), one CTA per
-// instance.  Warp w reduces tile columns w, w+8, ... (coalesced reads).
-__global__ void __launch_bounds__(kThreads) k_backward(Batch b, double* Z, size_t zs, int col) {
-    __shared__ double wk[GP_NB];
-    __shared__ double rhs[GP_NB];
+// Forward, block J, one instance per CTA (256 threads: thread (r, k) owns
+// row r of right-hand side k): Z_J holds [1 Y]_J less the products of the
+// tiles left of it; L_JJ z = Z_J by columns, x_c = v_c (1 / L_cc), then
+// v_r -= L_rc x_c for r > c.  Row c's owner publishes x_c before the one
+// barrier of step c; every other value stays in its owner's register.
+__global__ void __launch_bounds__(2 * GP_NB) k_fwd_diag_f64(Batch b, double* Z, size_t zs, int J) {
+    extern __shared__ double D[];
+    __shared__ double xc[2][GP_NB];
+    __shared__ double inv[GP_NB];
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
-    const int nt = b.nt;
-    const int npad = nt * GP_NB;
-    double* z = Z + (size_t)t * zs + (size_t)col * npad;
+    stage_diag(tile_ptr(b, t, J, J), D);
+    const int r = threadIdx.x & (GP_NB - 1), k = threadIdx.x >> 7;
+    double* z = Z + (size_t)t * zs + (size_t)k * b.nt * GP_NB + (size_t)J * GP_NB;
+    double v = z[r];
+    __syncthreads();
+    if (k == 0) inv[r] = 1.0 / D[r * kDiagStride + r];
+    __syncthreads();
+    for (int c = 0; c < GP_NB; ++c) {
+        if (r == c) {
+            v *= inv[c];
+            xc[k][c] = v;
+        }
+        __syncthreads();
+        if (r > c) v = fma(-D[c * kDiagStride + r], xc[k][c], v);
+    }
+    z[r] = v;
+}
+
+// Forward, tiles (I, J), I > J, one CTA each (1024 threads: thread (r, g)
+// takes columns 16 g .. 16 g + 15 of row r): Z_I -= L_IJ z_J, the 8 column
+// parts added in order.
+__global__ void __launch_bounds__(kTileThreads) k_fwd_tiles_f64(Batch b, double* Z, size_t zs, int J) {
+    __shared__ double xs[2][GP_NB];
+    __shared__ double part[8][2][GP_NB];
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int I = J + 1 + blockIdx.x;
+    const int npad = b.nt * GP_NB;
+    double* z0 = Z + (size_t)t * zs;
+    const int tid = threadIdx.x;
+    if (tid < 2 * GP_NB) xs[tid >> 7][tid & 127] = z0[(size_t)(tid >> 7) * npad + (size_t)J * GP_NB + (tid & 127)];
+    __syncthreads();
+    const double* L = tile_ptr(b, t, I, J);
+    const int r = tid & (GP_NB - 1), g = tid >> 7;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int c = 16 * g; c < 16 * g + 16; ++c) {
+        const double l = __ldg(L + (size_t)c * GP_NB + r);
+        a0 = fma(l, xs[0][c], a0);
+        a1 = fma(l, xs[1][c], a1);
+    }
+    part[g][0][r] = a0;
+    part[g][1][r] = a1;
+    __syncthreads();
+    if (tid < 2 * GP_NB) {
+        const int k = tid >> 7;
+        double s = part[0][k][r];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) s += part[q][k][r];
+        double* zi = z0 + (size_t)k * npad + (size_t)I * GP_NB + r;
+        *zi -= s;
+    }
+}
+
+// Backward, block I of column col, one instance per CTA (128 threads, one
+// row each): Z_I holds z_I less the products of the tiles below it;
+// L_II^T w = Z_I from the last column back, x_c = v_c (1 / L_cc), then
+// v_r -= L_cr x_c for r < c.
+__global__ void __launch_bounds__(GP_NB) k_bwd_diag_f64(Batch b, double* Z, size_t zs, int col, int I) {
+    extern __shared__ double D[];
+    __shared__ double xc[GP_NB];
+    __shared__ double inv[GP_NB];
+    const int t = blockIdx.x;
+    if (b.st[t].status != GP_OK) return;
+    stage_diag(tile_ptr(b, t, I, I), D);
+    const int r = threadIdx.x;
+    double* z = Z + (size_t)t * zs + (size_t)col * b.nt * GP_NB + (size_t)I * GP_NB;
+    double v = z[r];
+    __syncthreads();
+    inv[r] = 1.0 / D[r * kDiagStride + r];
+    __syncthreads();
+    for (int c = GP_NB - 1; c >= 0; --c) {
+        if (r == c) {
+            v *= inv[c];
+            xc[c] = v;
+        }
+        __syncthreads();
+        if (r < c) v = fma(-D[r * kDiagStride + c], xc[c], v);
+    }
+    z[r] = v;
+}
+
+// Backward, tiles (I, K), K < I, one CTA each (32 warps: warp w takes
+// columns w, w + 32, w + 64, w + 96, lane l rows l, l + 32, l + 64, l + 96,
+// then a shuffle sum): Z_K -= L_IK^T w_I.
+__global__ void __launch_bounds__(kTileThreads) k_bwd_tiles_f64(Batch b, double* Z, size_t zs, int col, int I) {
+    __shared__ double ws[GP_NB];
+    const int t = blockIdx.y;
+    if (b.st[t].status != GP_OK) return;
+    const int K = blockIdx.x;
+    double* z = Z + (size_t)t * zs + (size_t)col * b.nt * GP_NB;
+    if (threadIdx.x < GP_NB) ws[threadIdx.x] = z[(size_t)I * GP_NB + threadIdx.x];
+    __syncthreads();
+    const double* L = tile_ptr(b, t, I, K);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int I = nt - 1; I >= 0; --I) {
-        if (threadIdx.x < GP_NB) rhs[threadIdx.x] = z[I * GP_NB + threadIdx.x];
-        __syncthreads();
-        for (int K = I + 1; K < nt; ++K) {
-            if (threadIdx.x < GP_NB) wk[threadIdx.x] = z[K * GP_NB + threadIdx.x];
-            __syncthreads();
-            const double* L = tile_ptr(b, t, K, I);   // rows of block K, columns of block I
-            for (int c = w; c < GP_NB; c += kThreads / 32) {
-                double s = 0.0;
-                for (int k = lane; k < GP_NB; k += 32) s = fma(__ldg(L + c * GP_NB + k), wk[k], s);
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (lane == 0) rhs[c] -= s;
-            }
-            __syncthreads();
-        }
-        const double* D = tile_ptr(b, t, I, I);
-        for (int c = GP_NB - 1; c >= 0; --c) {
-            const double x = rhs[c] / __ldg(D + c * GP_NB + c);
-            __syncthreads();
-            if (threadIdx.x < c) rhs[threadIdx.x] = fma(-__ldg(D + threadIdx.x * GP_NB + c), x, rhs[threadIdx.x]);
-            if (threadIdx.x == 0) rhs[c] = x;
-            __syncthreads();
-        }
-        if (threadIdx.x < GP_NB) z[I * GP_NB + threadIdx.x] = rhs[threadIdx.x];
-        __syncthreads();
+    double s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double* Lc = L + (size_t)(w + 32 * q) * GP_NB;
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a = fma(__ldg(Lc + lane + 32 * j), ws[lane + 32 * j], a);
+        s[q] = a;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = s[q];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) z[(size_t)K * GP_NB + w + 32 * q] -= a;
     }
 }
 
@@ -220,13 +270,29 @@ cudaError_t launch_fit_finish(const Batch& b, double* Z, size_t zs, double* scal
     return cudaGetLastError();
 }
 
+int solve_f64_launches(int nt, bool backward) { return backward ? 2 * nt - 1 : 2 * nt; }
+
 cudaError_t launch_forward_solve(const Batch& b, double* Z, size_t zs, cudaStream_t s) {
-    k_forward<<<b.count, kThreads, 0, s>>>(b, Z, zs);
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_fwd_diag_f64, kDiagSmem, attr);
+    if (e != cudaSuccess) return e;
+    const int nt = b.nt;
+    k_rhs_f64<<<dim3((nt * GP_NB + kThreads - 1) / kThreads, b.count), kThreads, 0, s>>>(b, Z, zs);
+    for (int J = 0; J < nt; ++J) {
+        k_fwd_diag_f64<<<b.count, 2 * GP_NB, kDiagSmem, s>>>(b, Z, zs, J);
+        if (J + 1 < nt) k_fwd_tiles_f64<<<dim3(nt - 1 - J, b.count), kTileThreads, 0, s>>>(b, Z, zs, J);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_backward_solve(const Batch& b, double* Z, size_t zs, int col, cudaStream_t s) {
-    k_backward<<<b.count, kThreads, 0, s>>>(b, Z, zs, col);
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_bwd_diag_f64, kDiagSmem, attr);
+    if (e != cudaSuccess) return e;
+    for (int I = b.nt - 1; I >= 0; --I) {
+        k_bwd_diag_f64<<<b.count, GP_NB, kDiagSmem, s>>>(b, Z, zs, col, I);
+        if (I > 0) k_bwd_tiles_f64<<<dim3(I, b.count), kTileThreads, 0, s>>>(b, Z, zs, col, I);
+    }
     return cudaGetLastError();
 }
 
