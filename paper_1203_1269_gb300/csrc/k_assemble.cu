@@ -13,6 +13,8 @@
 // The double-float variant (split-precision path) keeps everything on the
 // FP32 pipes: on this GPU one FP64 pow costs as much as thousands of FP32
 // instructions, so the powers are exp(p ln|dx|) in double-float too.
+#include <cmath>
+
 #include "corr.cuh"
 #include "df.cuh"
 #include "gp_internal.cuh"
@@ -34,6 +36,57 @@ __device__ __forceinline__ double powabs(double diff, double p) {
     if (p == 2.0) return a * a;
     if (p == 1.0) return a;
     return (a == 0.0) ? 0.0 : pow(a, p);
+}
+
+// |dx|^p in double for a general p without a pow per term (the reduction
+// of P. T. P. Tang's table-driven logarithm, ACM TOMS 16 (1990), applied to
+// the power): a = 2^m F_j (1 + u) with F_j = 1 + j/64 the table point
+// nearest the mantissa (|u| <= 2^-7), so that
+//   a^p = [2^(m p) F_j^p] (1 + u)^p,
+// the bracket as a double-double product of two tables computed on the host
+// in long double, (1 + u)^p - 1 = p u + c2 u^2 + ... + c7 u^7 (the u^8 term
+// is below 2^-62), and one rounding at the end: a^p = A_hi + (A_hi t +
+// A_lo).  m outside [-60, 4] takes pow.
+constexpr int kP64NBits = 6;
+constexpr int kP64N = 1 << kP64NBits;
+constexpr int kP64Mlo = -60, kP64Mhi = 4;
+constexpr int kP64Ms = kP64Mhi - kP64Mlo + 1;
+struct PowTab64 {
+    int on;                       // general p on the power-exponential family
+    double c[8];                  // c[k] = C(p, k), k = 1 .. 7
+    double inv[kP64N];            // 1 / F_j (rounded: the division's residual is formed exactly)
+    double2 two[kP64Ms];          // 2^(m p), m = kP64Mlo .. kP64Mhi, as (hi, lo)
+    double2 f[kP64N];             // F_j^p as (hi, lo)
+};
+static_assert(sizeof(PowTab64) + 512 < 4096, "kernel parameters");
+
+__device__ __forceinline__ double pow_tab64(double a, double p, const PowTab64& t) {
+    const long long rb = __double_as_longlong(a) + (1LL << (51 - kP64NBits));   // a > 0
+    const int e = (int)(rb >> 52);
+    if (e - 1023 < kP64Mlo || e - 1023 > kP64Mhi) return pow(a, p);
+    const int j = (int)(rb >> (52 - kP64NBits)) & (kP64N - 1);
+    const double Fm = __longlong_as_double(rb & ~((1LL << (52 - kP64NBits)) - 1));   // 2^m F_j
+    const double g = __longlong_as_double((long long)(2046 - e) << 52);              // 2^-m
+    const double fh = (a - Fm) * g;                                                   // exact
+    const double F = Fm * g;
+    const double iv = t.inv[j];
+    const double uh = fh * iv;
+    const double ul = fma(-uh, F, fh) * iv;
+    double q = fma(uh, t.c[7], t.c[6]);
+    q = fma(uh, q, t.c[5]);
+    q = fma(uh, q, t.c[4]);
+    q = fma(uh, q, t.c[3]);
+    q = fma(uh, q, t.c[2]);
+    const double tt = fma(t.c[1], uh, fma(t.c[1], ul, uh * uh * q));
+    const double2 T = t.two[e - 1023 - kP64Mlo], P = t.f[j];
+    const double ah = T.x * P.x;
+    const double al = fma(T.x, P.x, -ah) + fma(T.x, P.y, T.y * P.x);
+    return ah + fma(ah, tt, al);
+}
+
+__device__ __forceinline__ double powabs_t(double diff, double p, const PowTab64& t) {
+    const double a = fabs(diff);
+    return (a == 0.0) ? 0.0 : pow_tab64(a, p, t);
 }
 
 // |dx|^p as double-float: p = 2 and p = 1 exactly in double (one FP64
@@ -79,12 +132,17 @@ __global__ void k_validate_theta(Batch b) {
     b.st[t] = s;
 }
 
-// grid.x = packed tiles * kSplit, grid.y = candidate groups; DB = bound on d
-template <int DB>
+// grid.x = packed tiles * kSplit, grid.y = candidate groups; DB = bound on d;
+// TAB: a general p on the power-exponential family, powers by pow_tab64
+template <int DB, bool TAB>
 __global__ void __launch_bounds__(kThreads)
-k_assemble_tiles(Batch b, int group) {
+k_assemble_tiles(Batch b, int group, PowTab64 ptab) {
     __shared__ double xs_r[GP_NB * DB];
     __shared__ double xs_c[kCols * DB];
+    __shared__ PowTab64 pt;
+    if (TAB)
+        for (int q = threadIdx.x; q < (int)(sizeof(PowTab64) / sizeof(int)); q += kThreads)
+            reinterpret_cast<int*>(&pt)[q] = reinterpret_cast<const int*>(&ptab)[q];
     const int nt = b.nt, n = b.n, d = b.d;
     const int tile_lin = blockIdx.x / kSplit;
     const int part = blockIdx.x % kSplit;
@@ -132,7 +190,8 @@ k_assemble_tiles(Batch b, int group) {
 #pragma unroll
         for (int k = 0; k < DB; ++k)
             D[k] = (k < d && !pad) ? (matern ? fabs(xs_r[r * DB + k] - xs_c[c * DB + k])
-                                             : powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p))
+                                             : (TAB ? powabs_t(xs_r[r * DB + k] - xs_c[c * DB + k], b.p, pt)
+                                                    : powabs(xs_r[r * DB + k] - xs_c[c * DB + k], b.p)))
                                    : 0.0;
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
@@ -371,6 +430,35 @@ static cudaError_t launch_asm_df(dim3 grid, size_t smem, cudaStream_t s, const B
     return cudaGetLastError();
 }
 
+// The tables of pow_tab64 for p, in long double (64 significant bits or
+// more), rounded to double-double; the last p's tables are kept per thread.
+static void pow_tab64_fill(double p, PowTab64& t) {
+    static thread_local double last_p = -1.0;
+    static thread_local PowTab64 last{};
+    if (p != last_p) {
+        last = PowTab64{};
+        last.on = 1;
+        long double c = 1.0L;
+        for (int k = 1; k < 8; ++k) {
+            c = c * ((long double)p - (long double)(k - 1)) / (long double)k;
+            last.c[k] = (double)c;
+        }
+        last.c[0] = 1.0;
+        auto split = [](long double v) {
+            const double h = (double)v;
+            return make_double2(h, (double)(v - (long double)h));
+        };
+        for (int j = 0; j < kP64N; ++j) {
+            const long double F = 1.0L + (long double)j / (long double)kP64N;
+            last.inv[j] = (double)(1.0L / F);
+            last.f[j] = split(powl(F, (long double)p));
+        }
+        for (int m = kP64Mlo; m <= kP64Mhi; ++m) last.two[m - kP64Mlo] = split(exp2l((long double)m * (long double)p));
+        last_p = p;
+    }
+    t = last;
+}
+
 cudaError_t launch_validate_theta(const Batch& b, cudaStream_t s) {
     k_validate_theta<<<(b.count + 127) / 128, 128, 0, s>>>(b);
     return cudaGetLastError();
@@ -423,12 +511,18 @@ cudaError_t launch_assemble_tiles(const Batch& b, cudaStream_t s) {
         }
         return e;
     }
+    PowTab64 pt{};
+    if (b.d <= 16 && !corr_is_matern(b.corr) && pow_mode(b.p) == kPowGeneral) pow_tab64_fill(b.p, pt);
+    const bool tab = pt.on != 0;
     if (b.d <= 4)
-        k_assemble_tiles<4><<<grid, kThreads, 0, s>>>(b, group);
+        tab ? k_assemble_tiles<4, true><<<grid, kThreads, 0, s>>>(b, group, pt)
+            : k_assemble_tiles<4, false><<<grid, kThreads, 0, s>>>(b, group, pt);
     else if (b.d <= 8)
-        k_assemble_tiles<8><<<grid, kThreads, 0, s>>>(b, group);
+        tab ? k_assemble_tiles<8, true><<<grid, kThreads, 0, s>>>(b, group, pt)
+            : k_assemble_tiles<8, false><<<grid, kThreads, 0, s>>>(b, group, pt);
     else if (b.d <= 16)
-        k_assemble_tiles<16><<<grid, kThreads, 0, s>>>(b, group);
+        tab ? k_assemble_tiles<16, true><<<grid, kThreads, 0, s>>>(b, group, pt)
+            : k_assemble_tiles<16, false><<<grid, kThreads, 0, s>>>(b, group, pt);
     else
         k_assemble_tiles_generic<<<grid, kThreads, 0, s>>>(b, group);
     return cudaGetLastError();
