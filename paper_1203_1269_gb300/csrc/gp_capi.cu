@@ -36,6 +36,9 @@ struct gp_ctx {
     // (forked from and joined back to it with the two events)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the FP64 factorisation's look-ahead: a high-priority stream
+    cudaStream_t la = nullptr;
+    cudaEvent_t ev_la0 = nullptr, ev_la1 = nullptr;
 };
 
 struct gp_model {
@@ -84,10 +87,12 @@ struct PhaseScope {
     int phase;
     int kernels;
     cudaEvent_t e0 = nullptr;
-    PhaseScope(gp_ctx* c, int ph, int k) : ctx(c), phase(ph), kernels(k) {
+    cudaStream_t st;
+    PhaseScope(gp_ctx* c, int ph, int k, cudaStream_t on = nullptr)
+        : ctx(c), phase(ph), kernels(k), st(on ? on : c->stream) {
         if (ctx->timing) {
             e0 = take_event(ctx);
-            cudaEventRecord(e0, ctx->stream);
+            cudaEventRecord(e0, st);
         }
     }
     ~PhaseScope() {
@@ -95,7 +100,7 @@ struct PhaseScope {
         ctx->phase_launches[phase] += kernels;
         if (ctx->timing) {
             cudaEvent_t e1 = take_event(ctx);
-            cudaEventRecord(e1, ctx->stream);
+            cudaEventRecord(e1, st);
             ctx->ev_open.push_back({phase, {e0, e1}});
         }
     }
@@ -183,8 +188,66 @@ bool chunk_batch(const gp_options& opt, size_t budget, size_t held, size_t per, 
     return true;
 }
 
-// Factor and solve `b.count` instances already assembled in b.A.
+int ensure_la(gp_ctx* ctx) {
+    if (ctx->la) return GP_OK;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&ctx->la, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_la0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_la1, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GP_ECUDA, "creating the look-ahead stream failed");
+    }
+    return GP_OK;
+}
+
+// Batches of at most this many instances factor with a look-ahead.
+constexpr int kLookaheadMax = 16;
+
+// Factor `b.count` instances already assembled in b.A.  A small batch (a
+// fit's one instance) cannot fill the GPU with the serial diagonal step and
+// the panel of a block column, so it looks ahead by one: after the update
+// of column J + 1 (its tiles only), the diagonal step and panel of J + 1 run
+// on a high-priority stream beside the rest of update J (their CTAs fit on
+// an SM beside an update CTA).  Every tile still takes its updates in
+// block-column order on the main stream: the same bits as without.
 int run_factor_f64(gp_ctx* ctx, const gp::Batch& b) {
+    const int nt = b.nt;
+    if (b.count <= kLookaheadMax && nt > 1) {
+        int rc = ensure_la(ctx);
+        if (rc) return rc;
+        {
+            PhaseScope ps(ctx, GP_PHASE_POTRF, 1);
+            GP_CUDA(ctx, gp::launch_potrf_f64(b, 0, ctx->stream));
+        }
+        {
+            PhaseScope ps(ctx, GP_PHASE_TRSM, 1);
+            GP_CUDA(ctx, gp::launch_trsm_f64(b, 0, ctx->stream));
+        }
+        for (int J = 0; J + 1 < nt; ++J) {
+            {
+                PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+                GP_CUDA(ctx, gp::launch_update_f64(b, J, ctx->stream, gp::kUpdateColumn));
+            }
+            GP_CUDA(ctx, cudaEventRecord(ctx->ev_la0, ctx->stream));
+            GP_CUDA(ctx, cudaStreamWaitEvent(ctx->la, ctx->ev_la0, 0));
+            {
+                PhaseScope ps(ctx, GP_PHASE_POTRF, 1, ctx->la);
+                GP_CUDA(ctx, gp::launch_potrf_f64(b, J + 1, ctx->la));
+            }
+            if (J + 2 < nt) {
+                PhaseScope ps(ctx, GP_PHASE_TRSM, 1, ctx->la);
+                GP_CUDA(ctx, gp::launch_trsm_f64(b, J + 1, ctx->la));
+            }
+            GP_CUDA(ctx, cudaEventRecord(ctx->ev_la1, ctx->la));
+            if (J + 2 < nt) {
+                PhaseScope ps(ctx, GP_PHASE_UPDATE, 1);
+                GP_CUDA(ctx, gp::launch_update_f64(b, J, ctx->stream, gp::kUpdateRest));
+            }
+            GP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_la1, 0));
+        }
+        return GP_OK;
+    }
     for (int J = 0; J < b.nt; ++J) {
         const int more = (J + 1 < b.nt) ? 1 : 0;
         {
@@ -1078,6 +1141,12 @@ void gp_destroy(gp_ctx* ctx) {
         cudaStreamDestroy(ctx->aux);
         cudaEventDestroy(ctx->ev_fork);
         cudaEventDestroy(ctx->ev_join);
+    }
+    if (ctx->la) {
+        cudaStreamSynchronize(ctx->la);
+        cudaStreamDestroy(ctx->la);
+        cudaEventDestroy(ctx->ev_la0);
+        cudaEventDestroy(ctx->ev_la1);
     }
     delete ctx;
 }

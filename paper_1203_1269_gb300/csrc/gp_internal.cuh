@@ -187,7 +187,9 @@ cudaError_t launch_assemble_dense(int n, int d, const double* x, const double* t
                                   double delta, double* R, cudaStream_t s);
 cudaError_t launch_potrf_f64(const Batch& b, int J, cudaStream_t s);
 cudaError_t launch_trsm_f64(const Batch& b, int J, cudaStream_t s);
-cudaError_t launch_update_f64(const Batch& b, int J, cudaStream_t s);
+// the tiles of a trailing update: all, column J + 1 only, or the others
+enum : int { kUpdateAll = 0, kUpdateColumn = 1, kUpdateRest = 2 };
+cudaError_t launch_update_f64(const Batch& b, int J, cudaStream_t s, int which = kUpdateAll);
 cudaError_t launch_forward_solve(const Batch& b, double* Z, size_t z_stride, cudaStream_t s);
 cudaError_t launch_finalize(const Batch& b, const double* Z, size_t z_stride, double* nll,
                             double* mu, double* sigma2, double* logdet, int* status,

@@ -101,18 +101,29 @@ __global__ void __launch_bounds__(kThreads) k_trsm_f64(Batch b, int J) {
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) Aij[q] = s[q];
 }
 
-// A_IK -= L_IJ L_KJ^T over the trailing lower triangle of tiles.
-// grid.x = m(m+1)/2 with m = nt - J - 1, grid.y = instances.
+// A_IK -= L_IJ L_KJ^T over the trailing lower triangle of tiles (which =
+// kUpdateAll, grid.x = m(m+1)/2 with m = nt - J - 1), its first column K =
+// J + 1 (kUpdateColumn, grid.x = m) or the rest (kUpdateRest, grid.x =
+// m(m-1)/2); grid.y = instances.
 // Thread (tx, ty) of a 16 x 16 layout owns rows tx + 16i and columns
 // ty + 16j (i, j < 8) of the 128 x 128 tile.
-__global__ void __launch_bounds__(kThreads) k_update_f64(Batch b, int J) {
+__global__ void __launch_bounds__(kThreads) k_update_f64(Batch b, int J, int which) {
     constexpr int KC = 16;
     __shared__ double As[KC][GP_NB];
     __shared__ double Bs[KC][GP_NB];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     int ii, kk;
-    tri_decode(blockIdx.x, ii, kk);
+    if (which == kUpdateColumn) {
+        ii = blockIdx.x;
+        kk = 0;
+    } else {
+        tri_decode(blockIdx.x, ii, kk);
+        if (which == kUpdateRest) {
+            ++ii;
+            ++kk;
+        }
+    }
     const int I = J + 1 + ii, K = J + 1 + kk;
     const double* __restrict__ Lij = inst_tile(b, t, I, J);
     const double* __restrict__ Lkj = inst_tile(b, t, K, J);
@@ -177,10 +188,11 @@ cudaError_t launch_trsm_f64(const Batch& b, int J, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_f64(const Batch& b, int J, cudaStream_t s) {
+cudaError_t launch_update_f64(const Batch& b, int J, cudaStream_t s, int which) {
     const int m = b.nt - J - 1;
-    if (m <= 0) return cudaSuccess;
-    k_update_f64<<<dim3(m * (m + 1) / 2, b.count), kThreads, 0, s>>>(b, J);
+    const int tiles = which == kUpdateColumn ? m : (which == kUpdateRest ? m * (m - 1) / 2 : m * (m + 1) / 2);
+    if (tiles <= 0) return cudaSuccess;
+    k_update_f64<<<dim3(tiles, b.count), kThreads, 0, s>>>(b, J, which);
     return cudaGetLastError();
 }
 

@@ -149,3 +149,29 @@ def test_concurrent_contexts_with_different_shapes():
     for t in threads:
         t.join()
     assert not errors, errors
+
+
+def test_fp64_lookahead_gives_the_same_bits(ctx):
+    """Batches of up to 16 instances factor in double with a look-ahead (the
+    next block column's diagonal step and panel on a second stream beside the
+    rest of the update); larger ones without.  Every tile takes its updates in
+    the same order, so 20 candidates in one batch and the same candidates one
+    at a time (and in a batch of 3) give the same bits; gp_fit's model holds
+    them too.  n = 700 (6 block columns, a ragged last one), p = 1.9."""
+    g = np.random.default_rng(515)
+    n, d = 700, 5
+    x = inputs.random_lhd(g, n, d)
+    y = inputs.y_sinsum(x)
+    th = inputs.log_uniform_thetas(g, 20, d, lo=-1.0, hi=1.0)
+    X, Y = dev(x), dev(y)
+    big = ctx.nll_batch(X, Y, dev(th), 1.9, 1e-6, "fp64")
+    three = ctx.nll_batch(X, Y, dev(th[:3]), 1.9, 1e-6, "fp64")
+    for k in ("nll", "mu", "sigma2", "logdet", "status"):
+        assert torch.equal(three[k], big[k][:3]), k
+    for t in (0, 7, 19):
+        one = ctx.nll_batch(X, Y, dev(th[t:t + 1]), 1.9, 1e-6, "fp64")
+        for k in ("nll", "mu", "sigma2", "logdet"):
+            assert torch.equal(one[k][0], big[k][t]), (t, k)
+        model = ctx.fit(X, Y, dev(th[t]), 1.9, 1e-6, "fp64")
+        assert model.nll == float(big["nll"][t])
+        model.free()
