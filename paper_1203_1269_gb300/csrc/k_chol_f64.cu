@@ -25,6 +25,7 @@ __device__ __forceinline__ double* inst_tile(const Batch& b, int t, int I, int J
 __global__ void __launch_bounds__(kThreads) k_potrf_f64(Batch b, int J) {
     extern __shared__ double s[];
     __shared__ double inv_piv;
+    __shared__ double logs[GP_NB];
     __shared__ int failed;
     const int t = blockIdx.x;
     if (b.st[t].status != GP_OK) return;
@@ -32,7 +33,6 @@ __global__ void __launch_bounds__(kThreads) k_potrf_f64(Batch b, int J) {
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) s[q] = T[q];
     if (threadIdx.x == 0) failed = -1;
     __syncthreads();
-    double logdet = 0.0;
     const int r = threadIdx.x % GP_NB;
     const int h = threadIdx.x / GP_NB;
     for (int c = 0; c < GP_NB; ++c) {
@@ -44,7 +44,6 @@ __global__ void __launch_bounds__(kThreads) k_potrf_f64(Batch b, int J) {
                 double l = sqrt(piv);
                 s[c * GP_NB + c] = l;
                 inv_piv = 1.0 / l;
-                logdet += log(l);
             }
         }
         __syncthreads();
@@ -70,21 +69,35 @@ __global__ void __launch_bounds__(kThreads) k_potrf_f64(Batch b, int J) {
         int rr = q % GP_NB, cc = q / GP_NB;
         if (rr >= cc) T[q] = s[q];
     }
-    if (threadIdx.x == 0) b.st[t].logdet += 2.0 * logdet;
+    // the pivots' logarithms off the serial path, summed in column order
+    if (threadIdx.x < GP_NB) logs[threadIdx.x] = log(s[threadIdx.x * GP_NB + threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double logdet = 0.0;
+        for (int c = 0; c < GP_NB; ++c) logdet += logs[c];
+        b.st[t].logdet += 2.0 * logdet;
+    }
 }
 
 // L_IJ = A_IJ L_JJ^-T for I = J + 1 + blockIdx.x.  The A tile sits in shared
 // memory; column c of X is finished, then removed from the columns after it.
+// Column c of L_JJ is read from a two-slot buffer that the second 128
+// threads fill one step ahead (the tile plus the buffer stay small enough
+// to share an SM with an update CTA).
 __global__ void __launch_bounds__(kThreads) k_trsm_f64(Batch b, int J) {
     extern __shared__ double s[];
     __shared__ double inv_diag[GP_NB];
+    __shared__ double col[2][GP_NB];
     const int t = blockIdx.y;
     if (b.st[t].status != GP_OK) return;
     const int I = J + 1 + blockIdx.x;
     const double* __restrict__ Ljj = inst_tile(b, t, J, J);
     double* Aij = inst_tile(b, t, I, J);
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) s[q] = Aij[q];
-    if (threadIdx.x < GP_NB) inv_diag[threadIdx.x] = 1.0 / Ljj[threadIdx.x * GP_NB + threadIdx.x];
+    if (threadIdx.x < GP_NB) {
+        inv_diag[threadIdx.x] = 1.0 / Ljj[threadIdx.x * GP_NB + threadIdx.x];
+        col[0][threadIdx.x] = __ldg(Ljj + threadIdx.x);
+    }
     __syncthreads();
     const int r = threadIdx.x % GP_NB;
     const int h = threadIdx.x / GP_NB;
@@ -93,9 +106,10 @@ __global__ void __launch_bounds__(kThreads) k_trsm_f64(Batch b, int J) {
         const double xrc = s[c * GP_NB + r] * inv_diag[c];
         __syncthreads();
         if (h == 0) s[c * GP_NB + r] = xrc;
-        const double* Lc = Ljj + c * GP_NB;   // column c of L_JJ (rows k > c below the diagonal)
+        if (h == 1 && c + 1 < GP_NB) col[(c + 1) & 1][r] = __ldg(Ljj + (c + 1) * GP_NB + r);
+        const double* Lc = col[c & 1];        // column c of L_JJ (rows k > c below the diagonal)
         for (int k = c + 1 + h; k < GP_NB; k += 2)
-            s[k * GP_NB + r] = fma(-xrc, __ldg(Lc + k), s[k * GP_NB + r]);
+            s[k * GP_NB + r] = fma(-xrc, Lc[k], s[k * GP_NB + r]);
         __syncthreads();
     }
     for (int q = threadIdx.x; q < GP_TILE_ELEMS; q += kThreads) Aij[q] = s[q];
