@@ -369,3 +369,28 @@ def test_model_outlives_context_and_clean_exit():
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "ok" in r.stdout
+
+
+@pytest.mark.parametrize("p", [0.6, 1.95])
+def test_assemble_tiles_power_across_scales(ctx, p):
+    """The double assembly's table powers (|dx| = 2^m F_j (1 + u) for 2^-60 <=
+    |dx| < 2^5, pow outside) against the oracle's pow, for coordinate
+    differences from 2^-70 to 2^6 in one dimension (S up to about 50).  Each
+    side rounds S to about an ulp, which exp(-S) turns into a relative error
+    of S ulps, so the entries agree within 8 (1 + S) 2^-53 relative; a
+    power wrong by a few ulps or more fails that."""
+    g = np.random.default_rng(90)
+    n = 300
+    x = np.empty((n, 2))
+    x[:, 0] = np.sort(2.0 ** g.uniform(-70.0, 6.0, n)) * np.where(g.random(n) < 0.5, -1.0, 1.0)
+    x[:, 1] = g.random(n)
+    th = np.array([30.0 / 64.0 ** p, 2.0])
+    buf = host(ctx.corr_assemble(dev(x), dev(th), p, 1e-8, "tiles"))
+    full = unpack_tiles(buf, n)
+    Ro = oracle.corr_matrix(x, th, p, 1e-8)
+    low, ref = np.tril(full[:n, :n]), np.tril(Ro)
+    mask = ref > 0
+    assert np.all(low[~mask] == 0.0)
+    S = -np.log(ref[mask])
+    rel = np.abs(low[mask] - ref[mask]) / ref[mask]
+    assert np.all(rel <= 8.0 * 2.0 ** -53 * (1.0 + np.maximum(S, 0.0))), np.max(rel / (1.0 + np.abs(S)))
