@@ -302,9 +302,12 @@ struct RhsArgs {
 // consecutive points of one design point.  Dynamic shared memory: the
 // points' coordinates [d][128], the design points' [128][d], theta, the
 // exp table, and with the tables theta_k 2^(m p) [d][kPowMs], F_j^p and 1/F_j.
+// DB > 0: d = DB exactly (the table path's d <= kPowMaxD), so that the loop
+// over the dimensions has a constant bound; DB = 0: d at run time.
+template <int DB>
 __global__ void __launch_bounds__(2 * GP_NB) k_var_rhs(RhsArgs g) {
     extern __shared__ dfl rsm[];
-    const int d = g.d;
+    const int d = DB > 0 ? DB : g.d;
     dfl* xsT = rsm;                        // [d][128]
     dfl* xd = xsT + d * GP_NB;             // [128][d]
     dfl* th = xd + GP_NB * d;              // [d]
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(2 * GP_NB) k_var_rhs(RhsArgs g) {
             dfl v = {0.f, 0.f};
             if (point_ok && i < g.n) {
                 float sh = 0.f, sl = 0.f;
+#pragma unroll
                 for (int k = 0; k < d; ++k) {
                     dfl dx = df_sub(xsT[k * GP_NB + r], xd[c * d + k]);
                     if (dx.hi < 0.f) dx = df_neg(dx);
@@ -901,6 +905,31 @@ static bool var_tc_fits() {
 
 // r and the partial means of npb point blocks from point m0 (RX null: means
 // only), then yhat: 2 kernels.
+// k_var_rhs for one d (0: any), its shared-memory limit raised once per
+// device and size
+template <int DB>
+static cudaError_t launch_rhs(dim3 grid, size_t smem, cudaStream_t s, const RhsArgs& r) {
+    static std::atomic<size_t> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(k_var_rhs<DB>, smem, attr);
+    if (e != cudaSuccess) return e;
+    k_var_rhs<DB><<<grid, 2 * GP_NB, smem, s>>>(r);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_rhs_exact(int d, dim3 grid, size_t smem, cudaStream_t s, const RhsArgs& r) {
+    switch (d) {
+#define GP_RHS_EXACT(D) \
+        case D: return launch_rhs<D>(grid, smem, s, r)
+        GP_RHS_EXACT(1); GP_RHS_EXACT(2); GP_RHS_EXACT(3); GP_RHS_EXACT(4);
+        GP_RHS_EXACT(5); GP_RHS_EXACT(6); GP_RHS_EXACT(7); GP_RHS_EXACT(8);
+        GP_RHS_EXACT(9); GP_RHS_EXACT(10); GP_RHS_EXACT(11); GP_RHS_EXACT(12);
+        GP_RHS_EXACT(13); GP_RHS_EXACT(14); GP_RHS_EXACT(15); GP_RHS_EXACT(16);
+#undef GP_RHS_EXACT
+        default: return launch_rhs<0>(grid, smem, s, r);
+    }
+}
+static_assert(kPowMaxD == 16, "launch_rhs_exact covers d = 1 .. kPowMaxD");
+
 cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, float2* MP, cudaStream_t s,
                               int* kernels) {
     *kernels = 0;
@@ -919,10 +948,8 @@ cudaError_t launch_var_points(const VarCall& c, int m0, int npb, float2* RX, flo
     r.c5 = (float)(b4 * (c.p - 4.0) / 5.0);
     const size_t rsmem = (size_t)(2 * GP_NB * c.d + c.d + kExpTab) * sizeof(dfl) +
                          (r.tabpow ? (size_t)(c.d * kPowMs + kPowN) * sizeof(dfl) + kPowN * sizeof(float) : 0);
-    static std::atomic<size_t> rattr[kMaxDevices];
-    cudaError_t e = raise_smem_limit(k_var_rhs, rsmem, rattr);
-    if (e != cudaSuccess) return e;
-    k_var_rhs<<<dim3(c.nt, npb), 2 * GP_NB, rsmem, s>>>(r);
+    cudaError_t e = r.tabpow ? launch_rhs_exact(c.d, dim3(c.nt, npb), rsmem, s, r)
+                             : launch_rhs<0>(dim3(c.nt, npb), rsmem, s, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_var_mean<<<(npb * GP_NB + 255) / 256, 256, 0, s>>>(MP, c.nt, c.N, m0, npb, c.sc, c.yhat);
     *kernels = 2;
